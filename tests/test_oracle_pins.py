@@ -1,0 +1,434 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test ties one part of the oracle to something other than itself: values
+the paper or a textbook prints, closed forms, invariants, special cases and
+brute force.  No GPU needed.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from conftest import read_golden
+from paper_1704_01144_gb300 import inputs as I
+from paper_1704_01144_gb300 import schedule as S
+
+
+# ----------------------------------------------------------- Riemann solver
+def test_riemann_star_matches_toro_table(oracle_mod):
+    """Exact star states of Toro's five standard tests (Table 4.3)."""
+    for ln in read_golden("toro_table_4_3.txt"):
+        vals = ln.split()
+        WL = tuple(map(float, vals[0:3]))
+        WR = tuple(map(float, vals[3:6]))
+        ps, us, _ = oracle_mod.riemann(WL, WR, tol=1e-12, maxit=100)
+        for got, txt in ((ps, vals[6]), (us, vals[7])):
+            decimals = len(txt.split(".")[1]) if "." in txt else 0
+            # one unit of the last printed digit, or 1e-5 relative (test 4's
+            # data are themselves test 3's star states rounded to 6 digits)
+            tol = max(10.0 ** (-decimals), 1e-5 * abs(float(txt)))
+            assert abs(got - float(txt)) <= tol, (ln, got)
+
+
+def test_wall_flux_is_the_mirrored_godunov_flux(oracle_mod):
+    """A slip wall mirrors the normal velocity: the symmetric Riemann problem
+    has u* = 0 exactly, the wall flux carries only the star pressure, and it
+    equals the Godunov flux against the mirrored ghost state up to
+    round-off."""
+    rng = np.random.default_rng(3)
+    for _ in range(50):
+        r, p = rng.uniform(0.3, 3.0, 2)
+        u = rng.uniform(-0.6, 0.6)
+        ps, us, _ = oracle_mod.riemann((r, u, p), (r, -u, p))
+        assert us == 0.0
+        n = rng.normal(size=3)
+        n /= np.linalg.norm(n)
+        vel = 0.4 * rng.normal(size=3)
+        WL = np.array([r, *vel, p])
+        un = vel @ n
+        Wg = np.array([r, *(vel - 2 * un * n), p])
+        F = oracle_mod.boundary_flux(1, WL, n)
+        assert F[0] == 0.0 and F[4] == 0.0
+        ps2, _, _ = oracle_mod.riemann((r, un, p), (r, -un, p))
+        np.testing.assert_allclose(F[1:4], ps2 * n, rtol=1e-14, atol=1e-15)
+        G = oracle_mod.godunov_flux(WL, Wg, n)
+        np.testing.assert_allclose(F, G, rtol=1e-10, atol=1e-12 * max(1.0, ps2))
+
+
+def test_transmissive_flux_is_the_physical_flux(oracle_mod):
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        W = np.array([rng.uniform(0.2, 2), *rng.uniform(-1, 1, 3), rng.uniform(0.2, 2)])
+        n = rng.normal(size=3)
+        n /= np.linalg.norm(n)
+        np.testing.assert_allclose(oracle_mod.boundary_flux(2, W, n), _physical_flux(W, n),
+                                   rtol=1e-14, atol=1e-15)
+        np.testing.assert_allclose(oracle_mod.godunov_flux(W, W, n), _physical_flux(W, n),
+                                   rtol=1e-12, atol=1e-13)
+
+
+def _physical_flux(W, n, gamma=1.4):
+    r, u, v, w, p = W
+    vel = np.array([u, v, w])
+    un = vel @ n
+    E = p / (gamma - 1) + 0.5 * r * vel @ vel
+    return np.array([r * un, *(r * un * vel + p * n), un * (E + p)])
+
+
+def test_riemann_identical_states_give_physical_flux(oracle_mod):
+    rng = np.random.default_rng(4)
+    for _ in range(50):
+        W = np.array([rng.uniform(0.2, 2), *rng.uniform(-1, 1, 3), rng.uniform(0.2, 2)])
+        n = rng.normal(size=3)
+        n /= np.linalg.norm(n)
+        F = oracle_mod.godunov_flux(W, W, n)
+        np.testing.assert_allclose(F, _physical_flux(W, n), rtol=1e-12, atol=1e-13)
+
+
+def test_riemann_supersonic_flow_is_upwind(oracle_mod):
+    """Both waves move right when the normal flow is supersonic: the Godunov
+    flux is the physical flux of the left state (and symmetrically)."""
+    n = np.array([0.0, 0.6, 0.8])
+    WL = np.array([1.0, 0.1, 3.0 * 0.6, 3.0 * 0.8, 1.0])    # u.n = 3 > c = 1.18
+    WR = np.array([0.8, 0.0, 2.5 * 0.6, 2.5 * 0.8, 0.9])
+    np.testing.assert_allclose(oracle_mod.godunov_flux(WL, WR, n), _physical_flux(WL, n),
+                               rtol=1e-12)
+    np.testing.assert_allclose(oracle_mod.godunov_flux(WR * [1, -1, -1, -1, 1],
+                                                       WL * [1, -1, -1, -1, 1], n),
+                               _physical_flux(WL * [1, -1, -1, -1, 1], n), rtol=1e-12)
+
+
+def test_riemann_flux_is_rotation_and_reflection_consistent(oracle_mod):
+    """F(WL, WR, n) = -F(WR, WL, -n): the face orientation does not matter."""
+    rng = np.random.default_rng(8)
+    for _ in range(30):
+        WL = np.array([rng.uniform(0.2, 2), *rng.uniform(-1, 1, 3), rng.uniform(0.2, 2)])
+        WR = np.array([rng.uniform(0.2, 2), *rng.uniform(-1, 1, 3), rng.uniform(0.2, 2)])
+        n = rng.normal(size=3)
+        n /= np.linalg.norm(n)
+        a = oracle_mod.godunov_flux(WL, WR, n)
+        b = oracle_mod.godunov_flux(WR, WL, -n)
+        np.testing.assert_allclose(a, -b, rtol=1e-10, atol=1e-12)
+
+
+def test_exact_sod_profile_is_self_similar(oracle_mod):
+    """Sampled exact solution: left state far left, right state far right,
+    star pressure between the tail of the fan and the shock."""
+    WL, WR = (1.0, 0.0, 1.0), (0.125, 0.0, 0.1)
+    assert oracle_mod.riemann_sample(WL, WR, -5.0) == pytest.approx(WL)
+    assert oracle_mod.riemann_sample(WL, WR, 5.0) == pytest.approx(WR)
+    r, u, p = oracle_mod.riemann_sample(WL, WR, 0.5)
+    assert p == pytest.approx(0.30313, abs=1e-5) and u == pytest.approx(0.92745, abs=1e-5)
+    assert r == pytest.approx(0.42632, abs=1e-5)      # Toro Table 4.3: rho*L
+    r, u, p = oracle_mod.riemann_sample(WL, WR, 1.2)
+    assert r == pytest.approx(0.26557, abs=1e-5)      # Toro Table 4.3: rho*R
+
+
+# ---------------------------------------------------- reconstruction / grad
+def test_muscl_reduces_to_textbook_1d_minmod(oracle_mod):
+    """On a uniform 1D chain the least-squares gradient is the central
+    difference; the face states must then be the textbook MUSCL-minmod
+    W_i + 1/2 minmod(W_i - W_{i-1}, W_{i+1} - W_i) and its mirror."""
+    rng = np.random.default_rng(11)
+    h = 0.1
+
+    def mm(a, b):
+        return np.where(a * b <= 0, 0.0, np.where(np.abs(a) < np.abs(b), a, b))
+
+    for _ in range(200):
+        q = rng.normal(size=(4, 5))          # cells i-1, i, i+1(=j), j+1
+        gi = (q[2] - q[0]) / (2 * h)
+        gj = (q[3] - q[1]) / (2 * h)
+        Gi = np.zeros(15)
+        Gj = np.zeros(15)
+        Gi[0::3] = gi
+        Gj[0::3] = gj
+        WL, WR = oracle_mod.muscl_pair(q[1], q[2], Gi, Gj, [h, 0.0, 0.0])
+        np.testing.assert_allclose(WL, q[1] + 0.5 * mm(q[1] - q[0], q[2] - q[1]), rtol=0,
+                                   atol=1e-14)
+        np.testing.assert_allclose(WR, q[2] - 0.5 * mm(q[3] - q[2], q[2] - q[1]), rtol=0,
+                                   atol=1e-14)
+
+
+def test_least_squares_gradient_exact_on_linear_fields(oracle_mod):
+    mesh, _ = I.blast_case(n=6, ratio=3.0)
+    o = oracle_mod.Oracle(mesh)
+    vol, xc = o.cell_geometry()
+    own, nb, bc, area, nrm = o.face_data()
+    interior = np.ones(o.n, bool)
+    interior[own[nb < 0]] = False
+    a = np.array([0.7, -1.3, 2.1])
+    g = o.scalar_gradient(3.0 + a @ xc)
+    np.testing.assert_allclose(g[:, interior].T, np.broadcast_to(a, (interior.sum(), 3)),
+                               rtol=1e-9, atol=1e-9)
+
+
+# ------------------------------------------------------------------ mesh
+def test_mesh_closure_and_volume(oracle_mod):
+    mesh, _ = I.blast_case(n=7, ratio=4.0)
+    o = oracle_mod.Oracle(mesh)
+    vol, xc = o.cell_geometry()
+    own, nb, bc, area, nrm = o.face_data()
+    assert vol.sum() == pytest.approx(1.0, rel=1e-13)
+    # every cell is closed: sum_f sigma_f A_f n_f = 0
+    acc = np.zeros((3, o.n))
+    An = area * nrm
+    for d in range(3):
+        np.add.at(acc[d], own, An[d])
+        np.add.at(acc[d], nb[nb >= 0], -An[d][nb >= 0])
+    assert np.abs(acc).max() < 1e-15
+    # Euler's relation for the face count: 4 T = 2 F_int + F_bnd
+    assert 4 * o.n == 2 * (nb >= 0).sum() + (nb < 0).sum()
+    assert (nb < 0).sum() == 6 * 2 * 7 * 7
+
+
+def test_mesh_rejects_inverted_tet(oracle_mod):
+    mesh, _ = I.sod_case(nx=4, ny=2, nz=2)
+    bad = mesh.tets.copy()
+    bad[3, [1, 2]] = bad[3, [2, 1]]
+    m2 = I.TetMesh(mesh.xyz, bad, mesh.face_bc, mesh.shape)
+    with pytest.raises(oracle_mod.OracleError):
+        oracle_mod.Oracle(m2)
+
+
+# -------------------------------------------------------------- schedule
+def test_tau_sequence_matches_paper_example(oracle_mod):
+    want = [int(x) for x in read_golden("schedule_theta3.txt")[0].split()]
+    assert S.tau_sequence(3) == want
+    begins = [lvl for kind, lvl, _ in oracle_mod.phase_list(3) if kind == "B"]
+    assert begins == want
+    assert oracle_mod.phase_list(3) == S.phases(3)
+    for theta in range(6):
+        assert len(oracle_mod.phase_list(theta)) == 3 * 2 ** theta - 1
+
+
+def _ulp_of_printed(txt):
+    return 10.0 ** (-(len(txt.split(".")[1]) if "." in txt else 0))
+
+
+def test_cost_model_reproduces_paper_tables():
+    """C(tau) = 2^(theta - tau) |Omega(tau)| applied to each table's printed
+    cell shares gives its printed computation shares, within the rounding of
+    the printed figures (half a unit of the cell share, propagated, plus one
+    unit of the computation share).  Table 3's tau_0 cell share (0.02 %) has
+    one significant digit, hence its wide interval."""
+    for ln in read_golden("level_tables.txt"):
+        head, cells_t, comp_t = ln.split("|")
+        cells_t, comp_t = cells_t.split(), comp_t.split()
+        cells = [float(x) / 100 for x in cells_t]
+        comp = [float(x) / 100 for x in comp_t]
+        got = S.level_cost_shares(cells)
+        theta = len(cells) - 1
+        total = sum(2.0 ** (theta - k) * float(x) for k, x in enumerate(cells_t))
+        rel_total = sum(2.0 ** (theta - k) * 0.5 * _ulp_of_printed(x)
+                        for k, x in enumerate(cells_t)) / total
+        for k, (g, c) in enumerate(zip(got, comp)):
+            rel_cells = 0.5 * _ulp_of_printed(cells_t[k]) / float(cells_t[k])
+            tol = g * (rel_cells + rel_total) + _ulp_of_printed(comp_t[k]) / 100 + 1e-9
+            assert abs(g - c) <= tol, (head, k, got, comp)
+
+
+def test_cycle_counts_follow_cost_model(oracle_mod):
+    """Per cycle, level k is updated 2^(theta-k) times and each face of level k
+    is evaluated twice per step (predictor and corrector)."""
+    mesh, prim = I.blast_case(n=8, ratio=6.0)
+    o = oracle_mod.Oracle(mesh, max_levels=4)
+    o.set_prim(prim)
+    dt, lev, counts = o.assign_levels()
+    assert (counts > 0).sum() >= 3
+    own, nb, bc, area, nrm = o.face_data()
+    flev = np.where(nb >= 0, np.minimum(lev[own], lev[np.maximum(nb, 0)]), lev[own])
+    o.advance(1)
+    st = o.stats()
+    theta = 3
+    for k in range(4):
+        assert st["updates"][k] == 2 ** (theta - k) * counts[k]
+        assert st["face_evals"][k] == 2 * 2 ** (theta - k) * (flev == k).sum()
+    assert st["updates"].sum() == S.cycle_cost(counts)
+
+
+# ------------------------------------------------------------------ levels
+def _levels_brute_force(o, cons, L, cfl=0.5, gamma=1.4):
+    vol, xc = o.cell_geometry()
+    own, nb, bc, area, nrm = o.face_data()
+    r = cons[0]
+    u = cons[1:4] / r
+    p = (gamma - 1) * (cons[4] - 0.5 * r * (u * u).sum(0))
+    c = np.sqrt(gamma * p / r)
+    S_ = np.zeros(o.n)
+    for side, cells in ((own, own), (nb, nb)):
+        m = cells >= 0
+        un = np.abs((u[:, cells[m]] * nrm[:, m]).sum(0))
+        np.add.at(S_, cells[m], area[m] * (un + c[cells[m]]))
+    dt = 2 * cfl * vol / S_
+    dtmin = dt.min()
+    k0 = np.clip(np.floor(np.log2(dt / dtmin)), 0, L - 1).astype(int)
+    # distance transform: k_i = min_j (k0_j + graph distance(i, j))
+    m = nb >= 0
+    adj = [[] for _ in range(o.n)]
+    for a, b in zip(own[m], nb[m]):
+        adj[a].append(b)
+        adj[b].append(a)
+    k = k0.copy()
+    order = np.argsort(k0, kind="stable")
+    import heapq
+    heap = [(k0[i], i) for i in order]
+    heapq.heapify(heap)
+    done = np.zeros(o.n, bool)
+    while heap:
+        d, i = heapq.heappop(heap)
+        if done[i]:
+            continue
+        done[i] = True
+        k[i] = d
+        for j in adj[i]:
+            if not done[j] and d + 1 < k[j]:
+                k[j] = d + 1
+                heapq.heappush(heap, (d + 1, j))
+    return dtmin, k
+
+
+def test_level_assignment_matches_brute_force(oracle_mod):
+    mesh, prim = I.blast_case(n=9, ratio=8.0)
+    o = oracle_mod.Oracle(mesh, max_levels=5)
+    o.set_prim(prim)
+    dtmin, lev, counts = o.assign_levels()
+    want_dt, want = _levels_brute_force(o, o.get_cons(), 5)
+    assert dtmin == pytest.approx(want_dt, rel=1e-14)
+    np.testing.assert_array_equal(lev, want)
+    assert (counts > 0).sum() >= 3
+    own, nb, *_ = o.face_data()
+    m = nb >= 0
+    assert np.abs(lev[own[m]].astype(int) - lev[nb[m]]).max() <= 1   # Sec. 2.2
+
+
+# ------------------------------------------------------- whole-scheme pins
+def test_free_stream_preserved_multilevel(oracle_mod):
+    mesh, prim = I.uniform_flow_case(n=6)
+    o = oracle_mod.Oracle(mesh, max_levels=3)
+    o.set_prim(prim)
+    U0 = o.get_cons()
+    _, _, counts = o.assign_levels()
+    assert (counts > 0).sum() >= 2
+    o.advance(3)
+    U = o.get_cons()
+    rel = np.abs(U - U0).max(axis=1) / np.abs(U0).max(axis=1)
+    assert rel.max() <= 1e-13
+
+
+@pytest.mark.parametrize("L", [1, 4])
+def test_conservation_ledger(oracle_mod, L):
+    """sum_i V_i U_i(t) + boundary flux integral = sum_i V_i U_i(0), to
+    round-off, across level interfaces too."""
+    mesh, prim = I.blast_case(n=10, ratio=8.0)
+    o = oracle_mod.Oracle(mesh, max_levels=L)
+    o.set_prim(prim)
+    vol, _ = o.cell_geometry()
+    M0 = (o.get_cons() * vol).sum(axis=1)
+    o.advance(3)
+    M1 = (o.get_cons() * vol).sum(axis=1)
+    led = o.boundary_ledger()
+    scale = np.abs(o.get_cons() * vol).sum(axis=1).max()
+    assert np.abs(M1 - M0 + led).max() <= 1e-14 * scale
+    assert led[0] == 0.0 and led[4] == 0.0        # walls pass no mass or energy
+
+
+def test_single_level_adaptive_equals_global_stepping_bitwise(oracle_mod):
+    mesh, prim = I.blast_case(n=7, ratio=4.0)
+    a = oracle_mod.Oracle(mesh, max_levels=1)
+    a.set_prim(prim)
+    g = oracle_mod.Oracle(mesh, max_levels=1)
+    g.set_prim(prim)
+    for _ in range(3):
+        dt, _, _ = a.assign_levels()
+        a.advance(1)
+        g.global_step(dt)
+    assert np.array_equal(a.get_cons(), g.get_cons())
+
+
+def test_sod_converges_to_exact_solution(oracle_mod):
+    errs = []
+    for nx in (32, 64, 128):
+        mesh, prim = I.sod_case(nx=nx, ny=2, nz=2)
+        o = oracle_mod.Oracle(mesh, max_levels=1)
+        o.set_prim(prim)
+        while o.t < 0.1:
+            o.advance(1)
+        W = oracle_mod.cons_to_prim(o.get_cons())
+        vol, xc = o.cell_geometry()
+        ex = np.array([oracle_mod.riemann_sample((1, 0, 1), (0.125, 0, 0.1), (x - 0.5) / o.t)[0]
+                       for x in xc[0]])
+        errs.append((vol * np.abs(W[0] - ex)).sum() / vol.sum())
+    assert errs[0] < 0.02
+    assert errs[1] < 0.75 * errs[0] and errs[2] < 0.75 * errs[1], errs
+
+
+def test_time_interpolation_is_consistent(oracle_mod):
+    """Time consistency across level interfaces: one adaptive cycle and the
+    same time covered by global steps of dt_min converge to each other faster
+    than first order as the CFL number halves (smooth, monotone data).  A
+    scheme that used the step-start state instead of the interpolated one
+    converges only at first order and fails this."""
+    rng = np.random.default_rng(5)
+    x = I.graded_coords(12, 6.0)
+    mesh = I.box_tet_mesh(x, x, x, jitter=0.1, rng=rng,
+                          bc_planes={k: 2 for k in ("x0", "x1", "y0", "y1", "z0", "z1")})
+    c = mesh.centroids()
+    s = 0.3 * c[:, 0] + 0.2 * c[:, 0] ** 2 + 0.1 * c[:, 1] + 0.05 * c[:, 2] ** 2
+    prim = np.empty((5, mesh.n_tets))
+    prim[0] = 1.0 + 0.5 * s
+    prim[1], prim[2], prim[3] = 0.4, 0.1, 0.05
+    prim[4] = 1.0 + s
+    rel = []
+    for cfl in (0.4, 0.2, 0.1, 0.05):
+        a = oracle_mod.Oracle(mesh, cfl=cfl, max_levels=3)
+        a.set_prim(prim)
+        dt, _, counts = a.assign_levels()
+        assert (counts > 0).all()
+        U0 = a.get_cons()
+        a.advance(1)
+        g = oracle_mod.Oracle(mesh, cfl=cfl, max_levels=1)
+        g.set_prim(prim)
+        for _ in range(4):
+            g.global_step(dt)
+        rel.append(np.abs(a.get_cons() - g.get_cons()).max() / np.abs(g.get_cons() - U0).max())
+    ratios = [rel[i] / rel[i + 1] for i in range(3)]
+    assert math.prod(ratios) ** (1 / 3) > 2.3, ratios
+
+
+def test_thread_count_invariance(oracle_mod):
+    mesh, prim = I.blast_case(n=8, ratio=8.0)
+    out = []
+    for nt in (1, max(2, oracle_mod.num_threads())):
+        oracle_mod.set_threads(nt)
+        o = oracle_mod.Oracle(mesh, max_levels=4)
+        o.set_prim(prim)
+        o.advance(2)
+        out.append(o.get_cons())
+    assert np.array_equal(out[0], out[1])
+
+
+def test_residual_stage1_matches_predictor(oracle_mod):
+    """The level residual at the cycle start is the predictor's slope:
+    U* - U^n = dt_k R_k for every cell after the first begin phase, and a
+    stage-2 residual is refused until the level's predicted state exists."""
+    mesh, prim = I.blast_case(n=7, ratio=8.0)
+    o = oracle_mod.Oracle(mesh, max_levels=3)
+    o.set_prim(prim)
+    dt, lev, counts = o.assign_levels()
+    assert (counts > 0).all()
+    R = np.zeros((5, o.n))
+    for k in range(3):
+        Rk = o.residual_level(k, 1)
+        assert np.all(Rk[:, lev != k] == 0)
+        R += Rk
+    with pytest.raises(RuntimeError):
+        o.residual_level(1, 2)
+    U0 = o.get_cons()
+    o.run_phases(1)                        # B(1): every level begins
+    Us = o.get_pred()
+    dtk = dt * 2.0 ** lev.astype(float)
+    np.testing.assert_allclose(Us - U0, dtk * R, rtol=1e-12, atol=1e-14 * np.abs(U0).max())
+    o.run_phases(3)                        # E(1,0), B(2), E(2,0)
+    R2 = o.residual_level(1, 2)            # level 1 ends at T = 2
+    assert np.isfinite(R2).all() and np.abs(R2[:, lev == 1]).max() > 0
