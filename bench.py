@@ -1,0 +1,396 @@
+#!/usr/bin/env python
+"""Benchmark of the temporally adaptive finite-volume hot path on GB300.
+
+Workload (default): spherical blast wave in the unit box on a 998,250-tet
+mesh (55^3 cubes, Kuhn split) graded 8:1 toward the centre with +-10 %
+seeded jitter, p = 10 inside r < 0.1 and 0.1 outside, rho = 1, L = 4
+temporal levels.  One step = one cycle of Algorithm 2 (level assignment +
+2^3 subiterations).  Metric: cell-updates per second weighted by the cost
+model of Sec. 2.2 (sum_k 2^(L-1-k) |Omega_k| per cycle), for the chosen form
+(FP32 reconstruction/flux, FP64 state and flux integrals) with plain FP64
+reported beside it.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOADS = {
+    # name: (mesh builder kwargs, levels)
+    "blast1m": (dict(n=55, ratio=8.0), 4),
+    "blast128k": (dict(n=28, ratio=8.0), 4),
+    "sod": (None, 1),
+}
+
+# Algorithmic bytes per face evaluation of the flux kernel (unique bytes the
+# method must move; each cell's primitives and gradients are shared by its 4
+# faces, so a face carries half a cell's worth):
+#   list index 4 + owner/neighbour 8 + geometry (n, r, A) + FA write 40
+#   + half a cell (W + G) ; corrector adds the FA read (40) and 2 level bytes.
+def flux_bytes_per_eval(fp32: bool) -> float:
+    geom = 28 if fp32 else 56
+    cell = (20 + 60) if fp32 else (40 + 120)
+    predictor = 4 + 8 + geom + 40 + cell / 2
+    corrector = predictor + 40 + 2
+    return 0.5 * (predictor + corrector)
+
+
+def launches_per_cycle(L: int) -> int:
+    """Kernels the library launches in one cycle: level assignment
+    (init, dt, levels, L-1 smoothing sweeps, 2 x (keys, hist, scan, scatter)),
+    4 per phase (prim, grad, flux, update) x (3 * 2^(L-1) - 1) phases, and
+    the end-of-cycle time advance."""
+    return (11 + (L - 1)) + 4 * (3 * 2 ** (L - 1) - 1) + 1
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for ln in fh:
+                parts = [p.strip() for p in ln.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def build_workload(name):
+    from paper_1704_01144_gb300 import inputs as I
+    kw, L = WORKLOADS[name]
+    if name == "sod":
+        mesh, prim = I.sod_case()
+    else:
+        mesh, prim = I.blast_case(**kw)
+    return mesh, prim, L
+
+
+def describe(name, mesh, L):
+    if name == "sod":
+        return {"workload": f"Sod tube, {mesh.n_tets} tets (64x4x4 cubes, Kuhn split), L=1"}
+    return {"workload": f"spherical blast wave, {mesh.n_tets} tets ({mesh.shape[0]}^3 cubes, "
+                        f"Kuhn split, 8:1 graded, 10% jitter), L={L} temporal levels"}
+
+
+# ------------------------------------------------------------------ ours ---
+def run_mode(fv, torch, mesh, prim, L, precision, steps, warmup, stream, flush, gpu_index):
+    g = fv.Mesh(mesh, max_levels=L, precision=precision)
+    g.set_state(prim)
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            g.advance(1, stream=stream, want_time=False)
+    torch.cuda.synchronize()
+    c0 = g.work_counters()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    if torch.distributed.is_initialized():
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    with ClockSampler(gpu_index) as clk:
+        with torch.cuda.stream(stream):
+            for k in range(steps):
+                flush.add_(1.0)                      # L2 flush between timed steps
+                ev[k][0].record(stream)
+                g.advance(1, stream=stream, want_time=False)
+                ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    if torch.distributed.is_initialized():
+        torch.distributed.barrier()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    c1 = g.work_counters()
+    st = g.status()
+    if st != 0:
+        raise RuntimeError(f"device status {st}: {fv.fv_last_error()}")
+    cell_updates = c1[1] - c0[1]
+    face_evals = c1[2] - c0[2]
+    # per-kernel-class timing (CUDA events on the launching stream), 2 cycles
+    g.profile_enable(True)
+    p0 = g.work_counters()
+    g.advance(2, stream=stream, want_time=False)
+    prof = g.profile_read()
+    p1 = g.work_counters()
+    g.profile_enable(False)
+    out = {
+        "ms_total": ms, "ms_per_step": ms / steps, "wall_s": t_wall,
+        "cell_updates": cell_updates, "face_evals": face_evals,
+        "value": cell_updates / (ms * 1e-3), "clocks": clk.summary(),
+        "prof": prof, "prof_face_evals": p1[2] - p0[2], "prof_cell_updates": p1[1] - p0[1],
+    }
+    return g, out
+
+
+def run_e2e(fv, torch, g, steps, warmup, stream):
+    """Through the public API with host (pinned) buffers: each step uploads
+    the state, advances one cycle and reads the state back."""
+    n = g.n
+    host = torch.empty((5, n), dtype=torch.float64, pin_memory=True)
+    g.get_state(out=host.numpy())
+    for _ in range(warmup):
+        g.set_conserved(host, stream=stream)
+        g.advance(1, stream=stream, want_time=False)
+        g.get_state(out=host, stream=stream)
+    total_cu = 0
+    t = 0.0
+    for _ in range(steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.set_conserved(host, stream=stream)           # H2D (synchronous)
+        g.advance(1, stream=stream, want_time=False)
+        g.get_state(out=host, stream=stream)           # D2H (synchronous)
+        t += time.perf_counter() - t0
+        total_cu += g.work_counters()[1]               # counters restart at set_conserved
+    return {"value": total_cu / t, "unit": "cell-updates/s",
+            "h2d_bytes_per_step": 5 * n * 8, "d2h_bytes_per_step": 5 * n * 8}
+
+
+def cpu_baseline(mesh, prim, L, budget_s=15.0, max_cycles=4):
+    from oracle import oracle as O
+    o = O.Oracle(mesh, max_levels=L)
+    o.set_prim(prim)
+    t0 = time.perf_counter()
+    cycles = 0
+    while cycles < max_cycles and (time.perf_counter() - t0) < budget_s:
+        o.advance(1)
+        cycles += 1
+    dt = time.perf_counter() - t0
+    cu = int(o.stats()["updates"].sum())
+    return {"value": cu / dt, "unit": "cell-updates/s", "cores": O.num_threads(),
+            "kind": "oracle",
+            "sample": f"first {cycles} cycle(s) of the same workload, FP64 CPU oracle "
+                      f"({O.num_threads()} OpenMP threads), {dt:.1f} s"}
+
+
+def main_ours(args):
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    from paper_1704_01144_gb300 import build as fvbuild
+    from paper_1704_01144_gb300 import fv
+    fvbuild.build()
+    mesh, prim, L = build_workload(args.workload)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    gpu_index = local
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        try:
+            gpu_index = int(vis.split(",")[local])
+        except ValueError:
+            pass
+
+    res = {}
+    for name, prec in (("fp64", fv.FV_FP64), ("fp32flux", fv.FV_FP32_FLUX)):
+        g, r = run_mode(fv, torch, mesh, prim, L, prec, args.steps, args.warmup, stream, flush,
+                        gpu_index)
+        r["g"] = g
+        res[name] = r
+    chosen = res["fp32flux"]
+    e2e = run_e2e(fv, torch, chosen["g"], max(3, min(args.steps, 10)), 1, stream)
+
+    # whole-job aggregate over ranks (replicas): sum of values, max of times
+    value = chosen["value"]
+    ms_step = chosen["ms_per_step"]
+    if ws > 1:
+        t = torch.tensor([value, ms_step, e2e["value"]], dtype=torch.float64, device="cuda")
+        vals = [torch.zeros_like(t) for _ in range(ws)]
+        torch.distributed.all_gather(vals, t)
+        vals = torch.stack(vals).cpu().numpy()
+        # every rank ran the same work: total = sum of per-rank work / max time
+        value = float(chosen["cell_updates"] * ws / (vals[:, 1].max() * args.steps * 1e-3))
+        ms_step = float(vals[:, 1].max())
+        e2e["value"] = float(vals[:, 2].sum())
+
+    peaks, peak_src = _load_peaks()
+
+    def roofline(r, fp32):
+        ms, n = r["prof"]["flux"]
+        if n == 0 or ms <= 0:
+            return None
+        bpe = flux_bytes_per_eval(fp32)
+        achieved = r["prof_face_evals"] * bpe / (ms * 1e-3) / 1e9
+        peak = float(peaks["hbm_gbs"])
+        return {"bound": "hbm", "kernel": "k_flux", "achieved": round(achieved, 1),
+                "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)",
+                "bytes_per_face_eval": bpe,
+                "avg_launch_ms": ms / n, "launches": n}
+
+    def kernel_shares(r):
+        tot = sum(v[0] for v in r["prof"].values())
+        return {k: {"ms": round(v[0], 3), "launches": v[1], "share": round(v[0] / tot, 4)}
+                for k, v in r["prof"].items()}
+
+    line = None
+    if rank == 0:
+        cpu = None if args.no_cpu_baseline else cpu_baseline(mesh, prim, L)
+        desc = describe(args.workload, mesh, L)
+        desc.update({"l2": "flushed between timed steps (256 MB write)",
+                     "step": "one cycle of Algorithm 2 (level assignment + 2^(L-1) subiterations)",
+                     "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
+                     "mode": "FP32 reconstruction/Riemann flux, FP64 state, residual sums and "
+                             "flux time integrals (chosen form); CUDA graph per cycle"})
+        line = {
+            "metric": "cell-updates/sec (adaptive-dt weighted) & HBM GB/s, chosen vs plain FP64",
+            "value": round(value, 1), "unit": "cell-updates/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 flux / f64 state", "data": "synthetic (seeded graded tet mesh, blast wave)",
+            "config": desc,
+            "clocks": chosen["clocks"],
+            "roofline": roofline(chosen, True),
+            "e2e": e2e,
+            "gpu_launches": launches_per_cycle(L) * args.steps,
+            "cpu_baseline": cpu,
+            "plain_fp64": {"value": round(res["fp64"]["value"], 1), "unit": "cell-updates/s",
+                           "ms_per_step": round(res["fp64"]["ms_per_step"], 4),
+                           "roofline": roofline(res["fp64"], False),
+                           "kernels": kernel_shares(res["fp64"]),
+                           "clocks": res["fp64"]["clocks"]},
+            "kernels": kernel_shares(chosen),
+            "cell_updates_per_step": chosen["cell_updates"] / args.steps,
+            "face_evals_per_step": chosen["face_evals"] / args.steps,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+# ------------------------------------------------------------- reference ---
+def main_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    mesh, prim, L = build_workload(args.workload)
+    o = O.Oracle(mesh, max_levels=L)
+    o.set_prim(prim)
+    for _ in range(args.warmup):
+        o.advance(1)
+    st0 = o.stats()["updates"].sum()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.advance(1)
+    dt = time.perf_counter() - t0
+    cu = int(o.stats()["updates"].sum() - st0)
+    value = cu / dt
+    desc = describe(args.workload, mesh, L)
+    desc["l2"] = "n/a (CPU)"
+    line = {
+        "impl": "reference",
+        "metric": "cell-updates/sec (adaptive-dt weighted) & HBM GB/s, chosen vs plain FP64",
+        "value": round(value, 1), "unit": "cell-updates/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded graded tet mesh, blast wave)", "config": desc,
+        "cpu_baseline": {"value": round(value, 1), "unit": "cell-updates/s",
+                         "cores": O.num_threads(), "kind": "oracle",
+                         "sample": f"cycles {args.warmup + 1}..{args.warmup + args.steps} of the "
+                                   f"workload on the FP64 CPU oracle"},
+        "e2e": {"value": round(value, 1), "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="blast1m")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        main_reference(args)
+    else:
+        main_ours(args)
+
+
+if __name__ == "__main__":
+    main()

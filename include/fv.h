@@ -1,0 +1,258 @@
+/*
+ * fv.h -- C ABI of the GB300 temporally adaptive finite-volume hot path.
+ *
+ * The library advances the inviscid compressible Euler equations (the
+ * integral balance law of Eq. 1 with no source term) on an unstructured
+ * tetrahedral mesh with the temporally adaptive explicit scheme of
+ * Algorithm 2 (Sec. 2.2): every cell gets a local explicit time step, cells
+ * are binned into levels k = 0..L-1 with dt_k = 2^k dt_min (neighbours at
+ * most one level apart), and one cycle ("iteration" in the paper) runs
+ * 2^(L-1) subiterations in which level k starts a step every 2^k
+ * subiterations.  Each level step is a predictor/corrector (Heun) step in
+ * flux form; states of neighbours on other levels are interpolated linearly
+ * in time; a coarse cell takes the time integral of the fine-side fluxes on a
+ * level interface, so the method conserves mass, momentum and energy.
+ * Fluxes: least-squares gradients, MUSCL reconstruction with the minmod
+ * limiter, exact Godunov Riemann solver (Newton on the star pressure).
+ *
+ * Conventions (all entry points):
+ *  - Every call returns FV_OK (0) or a negative FV_ERR_* code and never
+ *    aborts; fv_last_error() returns a message for the calling thread's last
+ *    failure.
+ *  - Device work is enqueued on `stream` (a cudaStream_t, NULL = legacy
+ *    default stream) and is asynchronous unless stated otherwise.
+ *  - Host arrays passed in are read during the call only (copied).
+ *    Device pointers passed in are borrowed, never freed, and must stay
+ *    valid until the work enqueued on `stream` has finished.
+ *  - Cell data exchanged with the caller are in the caller's tet order,
+ *    structure of arrays: component c of cell i at [c * n_tets + i].
+ *  - A mesh handle is not thread-safe; distinct handles are independent.
+ *  - The library owns the device memory it allocates for a mesh (freed by
+ *    fv_mesh_free) and calls cudaSetDevice(cfg.device) inside every call.
+ */
+#ifndef FV_H
+#define FV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FV_OK 0
+#define FV_ERR_INVALID_ARG (-1) /* bad argument or call out of order */
+#define FV_ERR_BAD_MESH (-2)    /* inverted/degenerate tet, non-manifold or untagged face */
+#define FV_ERR_CUDA (-3)        /* a CUDA runtime call failed */
+#define FV_ERR_NONPHYSICAL (-4) /* density or pressure not positive/finite */
+#define FV_ERR_RIEMANN (-5)     /* vacuum generation or Newton non-convergence */
+#define FV_ERR_TIMEOUT (-6)     /* a bounded device wait gave up */
+#define FV_ERR_NOMEM (-7)       /* device allocation failed */
+
+/* face boundary tags (face_bc) */
+#define FV_BC_INTERIOR 0
+#define FV_BC_WALL 1         /* slip wall: ghost mirrors the normal velocity */
+#define FV_BC_TRANSMISSIVE 2 /* ghost copies the interior state */
+
+/* precision modes */
+#define FV_FP64 0      /* everything in FP64 */
+#define FV_FP32_FLUX 1 /* reconstruction and Riemann flux in FP32; state,
+                          residual sums and flux time integrals in FP64 */
+
+/* initial guess of the Newton iteration on the star pressure */
+#define FV_GUESS_TWO_RAREFACTION 0
+#define FV_GUESS_MLP 1
+
+typedef struct fv_config {
+  double gamma;        /* ratio of specific heats (1.4) */
+  double cfl;          /* CFL number of the local time step (0.5) */
+  double newton_tol;   /* relative change that stops Newton (1e-10) */
+  int max_levels;      /* L: number of temporal levels, 1..8 */
+  int newton_max_iter; /* Newton iterations before FV_ERR_RIEMANN (50) */
+  int precision;       /* FV_FP64 or FV_FP32_FLUX */
+  int guess;           /* FV_GUESS_TWO_RAREFACTION or FV_GUESS_MLP */
+  int device;          /* CUDA device ordinal */
+} fv_config;
+
+typedef struct fv_mesh fv_mesh;
+
+/* Fills *cfg with the defaults shown above (device 0). */
+void fv_config_default(fv_config *cfg);
+
+/*
+ * Builds a mesh from host arrays (copied): node coordinates xyz[3*n_nodes]
+ * (x,y,z per node), tets[4*n_tets] node indices (positively oriented:
+ * det[x1-x0, x2-x0, x3-x0] > 0), face_bc[4*n_tets] where entry 4*t+j tags the
+ * face of tet t opposite its local node j (FV_BC_*; interior faces 0).
+ * Extracts faces, computes FP64 geometry (Sec. 2.1: the solver works on cells
+ * and faces), renumbers cells along a Morton curve and uploads everything to
+ * the device.  Synchronous.  Errors: FV_ERR_INVALID_ARG, FV_ERR_BAD_MESH,
+ * FV_ERR_NOMEM, FV_ERR_CUDA.  *out is NULL on failure.
+ */
+int fv_mesh_load(const double *xyz, int64_t n_nodes, const int64_t *tets, int64_t n_tets,
+                 const int8_t *face_bc, const fv_config *cfg, fv_mesh **out);
+
+/* Releases every device and host resource of the mesh (NULL is a no-op).
+ * Synchronises the device first. */
+void fv_mesh_free(fv_mesh *m);
+
+/* Number of cells / faces of the mesh. */
+int64_t fv_mesh_cells(const fv_mesh *m);
+int64_t fv_mesh_faces(const fv_mesh *m);
+
+/*
+ * Sets the state from primitives prim_soa[5*n_tets] = (rho, u, v, w, p),
+ * caller's cell order; host memory (on_device = 0) or device memory
+ * (on_device = 1).  Resets the cycle (levels must be reassigned), the
+ * interface accumulators and the boundary flux ledger; keeps the time.
+ * Errors: FV_ERR_INVALID_ARG, FV_ERR_CUDA.
+ */
+int fv_set_state(fv_mesh *m, const double *prim_soa, int on_device, void *stream);
+
+/*
+ * Writes the conserved state U^n = (rho, rho u, rho v, rho w, E) to
+ * cons_soa[5*n_tets] in the caller's cell order, host (on_device = 0,
+ * synchronous) or device (on_device = 1, asynchronous) memory.
+ */
+int fv_get_state(fv_mesh *m, double *cons_soa, int on_device, void *stream);
+
+/*
+ * Alg. 2 lines 1-2: computes every cell's local explicit time step
+ * dt_i = 2 CFL V_i / sum_f A_f (|u_i . n_f| + c_i), dt_min = min_i dt_i, the
+ * level k_i = max{k <= L-1 : 2^k dt_min <= dt_i}, then lowers levels until
+ * neighbours differ by at most one (Sec. 2.2), and builds the level-sorted
+ * cell and face lists.  Starts a cycle.  dt_min_out (may be NULL) receives
+ * dt_min and level_counts_out[L] (may be NULL) the cells per level; either
+ * non-NULL makes the call synchronous.  Errors: FV_ERR_INVALID_ARG (a cycle
+ * is in progress), FV_ERR_CUDA.
+ */
+int fv_assign_levels(fv_mesh *m, double *dt_min_out, int32_t *level_counts_out, void *stream);
+
+/* Local explicit time step dt_i of every cell (caller's order) computed by
+ * the last fv_assign_levels (Alg. 2 line 1): host dt_out[n_tets].
+ * Synchronous.  Errors: FV_ERR_INVALID_ARG before any level assignment. */
+int fv_get_local_dt(fv_mesh *m, double *dt_out);
+
+/* Level of every cell (caller's order) of the current cycle: host int8
+ * array levels_out[n_tets].  Synchronous. */
+int fv_get_levels(fv_mesh *m, int8_t *levels_out);
+
+/*
+ * The level-compacted lists of the current cycle (host, synchronous, any
+ * pointer may be NULL): cells_out[n_tets] caller's cell indices sorted by
+ * (level, no finer neighbour) with cell_off_out[2L+1] bucket offsets, and
+ * face_level_out[n_faces] / face_off_out[L+1] the face level of every face
+ * in library face order and the offsets of the face list sorted by level.
+ * A phase of level tau touches a prefix or a contiguous segment of them.
+ */
+int fv_get_level_lists(fv_mesh *m, int64_t *cells_out, int32_t *cell_off_out,
+                       int8_t *face_level_out, int32_t *face_off_out);
+
+/*
+ * The residual R_i = -(1/V_i) sum_f sigma_f F_f A_f (Eq. 1, S = 0) of every
+ * cell of level `level`, with every cell's state taken at the start
+ * (stage 1) or the end (stage 2) of that level's current step: U^n at the
+ * step start, the predicted U* at its end, and linear interpolation in time
+ * for neighbours on other levels.  Writes R_soa_dev[5*n_tets] (device
+ * memory, caller's order); entries of other cells are 0.  Changes no state.
+ * Errors: FV_ERR_INVALID_ARG when no cycle is active, when stage 2 is asked
+ * before the level's predictor ran, or when some level's state is not
+ * defined at that time (a finer level that has not reached it).
+ */
+int fv_residual_level(fv_mesh *m, int level, int stage, double *R_soa_dev, void *stream);
+
+/*
+ * Runs the next n_phases phases of the current cycle.  The phases of one
+ * cycle, for s = 1..2^(L-1): B(s) starts levels 0..tau(s) (Alg. 2 lines 5-9:
+ * predictor fluxes on faces of level <= tau, U* of those cells), then
+ * E(s,k) for k = 0,1,.. while s mod 2^k == 0 (corrector fluxes on faces of
+ * level k, flux time integrals, U^{n+1} of level-k cells).  3 * 2^(L-1) - 1
+ * phases in all; completing the last one ends the cycle (time advances by
+ * 2^(L-1) dt_min).  A pause/resume hook for phase-by-phase checks.
+ * Errors: FV_ERR_INVALID_ARG (no active cycle, or past its end).
+ */
+int fv_advance_phases(fv_mesh *m, int n_phases, void *stream);
+
+/*
+ * Advances n_cycles complete cycles (Alg. 2), each starting with level
+ * assignment; a cycle already in progress is completed first and counts as
+ * one.  *t_out (may be NULL) receives the time reached; the call then
+ * synchronises the stream.  Device-side errors (non-physical state, Riemann
+ * failure) are sticky and reported by fv_status.
+ */
+int fv_advance(fv_mesh *m, int n_cycles, double *t_out, void *stream);
+
+/* Physical time of the mesh (synchronous). */
+int fv_get_time(fv_mesh *m, double *t_out);
+
+/* Sets the physical time (only between cycles). */
+int fv_set_time(fv_mesh *m, double t);
+
+/*
+ * Sum over boundary faces of the time-integrated flux that left the domain
+ * since the last fv_set_state, out5[5] (host, synchronous).  With
+ * sum_i V_i U_i this gives the conservation ledger.
+ */
+int fv_boundary_ledger(fv_mesh *m, double *out5);
+
+/* Cell volumes in the caller's order, host vol_out[n_tets] (synchronous). */
+int fv_cell_volumes(fv_mesh *m, double *vol_out);
+
+/*
+ * Sticky device status of the mesh (synchronous): FV_OK, or the first of
+ * FV_ERR_NONPHYSICAL / FV_ERR_RIEMANN raised by a kernel since the last
+ * fv_set_state.
+ */
+int fv_status(fv_mesh *m);
+
+/*
+ * Sets the conserved state U = (rho, rho u, rho v, rho w, E) from
+ * cons_soa[5*n_tets] (caller's order), host (on_device = 0, synchronous) or
+ * device (on_device = 1) memory.  Same resets as fv_set_state.
+ */
+int fv_set_conserved(fv_mesh *m, const double *cons_soa, int on_device, void *stream);
+
+/*
+ * Work counters since the last fv_set_state/fv_set_conserved (synchronous):
+ * completed cycles, cell updates weighted as in the cost model of Sec. 2.2
+ * (sum over cycles of sum_k 2^(L-1-k) |Omega_k|) and face flux evaluations
+ * (predictor + corrector: sum over cycles of sum_k 2 * 2^(L-1-k) |faces of
+ * level k|).  Any pointer may be NULL.
+ */
+int fv_work_counters(fv_mesh *m, int64_t *cycles, int64_t *cell_updates, int64_t *face_evals);
+
+/*
+ * Whether fv_advance replays a captured CUDA graph of one whole cycle
+ * (default 1).  The graph is captured on the first fv_advance that starts a
+ * cycle on a non-legacy stream and replayed afterwards; the legacy default
+ * stream always runs the kernels one by one.
+ */
+int fv_use_graph(fv_mesh *m, int enable);
+
+/* kernel classes of the profiler */
+#define FV_PROF_LEVELS 0 /* level assignment: dt, levels, sorts */
+#define FV_PROF_PRIM 1   /* primitives at the phase time */
+#define FV_PROF_GRAD 2   /* least-squares gradients */
+#define FV_PROF_FLUX 3   /* reconstruction + Riemann flux */
+#define FV_PROF_UPDATE 4 /* per-cell gather and update */
+#define FV_PROF_N 5
+
+/*
+ * Per-kernel-class timing with CUDA events recorded on the launching stream
+ * around every launch (graphs are bypassed while enabled).  Enabling clears
+ * the totals.  fv_profile_read synchronises and returns, per class, the
+ * summed kernel time in ms and the number of launches.
+ */
+int fv_profile_enable(fv_mesh *m, int enable);
+int fv_profile_read(fv_mesh *m, double ms_out[FV_PROF_N], int64_t launches_out[FV_PROF_N]);
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char *fv_last_error(void);
+
+/* Library version string. */
+const char *fv_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FV_H */

@@ -1,0 +1,675 @@
+// fv_api.cu -- the C ABI of include/fv.h: mesh lifecycle, state transfer,
+// level assignment and the phase driver of Algorithm 2.
+//
+// The schedule of a cycle with theta = L - 1 (Alg. 2 lines 4-9) is a fixed
+// list of 3 * 2^theta - 1 phases:  for s = 1..2^theta,  B(s) starts the levels
+// 0..tau(s) at T = s - 1, then E(s, k) ends the step of level k at T = s for
+// k = 0, 1, ... while s mod 2^k == 0 (finest first).  The host keeps, per
+// level, the start time of the current step (tn, in dt_min units) and whether
+// the predicted state U* is valid; from them each phase gets the view of
+// every level at its time T: U^n (T == tn), U* (T == tn + 2^k) or the linear
+// interpolation in time between them.  The kernel sequence of a cycle is
+// therefore fixed; ranges come from the level-sorted lists on the device.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "fv_internal.h"
+
+
+namespace {
+
+thread_local std::string t_err;
+
+int fail(int code, const std::string &msg) {
+  t_err = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+  t_err = std::string(what) + ": " + cudaGetErrorString(e);
+  return FV_ERR_CUDA;
+}
+
+#define CK(call)                                            \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);     \
+  } while (0)
+
+#define CKL(call)                                                            \
+  do {                                                                       \
+    int r_ = (call);                                                         \
+    if (r_ != FV_OK) return fail(r_, std::string("kernel launch failed: ") + \
+                                         cudaGetErrorString(cudaGetLastError())); \
+  } while (0)
+
+struct Phase {
+  int kind;   // 0 begin, 1 end
+  int level;  // tau(s) for begin, k for end
+  int64_t T;  // time in dt_min units from the cycle start
+};
+
+std::vector<Phase> make_phases(int theta) {
+  std::vector<Phase> out;
+  int nsub = 1 << theta;
+  for (int s = 1; s <= nsub; ++s) {
+    int tau = 0;
+    for (int tmp = 1; tmp <= theta; ++tmp)
+      if ((s - 1) % (1 << tmp) == 0) tau = tmp;
+    out.push_back({0, tau, (int64_t)(s - 1)});
+    for (int k = 0; k <= theta && s % (1 << k) == 0; ++k) out.push_back({1, k, (int64_t)s});
+  }
+  return out;
+}
+
+}  // namespace
+
+struct fv_mesh {
+  fv_config cfg;
+  DevMesh d;
+  int L = 1, theta = 0;
+  int *new2old_dev = nullptr;  // Morton index -> caller's index
+  void *W = nullptr;           // phase-time primitives (FP64 or FP32)
+  double *FAt = nullptr;       // residual-hook scratch (5F)
+  int *cnt_scratch = nullptr;  // level-sort counts
+  std::vector<Phase> phases;
+  bool in_cycle = false;
+  int next_phase = 0;
+  int64_t tn[FV_MAXL];
+  bool pred[FV_MAXL];
+  std::vector<void *> allocs;
+  ProfHook prof;
+  bool use_graph = true;
+  cudaGraphExec_t cycle_graph = nullptr;
+  bool have_dt = false;
+};
+
+namespace {
+
+template <typename T>
+int dalloc(fv_mesh *m, T **p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(FV_ERR_NOMEM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+  }
+  m->allocs.push_back((void *)*p);
+  return FV_OK;
+}
+
+template <typename T>
+int upload(T *dst, const std::vector<T> &src) {
+  CK(cudaMemcpy(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return FV_OK;
+}
+
+PhaseLevels levels_at(const fv_mesh *m, int64_t T) {
+  PhaseLevels pl;
+  for (int j = 0; j < FV_MAXL; ++j) {
+    pl.w[j] = 0.0;
+    pl.mode[j] = 0;
+    if (j >= m->L) continue;
+    int64_t dd = T - m->tn[j];
+    int64_t span = (int64_t)1 << j;
+    if (dd <= 0 || dd > span || !m->pred[j]) continue;  // U^n (or not needed)
+    if (dd == span) {
+      pl.mode[j] = 1;
+    } else {
+      pl.mode[j] = 2;
+      pl.w[j] = (double)dd / (double)span;
+    }
+  }
+  return pl;
+}
+
+int run_phase(fv_mesh *m, const Phase &ph, cudaStream_t s) {
+  const int L = m->L;
+  const int nb = 2 * L;
+  auto cl = [nb](int b) { return b < 0 ? 0 : (b > nb ? nb : b); };
+  auto fclip = [L](int b) { return b < 0 ? 0 : (b > L ? L : b); };
+  PhaseLevels pl = levels_at(m, ph.T);
+  int rc;
+  if (ph.kind == 0) {
+    int tau = ph.level;
+    rc = fvk::launch_phase(m->d, m->cfg.precision, pl, 1, tau,
+                           0, cl(2 * (tau + 3)),          // prim: levels <= tau+2
+                           0, cl(2 * tau + 3),            // grad: levels <= tau + halo
+                           0, fclip(tau + 1),             // faces of level <= tau
+                           0, cl(2 * tau + 2),            // cells of level <= tau
+                           m->W, &m->prof, s);
+    if (rc) return fail(rc, "phase launch failed");
+    for (int j = 0; j <= tau; ++j) m->pred[j] = true;
+  } else {
+    int k = ph.level;
+    rc = fvk::launch_phase(m->d, m->cfg.precision, pl, 2, k,
+                           cl(2 * (k - 1)), cl(2 * (k + 3)),  // prim: levels k-1..k+2
+                           cl(2 * k), cl(2 * k + 3),          // grad: level k + halo of k+1
+                           fclip(k), fclip(k + 1),            // faces of level k
+                           cl(2 * k), cl(2 * k + 2),          // cells of level k
+                           m->W, &m->prof, s);
+    if (rc) return fail(rc, "phase launch failed");
+    m->tn[k] = ph.T;
+    m->pred[k] = false;
+  }
+  return FV_OK;
+}
+
+int start_cycle(fv_mesh *m, cudaStream_t s) {
+  int rc = fvk::launch_assign_levels(m->d, m->L, m->cnt_scratch, &m->prof, s);
+  if (rc) return fail(rc, "level assignment launch failed");
+  for (int j = 0; j < FV_MAXL; ++j) {
+    m->tn[j] = 0;
+    m->pred[j] = false;
+  }
+  m->in_cycle = true;
+  m->next_phase = 0;
+  m->have_dt = true;
+  return FV_OK;
+}
+
+int run_phases(fv_mesh *m, int n, cudaStream_t s) {
+  for (int q = 0; q < n; ++q) {
+    if (!m->in_cycle || m->next_phase >= (int)m->phases.size())
+      return fail(FV_ERR_INVALID_ARG, "no active cycle (assign levels first) or past its end");
+    int rc = run_phase(m, m->phases[m->next_phase], s);
+    if (rc) return rc;
+    m->next_phase++;
+    if (m->next_phase == (int)m->phases.size()) {
+      rc = fvk::launch_time_advance(m->d, m->theta, s);
+      if (rc) return fail(rc, "time advance launch failed");
+      m->in_cycle = false;
+      m->next_phase = 0;
+    }
+  }
+  return FV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void fv_config_default(fv_config *cfg) {
+  if (!cfg) return;
+  cfg->gamma = 1.4;
+  cfg->cfl = 0.5;
+  cfg->newton_tol = 1e-10;
+  cfg->max_levels = 1;
+  cfg->newton_max_iter = 50;
+  cfg->precision = FV_FP64;
+  cfg->guess = FV_GUESS_TWO_RAREFACTION;
+  cfg->device = 0;
+}
+
+const char *fv_last_error(void) { return t_err.c_str(); }
+
+const char *fv_version(void) { return "fv-gb300 0.1 (sm_103a)"; }
+
+void fv_mesh_free(fv_mesh *m) {
+  if (!m) return;
+  cudaSetDevice(m->cfg.device);
+  cudaDeviceSynchronize();
+  if (m->cycle_graph) cudaGraphExecDestroy(m->cycle_graph);
+  for (auto &r : m->prof.recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (void *p : m->allocs) cudaFree(p);
+  cudaGetLastError();
+  delete m;
+}
+
+int fv_mesh_load(const double *xyz, int64_t n_nodes, const int64_t *tets, int64_t n_tets,
+                 const int8_t *face_bc, const fv_config *cfg, fv_mesh **out) {
+  if (!out) return fail(FV_ERR_INVALID_ARG, "fv_mesh_load: out is NULL");
+  *out = nullptr;
+  if (!xyz || !tets || !face_bc || !cfg) return fail(FV_ERR_INVALID_ARG, "fv_mesh_load: NULL argument");
+  if (cfg->max_levels < 1 || cfg->max_levels > FV_MAXL || !(cfg->gamma > 1.0) || !(cfg->cfl > 0.0) ||
+      !(cfg->newton_tol > 0.0) || cfg->newton_max_iter < 1 ||
+      (cfg->precision != FV_FP64 && cfg->precision != FV_FP32_FLUX) ||
+      (cfg->guess != FV_GUESS_TWO_RAREFACTION))
+    return fail(FV_ERR_INVALID_ARG, "fv_mesh_load: invalid configuration");
+  CK(cudaSetDevice(cfg->device));
+  fvk::init_device_info();
+  HostMesh H;
+  std::string err;
+  int rc = fv_host_build(xyz, n_nodes, tets, n_tets, face_bc, H, &err);
+  if (rc) return fail(rc, err);
+  if (H.F > (int64_t)0x7fffffff / 16) return fail(FV_ERR_INVALID_ARG, "fv_mesh_load: mesh too large");
+
+  fv_mesh *m = new fv_mesh();
+  m->cfg = *cfg;
+  m->L = cfg->max_levels;
+  m->theta = m->L - 1;
+  m->phases = make_phases(m->theta);
+  DevMesh &d = m->d;
+  memset(&d, 0, sizeof d);
+  const size_t N = H.N, F = H.F;
+  d.N = (int)N;
+  d.F = (int)F;
+  d.L = m->L;
+  d.gamma = cfg->gamma;
+  d.cfl = cfg->cfl;
+  d.tol = cfg->newton_tol;
+  d.maxit = cfg->newton_max_iter;
+  const bool f32 = cfg->precision == FV_FP32_FLUX;
+  const int nblk_c = (int)((N + 1023) / 1024), nblk_f = (int)((F + 1023) / 1024);
+  size_t cnt_size = (size_t)16 * (nblk_c > nblk_f ? nblk_c : nblk_f) + 16;
+#define AL(p, n)                       \
+  do {                                 \
+    int r_ = dalloc(m, &(p), (n));     \
+    if (r_) {                          \
+      fv_mesh_free(m);                 \
+      return r_;                       \
+    }                                  \
+  } while (0)
+  AL(d.vol, N);
+  AL(d.cf, 4 * N);
+  AL(d.cnb, 4 * N);
+  AL(d.cown, N);
+  AL(d.lsw, 12 * N);
+  AL(d.fown, F);
+  AL(d.fnb, F);
+  AL(d.fn, 3 * F);
+  AL(d.farea, F);
+  AL(d.fr, 3 * F);
+  if (f32) {
+    AL(d.fn32, 3 * F);
+    AL(d.farea32, F);
+    AL(d.fr32, 3 * F);
+    AL(d.G32, 15 * N);
+    float *w;
+    AL(w, 5 * N);
+    m->W = w;
+  } else {
+    AL(d.G, 15 * N);
+    double *w;
+    AL(w, 5 * N);
+    m->W = w;
+  }
+  AL(d.Un, 5 * N);
+  AL(d.Us, 5 * N);
+  AL(d.FA, 5 * F);
+  AL(d.ACC, 5 * F);
+  AL(d.BND, 5 * F);
+  AL(d.lev, N);
+  AL(d.lev_tmp, N);
+  AL(d.flev, F);
+  AL(d.ckey, N);
+  AL(d.fkey, F);
+  AL(d.cl, N);
+  AL(d.fl, F);
+  AL(d.coff, 2 * FV_MAXL + 1);
+  AL(d.foff, FV_MAXL + 1);
+  AL(d.dt, N);
+  AL(d.dtmin_bits, 1);
+  AL(d.tdev, 1);
+  AL(d.status, 1);
+  AL(d.counters, 3);
+  AL(m->cnt_scratch, cnt_size);
+  AL(m->new2old_dev, N);
+  AL(m->FAt, 5 * F);
+#undef AL
+  std::vector<int> n2o(N);
+  for (size_t i = 0; i < N; ++i) n2o[i] = (int)H.new2old[i];
+  int urc = FV_OK;
+  urc |= upload(m->new2old_dev, n2o);
+  urc |= upload(d.vol, H.vol);
+  urc |= upload(d.cf, H.cf);
+  urc |= upload(d.cnb, H.cnb);
+  urc |= upload(d.cown, H.cown);
+  urc |= upload(d.lsw, H.lsw);
+  urc |= upload(d.fown, H.fown);
+  urc |= upload(d.fnb, H.fnb);
+  urc |= upload(d.fn, H.fn);
+  urc |= upload(d.farea, H.farea);
+  urc |= upload(d.fr, H.fr);
+  if (f32) {
+    std::vector<float> tmp(3 * F);
+    for (size_t q = 0; q < 3 * F; ++q) tmp[q] = (float)H.fn[q];
+    urc |= upload(d.fn32, tmp);
+    for (size_t q = 0; q < 3 * F; ++q) tmp[q] = (float)H.fr[q];
+    urc |= upload(d.fr32, tmp);
+    tmp.resize(F);
+    for (size_t q = 0; q < F; ++q) tmp[q] = (float)H.farea[q];
+    urc |= upload(d.farea32, tmp);
+  }
+  if (urc) {
+    fv_mesh_free(m);
+    return FV_ERR_CUDA;
+  }
+  cudaError_t e = cudaSuccess;
+  e = cudaMemset(d.ACC, 0, 5 * F * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(d.BND, 0, 5 * F * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(d.Un, 0, 5 * N * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(d.tdev, 0, sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(d.status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(d.counters, 0, 3 * sizeof(long long));
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    fv_mesh_free(m);
+    return cuda_fail(e, "fv_mesh_load");
+  }
+  for (int j = 0; j < FV_MAXL; ++j) {
+    m->tn[j] = 0;
+    m->pred[j] = false;
+  }
+  *out = m;
+  return FV_OK;
+}
+
+int64_t fv_mesh_cells(const fv_mesh *m) { return m ? m->d.N : 0; }
+int64_t fv_mesh_faces(const fv_mesh *m) { return m ? m->d.F : 0; }
+
+static int set_state_impl(fv_mesh *m, const double *src_host_or_dev, int on_device, bool conserved,
+                          cudaStream_t s) {
+  CK(cudaSetDevice(m->cfg.device));
+  const size_t N = m->d.N;
+  const double *src = src_host_or_dev;
+  if (!on_device) {
+    // stage through the residual scratch (5F >= 5N doubles since F >= N)
+    CK(cudaMemcpyAsync(m->FAt, src_host_or_dev, 5 * N * sizeof(double), cudaMemcpyHostToDevice, s));
+    src = m->FAt;
+  }
+  CK(cudaMemsetAsync(m->d.status, 0, sizeof(int), s));
+  if (conserved)
+    CKL(fvk::launch_set_cons(m->d, src, m->new2old_dev, s));
+  else
+    CKL(fvk::launch_set_state(m->d, src, m->new2old_dev, s));
+  CK(cudaMemsetAsync(m->d.ACC, 0, 5 * (size_t)m->d.F * sizeof(double), s));
+  CK(cudaMemsetAsync(m->d.BND, 0, 5 * (size_t)m->d.F * sizeof(double), s));
+  CK(cudaMemsetAsync(m->d.counters, 0, 3 * sizeof(long long), s));
+  if (!on_device) CK(cudaStreamSynchronize(s));
+  m->in_cycle = false;
+  m->next_phase = 0;
+  return FV_OK;
+}
+
+int fv_set_state(fv_mesh *m, const double *prim_soa, int on_device, void *stream) {
+  if (!m || !prim_soa) return fail(FV_ERR_INVALID_ARG, "fv_set_state: NULL argument");
+  return set_state_impl(m, prim_soa, on_device, false, (cudaStream_t)stream);
+}
+
+int fv_set_conserved(fv_mesh *m, const double *cons_soa, int on_device, void *stream) {
+  if (!m || !cons_soa) return fail(FV_ERR_INVALID_ARG, "fv_set_conserved: NULL argument");
+  return set_state_impl(m, cons_soa, on_device, true, (cudaStream_t)stream);
+}
+
+int fv_get_state(fv_mesh *m, double *cons_soa, int on_device, void *stream) {
+  if (!m || !cons_soa) return fail(FV_ERR_INVALID_ARG, "fv_get_state: NULL argument");
+  CK(cudaSetDevice(m->cfg.device));
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t N = m->d.N;
+  if (on_device) {
+    CKL(fvk::launch_get_state(m->d, cons_soa, m->new2old_dev, s));
+    return FV_OK;
+  }
+  CKL(fvk::launch_get_state(m->d, m->FAt, m->new2old_dev, s));
+  CK(cudaMemcpyAsync(cons_soa, m->FAt, 5 * N * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return FV_OK;
+}
+
+int fv_assign_levels(fv_mesh *m, double *dt_min_out, int32_t *level_counts_out, void *stream) {
+  if (!m) return fail(FV_ERR_INVALID_ARG, "fv_assign_levels: NULL mesh");
+  if (m->in_cycle && m->next_phase > 0)
+    return fail(FV_ERR_INVALID_ARG, "fv_assign_levels: a cycle is in progress");
+  CK(cudaSetDevice(m->cfg.device));
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = start_cycle(m, s);
+  if (rc) return rc;
+  if (dt_min_out || level_counts_out) {
+    unsigned long long bits = 0;
+    int coff[2 * FV_MAXL + 1];
+    CK(cudaMemcpyAsync(&bits, m->d.dtmin_bits, sizeof bits, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(coff, m->d.coff, (2 * m->L + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (dt_min_out) memcpy(dt_min_out, &bits, sizeof(double));
+    if (level_counts_out)
+      for (int k = 0; k < m->L; ++k) level_counts_out[k] = coff[2 * k + 2] - coff[2 * k];
+  }
+  return FV_OK;
+}
+
+int fv_get_local_dt(fv_mesh *m, double *dt_out) {
+  if (!m || !dt_out) return fail(FV_ERR_INVALID_ARG, "fv_get_local_dt: NULL argument");
+  if (!m->have_dt) return fail(FV_ERR_INVALID_ARG, "fv_get_local_dt: no level assignment yet");
+  CK(cudaSetDevice(m->cfg.device));
+  CK(cudaDeviceSynchronize());
+  const size_t N = m->d.N;
+  std::vector<double> dt(N);
+  std::vector<int> n2o(N);
+  CK(cudaMemcpy(dt.data(), m->d.dt, N * sizeof(double), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(n2o.data(), m->new2old_dev, N * sizeof(int), cudaMemcpyDeviceToHost));
+  for (size_t i = 0; i < N; ++i) dt_out[n2o[i]] = dt[i];
+  return FV_OK;
+}
+
+int fv_get_levels(fv_mesh *m, int8_t *levels_out) {
+  if (!m || !levels_out) return fail(FV_ERR_INVALID_ARG, "fv_get_levels: NULL argument");
+  CK(cudaSetDevice(m->cfg.device));
+  int8_t *tmp = (int8_t *)m->FAt;
+  CKL(fvk::launch_get_levels(m->d, tmp, m->new2old_dev, 0));
+  CK(cudaMemcpy(levels_out, tmp, m->d.N, cudaMemcpyDeviceToHost));
+  return FV_OK;
+}
+
+int fv_get_level_lists(fv_mesh *m, int64_t *cells_out, int32_t *cell_off_out,
+                       int8_t *face_level_out, int32_t *face_off_out) {
+  if (!m) return fail(FV_ERR_INVALID_ARG, "fv_get_level_lists: NULL mesh");
+  CK(cudaSetDevice(m->cfg.device));
+  CK(cudaDeviceSynchronize());
+  const size_t N = m->d.N, F = m->d.F;
+  if (cells_out) {
+    std::vector<int> cl(N), n2o(N);
+    CK(cudaMemcpy(cl.data(), m->d.cl, N * sizeof(int), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(n2o.data(), m->new2old_dev, N * sizeof(int), cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < N; ++i) cells_out[i] = (cl[i] >= 0 && (size_t)cl[i] < N) ? n2o[cl[i]] : -1;
+  }
+  if (cell_off_out) CK(cudaMemcpy(cell_off_out, m->d.coff, (2 * m->L + 1) * sizeof(int), cudaMemcpyDeviceToHost));
+  if (face_level_out) CK(cudaMemcpy(face_level_out, m->d.flev, F, cudaMemcpyDeviceToHost));
+  if (face_off_out) CK(cudaMemcpy(face_off_out, m->d.foff, (m->L + 1) * sizeof(int), cudaMemcpyDeviceToHost));
+  return FV_OK;
+}
+
+int fv_residual_level(fv_mesh *m, int level, int stage, double *R_soa_dev, void *stream) {
+  if (!m || !R_soa_dev) return fail(FV_ERR_INVALID_ARG, "fv_residual_level: NULL argument");
+  if (!m->in_cycle) return fail(FV_ERR_INVALID_ARG, "fv_residual_level: no active cycle");
+  if (level < 0 || level >= m->L || (stage != 1 && stage != 2))
+    return fail(FV_ERR_INVALID_ARG, "fv_residual_level: bad level or stage");
+  if (stage == 2 && !m->pred[level])
+    return fail(FV_ERR_INVALID_ARG, "fv_residual_level: the level's predictor has not run");
+  CK(cudaSetDevice(m->cfg.device));
+  cudaStream_t s = (cudaStream_t)stream;
+  int64_t T = m->tn[level] + (stage == 2 ? ((int64_t)1 << level) : 0);
+  // every level present in the mesh must have a defined state at T
+  int coff[2 * FV_MAXL + 1];
+  CK(cudaMemcpyAsync(coff, m->d.coff, (2 * m->L + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (int j = 0; j < m->L; ++j) {
+    if (coff[2 * j + 2] == coff[2 * j]) continue;
+    int64_t dd = T - m->tn[j];
+    if (dd < 0 || dd > ((int64_t)1 << j) || (dd > 0 && !m->pred[j]))
+      return fail(FV_ERR_INVALID_ARG, "fv_residual_level: states not available at that time");
+  }
+  PhaseLevels pl = levels_at(m, T);
+  int rc = fvk::launch_residual(m->d, m->cfg.precision, pl, level, m->W, m->FAt, R_soa_dev,
+                                m->new2old_dev, s);
+  if (rc) return fail(rc, "residual launch failed");
+  return FV_OK;
+}
+
+int fv_advance_phases(fv_mesh *m, int n_phases, void *stream) {
+  if (!m || n_phases < 0) return fail(FV_ERR_INVALID_ARG, "fv_advance_phases: bad argument");
+  CK(cudaSetDevice(m->cfg.device));
+  return run_phases(m, n_phases, (cudaStream_t)stream);
+}
+
+static int capture_cycle(fv_mesh *m, cudaStream_t s) {
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  int rc = start_cycle(m, s);
+  if (rc == FV_OK) rc = run_phases(m, (int)m->phases.size(), s);
+  cudaError_t e = cudaStreamEndCapture(s, &g);
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiateWithFlags(&m->cycle_graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    m->cycle_graph = nullptr;
+    return cuda_fail(e, "cudaGraphInstantiate");
+  }
+  return FV_OK;
+}
+
+int fv_advance(fv_mesh *m, int n_cycles, double *t_out, void *stream) {
+  if (!m || n_cycles < 0) return fail(FV_ERR_INVALID_ARG, "fv_advance: bad argument");
+  CK(cudaSetDevice(m->cfg.device));
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool graphable = m->use_graph && !m->prof.on && s != nullptr && s != cudaStreamLegacy &&
+                         s != cudaStreamPerThread;
+  for (int c = 0; c < n_cycles; ++c) {
+    int rc;
+    if (!m->in_cycle && graphable) {
+      if (!m->cycle_graph) {
+        rc = capture_cycle(m, s);
+        if (rc) return rc;
+      }
+      CK(cudaGraphLaunch(m->cycle_graph, s));
+      continue;
+    }
+    if (!m->in_cycle) {
+      rc = start_cycle(m, s);
+      if (rc) return rc;
+    }
+    rc = run_phases(m, (int)m->phases.size() - m->next_phase, s);
+    if (rc) return rc;
+  }
+  if (t_out) {
+    CK(cudaMemcpyAsync(t_out, m->d.tdev, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  return FV_OK;
+}
+
+int fv_use_graph(fv_mesh *m, int enable) {
+  if (!m) return fail(FV_ERR_INVALID_ARG, "fv_use_graph: NULL mesh");
+  m->use_graph = enable != 0;
+  return FV_OK;
+}
+
+int fv_work_counters(fv_mesh *m, int64_t *cycles, int64_t *cell_updates, int64_t *face_evals) {
+  if (!m) return fail(FV_ERR_INVALID_ARG, "fv_work_counters: NULL mesh");
+  CK(cudaSetDevice(m->cfg.device));
+  long long c[3];
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(c, m->d.counters, sizeof c, cudaMemcpyDeviceToHost));
+  if (cycles) *cycles = c[0];
+  if (cell_updates) *cell_updates = c[1];
+  if (face_evals) *face_evals = c[2];
+  return FV_OK;
+}
+
+int fv_profile_enable(fv_mesh *m, int enable) {
+  if (!m) return fail(FV_ERR_INVALID_ARG, "fv_profile_enable: NULL mesh");
+  CK(cudaSetDevice(m->cfg.device));
+  CK(cudaDeviceSynchronize());
+  for (auto &r : m->prof.recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  m->prof.recs.clear();
+  for (int c = 0; c < FV_PROF_N; ++c) {
+    m->prof.ms[c] = 0.0;
+    m->prof.launches[c] = 0;
+  }
+  m->prof.on = enable != 0;
+  return FV_OK;
+}
+
+int fv_profile_read(fv_mesh *m, double ms_out[FV_PROF_N], int64_t launches_out[FV_PROF_N]) {
+  if (!m) return fail(FV_ERR_INVALID_ARG, "fv_profile_read: NULL mesh");
+  CK(cudaSetDevice(m->cfg.device));
+  CK(cudaDeviceSynchronize());
+  for (auto &r : m->prof.recs) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, r.a, r.b));
+    m->prof.ms[r.cls] += ms;
+    m->prof.launches[r.cls] += 1;
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  m->prof.recs.clear();
+  for (int c = 0; c < FV_PROF_N; ++c) {
+    if (ms_out) ms_out[c] = m->prof.ms[c];
+    if (launches_out) launches_out[c] = m->prof.launches[c];
+  }
+  return FV_OK;
+}
+
+int fv_get_time(fv_mesh *m, double *t_out) {
+  if (!m || !t_out) return fail(FV_ERR_INVALID_ARG, "fv_get_time: NULL argument");
+  CK(cudaSetDevice(m->cfg.device));
+  CK(cudaMemcpy(t_out, m->d.tdev, sizeof(double), cudaMemcpyDeviceToHost));
+  return FV_OK;
+}
+
+int fv_set_time(fv_mesh *m, double t) {
+  if (!m) return fail(FV_ERR_INVALID_ARG, "fv_set_time: NULL mesh");
+  if (m->in_cycle && m->next_phase > 0) return fail(FV_ERR_INVALID_ARG, "fv_set_time: inside a cycle");
+  CK(cudaSetDevice(m->cfg.device));
+  CK(cudaMemcpy(m->d.tdev, &t, sizeof(double), cudaMemcpyHostToDevice));
+  return FV_OK;
+}
+
+int fv_boundary_ledger(fv_mesh *m, double *out5) {
+  if (!m || !out5) return fail(FV_ERR_INVALID_ARG, "fv_boundary_ledger: NULL argument");
+  CK(cudaSetDevice(m->cfg.device));
+  const size_t F = m->d.F;
+  std::vector<double> bnd(5 * F);
+  std::vector<int> fnb(F);
+  CK(cudaMemcpy(bnd.data(), m->d.BND, 5 * F * sizeof(double), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(fnb.data(), m->d.fnb, F * sizeof(int), cudaMemcpyDeviceToHost));
+  for (int c = 0; c < 5; ++c) {
+    double sum = 0.0;
+    for (size_t f = 0; f < F; ++f)
+      if (fnb[f] < 0) sum += bnd[c * F + f];
+    out5[c] = sum;
+  }
+  return FV_OK;
+}
+
+int fv_cell_volumes(fv_mesh *m, double *vol_out) {
+  if (!m || !vol_out) return fail(FV_ERR_INVALID_ARG, "fv_cell_volumes: NULL argument");
+  CK(cudaSetDevice(m->cfg.device));
+  const size_t N = m->d.N;
+  std::vector<double> v(N);
+  std::vector<int> n2o(N);
+  CK(cudaMemcpy(v.data(), m->d.vol, N * sizeof(double), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(n2o.data(), m->new2old_dev, N * sizeof(int), cudaMemcpyDeviceToHost));
+  for (size_t i = 0; i < N; ++i) vol_out[n2o[i]] = v[i];
+  return FV_OK;
+}
+
+int fv_status(fv_mesh *m) {
+  if (!m) return fail(FV_ERR_INVALID_ARG, "fv_status: NULL mesh");
+  int st = 0;
+  cudaError_t e = cudaSetDevice(m->cfg.device);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&st, m->d.status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "fv_status");
+  if (st & FV_STATUS_NONPHYS) return fail(FV_ERR_NONPHYSICAL, "non-physical state (rho or p <= 0)");
+  if (st & FV_STATUS_RIEMANN) return fail(FV_ERR_RIEMANN, "Riemann solver failed (vacuum or no convergence)");
+  return FV_OK;
+}
+
+}  // extern "C"

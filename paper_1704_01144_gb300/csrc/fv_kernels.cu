@@ -1,0 +1,729 @@
+// fv_kernels.cu -- the hot path of one temporally adaptive cycle (Alg. 2)
+// as CUDA kernels for sm_103a.
+//
+// Per cycle:  k_dt -> k_levels0 -> k_smooth x (L-1) -> cell/face keys ->
+//             counting sort (hist, scan, scatter) for cells and faces.
+// Per phase:  k_prim (states at the phase time, time-interpolated) ->
+//             k_grad (least-squares gradients) ->
+//             k_flux (MUSCL-minmod + exact Riemann; predictor stash or
+//                     corrector time integral + interface accumulation) ->
+//             k_update (per-cell gather over the 4 faces in fixed order, no
+//                       atomics; predictor U* or corrector U^{n+1}).
+//
+// Every phase kernel grid-strides over a range of a level-sorted list whose
+// bounds are read from device memory, so inactive levels cost a few idle
+// blocks and the launch sequence of a cycle is fixed (graph-capturable).
+// All face and cell data are structure-of-arrays; cells follow a Morton
+// curve, faces their owner cell.
+#include <cuda_runtime.h>
+
+#include "fv_internal.h"
+#include "fv_riemann.cuh"
+
+namespace fvk {
+
+static int g_num_sms = 0;
+static int num_sms() {
+  if (!g_num_sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 1;
+  }
+  return g_num_sms;
+}
+
+static inline int grid_for(int64_t items, int block, int per_sm) {
+  int64_t need = (items + block - 1) / block;
+  int64_t cap = (int64_t)num_sms() * per_sm;
+  if (need < 1) need = 1;
+  return (int)(need < cap ? need : cap);
+}
+
+#define FV_LAUNCH_CHECK()                        \
+  do {                                           \
+    cudaError_t e_ = cudaGetLastError();         \
+    if (e_ != cudaSuccess) return FV_ERR_CUDA;   \
+  } while (0)
+
+// ------------------------------------------------------------- helpers ---
+template <typename T>
+__device__ __forceinline__ void cons_to_prim(const T U[5], T gm1, T W[5]) {
+  T r = U[0];
+  T ri = T(1) / r;
+  T u = U[1] * ri, v = U[2] * ri, w = U[3] * ri;
+  T ke = T(0.5) * r * ((u * u + v * v) + w * w);
+  W[0] = r;
+  W[1] = u;
+  W[2] = v;
+  W[3] = w;
+  W[4] = gm1 * (U[4] - ke);
+}
+
+__device__ __forceinline__ double minmod(double a, double b) {
+  if (a > 0.0 && b > 0.0) return a < b ? a : b;
+  if (a < 0.0 && b < 0.0) return a > b ? a : b;
+  return 0.0;
+}
+__device__ __forceinline__ float minmod(float a, float b) {
+  if (a > 0.f && b > 0.f) return a < b ? a : b;
+  if (a < 0.f && b < 0.f) return a > b ? a : b;
+  return 0.f;
+}
+
+// ------------------------------------------------ level assignment (a1-a2)
+// dt_i = 2 CFL V_i / sum_j A_j (|u_i . n_j| + c_i), evaluated with
+// round-to-nearest intrinsics (no fused multiply-add) in the fixed order
+// j = 0..3, so that it is bitwise the same number as a plain FP64 host
+// evaluation of the same formula: temporal levels are integer decisions.
+__global__ void __launch_bounds__(256) k_dt(DevMesh d) {
+  const size_t N = d.N, F = d.F;
+  double local_min = __longlong_as_double(0x7ff0000000000000LL);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x) {
+    double r = d.Un[i];
+    double u = __ddiv_rn(d.Un[N + i], r), v = __ddiv_rn(d.Un[2 * N + i], r),
+           w = __ddiv_rn(d.Un[3 * N + i], r);
+    double uu = __dadd_rn(__dadd_rn(__dmul_rn(u, u), __dmul_rn(v, v)), __dmul_rn(w, w));
+    double ke = __dmul_rn(__dmul_rn(0.5, r), uu);
+    double p = __dmul_rn(d.gamma - 1.0, __dsub_rn(d.Un[4 * N + i], ke));
+    double c = __dsqrt_rn(__ddiv_rn(__dmul_rn(d.gamma, p), r));
+    double S = 0.0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int f = d.cf[j * N + i];
+      double un = __dadd_rn(__dadd_rn(__dmul_rn(u, d.fn[f]), __dmul_rn(v, d.fn[F + f])),
+                            __dmul_rn(w, d.fn[2 * F + f]));
+      S = __dadd_rn(S, __dmul_rn(d.farea[f], __dadd_rn(fabs(un), c)));
+    }
+    double dt = __ddiv_rn(__dmul_rn(__dmul_rn(2.0, d.cfl), d.vol[i]), S);
+    if (!(p > 0.0) || !(r > 0.0) || !isfinite(dt)) {
+      atomicOr(d.status, FV_STATUS_NONPHYS);
+      dt = __longlong_as_double(0x7ff0000000000000LL);
+    }
+    d.dt[i] = dt;
+    local_min = fmin(local_min, dt);
+  }
+  // block minimum, then one atomic per block on the bit pattern (positive
+  // doubles order like their bit patterns): order-independent, exact
+  __shared__ double sm[8];
+  for (int o = 16; o > 0; o >>= 1) local_min = fmin(local_min, __shfl_xor_sync(0xffffffff, local_min, o));
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = local_min;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : __longlong_as_double(0x7ff0000000000000LL);
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffff, v, o));
+    if (threadIdx.x == 0) atomicMin(d.dtmin_bits, (unsigned long long)__double_as_longlong(v));
+  }
+}
+
+__global__ void k_init_min(unsigned long long *bits) { *bits = 0x7ff0000000000000ULL; }
+
+// k_i = max{k <= L-1 : 2^k dt_min <= dt_i}
+__global__ void __launch_bounds__(256) k_levels0(DevMesh d, int L) {
+  double dtmin = __longlong_as_double((long long)*d.dtmin_bits);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x) {
+    double dt = d.dt[i];
+    int k = 0;
+    while (k + 1 < L && ldexp(dtmin, k + 1) <= dt) ++k;
+    d.lev_tmp[i] = (int8_t)k;
+  }
+}
+
+// one Jacobi sweep of k_i <- min(k_i, 1 + min_j k_j); L-1 sweeps reach the
+// fixed point (the result is min_j (k0_j + graph distance), and k0 <= L-1)
+__global__ void __launch_bounds__(256) k_smooth(DevMesh d, const int8_t *__restrict__ src,
+                                                int8_t *__restrict__ dst) {
+  const size_t N = d.N;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x) {
+    int k = src[i];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int nb = d.cnb[j * N + i];
+      if (nb >= 0) k = min(k, src[nb] + 1);
+    }
+    dst[i] = (int8_t)k;
+  }
+}
+
+// cell sort key: 2 level + (1 unless a neighbour is one level finer), so the
+// cells a phase touches are contiguous: levels <= tau followed by the
+// level-(tau+1) cells next to level tau
+__global__ void __launch_bounds__(256) k_cell_keys(DevMesh d) {
+  const size_t N = d.N;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x) {
+    int k = d.lev[i];
+    int finer = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int nb = d.cnb[j * N + i];
+      if (nb >= 0 && d.lev[nb] < k) finer = 1;
+    }
+    d.ckey[i] = (uint8_t)(2 * k + (finer ? 0 : 1));
+  }
+}
+
+// face level = min of the two cell levels; faces sort by it
+__global__ void __launch_bounds__(256) k_face_keys(DevMesh d) {
+  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < d.F; f += gridDim.x * blockDim.x) {
+    int a = d.lev[d.fown[f]];
+    int nb = d.fnb[f];
+    int k = nb >= 0 ? min(a, (int)d.lev[nb]) : a;
+    d.flev[f] = (int8_t)k;
+    d.fkey[f] = (uint8_t)k;
+  }
+}
+
+// ---- stable counting sort of small keys (< 16 buckets), 1024 items per block
+#define SORT_TILE 1024
+#define SORT_THREADS 256
+
+__global__ void __launch_bounds__(SORT_THREADS) k_sort_hist(const uint8_t *__restrict__ key, int n,
+                                                            int nb, int *cnt) {
+  __shared__ int h[16];
+  if (threadIdx.x < 16) h[threadIdx.x] = 0;
+  __syncthreads();
+  int base = blockIdx.x * SORT_TILE;
+  for (int r = 0; r < SORT_TILE / SORT_THREADS; ++r) {
+    int i = base + r * SORT_THREADS + threadIdx.x;
+    if (i < n) atomicAdd(&h[key[i]], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x < nb) cnt[threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
+}
+
+// exclusive scan over the bucket-major (bucket, block) counts; also writes
+// the bucket offsets off[0..nb]
+__global__ void __launch_bounds__(1024) k_sort_scan(int *cnt, int total, int nblk, int nb, int *off) {
+  __shared__ int warp_sums[32];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < total; base += 1024) {
+    int i = base + threadIdx.x;
+    int v = i < total ? cnt[i] : 0;
+    // inclusive warp scan
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffff, x, o);
+      if ((threadIdx.x & 31) >= o) x += y;
+    }
+    if ((threadIdx.x & 31) == 31) warp_sums[threadIdx.x >> 5] = x;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      int s = warp_sums[threadIdx.x];
+      for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffff, s, o);
+        if (threadIdx.x >= o) s += y;
+      }
+      warp_sums[threadIdx.x] = s;
+    }
+    __syncthreads();
+    int warp_prefix = (threadIdx.x >= 32) ? warp_sums[(threadIdx.x >> 5) - 1] : 0;
+    int excl = carry + warp_prefix + x - v;
+    if (i < total) {
+      cnt[i] = excl;
+      if (i % nblk == 0) off[i / nblk] = excl;
+    }
+    __syncthreads();
+    if (threadIdx.x == 1023) carry = excl + v;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) off[nb] = carry;
+}
+
+__global__ void __launch_bounds__(SORT_THREADS) k_sort_scatter(const uint8_t *__restrict__ key, int n,
+                                                               int nb, const int *__restrict__ cnt,
+                                                               int *__restrict__ out) {
+  __shared__ int wcount[SORT_THREADS / 32][16];
+  __shared__ int run[16];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x < 16) run[threadIdx.x] = threadIdx.x < nb ? cnt[threadIdx.x * gridDim.x + blockIdx.x] : 0;
+  int base = blockIdx.x * SORT_TILE;
+  for (int r = 0; r < SORT_TILE / SORT_THREADS; ++r) {
+    int i = base + r * SORT_THREADS + threadIdx.x;
+    int k = i < n ? (int)key[i] : -1;
+    if (lane < 16) wcount[warp][lane] = 0;
+    __syncthreads();
+    // lanes with equal keys: rank among them in lane (= item) order
+    unsigned mask = __match_any_sync(0xffffffff, k);
+    int rank = __popc(mask & ((1u << lane) - 1));
+    if (k >= 0 && rank == 0) wcount[warp][k] = __popc(mask);
+    __syncthreads();
+    if (k >= 0) {
+      int pre = run[k];
+      for (int w = 0; w < warp; ++w) pre += wcount[w][k];
+      out[pre + rank] = i;
+    }
+    __syncthreads();
+    if (threadIdx.x < 16) {
+      int s = 0;
+      for (int w = 0; w < SORT_THREADS / 32; ++w) s += wcount[w][threadIdx.x];
+      run[threadIdx.x] += s;
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------ state at a time --
+__device__ __forceinline__ void load_state(const DevMesh &d, const PhaseLevels &pl, int c,
+                                           double U[5]) {
+  const size_t N = d.N;
+  int k = d.lev[c];
+  int mode = pl.mode[k];
+  if (mode == 0) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) U[q] = d.Un[q * N + c];
+  } else if (mode == 1) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) U[q] = d.Us[q * N + c];
+  } else {
+    double w = pl.w[k];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      double a = d.Un[q * N + c], b = d.Us[q * N + c];
+      U[q] = a + w * (b - a);
+    }
+  }
+}
+
+// primitives of the cells of list range [coff[b0], coff[b1]) at the phase
+// time: W[5][N] in FP64 (FP64 mode) or W32 (FP32-flux mode)
+template <typename WT>
+__global__ void __launch_bounds__(256) k_prim(DevMesh d, const __grid_constant__ PhaseLevels pl, int b0, int b1, WT *W) {
+  const size_t N = d.N;
+  int beg = d.coff[b0], end = d.coff[b1];
+  double gm1 = d.gamma - 1.0;
+  for (int idx = beg + blockIdx.x * blockDim.x + threadIdx.x; idx < end; idx += gridDim.x * blockDim.x) {
+    int i = d.cl[idx];
+    double U[5], Wd[5];
+    load_state(d, pl, i, U);
+    cons_to_prim(U, gm1, Wd);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) W[q * N + i] = (WT)Wd[q];
+  }
+}
+
+// least-squares gradients of the primitives: g = sum_j w_j (W_nb(j) - W_i),
+// ghost states on boundary faces
+template <typename T>
+__global__ void __launch_bounds__(256) k_grad(DevMesh d, int b0, int b1, const T *__restrict__ W,
+                                              T *__restrict__ G) {
+  const size_t N = d.N, F = d.F;
+  int beg = d.coff[b0], end = d.coff[b1];
+  for (int idx = beg + blockIdx.x * blockDim.x + threadIdx.x; idx < end; idx += gridDim.x * blockDim.x) {
+    int i = d.cl[idx];
+    T Wi[5], g[15];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) Wi[q] = W[q * N + i];
+#pragma unroll
+    for (int q = 0; q < 15; ++q) g[q] = T(0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int nb = d.cnb[j * N + i];
+      T Wn[5];
+      if (nb >= 0) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) Wn[q] = W[q * N + nb];
+      } else {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) Wn[q] = Wi[q];
+        if (nb == -FV_BC_WALL) {
+          int f = d.cf[j * N + i];
+          T n0 = (T)d.fn[f], n1 = (T)d.fn[F + f], n2 = (T)d.fn[2 * F + f];
+          T un = (Wi[1] * n0 + Wi[2] * n1) + Wi[3] * n2;
+          Wn[1] = Wi[1] - (T(2) * un) * n0;
+          Wn[2] = Wi[2] - (T(2) * un) * n1;
+          Wn[3] = Wi[3] - (T(2) * un) * n2;
+        }
+      }
+      T w0 = (T)d.lsw[(3 * j) * N + i], w1 = (T)d.lsw[(3 * j + 1) * N + i],
+        w2 = (T)d.lsw[(3 * j + 2) * N + i];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        T dd = Wn[c] - Wi[c];
+        g[3 * c] += w0 * dd;
+        g[3 * c + 1] += w1 * dd;
+        g[3 * c + 2] += w2 * dd;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 15; ++q) G[q * N + i] = g[q];
+  }
+}
+
+// face flux of face f from the phase-time primitives W and gradients G:
+// F A in FA_out[5] (FP64).  Returns a nonzero status on Riemann failure.
+template <typename T>
+__device__ __forceinline__ int face_flux(const DevMesh &d, const GasT<T> &G, const T *__restrict__ W,
+                                         const T *__restrict__ Gr, const T *__restrict__ fn,
+                                         const T *__restrict__ fr, const T *__restrict__ farea, int f,
+                                         T FA[5]) {
+  const size_t N = d.N, Fn = d.F;
+  int L = d.fown[f], R = d.fnb[f];
+  T n[3] = {fn[f], fn[Fn + f], fn[2 * Fn + f]};
+  T r[3] = {fr[f], fr[Fn + f], fr[2 * Fn + f]};
+  T WL[5], WR[5], Fx[5];
+  int it, rc;
+  if (R >= 0) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      T wi = W[c * N + L], wj = W[c * N + R];
+      T dW = wj - wi;
+      T gir = (Gr[(3 * c) * N + L] * r[0] + Gr[(3 * c + 1) * N + L] * r[1]) + Gr[(3 * c + 2) * N + L] * r[2];
+      T gjr = (Gr[(3 * c) * N + R] * r[0] + Gr[(3 * c + 1) * N + R] * r[1]) + Gr[(3 * c + 2) * N + R] * r[2];
+      WL[c] = wi + T(0.5) * minmod(T(2) * gir - dW, dW);
+      WR[c] = wj - T(0.5) * minmod(T(2) * gjr - dW, dW);
+    }
+    rc = godunov_flux(G, WL, WR, n, Fx, it);
+  } else {
+    // reconstruct toward the ghost (mirror image of the cell in the face)
+    T Wi[5], Wg[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) Wi[c] = Wg[c] = W[c * N + L];
+    if (R == -FV_BC_WALL) {
+      T un = (Wi[1] * n[0] + Wi[2] * n[1]) + Wi[3] * n[2];
+#pragma unroll
+      for (int e = 0; e < 3; ++e) Wg[1 + e] = Wi[1 + e] - (T(2) * un) * n[e];
+    }
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      T dW = Wg[c] - Wi[c];
+      T gir = (Gr[(3 * c) * N + L] * r[0] + Gr[(3 * c + 1) * N + L] * r[1]) + Gr[(3 * c + 2) * N + L] * r[2];
+      WL[c] = Wi[c] + T(0.5) * minmod(T(2) * gir - dW, dW);
+    }
+    rc = boundary_flux(G, -R, WL, n, Fx, it);
+  }
+  T A = farea[f];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) FA[c] = Fx[c] * A;
+  return rc;
+}
+
+// stage 1 (predictor): FA[f] = F1 A.  stage 2 (corrector of `level`):
+// Phi = dt_k (F1 A + F2 A)/2 replaces FA[f]; on a level interface Phi is
+// added to ACC[f] (the coarse side's integral); on a boundary face to BND[f].
+template <typename T>
+__global__ void __launch_bounds__(128) k_flux(DevMesh d, GasT<T> G, int stage, int level, int b0,
+                                              int b1, const T *__restrict__ W, const T *__restrict__ Gr,
+                                              const T *__restrict__ fn, const T *__restrict__ fr,
+                                              const T *__restrict__ farea) {
+  const size_t F = d.F;
+  int beg = d.foff[b0], end = d.foff[b1];
+  double dtk = ldexp(__longlong_as_double((long long)*d.dtmin_bits), level);
+  for (int idx = beg + blockIdx.x * blockDim.x + threadIdx.x; idx < end; idx += gridDim.x * blockDim.x) {
+    int f = d.fl[idx];
+    T FAt[5];
+    int rc = face_flux(d, G, W, Gr, fn, fr, farea, f, FAt);
+    if (rc) atomicOr(d.status, FV_STATUS_RIEMANN);
+    if (stage == 1) {
+#pragma unroll
+      for (int c = 0; c < 5; ++c) d.FA[c * F + f] = (double)FAt[c];
+    } else {
+      int R = d.fnb[f];
+      bool iface = R >= 0 && d.lev[d.fown[f]] != d.lev[R];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        double phi = dtk * (0.5 * (d.FA[c * F + f] + (double)FAt[c]));
+        d.FA[c * F + f] = phi;
+        if (iface) d.ACC[c * F + f] += phi;
+        if (R < 0) d.BND[c * F + f] += phi;
+      }
+    }
+  }
+}
+
+// per-cell gather over its 4 faces in local order (deterministic, no
+// atomics).  stage 1: U* = U^n + dt_k (-S/V) with S = sum sigma F1 A;
+// stage 2 (level k): U^{n+1} = U^n - S/V with S = sum sigma Phi, where faces
+// to finer neighbours contribute (and reset) their accumulated integral.
+__global__ void __launch_bounds__(256) k_update(DevMesh d, int stage, int level, int b0, int b1) {
+  const size_t N = d.N, F = d.F;
+  int beg = d.coff[b0], end = d.coff[b1];
+  double dtmin = __longlong_as_double((long long)*d.dtmin_bits);
+  double gm1 = d.gamma - 1.0;
+  for (int idx = beg + blockIdx.x * blockDim.x + threadIdx.x; idx < end; idx += gridDim.x * blockDim.x) {
+    int i = d.cl[idx];
+    unsigned own = d.cown[i];
+    double S[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int f = d.cf[j * N + i];
+      double s = ((own >> j) & 1u) ? 1.0 : -1.0;
+      if (stage == 1 || d.flev[f] == level) {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) S[c] += s * d.FA[c * F + f];
+      } else {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          S[c] += s * d.ACC[c * F + f];
+          d.ACC[c * F + f] = 0.0;
+        }
+      }
+    }
+    double V = d.vol[i];
+    double Un[5], Uo[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) Un[c] = d.Un[c * N + i];
+    if (stage == 1) {
+      double dtk = ldexp(dtmin, (int)d.lev[i]);
+#pragma unroll
+      for (int c = 0; c < 5; ++c) Uo[c] = Un[c] + dtk * (-S[c] / V);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 5; ++c) Uo[c] = Un[c] - S[c] / V;
+    }
+    double Wc[5];
+    cons_to_prim(Uo, gm1, Wc);
+    if (!(Wc[0] > 0.0) || !(Wc[4] > 0.0) || !isfinite(Wc[0] + Wc[1] + Wc[2] + Wc[3] + Wc[4]))
+      atomicOr(d.status, FV_STATUS_NONPHYS);
+    double *dst = stage == 1 ? d.Us : d.Un;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) dst[c * N + i] = Uo[c];
+  }
+}
+
+// R = -(1/V) sum sigma F A for the cells of one level (residual hook);
+// written in the caller's order
+__global__ void __launch_bounds__(256) k_residual(DevMesh d, int level, const double *__restrict__ FAt,
+                                                  double *__restrict__ R, const int *__restrict__ new2old) {
+  const size_t N = d.N, F = d.F;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x) {
+    int o = new2old[i];
+    if (d.lev[i] != level) {
+#pragma unroll
+      for (int c = 0; c < 5; ++c) R[c * N + o] = 0.0;
+      continue;
+    }
+    unsigned own = d.cown[i];
+    double S[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int f = d.cf[j * N + i];
+      double s = ((own >> j) & 1u) ? 1.0 : -1.0;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) S[c] += s * FAt[c * F + f];
+    }
+    double V = d.vol[i];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) R[c * N + o] = -S[c] / V;
+  }
+}
+
+// F A of every face touching a level-`level` cell into FAt (residual hook)
+template <typename T>
+__global__ void __launch_bounds__(128) k_flux_all(DevMesh d, GasT<T> G, int level, const T *__restrict__ W,
+                                                  const T *__restrict__ Gr, const T *__restrict__ fn,
+                                                  const T *__restrict__ fr, const T *__restrict__ farea,
+                                                  double *__restrict__ FAt) {
+  const size_t F = d.F;
+  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < d.F; f += gridDim.x * blockDim.x) {
+    int R = d.fnb[f];
+    bool touch = d.lev[d.fown[f]] == level || (R >= 0 && d.lev[R] == level);
+    if (!touch) continue;
+    T FAx[5];
+    if (face_flux(d, G, W, Gr, fn, fr, farea, f, FAx)) atomicOr(d.status, FV_STATUS_RIEMANN);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) FAt[c * F + f] = (double)FAx[c];
+  }
+}
+
+// primitives / gradients of every cell (residual hook: a plain, unsorted pass)
+template <typename WT>
+__global__ void __launch_bounds__(256) k_prim_all(DevMesh d, const __grid_constant__ PhaseLevels pl, WT *W) {
+  const size_t N = d.N;
+  double gm1 = d.gamma - 1.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x) {
+    double U[5], Wd[5];
+    load_state(d, pl, i, U);
+    cons_to_prim(U, gm1, Wd);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) W[q * N + i] = (WT)Wd[q];
+  }
+}
+
+// end of a cycle: t += 2^theta dt_min, and the work counters of the cost
+// model: sum_k 2^(theta-k) |Omega_k| cell updates, twice that over faces
+__global__ void k_time_advance(DevMesh d, int theta) {
+  d.tdev[0] += ldexp(__longlong_as_double((long long)*d.dtmin_bits), theta);
+  long long cu = 0, fe = 0;
+  for (int k = 0; k <= theta; ++k) {
+    cu += (long long)(d.coff[2 * k + 2] - d.coff[2 * k]) << (theta - k);
+    fe += (long long)(d.foff[k + 1] - d.foff[k]) << (theta - k + 1);
+  }
+  d.counters[0] += 1;
+  d.counters[1] += cu;
+  d.counters[2] += fe;
+}
+
+// caller-order primitives -> Morton-order conserved state
+__global__ void __launch_bounds__(256) k_set_state(DevMesh d, const double *__restrict__ prim,
+                                                   const int *__restrict__ new2old) {
+  const size_t N = d.N;
+  double gm1 = d.gamma - 1.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x) {
+    int o = new2old[i];
+    double r = prim[o], u = prim[N + o], v = prim[2 * N + o], w = prim[3 * N + o], p = prim[4 * N + o];
+    if (!(r > 0.0) || !(p > 0.0)) atomicOr(d.status, FV_STATUS_NONPHYS);
+    d.Un[i] = r;
+    d.Un[N + i] = __dmul_rn(r, u);
+    d.Un[2 * N + i] = __dmul_rn(r, v);
+    d.Un[3 * N + i] = __dmul_rn(r, w);
+    double uu = __dadd_rn(__dadd_rn(__dmul_rn(u, u), __dmul_rn(v, v)), __dmul_rn(w, w));
+    d.Un[4 * N + i] = __dadd_rn(__ddiv_rn(p, gm1), __dmul_rn(__dmul_rn(0.5, r), uu));
+  }
+}
+
+__global__ void __launch_bounds__(256) k_set_cons(DevMesh d, const double *__restrict__ cons,
+                                                  const int *__restrict__ new2old) {
+  const size_t N = d.N;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x) {
+    int o = new2old[i];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) d.Un[c * N + i] = cons[c * N + o];
+    if (!(cons[o] > 0.0)) atomicOr(d.status, FV_STATUS_NONPHYS);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_get_state(DevMesh d, double *__restrict__ cons,
+                                                   const int *__restrict__ new2old) {
+  const size_t N = d.N;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x) {
+    int o = new2old[i];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) cons[c * N + o] = d.Un[c * N + i];
+  }
+}
+
+__global__ void __launch_bounds__(256) k_get_levels(DevMesh d, int8_t *__restrict__ lev,
+                                                    const int *__restrict__ new2old) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x)
+    lev[new2old[i]] = d.lev[i];
+}
+
+// ================================================================ hosts ==
+void init_device_info() { num_sms(); }
+
+int launch_assign_levels(const DevMesh &d, int L, int *cnt_scratch, ProfHook *ph, cudaStream_t s) {
+  int g = grid_for(d.N, 256, 8);
+  ProfScope scope(ph, FV_PROF_LEVELS, s);
+  k_init_min<<<1, 1, 0, s>>>(d.dtmin_bits);
+  k_dt<<<g, 256, 0, s>>>(d);
+  k_levels0<<<g, 256, 0, s>>>(d, L);
+  // L-1 Jacobi sweeps between lev_tmp and lev; the result must land in lev
+  const int8_t *src = d.lev_tmp;
+  int8_t *dst = d.lev;
+  if (L == 1) {
+    cudaMemcpyAsync(d.lev, d.lev_tmp, d.N, cudaMemcpyDeviceToDevice, s);
+  } else {
+    // with an even number of sweeps, start with a copy so the last one writes lev
+    if ((L - 1) % 2 == 0) {
+      cudaMemcpyAsync(d.lev, d.lev_tmp, d.N, cudaMemcpyDeviceToDevice, s);
+      src = d.lev;
+      dst = d.lev_tmp;
+    }
+    for (int sw = 0; sw < L - 1; ++sw) {
+      k_smooth<<<g, 256, 0, s>>>(d, src, dst);
+      const int8_t *t = dst;
+      dst = (int8_t *)src;
+      src = t;
+    }
+  }
+  FV_LAUNCH_CHECK();
+  // cell keys and sort (2L buckets)
+  k_cell_keys<<<g, 256, 0, s>>>(d);
+  int nblk = (d.N + SORT_TILE - 1) / SORT_TILE;
+  k_sort_hist<<<nblk, SORT_THREADS, 0, s>>>(d.ckey, d.N, 2 * L, cnt_scratch);
+  k_sort_scan<<<1, 1024, 0, s>>>(cnt_scratch, 2 * L * nblk, nblk, 2 * L, d.coff);
+  k_sort_scatter<<<nblk, SORT_THREADS, 0, s>>>(d.ckey, d.N, 2 * L, cnt_scratch, d.cl);
+  // faces (L buckets)
+  int gf = grid_for(d.F, 256, 8);
+  k_face_keys<<<gf, 256, 0, s>>>(d);
+  int nblkf = (d.F + SORT_TILE - 1) / SORT_TILE;
+  k_sort_hist<<<nblkf, SORT_THREADS, 0, s>>>(d.fkey, d.F, L, cnt_scratch);
+  k_sort_scan<<<1, 1024, 0, s>>>(cnt_scratch, L * nblkf, nblkf, L, d.foff);
+  k_sort_scatter<<<nblkf, SORT_THREADS, 0, s>>>(d.fkey, d.F, L, cnt_scratch, d.fl);
+  FV_LAUNCH_CHECK();
+  return FV_OK;
+}
+
+int launch_phase(const DevMesh &d, int precision, const PhaseLevels &pl, int stage, int level,
+                 int pb0, int pb1, int gb0, int gb1, int fb0, int fb1, int ub0, int ub1,
+                 void *Wbuf, ProfHook *ph, cudaStream_t s) {
+  int gc = grid_for(d.N, 256, 8);
+  int gfx = grid_for(d.F, 128, 16);
+  if (precision == FV_FP64) {
+    double *W = (double *)Wbuf;
+    GasT<double> G = GasT<double>::make(d.gamma, d.tol, d.maxit);
+    { ProfScope sc(ph, FV_PROF_PRIM, s); k_prim<double><<<gc, 256, 0, s>>>(d, pl, pb0, pb1, W); }
+    { ProfScope sc(ph, FV_PROF_GRAD, s); k_grad<double><<<gc, 256, 0, s>>>(d, gb0, gb1, W, d.G); }
+    { ProfScope sc(ph, FV_PROF_FLUX, s);
+      k_flux<double><<<gfx, 128, 0, s>>>(d, G, stage, level, fb0, fb1, W, d.G, d.fn, d.fr, d.farea); }
+  } else {
+    float *W = (float *)Wbuf;
+    double tol32 = d.tol > 2e-6 ? d.tol : 2e-6;
+    GasT<float> G = GasT<float>::make(d.gamma, tol32, d.maxit);
+    { ProfScope sc(ph, FV_PROF_PRIM, s); k_prim<float><<<gc, 256, 0, s>>>(d, pl, pb0, pb1, W); }
+    { ProfScope sc(ph, FV_PROF_GRAD, s); k_grad<float><<<gc, 256, 0, s>>>(d, gb0, gb1, W, d.G32); }
+    { ProfScope sc(ph, FV_PROF_FLUX, s);
+      k_flux<float><<<gfx, 128, 0, s>>>(d, G, stage, level, fb0, fb1, W, d.G32, d.fn32, d.fr32, d.farea32); }
+  }
+  { ProfScope sc(ph, FV_PROF_UPDATE, s); k_update<<<gc, 256, 0, s>>>(d, stage, level, ub0, ub1); }
+  FV_LAUNCH_CHECK();
+  return FV_OK;
+}
+
+int launch_residual(const DevMesh &d, int precision, const PhaseLevels &pl, int level, void *Wbuf,
+                    double *FAt, double *R, const int *new2old, cudaStream_t s) {
+  int gc = grid_for(d.N, 256, 8);
+  int gfx = grid_for(d.F, 128, 16);
+  if (precision == FV_FP64) {
+    double *W = (double *)Wbuf;
+    GasT<double> G = GasT<double>::make(d.gamma, d.tol, d.maxit);
+    k_prim_all<double><<<gc, 256, 0, s>>>(d, pl, W);
+    // gradients of every cell: the list range covering all cells
+    k_grad<double><<<gc, 256, 0, s>>>(d, 0, 2 * d.L, W, d.G);
+    k_flux_all<double><<<gfx, 128, 0, s>>>(d, G, level, W, d.G, d.fn, d.fr, d.farea, FAt);
+  } else {
+    float *W = (float *)Wbuf;
+    double tol32 = d.tol > 2e-6 ? d.tol : 2e-6;
+    GasT<float> G = GasT<float>::make(d.gamma, tol32, d.maxit);
+    k_prim_all<float><<<gc, 256, 0, s>>>(d, pl, W);
+    k_grad<float><<<gc, 256, 0, s>>>(d, 0, 2 * d.L, W, d.G32);
+    k_flux_all<float><<<gfx, 128, 0, s>>>(d, G, level, W, d.G32, d.fn32, d.fr32, d.farea32, FAt);
+  }
+  k_residual<<<gc, 256, 0, s>>>(d, level, FAt, R, new2old);
+  FV_LAUNCH_CHECK();
+  return FV_OK;
+}
+
+int launch_time_advance(const DevMesh &d, int theta, cudaStream_t s) {
+  k_time_advance<<<1, 1, 0, s>>>(d, theta);
+  FV_LAUNCH_CHECK();
+  return FV_OK;
+}
+
+int launch_set_state(const DevMesh &d, const double *prim, const int *new2old, cudaStream_t s) {
+  k_set_state<<<grid_for(d.N, 256, 8), 256, 0, s>>>(d, prim, new2old);
+  FV_LAUNCH_CHECK();
+  return FV_OK;
+}
+
+int launch_set_cons(const DevMesh &d, const double *cons, const int *new2old, cudaStream_t s) {
+  k_set_cons<<<grid_for(d.N, 256, 8), 256, 0, s>>>(d, cons, new2old);
+  FV_LAUNCH_CHECK();
+  return FV_OK;
+}
+
+int launch_get_state(const DevMesh &d, double *cons, const int *new2old, cudaStream_t s) {
+  k_get_state<<<grid_for(d.N, 256, 8), 256, 0, s>>>(d, cons, new2old);
+  FV_LAUNCH_CHECK();
+  return FV_OK;
+}
+
+int launch_get_levels(const DevMesh &d, int8_t *lev, const int *new2old, cudaStream_t s) {
+  k_get_levels<<<grid_for(d.N, 256, 8), 256, 0, s>>>(d, lev, new2old);
+  FV_LAUNCH_CHECK();
+  return FV_OK;
+}
+
+}  // namespace fvk

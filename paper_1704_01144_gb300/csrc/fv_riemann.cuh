@@ -1,0 +1,235 @@
+// fv_riemann.cuh -- exact Godunov flux for the Euler equations on the GPU,
+// templated on the arithmetic type (double: FP64 mode, float: FP32-flux
+// mode).
+//
+// The paper (Sec. 2.1) computes face fluxes with Godunov's method, i.e. from
+// the solution of the Riemann problem between the two face states.  The
+// exact solver follows the published construction (Toro, "Riemann Solvers
+// and Numerical Methods for Fluid Dynamics", ch. 4): pressure functions f_K
+// (shock branch for p > p_K, rarefaction branch otherwise), Newton on
+// f_L(p) + f_R(p) + (u_R - u_L) = 0 from the two-rarefaction guess, the
+// solution sampled on the face (x/t = 0).  Written from the equations.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace fvk {
+
+template <typename T>
+struct GasT {
+  T g, gm1, gp1;
+  T k_gm1_gp1;    // (g-1)/(g+1)
+  T z;            // (g-1)/(2g)
+  T inv_z;        // 2g/(g-1)
+  T two_gm1;      // 2/(g-1)
+  T shock_a;      // (g+1)/(2g)
+  T shock_b;      // (g-1)/(2g)
+  T inv_g;        // 1/g
+  T tol;
+  int maxit;
+  __host__ __device__ static GasT make(double gamma, double tol, int maxit) {
+    GasT G;
+    G.g = (T)gamma;
+    G.gm1 = (T)(gamma - 1.0);
+    G.gp1 = (T)(gamma + 1.0);
+    G.k_gm1_gp1 = (T)((gamma - 1.0) / (gamma + 1.0));
+    G.z = (T)((gamma - 1.0) / (2.0 * gamma));
+    G.inv_z = (T)(2.0 * gamma / (gamma - 1.0));
+    G.two_gm1 = (T)(2.0 / (gamma - 1.0));
+    G.shock_a = (T)((gamma + 1.0) / (2.0 * gamma));
+    G.shock_b = (T)((gamma - 1.0) / (2.0 * gamma));
+    G.inv_g = (T)(1.0 / gamma);
+    G.tol = (T)tol;
+    G.maxit = maxit;
+    return G;
+  }
+};
+
+__device__ __forceinline__ double fpow(double a, double b) { return pow(a, b); }
+__device__ __forceinline__ float fpow(float a, float b) { return powf(a, b); }
+__device__ __forceinline__ double fsqrt(double a) { return sqrt(a); }
+__device__ __forceinline__ float fsqrt(float a) { return sqrtf(a); }
+
+// pressure function of side K and its derivative (Toro Eqs. 4.6-4.7, 4.37)
+template <typename T>
+__device__ __forceinline__ void pressure_fn(const GasT<T> &G, T p, T rK, T pK, T aK, T &f, T &df) {
+  if (p > pK) {
+    T A = T(2) / (G.gp1 * rK);
+    T B = G.k_gm1_gp1 * pK;
+    T q = fsqrt(A / (p + B));
+    f = (p - pK) * q;
+    df = q * (T(1) - T(0.5) * (p - pK) / (B + p));
+  } else {
+    T pr = p / pK;
+    T pz = fpow(pr, G.z);
+    f = (G.two_gm1 * aK) * (pz - T(1));
+    // d/dp of the rarefaction branch: (p/pK)^(-(g+1)/(2g)) / (rK aK), and
+    // -(g+1)/(2g) = z - 1
+    df = (pz / pr) / (rK * aK);
+  }
+}
+
+// Star pressure/velocity.  Returns 0, or 1 (vacuum), 2 (no convergence).
+template <typename T>
+__device__ __forceinline__ int riemann_star(const GasT<T> &G, T rL, T uL, T pL, T rR, T uR, T pR,
+                                            T &ps, T &us, int &iters) {
+  T aL = fsqrt(G.g * pL / rL), aR = fsqrt(G.g * pR / rR);
+  T du = uR - uL;
+  if (G.two_gm1 * (aL + aR) <= du) return 1;
+  T num = aL + aR - T(0.5) * G.gm1 * du;
+  T den = aL / fpow(pL, G.z) + aR / fpow(pR, G.z);
+  T p = fpow(num / den, G.inv_z);
+  T pfloor = T(1e-6) * (pL < pR ? pL : pR);
+  if (p < pfloor) p = pfloor;
+  int it;
+  bool conv = false;
+  for (it = 1; it <= G.maxit; ++it) {
+    T fL, dfL, fR, dfR;
+    pressure_fn(G, p, rL, pL, aL, fL, dfL);
+    pressure_fn(G, p, rR, pR, aR, fR, dfR);
+    T pn = p - (fL + fR + du) / (dfL + dfR);
+    if (pn < pfloor) pn = pfloor;
+    T change = fabs(pn - p) / (T(0.5) * (pn + p));
+    p = pn;
+    if (change <= G.tol) {
+      conv = true;
+      break;
+    }
+  }
+  iters = it;
+  if (!conv || !(p > T(0)) || !isfinite(p)) return 2;
+  T fL, dfL, fR, dfR;
+  pressure_fn(G, p, rL, pL, aL, fL, dfL);
+  pressure_fn(G, p, rR, pR, aR, fR, dfR);
+  ps = p;
+  us = T(0.5) * (uL + uR) + T(0.5) * (fR - fL);
+  return 0;
+}
+
+// the state on the face (x/t = 0) of the Riemann solution; side 0 = left of
+// the contact (u* >= 0), 1 = right
+template <typename T>
+__device__ __forceinline__ void sample_face(const GasT<T> &G, T rL, T uL, T pL, T rR, T uR, T pR,
+                                            T ps, T us, T &r, T &u, T &p, int &side) {
+  if (T(0) <= us) {
+    side = 0;
+    T aL = fsqrt(G.g * pL / rL);
+    if (ps > pL) {
+      T SL = uL - aL * fsqrt(G.shock_a * (ps / pL) + G.shock_b);
+      if (T(0) <= SL) {
+        r = rL; u = uL; p = pL;
+      } else {
+        T q = ps / pL;
+        r = rL * ((q + G.k_gm1_gp1) / (G.k_gm1_gp1 * q + T(1)));
+        u = us; p = ps;
+      }
+    } else {
+      T SHL = uL - aL;
+      if (T(0) <= SHL) {
+        r = rL; u = uL; p = pL;
+      } else {
+        T pr = ps / pL;
+        T STL = us - aL * fpow(pr, G.z);
+        if (T(0) >= STL) {
+          r = rL * fpow(pr, G.inv_g);
+          u = us; p = ps;
+        } else {
+          T c = T(2) / G.gp1 + (G.gm1 / (G.gp1 * aL)) * uL;
+          r = rL * fpow(c, G.two_gm1);
+          u = (T(2) / G.gp1) * (aL + T(0.5) * G.gm1 * uL);
+          p = pL * fpow(c, G.inv_z);
+        }
+      }
+    }
+  } else {
+    side = 1;
+    T aR = fsqrt(G.g * pR / rR);
+    if (ps > pR) {
+      T SR = uR + aR * fsqrt(G.shock_a * (ps / pR) + G.shock_b);
+      if (T(0) >= SR) {
+        r = rR; u = uR; p = pR;
+      } else {
+        T q = ps / pR;
+        r = rR * ((q + G.k_gm1_gp1) / (G.k_gm1_gp1 * q + T(1)));
+        u = us; p = ps;
+      }
+    } else {
+      T SHR = uR + aR;
+      if (T(0) >= SHR) {
+        r = rR; u = uR; p = pR;
+      } else {
+        T pr = ps / pR;
+        T STR = us + aR * fpow(pr, G.z);
+        if (T(0) <= STR) {
+          r = rR * fpow(pr, G.inv_g);
+          u = us; p = ps;
+        } else {
+          T c = T(2) / G.gp1 - (G.gm1 / (G.gp1 * aR)) * uR;
+          r = rR * fpow(c, G.two_gm1);
+          u = (T(2) / G.gp1) * (-aR + T(0.5) * G.gm1 * uR);
+          p = pR * fpow(c, G.inv_z);
+        }
+      }
+    }
+  }
+}
+
+// Godunov flux per unit area through an interior face with unit normal n;
+// the tangential velocity comes from the upwind side of the contact.
+// Returns 0 or the riemann_star error.
+template <typename T>
+__device__ __forceinline__ int godunov_flux(const GasT<T> &G, const T WL[5], const T WR[5],
+                                            const T n[3], T F[5], int &iters) {
+  T unL = (WL[1] * n[0] + WL[2] * n[1]) + WL[3] * n[2];
+  T unR = (WR[1] * n[0] + WR[2] * n[1]) + WR[3] * n[2];
+  T ps, us;
+  int rc = riemann_star(G, WL[0], unL, WL[4], WR[0], unR, WR[4], ps, us, iters);
+  if (rc) return rc;
+  T r0, un0, p0;
+  int side;
+  sample_face(G, WL[0], unL, WL[4], WR[0], unR, WR[4], ps, us, r0, un0, p0, side);
+  const bool left = side == 0;
+  T uns = left ? unL : unR;
+  T V0[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) V0[d] = un0 * n[d] + ((left ? WL[1 + d] : WR[1 + d]) - uns * n[d]);
+  T mass = r0 * un0;
+  T E0 = p0 / G.gm1 + T(0.5) * r0 * ((V0[0] * V0[0] + V0[1] * V0[1]) + V0[2] * V0[2]);
+  F[0] = mass;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) F[1 + d] = mass * V0[d] + p0 * n[d];
+  F[4] = un0 * (E0 + p0);
+  return 0;
+}
+
+// Boundary fluxes: a slip wall solves (rho, u_n, p | rho, -u_n, p), whose
+// contact speed is exactly 0, so only the star pressure crosses it; a
+// transmissive face has identical states on both sides, whose Godunov flux
+// is the physical flux.
+template <typename T>
+__device__ __forceinline__ int boundary_flux(const GasT<T> &G, int bc, const T WL[5], const T n[3],
+                                             T F[5], int &iters) {
+  T un = (WL[1] * n[0] + WL[2] * n[1]) + WL[3] * n[2];
+  if (bc == 1) {
+    T ps, us;
+    int rc = riemann_star(G, WL[0], un, WL[4], WL[0], -un, WL[4], ps, us, iters);
+    if (rc) return rc;
+    F[0] = T(0);
+    F[1] = ps * n[0];
+    F[2] = ps * n[1];
+    F[3] = ps * n[2];
+    F[4] = T(0);
+    return 0;
+  }
+  iters = 0;
+  T r = WL[0], p = WL[4];
+  T E = p / G.gm1 + T(0.5) * r * ((WL[1] * WL[1] + WL[2] * WL[2]) + WL[3] * WL[3]);
+  T mass = r * un;
+  F[0] = mass;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) F[1 + d] = mass * WL[1 + d] + p * n[d];
+  F[4] = un * (E + p);
+  return 0;
+}
+
+}  // namespace fvk

@@ -1,0 +1,416 @@
+"""Thin ctypes binding of ``libfv.so`` (include/fv.h), same entry-point names.
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  Host data are numpy arrays; device buffers are torch CUDA
+tensors (PyTorch supplies device memory and streams, nothing else).  There is
+no CPU fallback: if the library is missing, loading fails with an error.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+FV_OK = 0
+FV_ERR_INVALID_ARG = -1
+FV_ERR_BAD_MESH = -2
+FV_ERR_CUDA = -3
+FV_ERR_NONPHYSICAL = -4
+FV_ERR_RIEMANN = -5
+FV_ERR_TIMEOUT = -6
+FV_ERR_NOMEM = -7
+
+FV_BC_INTERIOR, FV_BC_WALL, FV_BC_TRANSMISSIVE = 0, 1, 2
+FV_FP64, FV_FP32_FLUX = 0, 1
+FV_GUESS_TWO_RAREFACTION, FV_GUESS_MLP = 0, 1
+
+_ERR_NAMES = {
+    FV_ERR_INVALID_ARG: "FV_ERR_INVALID_ARG", FV_ERR_BAD_MESH: "FV_ERR_BAD_MESH",
+    FV_ERR_CUDA: "FV_ERR_CUDA", FV_ERR_NONPHYSICAL: "FV_ERR_NONPHYSICAL",
+    FV_ERR_RIEMANN: "FV_ERR_RIEMANN", FV_ERR_TIMEOUT: "FV_ERR_TIMEOUT",
+    FV_ERR_NOMEM: "FV_ERR_NOMEM",
+}
+
+
+class FvError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        super().__init__(f"{what}: {_ERR_NAMES.get(code, code)}: {fv_last_error()}")
+
+
+class fv_config(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("cfl", C.c_double), ("newton_tol", C.c_double),
+                ("max_levels", C.c_int), ("newton_max_iter", C.c_int), ("precision", C.c_int),
+                ("guess", C.c_int), ("device", C.c_int)]
+
+
+_lib = None
+
+# entry points declared in include/fv.h (checked by the tests)
+EXPORTS = [
+    "fv_config_default", "fv_mesh_load", "fv_mesh_free", "fv_mesh_cells", "fv_mesh_faces",
+    "fv_set_state", "fv_get_state", "fv_assign_levels", "fv_get_levels", "fv_residual_level",
+    "fv_advance_phases", "fv_advance", "fv_get_time", "fv_set_time", "fv_boundary_ledger",
+    "fv_cell_volumes", "fv_status", "fv_last_error", "fv_version", "fv_set_conserved",
+    "fv_work_counters", "fv_use_graph", "fv_profile_enable", "fv_profile_read",
+    "fv_get_level_lists", "fv_get_local_dt",
+]
+
+FV_PROF_LEVELS, FV_PROF_PRIM, FV_PROF_GRAD, FV_PROF_FLUX, FV_PROF_UPDATE = range(5)
+FV_PROF_N = 5
+PROF_NAMES = ["levels", "prim", "grad", "flux", "update"]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libfv.so (built by ``paper_1704_01144_gb300.build.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: run paper_1704_01144_gb300.build.build() "
+                          "(there is no CPU fallback)")
+    L = C.CDLL(path)
+    vp, dp, i64, i8p, i32p = C.c_void_p, C.POINTER(C.c_double), C.c_int64, C.POINTER(C.c_int8), \
+        C.POINTER(C.c_int32)
+    L.fv_config_default.argtypes = [C.POINTER(fv_config)]
+    L.fv_config_default.restype = None
+    L.fv_mesh_load.argtypes = [dp, i64, C.POINTER(C.c_int64), i64, i8p, C.POINTER(fv_config),
+                               C.POINTER(vp)]
+    L.fv_mesh_free.argtypes = [vp]
+    L.fv_mesh_free.restype = None
+    L.fv_mesh_cells.argtypes = [vp]
+    L.fv_mesh_cells.restype = i64
+    L.fv_mesh_faces.argtypes = [vp]
+    L.fv_mesh_faces.restype = i64
+    L.fv_set_state.argtypes = [vp, vp, C.c_int, vp]
+    L.fv_get_state.argtypes = [vp, vp, C.c_int, vp]
+    L.fv_assign_levels.argtypes = [vp, dp, i32p, vp]
+    L.fv_get_levels.argtypes = [vp, i8p]
+    L.fv_residual_level.argtypes = [vp, C.c_int, C.c_int, vp, vp]
+    L.fv_advance_phases.argtypes = [vp, C.c_int, vp]
+    L.fv_advance.argtypes = [vp, C.c_int, dp, vp]
+    L.fv_get_time.argtypes = [vp, dp]
+    L.fv_set_time.argtypes = [vp, C.c_double]
+    L.fv_boundary_ledger.argtypes = [vp, dp]
+    L.fv_cell_volumes.argtypes = [vp, dp]
+    L.fv_status.argtypes = [vp]
+    L.fv_set_conserved.argtypes = [vp, vp, C.c_int, vp]
+    L.fv_work_counters.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                   C.POINTER(C.c_int64)]
+    L.fv_use_graph.argtypes = [vp, C.c_int]
+    L.fv_profile_enable.argtypes = [vp, C.c_int]
+    L.fv_profile_read.argtypes = [vp, dp, C.POINTER(C.c_int64)]
+    L.fv_get_local_dt.argtypes = [vp, dp]
+    L.fv_get_level_lists.argtypes = [vp, C.POINTER(C.c_int64), i32p, i8p, i32p]
+    L.fv_last_error.restype = C.c_char_p
+    L.fv_version.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def _check(rc, what):
+    if rc != FV_OK:
+        raise FvError(rc, what)
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return C.c_void_p(0)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t, dtype_name="float64"):
+    """Device pointer of a contiguous torch CUDA tensor."""
+    if not (hasattr(t, "is_cuda") and t.is_cuda):
+        raise TypeError("expected a torch CUDA tensor")
+    if not t.is_contiguous() or str(t.dtype) != f"torch.{dtype_name}":
+        raise TypeError(f"expected a contiguous {dtype_name} tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+# ---------------------------------------------------------------- entry points
+def fv_config_default(**overrides) -> fv_config:
+    cfg = fv_config()
+    lib().fv_config_default(C.byref(cfg))
+    for k, v in overrides.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+def fv_last_error() -> str:
+    return lib().fv_last_error().decode()
+
+
+def fv_version() -> str:
+    return lib().fv_version().decode()
+
+
+def fv_mesh_load(xyz, tets, face_bc, cfg: fv_config):
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    tets = np.ascontiguousarray(tets, dtype=np.int64)
+    face_bc = np.ascontiguousarray(face_bc, dtype=np.int8)
+    if xyz.ndim != 2 or xyz.shape[1] != 3 or tets.ndim != 2 or tets.shape[1] != 4 \
+            or face_bc.shape != tets.shape:
+        raise ValueError("xyz (n,3), tets (m,4) and face_bc (m,4) expected")
+    h = C.c_void_p()
+    rc = lib().fv_mesh_load(xyz.ctypes.data_as(C.POINTER(C.c_double)), xyz.shape[0],
+                            tets.ctypes.data_as(C.POINTER(C.c_int64)), tets.shape[0],
+                            face_bc.ctypes.data_as(C.POINTER(C.c_int8)), C.byref(cfg), C.byref(h))
+    _check(rc, "fv_mesh_load")
+    return h
+
+
+def fv_mesh_free(h):
+    lib().fv_mesh_free(h)
+
+
+def fv_mesh_cells(h) -> int:
+    return int(lib().fv_mesh_cells(h))
+
+
+def fv_mesh_faces(h) -> int:
+    return int(lib().fv_mesh_faces(h))
+
+
+def fv_set_state(h, prim, stream=None):
+    """prim: numpy (5, n) host array or torch CUDA float64 tensor (5, n)."""
+    if isinstance(prim, np.ndarray):
+        p = np.ascontiguousarray(prim, dtype=np.float64)
+        _check(lib().fv_set_state(h, C.c_void_p(p.ctypes.data), 0, _stream(stream)), "fv_set_state")
+    else:
+        _check(lib().fv_set_state(h, _dptr(prim), 1, _stream(stream)), "fv_set_state")
+
+
+def fv_set_conserved(h, cons, stream=None):
+    """cons: numpy (5, n) host array (pinned torch CPU tensors work too) or a
+    torch CUDA float64 tensor (5, n)."""
+    if isinstance(cons, np.ndarray):
+        c = np.ascontiguousarray(cons, dtype=np.float64)
+        _check(lib().fv_set_conserved(h, C.c_void_p(c.ctypes.data), 0, _stream(stream)),
+               "fv_set_conserved")
+    elif hasattr(cons, "is_cuda") and not cons.is_cuda:
+        _check(lib().fv_set_conserved(h, C.c_void_p(cons.data_ptr()), 0, _stream(stream)),
+               "fv_set_conserved")
+    else:
+        _check(lib().fv_set_conserved(h, _dptr(cons), 1, _stream(stream)), "fv_set_conserved")
+
+
+def fv_work_counters(h):
+    """(cycles, C(tau)-weighted cell updates, face evaluations) since the
+    last state reset."""
+    a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+    _check(lib().fv_work_counters(h, C.byref(a), C.byref(b), C.byref(c)), "fv_work_counters")
+    return a.value, b.value, c.value
+
+
+def fv_use_graph(h, enable):
+    _check(lib().fv_use_graph(h, int(bool(enable))), "fv_use_graph")
+
+
+def fv_profile_enable(h, enable):
+    _check(lib().fv_profile_enable(h, int(bool(enable))), "fv_profile_enable")
+
+
+def fv_profile_read(h):
+    """{class name: (total ms, launches)} of the profiled kernel classes."""
+    ms = (C.c_double * FV_PROF_N)()
+    n = (C.c_int64 * FV_PROF_N)()
+    _check(lib().fv_profile_read(h, ms, n), "fv_profile_read")
+    return {PROF_NAMES[i]: (ms[i], n[i]) for i in range(FV_PROF_N)}
+
+
+def fv_get_state(h, out=None, stream=None):
+    """Conserved state (5, n).  out: None (returns a numpy array), a numpy
+    array, or a torch CUDA float64 tensor (filled asynchronously)."""
+    n = fv_mesh_cells(h)
+    if out is None:
+        out = np.empty((5, n))
+    if isinstance(out, np.ndarray):
+        _check(lib().fv_get_state(h, C.c_void_p(out.ctypes.data), 0, _stream(stream)), "fv_get_state")
+    elif hasattr(out, "is_cuda") and not out.is_cuda:
+        _check(lib().fv_get_state(h, C.c_void_p(out.data_ptr()), 0, _stream(stream)), "fv_get_state")
+    else:
+        _check(lib().fv_get_state(h, _dptr(out), 1, _stream(stream)), "fv_get_state")
+    return out
+
+
+def fv_assign_levels(h, max_levels, stream=None, sync=True):
+    """Returns (dt_min, counts per level) when sync, else (None, None)."""
+    if not sync:
+        _check(lib().fv_assign_levels(h, None, None, _stream(stream)), "fv_assign_levels")
+        return None, None
+    dt = C.c_double()
+    counts = np.zeros(max_levels, dtype=np.int32)
+    _check(lib().fv_assign_levels(h, C.byref(dt), counts.ctypes.data_as(C.POINTER(C.c_int32)),
+                                  _stream(stream)), "fv_assign_levels")
+    return dt.value, counts
+
+
+def fv_get_local_dt(h):
+    out = np.empty(fv_mesh_cells(h))
+    _check(lib().fv_get_local_dt(h, out.ctypes.data_as(C.POINTER(C.c_double))), "fv_get_local_dt")
+    return out
+
+
+def fv_get_levels(h):
+    out = np.empty(fv_mesh_cells(h), dtype=np.int8)
+    _check(lib().fv_get_levels(h, out.ctypes.data_as(C.POINTER(C.c_int8))), "fv_get_levels")
+    return out
+
+
+def fv_get_level_lists(h, max_levels):
+    """(cells sorted by (level, no finer neighbour) in caller's indices,
+    cell bucket offsets [2L+1], face level per library face, face offsets
+    [L+1])."""
+    n, nf = fv_mesh_cells(h), fv_mesh_faces(h)
+    cells = np.empty(n, dtype=np.int64)
+    coff = np.empty(2 * max_levels + 1, dtype=np.int32)
+    flev = np.empty(nf, dtype=np.int8)
+    foff = np.empty(max_levels + 1, dtype=np.int32)
+    _check(lib().fv_get_level_lists(h, cells.ctypes.data_as(C.POINTER(C.c_int64)),
+                                    coff.ctypes.data_as(C.POINTER(C.c_int32)),
+                                    flev.ctypes.data_as(C.POINTER(C.c_int8)),
+                                    foff.ctypes.data_as(C.POINTER(C.c_int32))),
+           "fv_get_level_lists")
+    return cells, coff, flev, foff
+
+
+def fv_residual_level(h, level, stage, R, stream=None):
+    """R: torch CUDA float64 tensor (5, n), filled asynchronously."""
+    _check(lib().fv_residual_level(h, int(level), int(stage), _dptr(R), _stream(stream)),
+           "fv_residual_level")
+    return R
+
+
+def fv_advance_phases(h, n_phases, stream=None):
+    _check(lib().fv_advance_phases(h, int(n_phases), _stream(stream)), "fv_advance_phases")
+
+
+def fv_advance(h, n_cycles, stream=None, want_time=True):
+    if want_time:
+        t = C.c_double()
+        _check(lib().fv_advance(h, int(n_cycles), C.byref(t), _stream(stream)), "fv_advance")
+        return t.value
+    _check(lib().fv_advance(h, int(n_cycles), None, _stream(stream)), "fv_advance")
+    return None
+
+
+def fv_get_time(h) -> float:
+    t = C.c_double()
+    _check(lib().fv_get_time(h, C.byref(t)), "fv_get_time")
+    return t.value
+
+
+def fv_set_time(h, t):
+    _check(lib().fv_set_time(h, float(t)), "fv_set_time")
+
+
+def fv_boundary_ledger(h):
+    out = np.empty(5)
+    _check(lib().fv_boundary_ledger(h, out.ctypes.data_as(C.POINTER(C.c_double))),
+           "fv_boundary_ledger")
+    return out
+
+
+def fv_cell_volumes(h):
+    out = np.empty(fv_mesh_cells(h))
+    _check(lib().fv_cell_volumes(h, out.ctypes.data_as(C.POINTER(C.c_double))), "fv_cell_volumes")
+    return out
+
+
+def fv_status(h) -> int:
+    return int(lib().fv_status(h))
+
+
+# ------------------------------------------------------------ convenience
+class Mesh:
+    """Owns one fv_mesh handle."""
+
+    def __init__(self, mesh, **cfg):
+        self.cfg = fv_config_default(**cfg)
+        self.h = fv_mesh_load(mesh.xyz, mesh.tets, mesh.face_bc, self.cfg)
+        self.n = fv_mesh_cells(self.h)
+        self.nf = fv_mesh_faces(self.h)
+        self.L = self.cfg.max_levels
+
+    def close(self):
+        if getattr(self, "h", None):
+            fv_mesh_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, prim, stream=None):
+        fv_set_state(self.h, prim, stream)
+
+    def set_conserved(self, cons, stream=None):
+        fv_set_conserved(self.h, cons, stream)
+
+    def work_counters(self):
+        return fv_work_counters(self.h)
+
+    def use_graph(self, enable):
+        fv_use_graph(self.h, enable)
+
+    def profile_enable(self, enable):
+        fv_profile_enable(self.h, enable)
+
+    def profile_read(self):
+        return fv_profile_read(self.h)
+
+    def get_state(self, out=None, stream=None):
+        return fv_get_state(self.h, out, stream)
+
+    def assign_levels(self, stream=None, sync=True):
+        return fv_assign_levels(self.h, self.L, stream, sync)
+
+    def local_dt(self):
+        return fv_get_local_dt(self.h)
+
+    def levels(self):
+        return fv_get_levels(self.h)
+
+    def level_lists(self):
+        return fv_get_level_lists(self.h, self.L)
+
+    def residual_level(self, level, stage, R, stream=None):
+        return fv_residual_level(self.h, level, stage, R, stream)
+
+    def advance_phases(self, n, stream=None):
+        fv_advance_phases(self.h, n, stream)
+
+    def advance(self, n_cycles=1, stream=None, want_time=True):
+        return fv_advance(self.h, n_cycles, stream, want_time)
+
+    @property
+    def t(self):
+        return fv_get_time(self.h)
+
+    def boundary_ledger(self):
+        return fv_boundary_ledger(self.h)
+
+    def volumes(self):
+        return fv_cell_volumes(self.h)
+
+    def status(self):
+        return fv_status(self.h)

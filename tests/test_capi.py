@@ -1,0 +1,64 @@
+"""The C-ABI library builds, loads and exports every symbol include/fv.h
+declares (no GPU calls)."""
+import os
+import re
+import subprocess
+
+import pytest
+
+from conftest import ROOT
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "fv.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fv_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def libfv():
+    from paper_1704_01144_gb300 import build, fv
+    build.build()
+    return fv.lib()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("fv_mesh_load", "fv_assign_levels", "fv_residual_level", "fv_advance"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libfv):
+    from paper_1704_01144_gb300 import fv
+    out = subprocess.run(["nm", "-D", "--defined-only", fv.library_path()], capture_output=True,
+                         text=True, check=True).stdout
+    exported = {ln.split()[-1] for ln in out.splitlines() if ln.split() and ln.split()[-2] == "T"}
+    missing = [n for n in _declared() if n not in exported]
+    assert not missing, missing
+    for n in _declared():
+        getattr(libfv, n)
+    assert sorted(fv.EXPORTS) == sorted(n for n in _declared() if n in fv.EXPORTS)
+
+
+def test_version_and_defaults(libfv):
+    from paper_1704_01144_gb300 import fv
+    assert "sm_103a" in fv.fv_version()
+    cfg = fv.fv_config_default()
+    assert cfg.gamma == 1.4 and cfg.cfl == 0.5 and cfg.newton_tol == 1e-10
+    assert cfg.newton_max_iter == 50 and cfg.max_levels == 1
+
+
+def test_library_is_built_for_sm_103a_only(libfv):
+    from paper_1704_01144_gb300 import build
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_null_handle_is_rejected_without_gpu(libfv):
+    from paper_1704_01144_gb300 import fv
+    import ctypes as C
+    assert libfv.fv_status(None) == fv.FV_ERR_INVALID_ARG
+    assert libfv.fv_advance(None, 1, None, None) == fv.FV_ERR_INVALID_ARG
+    assert "fv_advance" in fv.fv_last_error()
+    out = C.c_void_p(1)
+    assert libfv.fv_mesh_load(None, 0, None, 0, None, None, C.byref(out)) == fv.FV_ERR_INVALID_ARG
+    assert out.value is None

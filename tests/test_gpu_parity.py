@@ -1,0 +1,288 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Bar: levels and dt_min bit-exact; FP64 results within 1e-12 relative L-inf
+(per component, normalised by the oracle field's max magnitude); the
+FP32-flux mode within the tolerance stated in its test.
+"""
+import numpy as np
+import pytest
+
+from paper_1704_01144_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP64 = 1e-12
+
+
+def rel_linf(a, b):
+    """max_c max_i |a_ci - b_ci| / max_i |b_ci| (components of scale 0 are
+    measured against the largest component scale)."""
+    a = np.asarray(a)
+    b = np.asarray(b)
+    scale = np.abs(b).max(axis=1)
+    floor = max(scale.max(), 1e-300) * 1e-3
+    scale = np.maximum(scale, floor)
+    return float((np.abs(a - b).max(axis=1) / scale).max())
+
+
+@pytest.fixture(scope="module")
+def fvmod():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1704_01144_gb300 import build, fv
+    build.build()
+    fv.lib()
+    return fv
+
+
+@pytest.fixture(scope="module")
+def orc():
+    from oracle import oracle as O
+    O.lib()
+    return O
+
+
+def residual_scale(o, L):
+    """Per-component scale of the residual field over every level at the
+    cycle start (levels in quiescent flow have residuals of pure round-off,
+    so each level is measured against the whole field)."""
+    sc = np.zeros(5)
+    for k in range(L):
+        sc = np.maximum(sc, np.abs(o.residual_level(k, 1)).max(axis=1))
+    return np.maximum(sc, sc.max() * 1e-3)
+
+
+def rel_err_scaled(a, b, scale):
+    return float((np.abs(np.asarray(a) - np.asarray(b)).max(axis=1) / scale).max())
+
+
+def pair(fvmod, orc, mesh, prim, L, **cfg):
+    g = fvmod.Mesh(mesh, max_levels=L, **cfg)
+    g.set_state(prim)
+    o = orc.Oracle(mesh, max_levels=L)
+    o.set_prim(prim)
+    return g, o
+
+
+def test_initial_state_roundtrip(fvmod, orc):
+    mesh, prim = I.blast_case(n=9, ratio=8.0)
+    g, o = pair(fvmod, orc, mesh, prim, 4)
+    assert np.array_equal(g.get_state(), o.get_cons())
+    vol, _ = o.cell_geometry()
+    assert np.array_equal(g.volumes(), vol)
+
+
+@pytest.mark.parametrize("n,L", [(9, 4), (11, 5), (7, 1)])
+def test_levels_and_dtmin_bit_exact(fvmod, orc, n, L):
+    mesh, prim = I.blast_case(n=n, ratio=8.0)
+    g, o = pair(fvmod, orc, mesh, prim, L)
+    dg, cg = g.assign_levels()
+    do, lo, co = o.assign_levels()
+    assert dg == do
+    np.testing.assert_array_equal(cg, co)
+    np.testing.assert_array_equal(g.levels(), lo)
+    dt = g.local_dt()
+    assert dt.min() == dg
+    # before smoothing every cell sits at the largest k with 2^k dt_min <= dt_i;
+    # smoothing only lowers levels
+    k0 = np.minimum(np.floor(np.log2(dt / dg)), L - 1)
+    assert np.all(lo <= k0 + 1e-9)
+
+
+@pytest.mark.parametrize("L", [1, 3, 4])
+def test_residual_stage1_per_level(fvmod, orc, L):
+    import torch
+    mesh, prim = I.blast_case(n=10, ratio=8.0)
+    g, o = pair(fvmod, orc, mesh, prim, L)
+    g.assign_levels()
+    _, lev, counts = o.assign_levels()
+    R = torch.empty((5, g.n), dtype=torch.float64, device="cuda")
+    scale = residual_scale(o, L)
+    for k in range(L):
+        if counts[k] == 0:
+            continue
+        g.residual_level(k, 1, R)
+        torch.cuda.synchronize()
+        Ro = o.residual_level(k, 1)
+        Rg = R.cpu().numpy()
+        assert np.all(Rg[:, lev != k] == 0)
+        assert rel_err_scaled(Rg[:, lev == k], Ro[:, lev == k], scale) <= TOL_FP64
+
+
+def test_phase_by_phase_matches_oracle(fvmod, orc):
+    """Pause after every phase of a 4-level cycle (the paper's pause/resume
+    non-regression idea) and compare the state; at pause points where a
+    level's corrector comes next, compare its stage-2 residual too."""
+    import torch
+    from paper_1704_01144_gb300 import schedule as S
+    mesh, prim = I.blast_case(n=9, ratio=8.0)
+    L = 4
+    g, o = pair(fvmod, orc, mesh, prim, L)
+    g.assign_levels()
+    _, lev, counts = o.assign_levels()
+    R = torch.empty((5, g.n), dtype=torch.float64, device="cuda")
+    scale = residual_scale(o, L)
+    phases = S.phases(L - 1)
+    for idx, (kind, level, T) in enumerate(phases):
+        if kind == "E" and counts[level] > 0:
+            g.residual_level(level, 2, R)
+            torch.cuda.synchronize()
+            Ro = o.residual_level(level, 2)
+            assert rel_err_scaled(R.cpu().numpy()[:, lev == level], Ro[:, lev == level],
+                                  scale) <= TOL_FP64, idx
+        g.advance_phases(1)
+        o.run_phases(1)
+        assert rel_linf(g.get_state(), o.get_cons()) <= TOL_FP64, (idx, kind, level)
+    assert g.status() == 0
+
+
+def test_sod_100_steps(fvmod, orc):
+    """Config 1: Sod tube on 6,144 tets, single level, CFL 0.5, 100 steps."""
+    mesh, prim = I.sod_case()
+    g, o = pair(fvmod, orc, mesh, prim, 1)
+    tg = g.advance(100)
+    to = o.advance(100)
+    assert abs(tg - to) <= 1e-13 * to
+    assert rel_linf(g.get_state(), o.get_cons()) <= TOL_FP64
+    assert g.status() == 0
+
+
+@pytest.mark.parametrize("L", [2, 4])
+def test_blast_cycles(fvmod, orc, L):
+    mesh, prim = I.blast_case(n=12, ratio=8.0)
+    g, o = pair(fvmod, orc, mesh, prim, L)
+    for c in range(3):
+        g.advance(1)
+        o.advance(1)
+        np.testing.assert_array_equal(g.levels(), o.levels())
+        assert rel_linf(g.get_state(), o.get_cons()) <= TOL_FP64, c
+    assert g.status() == 0
+
+
+def test_conservation_ledger_gpu(fvmod):
+    mesh, prim = I.blast_case(n=12, ratio=8.0)
+    g = fvmod.Mesh(mesh, max_levels=4)
+    g.set_state(prim)
+    vol = g.volumes()
+    M0 = (g.get_state() * vol).sum(axis=1)
+    g.advance(4)
+    U = g.get_state()
+    M1 = (U * vol).sum(axis=1)
+    led = g.boundary_ledger()
+    scale = np.abs(U * vol).sum(axis=1).max()
+    assert np.abs(M1 - M0 + led).max() <= 1e-14 * scale
+    assert led[0] == 0.0 and led[4] == 0.0
+
+
+def test_free_stream_gpu(fvmod):
+    mesh, prim = I.uniform_flow_case(n=8)
+    g = fvmod.Mesh(mesh, max_levels=3)
+    g.set_state(prim)
+    U0 = g.get_state()
+    g.advance(3)
+    U = g.get_state()
+    assert (np.abs(U - U0).max(axis=1) / np.abs(U0).max(axis=1)).max() <= 1e-13
+
+
+def test_determinism_bitwise(fvmod):
+    mesh, prim = I.blast_case(n=12, ratio=8.0)
+    out = []
+    for _ in range(2):
+        g = fvmod.Mesh(mesh, max_levels=4)
+        g.set_state(prim)
+        g.advance(3)
+        out.append(g.get_state())
+        g.close()
+    assert np.array_equal(out[0], out[1])
+
+
+def test_level_lists_are_stable_sorted_permutations(fvmod, orc):
+    """The level-compacted lists: a permutation of the cells sorted by
+    (level, no finer neighbour), stable in the library's Morton order, with
+    bucket offsets matching the level counts; face levels are min(k_L, k_R)
+    and the face offsets count them."""
+    mesh, prim = I.blast_case(n=11, ratio=8.0)
+    L = 4
+    g, o = pair(fvmod, orc, mesh, prim, L)
+    g.assign_levels()
+    _, lev, counts = o.assign_levels()
+    cells, coff, flev, foff = g.level_lists()
+    assert np.array_equal(np.sort(cells), np.arange(g.n))
+    own, nb, *_ = o.face_data()
+    finer = np.zeros(g.n, bool)
+    m = nb >= 0
+    a, b = own[m], nb[m]
+    finer[a[lev[b] < lev[a]]] = True
+    finer[b[lev[a] < lev[b]]] = True
+    key = 2 * lev.astype(int) + (~finer).astype(int)
+    for bkt in range(2 * L):
+        assert np.all(key[cells[coff[bkt]:coff[bkt + 1]]] == bkt)
+    for k in range(L):
+        assert coff[2 * k + 2] - coff[2 * k] == counts[k]
+    flev_o = np.where(m, np.minimum(lev[own], lev[np.maximum(nb, 0)]), lev[own])
+    assert np.array_equal(np.bincount(flev, minlength=L), np.bincount(flev_o, minlength=L))
+    assert np.array_equal(np.diff(foff), np.bincount(flev, minlength=L))
+
+
+def test_ragged_sizes_and_tiny_mesh(fvmod, orc):
+    """Meshes whose cell and face counts are not multiples of any tile (a
+    single cube: 6 tets) still match."""
+    for shape in ((1, 1, 1), (3, 2, 1), (5, 3, 2)):
+        rng = np.random.default_rng(sum(shape))
+        xs = [I.graded_coords(s, 2.0) for s in shape]
+        mesh = I.box_tet_mesh(*xs, jitter=0.1, rng=rng)
+        c = mesh.centroids()
+        prim = np.empty((5, mesh.n_tets))
+        prim[0] = 1.0 + 0.1 * c[:, 0]
+        prim[1:4] = 0.05
+        prim[4] = 1.0 + 0.5 * (c[:, 1] < 0.5)
+        g, o = pair(fvmod, orc, mesh, prim, 2)
+        g.advance(2)
+        o.advance(2)
+        assert rel_linf(g.get_state(), o.get_cons()) <= TOL_FP64, shape
+
+
+def test_bad_mesh_rejected(fvmod):
+    mesh, _ = I.sod_case(nx=4, ny=2, nz=2)
+    bad = mesh.tets.copy()
+    bad[3, [1, 2]] = bad[3, [2, 1]]
+    with pytest.raises(fvmod.FvError) as e:
+        fvmod.fv_mesh_load(mesh.xyz, bad, mesh.face_bc, fvmod.fv_config_default())
+    assert e.value.code == fvmod.FV_ERR_BAD_MESH
+    bc = mesh.face_bc.copy()
+    bc[bc > 0] = 0                           # open boundary without a tag
+    with pytest.raises(fvmod.FvError) as e:
+        fvmod.fv_mesh_load(mesh.xyz, mesh.tets, bc, fvmod.fv_config_default())
+    assert e.value.code == fvmod.FV_ERR_BAD_MESH
+
+
+def test_nonphysical_state_reported(fvmod):
+    """A negative pressure planted in the host input is reported as a sticky
+    status (no GPU fault)."""
+    mesh, prim = I.blast_case(n=5)
+    g = fvmod.Mesh(mesh, max_levels=2)
+    bad = prim.copy()
+    bad[4, 7] = -1.0
+    g.set_state(bad)
+    assert g.status() == fvmod.FV_ERR_NONPHYSICAL
+    g.set_state(prim)
+    assert g.status() == 0
+
+
+def test_calls_out_of_order_rejected(fvmod):
+    import torch
+    mesh, prim = I.blast_case(n=5)
+    g = fvmod.Mesh(mesh, max_levels=3)
+    g.set_state(prim)
+    R = torch.empty((5, g.n), dtype=torch.float64, device="cuda")
+    with pytest.raises(fvmod.FvError):
+        g.residual_level(0, 1, R)            # no cycle yet
+    with pytest.raises(fvmod.FvError):
+        g.advance_phases(1)
+    g.assign_levels()
+    with pytest.raises(fvmod.FvError):
+        g.residual_level(1, 2, R)            # level 1 has not begun
+    g.advance_phases(1)
+    with pytest.raises(fvmod.FvError):
+        g.assign_levels()                    # a cycle is in progress
