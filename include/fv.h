@@ -245,6 +245,38 @@ int fv_use_graph(fv_mesh *m, int enable);
 int fv_profile_enable(fv_mesh *m, int enable);
 int fv_profile_read(fv_mesh *m, double ms_out[FV_PROF_N], int64_t launches_out[FV_PROF_N]);
 
+/* Largest n_cells fv_assign_levels_noalloc accepts (its static scratch). */
+#define FV_NOALLOC_MAX_CELLS (1 << 22)
+
+/*
+ * Level assignment that allocates nothing, for callers that cannot call
+ * cudaMalloc when they need it: a host application that gives the library
+ * only memory from its own fixed-budget pool, or a time loop being recorded
+ * into a CUDA graph, where an allocation would synchronise the device or
+ * break the capture.  The paper has no counterpart of this entry point.
+ *
+ * Same result as the level part of fv_assign_levels, on caller-owned device
+ * arrays: dt_min = min_i dt_dev[i]; k_i = max{k <= max_levels-1 :
+ * 2^k dt_min <= dt_i}; then max_levels-1 sweeps of
+ * k_i <- min(k_i, 1 + min_j k_nbr(i,j)).  Inputs: dt_dev[n_cells] positive
+ * finite local time steps; nbr_dev[4*n_cells] with nbr_dev[j*n_cells + i]
+ * the neighbour of cell i across its face j (any negative value: boundary).
+ * Outputs: levels_dev[n_cells] and *dt_min_dev.  All four pointers are
+ * device memory owned by the caller.  Asynchronous on `stream`.
+ *
+ * Scratch: one static device array of 256 + FV_NOALLOC_MAX_CELLS bytes that
+ * every GPU which loads this library holds until the process exits.  The
+ * first call on a device looks up that array's device address (with the
+ * device current), so make it before any stream capture.  All calls share
+ * the array and each re-initialises what it uses; calls that overlap on the
+ * GPU (other streams or threads on the same device) race on it.
+ * Errors: FV_ERR_INVALID_ARG for a NULL pointer, n_cells outside
+ * [1, FV_NOALLOC_MAX_CELLS] or max_levels outside [1, 8]; FV_ERR_CUDA.
+ */
+int fv_assign_levels_noalloc(const double *dt_dev, const int32_t *nbr_dev, int64_t n_cells,
+                             int max_levels, int8_t *levels_dev, double *dt_min_dev,
+                             void *stream);
+
 /* Message of the calling thread's last failed call ("" if none). */
 const char *fv_last_error(void);
 

@@ -68,6 +68,8 @@ std::vector<Phase> make_phases(int theta) {
 
 }  // namespace
 
+void fv_internal_set_error(const std::string &msg) { t_err = msg; }
+
 struct fv_mesh {
   fv_config cfg;
   DevMesh d;

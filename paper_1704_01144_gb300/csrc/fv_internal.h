@@ -86,6 +86,9 @@ struct HostMesh {
 int fv_host_build(const double *xyz, int64_t n_nodes, const int64_t *tets, int64_t n_tets,
                   const int8_t *face_bc, HostMesh &out, std::string *err);
 
+// sets the message fv_last_error() returns to the calling thread
+void fv_internal_set_error(const std::string &msg);
+
 // Optional per-kernel-class timing: events recorded on the launching stream
 // around each launch when a hook is active.
 struct ProfHook {

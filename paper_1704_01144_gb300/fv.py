@@ -56,8 +56,10 @@ EXPORTS = [
     "fv_advance_phases", "fv_advance", "fv_get_time", "fv_set_time", "fv_boundary_ledger",
     "fv_cell_volumes", "fv_status", "fv_last_error", "fv_version", "fv_set_conserved",
     "fv_work_counters", "fv_use_graph", "fv_profile_enable", "fv_profile_read",
-    "fv_get_level_lists", "fv_get_local_dt",
+    "fv_get_level_lists", "fv_get_local_dt", "fv_assign_levels_noalloc",
 ]
+
+FV_NOALLOC_MAX_CELLS = 1 << 22
 
 FV_PROF_LEVELS, FV_PROF_PRIM, FV_PROF_GRAD, FV_PROF_FLUX, FV_PROF_UPDATE = range(5)
 FV_PROF_N = 5
@@ -109,6 +111,7 @@ def lib():
     L.fv_profile_enable.argtypes = [vp, C.c_int]
     L.fv_profile_read.argtypes = [vp, dp, C.POINTER(C.c_int64)]
     L.fv_get_local_dt.argtypes = [vp, dp]
+    L.fv_assign_levels_noalloc.argtypes = [vp, vp, i64, C.c_int, vp, vp, vp]
     L.fv_get_level_lists.argtypes = [vp, C.POINTER(C.c_int64), i32p, i8p, i32p]
     L.fv_last_error.restype = C.c_char_p
     L.fv_version.restype = C.c_char_p
@@ -266,6 +269,16 @@ def fv_get_local_dt(h):
     out = np.empty(fv_mesh_cells(h))
     _check(lib().fv_get_local_dt(h, out.ctypes.data_as(C.POINTER(C.c_double))), "fv_get_local_dt")
     return out
+
+
+def fv_assign_levels_noalloc(dt, nbr, max_levels, levels_out, dt_min_out, stream=None):
+    """Allocation-free level assignment on caller-owned torch CUDA tensors:
+    dt (n,) float64, nbr (4, n) int32, levels_out (n,) int8, dt_min_out (1,)
+    float64.  Asynchronous on `stream`."""
+    n = int(dt.shape[0])
+    _check(lib().fv_assign_levels_noalloc(_dptr(dt), _dptr(nbr, "int32"), n, int(max_levels),
+                                          _dptr(levels_out, "int8"), _dptr(dt_min_out),
+                                          _stream(stream)), "fv_assign_levels_noalloc")
 
 
 def fv_get_levels(h):
