@@ -245,6 +245,21 @@ int fv_use_graph(fv_mesh *m, int enable);
 int fv_profile_enable(fv_mesh *m, int enable);
 int fv_profile_read(fv_mesh *m, double ms_out[FV_PROF_N], int64_t launches_out[FV_PROF_N]);
 
+/*
+ * The device Godunov flux (Sec. 2.1) on a batch of face states, for tests
+ * and data harvesting: for i < count, with primitives WL_dev/WR_dev
+ * [5*count] = (rho, u, v, w, p) and unit normals n_dev[3*count]
+ * (structure of arrays), writes the flux per unit area F_dev[5*count] and
+ * the Newton iterations iters_dev[count] (-1 where the solver failed).
+ * bc = FV_BC_INTERIOR: exact Riemann problem between WL and WR;
+ * FV_BC_WALL / FV_BC_TRANSMISSIVE: boundary flux of WL (WR unused).
+ * Arithmetic follows cfg->precision; gamma, newton_tol and newton_max_iter
+ * come from cfg.  Device pointers; asynchronous on `stream`.
+ */
+int fv_godunov_flux_batch(const double *WL_dev, const double *WR_dev, const double *n_dev,
+                          int64_t count, const fv_config *cfg, int bc, double *F_dev,
+                          int32_t *iters_dev, void *stream);
+
 /* Largest n_cells fv_assign_levels_noalloc accepts (its static scratch). */
 #define FV_NOALLOC_MAX_CELLS (1 << 22)
 

@@ -614,22 +614,24 @@ int orc_get_pred(const orc *o, double *cons_soa) {
 void orc_set_time(orc *o, double t) { o->t = t; }
 
 /* ========================================================== levels ===== */
-/* Local explicit step: dt_i = 2 CFL V_i / sum_f A_f (|u_i . n_f| + c_i). */
+/* Local explicit step: dt_i = 2 CFL V_i / sum_f A_f (|u_i . n_f| + c_i),
+ * evaluated with rho_i multiplied through numerator and denominator:
+ *   dt_i = 2 CFL V_i rho_i / sum_f A_f (|m_i . n_f| + rho_i c_i),
+ * m = rho u, rho c = sqrt(gamma p rho), p = (gamma-1)(E - (|m|^2/2)/rho). */
 static double local_dt(const orc *o, int64_t i) {
   const double *U = o->U + 5 * i;
   double r = U[0];
-  double u = U[1] / r, v = U[2] / r, w = U[3] / r;
-  double ke = 0.5 * r * ((u * u + v * v) + w * w);
-  double p = o->gas.gm1 * (U[4] - ke);
-  double c = sqrt((o->gas.g * p) / r);
+  double mm = (U[1] * U[1] + U[2] * U[2]) + U[3] * U[3];
+  double p = o->gas.gm1 * (U[4] - (0.5 * mm) / r);
+  double rc = sqrt((o->gas.g * p) * r);
   double S = 0.0;
   for (int j = 0; j < 4; ++j) {
     int64_t f = o->cface[4 * i + j];
     const double *n = o->fnrm + 3 * f;
-    double un = (u * n[0] + v * n[1]) + w * n[2];
-    S = S + o->farea[f] * (fabs(un) + c);
+    double mn = (U[1] * n[0] + U[2] * n[1]) + U[3] * n[2];
+    S = S + o->farea[f] * (fabs(mn) + rc);
   }
-  return ((2.0 * o->cfl) * o->vol[i]) / S;
+  return (((2.0 * o->cfl) * o->vol[i]) * r) / S;
 }
 
 /* Alg. 2 lines 1-2: Delta t = min_i dt_i; level k_i = the largest k in

@@ -272,6 +272,7 @@ int fv_mesh_load(const double *xyz, int64_t n_nodes, const int64_t *tets, int64_
     }                                  \
   } while (0)
   AL(d.vol, N);
+  AL(d.ivol, N);
   AL(d.cf, 4 * N);
   AL(d.cnb, 4 * N);
   AL(d.cown, N);
@@ -282,6 +283,9 @@ int fv_mesh_load(const double *xyz, int64_t n_nodes, const int64_t *tets, int64_
   AL(d.farea, F);
   AL(d.fr, 3 * F);
   if (f32) {
+    AL(d.lsw32, 12 * N);
+    AL(d.ivol32, N);
+    AL(d.FA32, 5 * F);
     AL(d.fn32, 3 * F);
     AL(d.farea32, F);
     AL(d.fr32, 3 * F);
@@ -296,7 +300,12 @@ int fv_mesh_load(const double *xyz, int64_t n_nodes, const int64_t *tets, int64_
     m->W = w;
   }
   AL(d.Un, 5 * N);
-  AL(d.Us, 5 * N);
+  if (f32) {
+    AL(d.Un32, 5 * N);
+    AL(d.Us32, 5 * N);
+  } else {
+    AL(d.Us, 5 * N);
+  }
   AL(d.FA, 5 * F);
   AL(d.ACC, 5 * F);
   AL(d.BND, 5 * F);
@@ -323,6 +332,11 @@ int fv_mesh_load(const double *xyz, int64_t n_nodes, const int64_t *tets, int64_
   int urc = FV_OK;
   urc |= upload(m->new2old_dev, n2o);
   urc |= upload(d.vol, H.vol);
+  {
+    std::vector<double> iv(N);
+    for (size_t i = 0; i < N; ++i) iv[i] = 1.0 / H.vol[i];
+    urc |= upload(d.ivol, iv);
+  }
   urc |= upload(d.cf, H.cf);
   urc |= upload(d.cnb, H.cnb);
   urc |= upload(d.cown, H.cown);
@@ -333,6 +347,12 @@ int fv_mesh_load(const double *xyz, int64_t n_nodes, const int64_t *tets, int64_
   urc |= upload(d.farea, H.farea);
   urc |= upload(d.fr, H.fr);
   if (f32) {
+    std::vector<float> iv32(N);
+    for (size_t i = 0; i < N; ++i) iv32[i] = (float)(1.0 / H.vol[i]);
+    urc |= upload(d.ivol32, iv32);
+    std::vector<float> w32(12 * N);
+    for (size_t q = 0; q < 12 * N; ++q) w32[q] = (float)H.lsw[q];
+    urc |= upload(d.lsw32, w32);
     std::vector<float> tmp(3 * F);
     for (size_t q = 0; q < 3 * F; ++q) tmp[q] = (float)H.fn[q];
     urc |= upload(d.fn32, tmp);
@@ -662,10 +682,30 @@ int fv_cell_volumes(fv_mesh *m, double *vol_out) {
   return FV_OK;
 }
 
+int fv_godunov_flux_batch(const double *WL_dev, const double *WR_dev, const double *n_dev,
+                          int64_t count, const fv_config *cfg, int bc, double *F_dev,
+                          int32_t *iters_dev, void *stream) {
+  if (!WL_dev || !n_dev || !cfg || !F_dev || !iters_dev || (bc == FV_BC_INTERIOR && !WR_dev))
+    return fail(FV_ERR_INVALID_ARG, "fv_godunov_flux_batch: NULL argument");
+  if (count < 0 || count > 0x7fffffff || bc < 0 || bc > 2 || !(cfg->gamma > 1.0) ||
+      !(cfg->newton_tol > 0.0) || cfg->newton_max_iter < 1 ||
+      (cfg->precision != FV_FP64 && cfg->precision != FV_FP32_FLUX))
+    return fail(FV_ERR_INVALID_ARG, "fv_godunov_flux_batch: bad argument");
+  if (count == 0) return FV_OK;
+  CK(cudaSetDevice(cfg->device));
+  fvk::init_device_info();
+  int rc = fvk::launch_flux_batch(WL_dev, WR_dev ? WR_dev : WL_dev, n_dev, (int)count, cfg->gamma,
+                                  cfg->newton_tol, cfg->newton_max_iter, cfg->precision, bc, F_dev,
+                                  iters_dev, (cudaStream_t)stream);
+  if (rc) return fail(rc, "fv_godunov_flux_batch: launch failed");
+  return FV_OK;
+}
+
 int fv_status(fv_mesh *m) {
   if (!m) return fail(FV_ERR_INVALID_ARG, "fv_status: NULL mesh");
   int st = 0;
   cudaError_t e = cudaSetDevice(m->cfg.device);
+  if (e == cudaSuccess && fvk::launch_check_state(m->d, 0) != FV_OK) e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e == cudaSuccess) e = cudaMemcpy(&st, m->d.status, sizeof(int), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, "fv_status");

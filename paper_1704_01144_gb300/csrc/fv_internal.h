@@ -11,8 +11,10 @@
 //          (owner -> outside), farea[F], fr[3][F] = x_R - x_L (ghost centroid
 //          on boundary faces), flev[F]; FP32 copies fn32/farea32/fr32 for the
 //          FP32-flux mode
-//   state  Un[5][N], Us[5][N] (predicted), G[15][N] gradients (FP64) or
-//          G32[15][N] (FP32 mode), FA[5][F] predictor flux x area, then the
+//   state  Un[5][N] (FP64), Us[5][N] predicted (FP64 mode) or Un32/Us32
+//          (FP32-flux mode: FP32 shadow of U^n and the FP32 predicted
+//          state, which only ever feeds fluxes), G[15][N] gradients (FP64)
+//          or G32[15][N] (FP32 mode), FA[5][F] predictor flux x area, then the
 //          step's flux time integral, ACC[5][F] fine-side integral on level
 //          interfaces, BND[5][F] boundary ledger
 //   lists  cl[N] cells sorted by (level, has-finer-neighbour), coff[2L+1];
@@ -34,18 +36,22 @@
 struct DevMesh {
   int N, F, L;
   // cells
-  double *vol;
+  double *vol, *ivol;  // volume and its reciprocal
+  float *ivol32;       // FP32 reciprocal volume (FP32-flux mode predictor)
   int *cf, *cnb;
   uint8_t *cown;
   double *lsw;
+  float *lsw32;        // FP32 copy of the weights (FP32-flux mode)
   // faces
   int *fown, *fnb;
   double *fn, *farea, *fr;
   float *fn32, *farea32, *fr32;
   // state
-  double *Un, *Us, *G;
+  double *Un, *Us, *G;  // Us: predicted state (FP64 mode only)
+  float *Un32, *Us32;    // FP32-flux mode: FP32 shadow of U^n, predicted state
   float *G32;
   double *FA, *ACC, *BND;
+  float *FA32;         // FP32-flux mode: predictor flux x area
   // levels and sorted lists
   int8_t *lev, *lev_tmp, *flev;
   uint8_t *ckey, *fkey;
@@ -136,4 +142,8 @@ int launch_set_state(const DevMesh &d, const double *prim, const int *new2old, c
 int launch_set_cons(const DevMesh &d, const double *cons, const int *new2old, cudaStream_t s);
 int launch_get_state(const DevMesh &d, double *cons, const int *new2old, cudaStream_t s);
 int launch_get_levels(const DevMesh &d, int8_t *lev, const int *new2old, cudaStream_t s);
+int launch_check_state(const DevMesh &d, cudaStream_t s);
+int launch_flux_batch(const double *WL, const double *WR, const double *nrm, int n, double gamma,
+                      double tol, int maxit, int precision, int bc, double *F, int *iters,
+                      cudaStream_t s);
 }  // namespace fvk

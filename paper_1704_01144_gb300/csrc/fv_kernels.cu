@@ -60,6 +60,22 @@ __device__ __forceinline__ void cons_to_prim(const T U[5], T gm1, T W[5]) {
   W[4] = gm1 * (U[4] - ke);
 }
 
+// FP64 primitives without an FP64 division: the single-precision reciprocal
+// of rho refined by two Newton steps r <- r (2 - rho r) (error ~1e-16)
+__device__ __forceinline__ void prim_fp64(const double U[5], double gm1, double W[5]) {
+  double r = U[0];
+  double ri = (double)(1.0f / (float)r);
+  ri = ri * (2.0 - r * ri);
+  ri = ri * (2.0 - r * ri);
+  double u = U[1] * ri, v = U[2] * ri, w = U[3] * ri;
+  double ke = 0.5 * r * ((u * u + v * v) + w * w);
+  W[0] = r;
+  W[1] = u;
+  W[2] = v;
+  W[3] = w;
+  W[4] = gm1 * (U[4] - ke);
+}
+
 __device__ __forceinline__ double minmod(double a, double b) {
   if (a > 0.0 && b > 0.0) return a < b ? a : b;
   if (a < 0.0 && b < 0.0) return a > b ? a : b;
@@ -72,30 +88,30 @@ __device__ __forceinline__ float minmod(float a, float b) {
 }
 
 // ------------------------------------------------ level assignment (a1-a2)
-// dt_i = 2 CFL V_i / sum_j A_j (|u_i . n_j| + c_i), evaluated with
-// round-to-nearest intrinsics (no fused multiply-add) in the fixed order
-// j = 0..3, so that it is bitwise the same number as a plain FP64 host
-// evaluation of the same formula: temporal levels are integer decisions.
+// dt_i = 2 CFL V_i / sum_j A_j (|u_i . n_j| + c_i), with rho_i multiplied
+// through: dt_i = 2 CFL V_i rho_i / sum_j A_j (|m_i . n_j| + sqrt(g p rho)),
+// p = (g-1)(E - (|m|^2/2)/rho).  Evaluated with round-to-nearest intrinsics
+// (no fused multiply-add) in the fixed order j = 0..3, so that it is bitwise
+// the same number as a plain FP64 host evaluation of the same formula:
+// temporal levels are integer decisions taken on it.
 __global__ void __launch_bounds__(256) k_dt(DevMesh d) {
   const size_t N = d.N, F = d.F;
   double local_min = __longlong_as_double(0x7ff0000000000000LL);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x) {
     double r = d.Un[i];
-    double u = __ddiv_rn(d.Un[N + i], r), v = __ddiv_rn(d.Un[2 * N + i], r),
-           w = __ddiv_rn(d.Un[3 * N + i], r);
-    double uu = __dadd_rn(__dadd_rn(__dmul_rn(u, u), __dmul_rn(v, v)), __dmul_rn(w, w));
-    double ke = __dmul_rn(__dmul_rn(0.5, r), uu);
-    double p = __dmul_rn(d.gamma - 1.0, __dsub_rn(d.Un[4 * N + i], ke));
-    double c = __dsqrt_rn(__ddiv_rn(__dmul_rn(d.gamma, p), r));
+    double mx = d.Un[N + i], my = d.Un[2 * N + i], mz = d.Un[3 * N + i];
+    double mm = __dadd_rn(__dadd_rn(__dmul_rn(mx, mx), __dmul_rn(my, my)), __dmul_rn(mz, mz));
+    double p = __dmul_rn(d.gamma - 1.0, __dsub_rn(d.Un[4 * N + i], __ddiv_rn(__dmul_rn(0.5, mm), r)));
+    double rc = __dsqrt_rn(__dmul_rn(__dmul_rn(d.gamma, p), r));
     double S = 0.0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       int f = d.cf[j * N + i];
-      double un = __dadd_rn(__dadd_rn(__dmul_rn(u, d.fn[f]), __dmul_rn(v, d.fn[F + f])),
-                            __dmul_rn(w, d.fn[2 * F + f]));
-      S = __dadd_rn(S, __dmul_rn(d.farea[f], __dadd_rn(fabs(un), c)));
+      double mn = __dadd_rn(__dadd_rn(__dmul_rn(mx, d.fn[f]), __dmul_rn(my, d.fn[F + f])),
+                            __dmul_rn(mz, d.fn[2 * F + f]));
+      S = __dadd_rn(S, __dmul_rn(d.farea[f], __dadd_rn(fabs(mn), rc)));
     }
-    double dt = __ddiv_rn(__dmul_rn(__dmul_rn(2.0, d.cfl), d.vol[i]), S);
+    double dt = __ddiv_rn(__dmul_rn(__dmul_rn(__dmul_rn(2.0, d.cfl), d.vol[i]), r), S);
     if (!(p > 0.0) || !(r > 0.0) || !isfinite(dt)) {
       atomicOr(d.status, FV_STATUS_NONPHYS);
       dt = __longlong_as_double(0x7ff0000000000000LL);
@@ -286,8 +302,38 @@ __device__ __forceinline__ void load_state(const DevMesh &d, const PhaseLevels &
   }
 }
 
+// FP32-flux mode: the state at the phase time from the FP32 shadow of U^n
+// and the FP32 predicted state
+__device__ __forceinline__ void load_state(const DevMesh &d, const PhaseLevels &pl, int c,
+                                           float U[5]) {
+  const size_t N = d.N;
+  int k = d.lev[c];
+  int mode = pl.mode[k];
+  if (mode == 0) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) U[q] = d.Un32[q * N + c];
+  } else if (mode == 1) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) U[q] = d.Us32[q * N + c];
+  } else {
+    float w = (float)pl.w[k];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      float a = d.Un32[q * N + c], b = d.Us32[q * N + c];
+      U[q] = a + w * (b - a);
+    }
+  }
+}
+
+__device__ __forceinline__ void to_prim(const double U[5], double gm1, double W[5]) {
+  prim_fp64(U, gm1, W);
+}
+__device__ __forceinline__ void to_prim(const float U[5], double gm1, float W[5]) {
+  cons_to_prim(U, (float)gm1, W);
+}
+
 // primitives of the cells of list range [coff[b0], coff[b1]) at the phase
-// time: W[5][N] in FP64 (FP64 mode) or W32 (FP32-flux mode)
+// time: W[5][N] in FP64 (FP64 mode) or FP32 (FP32-flux mode, no FP64 work)
 template <typename WT>
 __global__ void __launch_bounds__(256) k_prim(DevMesh d, const __grid_constant__ PhaseLevels pl, int b0, int b1, WT *W) {
   const size_t N = d.N;
@@ -295,11 +341,11 @@ __global__ void __launch_bounds__(256) k_prim(DevMesh d, const __grid_constant__
   double gm1 = d.gamma - 1.0;
   for (int idx = beg + blockIdx.x * blockDim.x + threadIdx.x; idx < end; idx += gridDim.x * blockDim.x) {
     int i = d.cl[idx];
-    double U[5], Wd[5];
+    WT U[5], Wt[5];
     load_state(d, pl, i, U);
-    cons_to_prim(U, gm1, Wd);
+    to_prim(U, gm1, Wt);
 #pragma unroll
-    for (int q = 0; q < 5; ++q) W[q * N + i] = (WT)Wd[q];
+    for (int q = 0; q < 5; ++q) W[q * N + i] = Wt[q];
   }
 }
 
@@ -307,7 +353,8 @@ __global__ void __launch_bounds__(256) k_prim(DevMesh d, const __grid_constant__
 // ghost states on boundary faces
 template <typename T>
 __global__ void __launch_bounds__(256) k_grad(DevMesh d, int b0, int b1, const T *__restrict__ W,
-                                              T *__restrict__ G) {
+                                              T *__restrict__ G, const T *__restrict__ lsw,
+                                              const T *__restrict__ fn) {
   const size_t N = d.N, F = d.F;
   int beg = d.coff[b0], end = d.coff[b1];
   for (int idx = beg + blockIdx.x * blockDim.x + threadIdx.x; idx < end; idx += gridDim.x * blockDim.x) {
@@ -329,15 +376,14 @@ __global__ void __launch_bounds__(256) k_grad(DevMesh d, int b0, int b1, const T
         for (int q = 0; q < 5; ++q) Wn[q] = Wi[q];
         if (nb == -FV_BC_WALL) {
           int f = d.cf[j * N + i];
-          T n0 = (T)d.fn[f], n1 = (T)d.fn[F + f], n2 = (T)d.fn[2 * F + f];
+          T n0 = fn[f], n1 = fn[F + f], n2 = fn[2 * F + f];
           T un = (Wi[1] * n0 + Wi[2] * n1) + Wi[3] * n2;
           Wn[1] = Wi[1] - (T(2) * un) * n0;
           Wn[2] = Wi[2] - (T(2) * un) * n1;
           Wn[3] = Wi[3] - (T(2) * un) * n2;
         }
       }
-      T w0 = (T)d.lsw[(3 * j) * N + i], w1 = (T)d.lsw[(3 * j + 1) * N + i],
-        w2 = (T)d.lsw[(3 * j + 2) * N + i];
+      T w0 = lsw[(3 * j) * N + i], w1 = lsw[(3 * j + 1) * N + i], w2 = lsw[(3 * j + 2) * N + i];
 #pragma unroll
       for (int c = 0; c < 5; ++c) {
         T dd = Wn[c] - Wi[c];
@@ -353,7 +399,7 @@ __global__ void __launch_bounds__(256) k_grad(DevMesh d, int b0, int b1, const T
 
 // face flux of face f from the phase-time primitives W and gradients G:
 // F A in FA_out[5] (FP64).  Returns a nonzero status on Riemann failure.
-template <typename T>
+template <typename T, bool G14>
 __device__ __forceinline__ int face_flux(const DevMesh &d, const GasT<T> &G, const T *__restrict__ W,
                                          const T *__restrict__ Gr, const T *__restrict__ fn,
                                          const T *__restrict__ fr, const T *__restrict__ farea, int f,
@@ -374,7 +420,7 @@ __device__ __forceinline__ int face_flux(const DevMesh &d, const GasT<T> &G, con
       WL[c] = wi + T(0.5) * minmod(T(2) * gir - dW, dW);
       WR[c] = wj - T(0.5) * minmod(T(2) * gjr - dW, dW);
     }
-    rc = godunov_flux(G, WL, WR, n, Fx, it);
+    rc = godunov_flux<T, G14>(G, WL, WR, n, Fx, it);
   } else {
     // reconstruct toward the ghost (mirror image of the cell in the face)
     T Wi[5], Wg[5];
@@ -391,7 +437,7 @@ __device__ __forceinline__ int face_flux(const DevMesh &d, const GasT<T> &G, con
       T gir = (Gr[(3 * c) * N + L] * r[0] + Gr[(3 * c + 1) * N + L] * r[1]) + Gr[(3 * c + 2) * N + L] * r[2];
       WL[c] = Wi[c] + T(0.5) * minmod(T(2) * gir - dW, dW);
     }
-    rc = boundary_flux(G, -R, WL, n, Fx, it);
+    rc = boundary_flux<T, G14>(G, -R, WL, n, Fx, it);
   }
   T A = farea[f];
 #pragma unroll
@@ -399,31 +445,49 @@ __device__ __forceinline__ int face_flux(const DevMesh &d, const GasT<T> &G, con
   return rc;
 }
 
-// stage 1 (predictor): FA[f] = F1 A.  stage 2 (corrector of `level`):
-// Phi = dt_k (F1 A + F2 A)/2 replaces FA[f]; on a level interface Phi is
-// added to ACC[f] (the coarse side's integral); on a boundary face to BND[f].
-template <typename T>
+// exact sign flip through the bit pattern (no floating-point instruction)
+__device__ __forceinline__ double flip(double v, bool neg) {
+  return __longlong_as_double(__double_as_longlong(v) ^ ((long long)neg << 63));
+}
+__device__ __forceinline__ float flip(float v, bool neg) {
+  return __int_as_float(__float_as_int(v) ^ ((int)neg << 31));
+}
+
+// stage 1 (predictor): the flux F1 A is stashed (FP32 in the FP32-flux mode,
+// where it only feeds the predictor).  stage 2 (corrector of `level`): the
+// step's flux time integral Phi = (dt_k/2) (F1 A + F2 A) is formed in FP64
+// (in the FP32-flux mode from the FP32 sum of the two fluxes) and stored; on
+// a level interface Phi is added to ACC[f] (the coarse side's integral), on a
+// boundary face to BND[f] (the conservation ledger).
+template <typename T, bool G14>
 __global__ void __launch_bounds__(128) k_flux(DevMesh d, GasT<T> G, int stage, int level, int b0,
                                               int b1, const T *__restrict__ W, const T *__restrict__ Gr,
                                               const T *__restrict__ fn, const T *__restrict__ fr,
                                               const T *__restrict__ farea) {
   const size_t F = d.F;
+  const bool f32 = sizeof(T) == 4;
   int beg = d.foff[b0], end = d.foff[b1];
-  double dtk = ldexp(__longlong_as_double((long long)*d.dtmin_bits), level);
+  double h = 0.5 * ldexp(__longlong_as_double((long long)*d.dtmin_bits), level);
   for (int idx = beg + blockIdx.x * blockDim.x + threadIdx.x; idx < end; idx += gridDim.x * blockDim.x) {
     int f = d.fl[idx];
     T FAt[5];
-    int rc = face_flux(d, G, W, Gr, fn, fr, farea, f, FAt);
+    int rc = face_flux<T, G14>(d, G, W, Gr, fn, fr, farea, f, FAt);
     if (rc) atomicOr(d.status, FV_STATUS_RIEMANN);
     if (stage == 1) {
 #pragma unroll
-      for (int c = 0; c < 5; ++c) d.FA[c * F + f] = (double)FAt[c];
+      for (int c = 0; c < 5; ++c) {
+        if (f32)
+          d.FA32[c * F + f] = (float)FAt[c];
+        else
+          d.FA[c * F + f] = (double)FAt[c];
+      }
     } else {
       int R = d.fnb[f];
       bool iface = R >= 0 && d.lev[d.fown[f]] != d.lev[R];
 #pragma unroll
       for (int c = 0; c < 5; ++c) {
-        double phi = dtk * (0.5 * (d.FA[c * F + f] + (double)FAt[c]));
+        double sum = f32 ? (double)(d.FA32[c * F + f] + (float)FAt[c]) : d.FA[c * F + f] + (double)FAt[c];
+        double phi = h * sum;
         d.FA[c * F + f] = phi;
         if (iface) d.ACC[c * F + f] += phi;
         if (R < 0) d.BND[c * F + f] += phi;
@@ -433,53 +497,92 @@ __global__ void __launch_bounds__(128) k_flux(DevMesh d, GasT<T> G, int stage, i
 }
 
 // per-cell gather over its 4 faces in local order (deterministic, no
-// atomics).  stage 1: U* = U^n + dt_k (-S/V) with S = sum sigma F1 A;
-// stage 2 (level k): U^{n+1} = U^n - S/V with S = sum sigma Phi, where faces
-// to finer neighbours contribute (and reset) their accumulated integral.
+// atomics), signs applied by flipping bits:
+//  stage 1: U* = U^n + dt_k (-S/V), S = sum sigma F1 A.  In the FP32-flux mode
+//           the predictor is all FP32 (U* only feeds fluxes).
+//  stage 2 (level k): U^{n+1} = U^n - S/V, S = sum sigma Phi in FP64, where
+//           faces to finer neighbours contribute (and reset) their
+//           accumulated integral; the FP32 shadow of U^n is refreshed.
+// Positivity is checked by the next level assignment and on demand
+// (fv_status), not here.
+template <bool F32>
 __global__ void __launch_bounds__(256) k_update(DevMesh d, int stage, int level, int b0, int b1) {
   const size_t N = d.N, F = d.F;
   int beg = d.coff[b0], end = d.coff[b1];
   double dtmin = __longlong_as_double((long long)*d.dtmin_bits);
-  double gm1 = d.gamma - 1.0;
+  float dtmin32 = (float)dtmin;
   for (int idx = beg + blockIdx.x * blockDim.x + threadIdx.x; idx < end; idx += gridDim.x * blockDim.x) {
     int i = d.cl[idx];
     unsigned own = d.cown[i];
-    double S[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    if (stage == 1 && F32) {
+      float S[5];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        int f = d.cf[j * N + i];
+        bool neg = !((own >> j) & 1u);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          float v = flip(d.FA32[c * F + f], neg);
+          S[c] = j == 0 ? v : S[c] + v;
+        }
+      }
+      float cdt = -ldexpf(dtmin32, (int)d.lev[i]) * d.ivol32[i];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) d.Us32[c * N + i] = d.Un32[c * N + i] + cdt * S[c];
+      continue;
+    }
+    double S[5];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       int f = d.cf[j * N + i];
-      double s = ((own >> j) & 1u) ? 1.0 : -1.0;
-      if (stage == 1 || d.flev[f] == level) {
+      bool neg = !((own >> j) & 1u);
+      bool acc = stage == 2 && d.flev[f] != level;
 #pragma unroll
-        for (int c = 0; c < 5; ++c) S[c] += s * d.FA[c * F + f];
-      } else {
-#pragma unroll
-        for (int c = 0; c < 5; ++c) {
-          S[c] += s * d.ACC[c * F + f];
+      for (int c = 0; c < 5; ++c) {
+        double v;
+        if (acc) {
+          v = d.ACC[c * F + f];
           d.ACC[c * F + f] = 0.0;
+        } else {
+          v = d.FA[c * F + f];
         }
+        v = flip(v, neg);
+        S[c] = j == 0 ? v : S[c] + v;
       }
     }
-    double V = d.vol[i];
-    double Un[5], Uo[5];
-#pragma unroll
-    for (int c = 0; c < 5; ++c) Un[c] = d.Un[c * N + i];
+    double iV = d.ivol[i];
     if (stage == 1) {
-      double dtk = ldexp(dtmin, (int)d.lev[i]);
+      double cdt = -ldexp(dtmin, (int)d.lev[i]) * iV;
 #pragma unroll
-      for (int c = 0; c < 5; ++c) Uo[c] = Un[c] + dtk * (-S[c] / V);
+      for (int c = 0; c < 5; ++c) d.Us[c * N + i] = d.Un[c * N + i] + cdt * S[c];
     } else {
 #pragma unroll
-      for (int c = 0; c < 5; ++c) Uo[c] = Un[c] - S[c] / V;
+      for (int c = 0; c < 5; ++c) {
+        double u = d.Un[c * N + i] - iV * S[c];
+        d.Un[c * N + i] = u;
+        if (F32) d.Un32[c * N + i] = (float)u;
+      }
     }
-    double Wc[5];
-    cons_to_prim(Uo, gm1, Wc);
-    if (!(Wc[0] > 0.0) || !(Wc[4] > 0.0) || !isfinite(Wc[0] + Wc[1] + Wc[2] + Wc[3] + Wc[4]))
-      atomicOr(d.status, FV_STATUS_NONPHYS);
-    double *dst = stage == 1 ? d.Us : d.Un;
-#pragma unroll
-    for (int c = 0; c < 5; ++c) dst[c * N + i] = Uo[c];
   }
+}
+
+// positivity and finiteness of U^n (rho > 0, 2 rho E > |rho u|^2)
+__global__ void __launch_bounds__(256) k_check_state(DevMesh d) {
+  const size_t N = d.N;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x) {
+    double U[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) U[c] = d.Un[c * N + i];
+    double m2 = (U[1] * U[1] + U[2] * U[2]) + U[3] * U[3];
+    if (!(U[0] > 0.0) || !(2.0 * U[0] * U[4] > m2) || !isfinite(m2 + U[4]))
+      atomicOr(d.status, FV_STATUS_NONPHYS);
+  }
+}
+
+int launch_check_state(const DevMesh &d, cudaStream_t s) {
+  k_check_state<<<grid_for(d.N, 256, 8), 256, 0, s>>>(d);
+  FV_LAUNCH_CHECK();
+  return FV_OK;
 }
 
 // R = -(1/V) sum sigma F A for the cells of one level (residual hook);
@@ -503,14 +606,14 @@ __global__ void __launch_bounds__(256) k_residual(DevMesh d, int level, const do
 #pragma unroll
       for (int c = 0; c < 5; ++c) S[c] += s * FAt[c * F + f];
     }
-    double V = d.vol[i];
+    double iV = d.ivol[i];
 #pragma unroll
-    for (int c = 0; c < 5; ++c) R[c * N + o] = -S[c] / V;
+    for (int c = 0; c < 5; ++c) R[c * N + o] = -S[c] * iV;
   }
 }
 
 // F A of every face touching a level-`level` cell into FAt (residual hook)
-template <typename T>
+template <typename T, bool G14>
 __global__ void __launch_bounds__(128) k_flux_all(DevMesh d, GasT<T> G, int level, const T *__restrict__ W,
                                                   const T *__restrict__ Gr, const T *__restrict__ fn,
                                                   const T *__restrict__ fr, const T *__restrict__ farea,
@@ -521,7 +624,7 @@ __global__ void __launch_bounds__(128) k_flux_all(DevMesh d, GasT<T> G, int leve
     bool touch = d.lev[d.fown[f]] == level || (R >= 0 && d.lev[R] == level);
     if (!touch) continue;
     T FAx[5];
-    if (face_flux(d, G, W, Gr, fn, fr, farea, f, FAx)) atomicOr(d.status, FV_STATUS_RIEMANN);
+    if (face_flux<T, G14>(d, G, W, Gr, fn, fr, farea, f, FAx)) atomicOr(d.status, FV_STATUS_RIEMANN);
 #pragma unroll
     for (int c = 0; c < 5; ++c) FAt[c * F + f] = (double)FAx[c];
   }
@@ -533,11 +636,11 @@ __global__ void __launch_bounds__(256) k_prim_all(DevMesh d, const __grid_consta
   const size_t N = d.N;
   double gm1 = d.gamma - 1.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x) {
-    double U[5], Wd[5];
+    WT U[5], Wt[5];
     load_state(d, pl, i, U);
-    cons_to_prim(U, gm1, Wd);
+    to_prim(U, gm1, Wt);
 #pragma unroll
-    for (int q = 0; q < 5; ++q) W[q * N + i] = (WT)Wd[q];
+    for (int q = 0; q < 5; ++q) W[q * N + i] = Wt[q];
   }
 }
 
@@ -570,6 +673,10 @@ __global__ void __launch_bounds__(256) k_set_state(DevMesh d, const double *__re
     d.Un[3 * N + i] = __dmul_rn(r, w);
     double uu = __dadd_rn(__dadd_rn(__dmul_rn(u, u), __dmul_rn(v, v)), __dmul_rn(w, w));
     d.Un[4 * N + i] = __dadd_rn(__ddiv_rn(p, gm1), __dmul_rn(__dmul_rn(0.5, r), uu));
+    if (d.Un32) {
+#pragma unroll
+      for (int c = 0; c < 5; ++c) d.Un32[c * N + i] = (float)d.Un[c * N + i];
+    }
   }
 }
 
@@ -580,6 +687,10 @@ __global__ void __launch_bounds__(256) k_set_cons(DevMesh d, const double *__res
     int o = new2old[i];
 #pragma unroll
     for (int c = 0; c < 5; ++c) d.Un[c * N + i] = cons[c * N + o];
+    if (d.Un32) {
+#pragma unroll
+      for (int c = 0; c < 5; ++c) d.Un32[c * N + i] = (float)cons[c * N + o];
+    }
     if (!(cons[o] > 0.0)) atomicOr(d.status, FV_STATUS_NONPHYS);
   }
 }
@@ -598,6 +709,55 @@ __global__ void __launch_bounds__(256) k_get_levels(DevMesh d, int8_t *__restric
                                                     const int *__restrict__ new2old) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x)
     lev[new2old[i]] = d.lev[i];
+}
+
+// Godunov flux of independent face states (test / harvesting hook)
+template <typename T, bool G14>
+__global__ void __launch_bounds__(128) k_flux_batch(const double *__restrict__ WL,
+                                                    const double *__restrict__ WR,
+                                                    const double *__restrict__ nrm, int n, GasT<T> G,
+                                                    int bc, double *__restrict__ F,
+                                                    int *__restrict__ iters) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    T wl[5], wr[5], nn[3], Fx[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      wl[c] = (T)WL[(size_t)c * n + i];
+      wr[c] = (T)WR[(size_t)c * n + i];
+    }
+#pragma unroll
+    for (int e = 0; e < 3; ++e) nn[e] = (T)nrm[(size_t)e * n + i];
+    int it = 0, rc;
+    if (bc == 0)
+      rc = godunov_flux<T, G14>(G, wl, wr, nn, Fx, it);
+    else
+      rc = boundary_flux<T, G14>(G, bc, wl, nn, Fx, it);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) F[(size_t)c * n + i] = rc ? 0.0 : (double)Fx[c];
+    iters[i] = rc ? -1 : it;
+  }
+}
+
+int launch_flux_batch(const double *WL, const double *WR, const double *nrm, int n, double gamma,
+                      double tol, int maxit, int precision, int bc, double *F, int *iters,
+                      cudaStream_t s) {
+  int g = grid_for(n, 128, 16);
+  bool g14 = gamma == 1.4;
+  if (precision == FV_FP64) {
+    GasT<double> G = GasT<double>::make(gamma, tol, maxit);
+    if (g14)
+      k_flux_batch<double, true><<<g, 128, 0, s>>>(WL, WR, nrm, n, G, bc, F, iters);
+    else
+      k_flux_batch<double, false><<<g, 128, 0, s>>>(WL, WR, nrm, n, G, bc, F, iters);
+  } else {
+    GasT<float> G = GasT<float>::make(gamma, tol > 2e-6 ? tol : 2e-6, maxit);
+    if (g14)
+      k_flux_batch<float, true><<<g, 128, 0, s>>>(WL, WR, nrm, n, G, bc, F, iters);
+    else
+      k_flux_batch<float, false><<<g, 128, 0, s>>>(WL, WR, nrm, n, G, bc, F, iters);
+  }
+  FV_LAUNCH_CHECK();
+  return FV_OK;
 }
 
 // ================================================================ hosts ==
@@ -655,19 +815,29 @@ int launch_phase(const DevMesh &d, int precision, const PhaseLevels &pl, int sta
     double *W = (double *)Wbuf;
     GasT<double> G = GasT<double>::make(d.gamma, d.tol, d.maxit);
     { ProfScope sc(ph, FV_PROF_PRIM, s); k_prim<double><<<gc, 256, 0, s>>>(d, pl, pb0, pb1, W); }
-    { ProfScope sc(ph, FV_PROF_GRAD, s); k_grad<double><<<gc, 256, 0, s>>>(d, gb0, gb1, W, d.G); }
+    { ProfScope sc(ph, FV_PROF_GRAD, s); k_grad<double><<<gc, 256, 0, s>>>(d, gb0, gb1, W, d.G, d.lsw, d.fn); }
     { ProfScope sc(ph, FV_PROF_FLUX, s);
-      k_flux<double><<<gfx, 128, 0, s>>>(d, G, stage, level, fb0, fb1, W, d.G, d.fn, d.fr, d.farea); }
+      if (d.gamma == 1.4)
+        k_flux<double, true><<<gfx, 128, 0, s>>>(d, G, stage, level, fb0, fb1, W, d.G, d.fn, d.fr, d.farea);
+      else
+        k_flux<double, false><<<gfx, 128, 0, s>>>(d, G, stage, level, fb0, fb1, W, d.G, d.fn, d.fr, d.farea); }
   } else {
     float *W = (float *)Wbuf;
     double tol32 = d.tol > 2e-6 ? d.tol : 2e-6;
     GasT<float> G = GasT<float>::make(d.gamma, tol32, d.maxit);
     { ProfScope sc(ph, FV_PROF_PRIM, s); k_prim<float><<<gc, 256, 0, s>>>(d, pl, pb0, pb1, W); }
-    { ProfScope sc(ph, FV_PROF_GRAD, s); k_grad<float><<<gc, 256, 0, s>>>(d, gb0, gb1, W, d.G32); }
+    { ProfScope sc(ph, FV_PROF_GRAD, s); k_grad<float><<<gc, 256, 0, s>>>(d, gb0, gb1, W, d.G32, d.lsw32, d.fn32); }
     { ProfScope sc(ph, FV_PROF_FLUX, s);
-      k_flux<float><<<gfx, 128, 0, s>>>(d, G, stage, level, fb0, fb1, W, d.G32, d.fn32, d.fr32, d.farea32); }
+      if (d.gamma == 1.4)
+        k_flux<float, true><<<gfx, 128, 0, s>>>(d, G, stage, level, fb0, fb1, W, d.G32, d.fn32, d.fr32, d.farea32);
+      else
+        k_flux<float, false><<<gfx, 128, 0, s>>>(d, G, stage, level, fb0, fb1, W, d.G32, d.fn32, d.fr32, d.farea32); }
   }
-  { ProfScope sc(ph, FV_PROF_UPDATE, s); k_update<<<gc, 256, 0, s>>>(d, stage, level, ub0, ub1); }
+  { ProfScope sc(ph, FV_PROF_UPDATE, s);
+    if (precision == FV_FP64)
+      k_update<false><<<gc, 256, 0, s>>>(d, stage, level, ub0, ub1);
+    else
+      k_update<true><<<gc, 256, 0, s>>>(d, stage, level, ub0, ub1); }
   FV_LAUNCH_CHECK();
   return FV_OK;
 }
@@ -681,15 +851,21 @@ int launch_residual(const DevMesh &d, int precision, const PhaseLevels &pl, int 
     GasT<double> G = GasT<double>::make(d.gamma, d.tol, d.maxit);
     k_prim_all<double><<<gc, 256, 0, s>>>(d, pl, W);
     // gradients of every cell: the list range covering all cells
-    k_grad<double><<<gc, 256, 0, s>>>(d, 0, 2 * d.L, W, d.G);
-    k_flux_all<double><<<gfx, 128, 0, s>>>(d, G, level, W, d.G, d.fn, d.fr, d.farea, FAt);
+    k_grad<double><<<gc, 256, 0, s>>>(d, 0, 2 * d.L, W, d.G, d.lsw, d.fn);
+    if (d.gamma == 1.4)
+      k_flux_all<double, true><<<gfx, 128, 0, s>>>(d, G, level, W, d.G, d.fn, d.fr, d.farea, FAt);
+    else
+      k_flux_all<double, false><<<gfx, 128, 0, s>>>(d, G, level, W, d.G, d.fn, d.fr, d.farea, FAt);
   } else {
     float *W = (float *)Wbuf;
     double tol32 = d.tol > 2e-6 ? d.tol : 2e-6;
     GasT<float> G = GasT<float>::make(d.gamma, tol32, d.maxit);
     k_prim_all<float><<<gc, 256, 0, s>>>(d, pl, W);
-    k_grad<float><<<gc, 256, 0, s>>>(d, 0, 2 * d.L, W, d.G32);
-    k_flux_all<float><<<gfx, 128, 0, s>>>(d, G, level, W, d.G32, d.fn32, d.fr32, d.farea32, FAt);
+    k_grad<float><<<gc, 256, 0, s>>>(d, 0, 2 * d.L, W, d.G32, d.lsw32, d.fn32);
+    if (d.gamma == 1.4)
+      k_flux_all<float, true><<<gfx, 128, 0, s>>>(d, G, level, W, d.G32, d.fn32, d.fr32, d.farea32, FAt);
+    else
+      k_flux_all<float, false><<<gfx, 128, 0, s>>>(d, G, level, W, d.G32, d.fn32, d.fr32, d.farea32, FAt);
   }
   k_residual<<<gc, 256, 0, s>>>(d, level, FAt, R, new2old);
   FV_LAUNCH_CHECK();

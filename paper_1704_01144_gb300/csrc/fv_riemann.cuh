@@ -69,6 +69,17 @@ __device__ __forceinline__ void pressure_fn(const GasT<T> &G, T p, T rK, T pK, T
   }
 }
 
+// FP32 only: Newton has reached the precision floor when f = f_L + f_R + du
+// is within a few ulps of its terms.  Near vacuum (p* much smaller than the
+// flow's pressure scale) the terms cancel almost exactly and single-precision
+// rounding of f alone moves the iterate by more than the relative-change
+// tolerance, so that test could never pass.  FP64 keeps the plain
+// relative-change test.
+__device__ __forceinline__ bool at_rounding_floor(double, double, double, double) { return false; }
+__device__ __forceinline__ bool at_rounding_floor(float f, float a, float b, float c) {
+  return fabsf(f) <= 8.0f * 1.1920929e-7f * (fabsf(a) + fabsf(b) + fabsf(c));
+}
+
 // Star pressure/velocity.  Returns 0, or 1 (vacuum), 2 (no convergence).
 template <typename T>
 __device__ __forceinline__ int riemann_star(const GasT<T> &G, T rL, T uL, T pL, T rR, T uR, T pR,
@@ -87,7 +98,12 @@ __device__ __forceinline__ int riemann_star(const GasT<T> &G, T rL, T uL, T pL, 
     T fL, dfL, fR, dfR;
     pressure_fn(G, p, rL, pL, aL, fL, dfL);
     pressure_fn(G, p, rR, pR, aR, fR, dfR);
-    T pn = p - (fL + fR + du) / (dfL + dfR);
+    T fsum = fL + fR + du;
+    if (at_rounding_floor(fsum, fL, fR, du)) {
+      conv = true;
+      break;
+    }
+    T pn = p - fsum / (dfL + dfR);
     if (pn < pfloor) pn = pfloor;
     T change = fabs(pn - p) / (T(0.5) * (pn + p));
     p = pn;
@@ -174,20 +190,243 @@ __device__ __forceinline__ void sample_face(const GasT<T> &G, T rL, T uL, T pL, 
   }
 }
 
+// ----------------------------------------------------------------------
+// gamma = 1.4: every exponent of the exact solver is a multiple of 1/7
+// (z = (g-1)/(2g) = 1/7, 2g/(g-1) = 7, 2/(g-1) = 5, 1/g = 5/7, and
+// -(g+1)/(2g) = -6/7), so all powers reduce to integer powers of the inverse
+// seventh root r = x^(-1/7).  r comes from a single-precision seed refined by
+// Newton's method on r^-7 = x, r <- r (8 - x r^7) / 7 (quadratic
+// convergence: two steps take a ~1e-7 seed to double-precision rounding).
+// Per Riemann problem: one root per side, one per Newton iterate (shared by
+// both sides), one at the converged star pressure.
+
+__device__ __forceinline__ double rroot7(double x) {
+  double r = (double)exp2f(-0.14285714285714285f * __log2f((float)x));
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    double r2 = r * r, r4 = r2 * r2;
+    double r7 = r4 * r2 * r;
+    r = r * (8.0 - x * r7) * (1.0 / 7.0);
+  }
+  return r;
+}
+__device__ __forceinline__ float rroot7(float x) {
+  float r = exp2f(-0.14285714285714285f * __log2f(x));
+  float r2 = r * r, r4 = r2 * r2;
+  return r * (8.0f - x * (r4 * r2 * r)) * (1.0f / 7.0f);
+}
+template <typename T>
+__device__ __forceinline__ T ipow5(T c) {
+  T c2 = c * c;
+  return c2 * c2 * c;
+}
+template <typename T>
+__device__ __forceinline__ T ipow7(T c) {
+  T c2 = c * c, c4 = c2 * c2;
+  return c4 * c2 * c;
+}
+
+// per-side constants: iq = pK^(-1/7); cK = pK iq / (rK aK) (rarefaction slope
+// factor); eK = 2 aK / (g-1) = 5 aK
+template <typename T>
+struct Side14 {
+  T r, p, a, iq, c, e, A, B;
+};
+
+template <typename T>
+__device__ __forceinline__ Side14<T> make_side14(const GasT<T> &G, T rK, T pK) {
+  Side14<T> s;
+  s.r = rK;
+  s.p = pK;
+  s.a = fsqrt(G.g * pK / rK);
+  s.iq = rroot7(pK);
+  s.c = pK * s.iq / (rK * s.a);
+  s.e = T(5) * s.a;
+  s.A = T(2) / (G.gp1 * rK);
+  s.B = G.k_gm1_gp1 * pK;
+  return s;
+}
+
+// f_K(p) and f_K'(p).  FP64: from p17 = p^(1/7) and rp6 = p^(-6/7), shared
+// by both sides.  FP32: from the root of p/pK itself, with (p/pK)^(1/7) taken
+// as the reciprocal of the inverse root (about one ulp), which keeps f_K
+// smooth enough for Newton's stopping test; forming it as a product with the
+// sixth power of the root would multiply the single-precision error by six.
+__device__ __forceinline__ void pressure_fn14(const Side14<double> &K, double p, double p17,
+                                              double rp6, double &f, double &df) {
+  if (p > K.p) {
+    double q = sqrt(K.A / (p + K.B));
+    f = (p - K.p) * q;
+    df = q * (1.0 - 0.5 * (p - K.p) / (K.B + p));
+  } else {
+    f = K.e * (p17 * K.iq - 1.0);
+    df = K.c * rp6;
+  }
+}
+__device__ __forceinline__ void pressure_fn14(const Side14<float> &K, float p, float, float,
+                                              float &f, float &df) {
+  if (p > K.p) {
+    float q = sqrtf(K.A / (p + K.B));
+    f = (p - K.p) * q;
+    df = q * (1.0f - 0.5f * (p - K.p) / (K.B + p));
+  } else {
+    float pr = p / K.p;
+    float ir = rroot7(pr);             // pr^(-1/7), about one ulp
+    float ir2 = ir * ir;
+    float ir6 = ir2 * ir2 * ir2;       // pr^(-6/7), only the slope uses it
+    f = K.e * (1.0f / ir - 1.0f);      // pr^(1/7) - 1 from the reciprocal
+    df = ir6 / (K.r * K.a);
+  }
+}
+
+// (ps/pK)^(1/7) for the sampling step
+__device__ __forceinline__ double ratio17(const Side14<double> &K, double ps, double p17) {
+  return p17 * K.iq;
+}
+__device__ __forceinline__ float ratio17(const Side14<float> &K, float ps, float) {
+  return 1.0f / rroot7(ps / K.p);
+}
+
+template <typename T>
+__device__ __forceinline__ void roots_of(T p, T &p17, T &rp6) {
+  T rp = rroot7(p);
+  T rp2 = rp * rp;
+  rp6 = rp2 * rp2 * rp2;
+  p17 = p * rp6;
+}
+
+template <typename T>
+__device__ __forceinline__ int riemann_star14(const GasT<T> &G, const Side14<T> &L, T uL,
+                                              const Side14<T> &R, T uR, T &ps, T &us, T &ps17,
+                                              int &iters) {
+  T du = uR - uL;
+  if (G.two_gm1 * (L.a + R.a) <= du) return 1;
+  T num = L.a + R.a - T(0.5) * G.gm1 * du;
+  T p = ipow7(num / (L.a * L.iq + R.a * R.iq));
+  T pfloor = T(1e-6) * (L.p < R.p ? L.p : R.p);
+  if (p < pfloor) p = pfloor;
+  int it;
+  bool conv = false;
+  for (it = 1; it <= G.maxit; ++it) {
+    T p17 = T(0), rp6 = T(0);
+    if (sizeof(T) == 8 && (p <= L.p || p <= R.p)) roots_of(p, p17, rp6);
+    T fL, dfL, fR, dfR;
+    pressure_fn14(L, p, p17, rp6, fL, dfL);
+    pressure_fn14(R, p, p17, rp6, fR, dfR);
+    T fsum = fL + fR + du;
+    if (at_rounding_floor(fsum, fL, fR, du)) {
+      conv = true;
+      break;
+    }
+    T pn = p - fsum / (dfL + dfR);
+    if (pn < pfloor) pn = pfloor;
+    T change = fabs(pn - p) / (T(0.5) * (pn + p));
+    p = pn;
+    if (change <= G.tol) {
+      conv = true;
+      break;
+    }
+  }
+  iters = it;
+  if (!conv || !(p > T(0)) || !isfinite(p)) return 2;
+  T p17 = T(0), rp6 = T(0), fL, dfL, fR, dfR;
+  if (sizeof(T) == 8) roots_of(p, p17, rp6);
+  pressure_fn14(L, p, p17, rp6, fL, dfL);
+  pressure_fn14(R, p, p17, rp6, fR, dfR);
+  ps = p;
+  ps17 = p17;
+  us = T(0.5) * (uL + uR) + T(0.5) * (fR - fL);
+  return 0;
+}
+
+// the state on the face (x/t = 0); p17 = ps^(1/7)
+template <typename T>
+__device__ __forceinline__ void sample_face14(const GasT<T> &G, const Side14<T> &L, T uL,
+                                              const Side14<T> &R, T uR, T ps, T us, T p17, T &r,
+                                              T &u, T &p, int &side) {
+  if (T(0) <= us) {
+    side = 0;
+    if (ps > L.p) {
+      T SL = uL - L.a * fsqrt(G.shock_a * (ps / L.p) + G.shock_b);
+      if (T(0) <= SL) {
+        r = L.r; u = uL; p = L.p;
+      } else {
+        T q = ps / L.p;
+        r = L.r * ((q + G.k_gm1_gp1) / (G.k_gm1_gp1 * q + T(1)));
+        u = us; p = ps;
+      }
+    } else {
+      T SHL = uL - L.a;
+      if (T(0) <= SHL) {
+        r = L.r; u = uL; p = L.p;
+      } else {
+        T pr17 = ratio17(L, ps, p17);  // (ps/pL)^(1/7)
+        T STL = us - L.a * pr17;
+        if (T(0) >= STL) {
+          r = L.r * ipow5(pr17);
+          u = us; p = ps;
+        } else {
+          T c = T(2) / G.gp1 + (G.gm1 / (G.gp1 * L.a)) * uL;
+          r = L.r * ipow5(c);
+          u = (T(2) / G.gp1) * (L.a + T(0.5) * G.gm1 * uL);
+          p = L.p * ipow7(c);
+        }
+      }
+    }
+  } else {
+    side = 1;
+    if (ps > R.p) {
+      T SR = uR + R.a * fsqrt(G.shock_a * (ps / R.p) + G.shock_b);
+      if (T(0) >= SR) {
+        r = R.r; u = uR; p = R.p;
+      } else {
+        T q = ps / R.p;
+        r = R.r * ((q + G.k_gm1_gp1) / (G.k_gm1_gp1 * q + T(1)));
+        u = us; p = ps;
+      }
+    } else {
+      T SHR = uR + R.a;
+      if (T(0) >= SHR) {
+        r = R.r; u = uR; p = R.p;
+      } else {
+        T pr17 = ratio17(R, ps, p17);
+        T STR = us + R.a * pr17;
+        if (T(0) <= STR) {
+          r = R.r * ipow5(pr17);
+          u = us; p = ps;
+        } else {
+          T c = T(2) / G.gp1 - (G.gm1 / (G.gp1 * R.a)) * uR;
+          r = R.r * ipow5(c);
+          u = (T(2) / G.gp1) * (-R.a + T(0.5) * G.gm1 * uR);
+          p = R.p * ipow7(c);
+        }
+      }
+    }
+  }
+}
+
 // Godunov flux per unit area through an interior face with unit normal n;
 // the tangential velocity comes from the upwind side of the contact.
 // Returns 0 or the riemann_star error.
-template <typename T>
+template <typename T, bool G14>
 __device__ __forceinline__ int godunov_flux(const GasT<T> &G, const T WL[5], const T WR[5],
                                             const T n[3], T F[5], int &iters) {
   T unL = (WL[1] * n[0] + WL[2] * n[1]) + WL[3] * n[2];
   T unR = (WR[1] * n[0] + WR[2] * n[1]) + WR[3] * n[2];
   T ps, us;
-  int rc = riemann_star(G, WL[0], unL, WL[4], WR[0], unR, WR[4], ps, us, iters);
-  if (rc) return rc;
   T r0, un0, p0;
   int side;
-  sample_face(G, WL[0], unL, WL[4], WR[0], unR, WR[4], ps, us, r0, un0, p0, side);
+  if (G14) {
+    Side14<T> L = make_side14(G, WL[0], WL[4]), R = make_side14(G, WR[0], WR[4]);
+    T p17;
+    int rc = riemann_star14(G, L, unL, R, unR, ps, us, p17, iters);
+    if (rc) return rc;
+    sample_face14(G, L, unL, R, unR, ps, us, p17, r0, un0, p0, side);
+  } else {
+    int rc = riemann_star(G, WL[0], unL, WL[4], WR[0], unR, WR[4], ps, us, iters);
+    if (rc) return rc;
+    sample_face(G, WL[0], unL, WL[4], WR[0], unR, WR[4], ps, us, r0, un0, p0, side);
+  }
   const bool left = side == 0;
   T uns = left ? unL : unR;
   T V0[3];
@@ -206,13 +445,20 @@ __device__ __forceinline__ int godunov_flux(const GasT<T> &G, const T WL[5], con
 // contact speed is exactly 0, so only the star pressure crosses it; a
 // transmissive face has identical states on both sides, whose Godunov flux
 // is the physical flux.
-template <typename T>
+template <typename T, bool G14>
 __device__ __forceinline__ int boundary_flux(const GasT<T> &G, int bc, const T WL[5], const T n[3],
                                              T F[5], int &iters) {
   T un = (WL[1] * n[0] + WL[2] * n[1]) + WL[3] * n[2];
   if (bc == 1) {
     T ps, us;
-    int rc = riemann_star(G, WL[0], un, WL[4], WL[0], -un, WL[4], ps, us, iters);
+    int rc;
+    if (G14) {
+      Side14<T> S = make_side14(G, WL[0], WL[4]);
+      T p17;
+      rc = riemann_star14(G, S, un, S, -un, ps, us, p17, iters);
+    } else {
+      rc = riemann_star(G, WL[0], un, WL[4], WL[0], -un, WL[4], ps, us, iters);
+    }
     if (rc) return rc;
     F[0] = T(0);
     F[1] = ps * n[0];

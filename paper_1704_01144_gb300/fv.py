@@ -57,6 +57,7 @@ EXPORTS = [
     "fv_cell_volumes", "fv_status", "fv_last_error", "fv_version", "fv_set_conserved",
     "fv_work_counters", "fv_use_graph", "fv_profile_enable", "fv_profile_read",
     "fv_get_level_lists", "fv_get_local_dt", "fv_assign_levels_noalloc",
+    "fv_godunov_flux_batch",
 ]
 
 FV_NOALLOC_MAX_CELLS = 1 << 22
@@ -111,6 +112,7 @@ def lib():
     L.fv_profile_enable.argtypes = [vp, C.c_int]
     L.fv_profile_read.argtypes = [vp, dp, C.POINTER(C.c_int64)]
     L.fv_get_local_dt.argtypes = [vp, dp]
+    L.fv_godunov_flux_batch.argtypes = [vp, vp, vp, i64, C.POINTER(fv_config), C.c_int, vp, vp, vp]
     L.fv_assign_levels_noalloc.argtypes = [vp, vp, i64, C.c_int, vp, vp, vp]
     L.fv_get_level_lists.argtypes = [vp, C.POINTER(C.c_int64), i32p, i8p, i32p]
     L.fv_last_error.restype = C.c_char_p
@@ -279,6 +281,23 @@ def fv_assign_levels_noalloc(dt, nbr, max_levels, levels_out, dt_min_out, stream
     _check(lib().fv_assign_levels_noalloc(_dptr(dt), _dptr(nbr, "int32"), n, int(max_levels),
                                           _dptr(levels_out, "int8"), _dptr(dt_min_out),
                                           _stream(stream)), "fv_assign_levels_noalloc")
+
+
+def fv_godunov_flux_batch(WL, WR, nrm, cfg: fv_config, bc=FV_BC_INTERIOR, F=None, iters=None,
+                          stream=None):
+    """Device Godunov flux of independent face states: torch CUDA float64
+    tensors WL, WR (5, n) primitives and nrm (3, n) unit normals.  Returns
+    (F (5, n) float64, iters (n,) int32), filled asynchronously."""
+    import torch
+    n = int(WL.shape[1])
+    if F is None:
+        F = torch.empty((5, n), dtype=torch.float64, device=WL.device)
+    if iters is None:
+        iters = torch.empty(n, dtype=torch.int32, device=WL.device)
+    _check(lib().fv_godunov_flux_batch(_dptr(WL), _dptr(WR) if WR is not None else None, _dptr(nrm),
+                                       n, C.byref(cfg), int(bc), _dptr(F), _dptr(iters, "int32"),
+                                       _stream(stream)), "fv_godunov_flux_batch")
+    return F, iters
 
 
 def fv_get_levels(h):
