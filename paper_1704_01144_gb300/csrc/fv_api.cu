@@ -76,7 +76,7 @@ struct fv_mesh {
   int L = 1, theta = 0;
   int *new2old_dev = nullptr;  // Morton index -> caller's index
   void *W = nullptr;           // phase-time primitives (FP64 or FP32)
-  double *FAt = nullptr;       // residual-hook scratch (5F)
+  double *FAt = nullptr;       // residual-hook scratch (REC_FA x F; also host staging)
   int *cnt_scratch = nullptr;  // level-sort counts
   std::vector<Phase> phases;
   bool in_cycle = false;
@@ -273,30 +273,25 @@ int fv_mesh_load(const double *xyz, int64_t n_nodes, const int64_t *tets, int64_
   } while (0)
   AL(d.vol, N);
   AL(d.ivol, N);
-  AL(d.cf, 4 * N);
-  AL(d.cnb, 4 * N);
+  AL(d.cf4, N);
+  AL(d.cnb4, N);
   AL(d.cown, N);
-  AL(d.lsw, 12 * N);
-  AL(d.fown, F);
-  AL(d.fnb, F);
-  AL(d.fn, 3 * F);
-  AL(d.farea, F);
-  AL(d.fr, 3 * F);
+  AL(d.lsw, REC_LSW * N);
+  AL(d.fcell, F);
+  AL(d.fgeo, REC_FG * F);
   if (f32) {
-    AL(d.lsw32, 12 * N);
+    AL(d.lsw32, REC_LSW * N);
     AL(d.ivol32, N);
-    AL(d.FA32, 5 * F);
-    AL(d.fn32, 3 * F);
-    AL(d.farea32, F);
-    AL(d.fr32, 3 * F);
-    AL(d.G32, 15 * N);
+    AL(d.FA32, REC_FA32 * F);
+    AL(d.fgeo32, REC_FG * F);
+    AL(d.G32, REC_G * N);
     float *w;
-    AL(w, 5 * N);
+    AL(w, REC_W * N);
     m->W = w;
   } else {
-    AL(d.G, 15 * N);
+    AL(d.G, REC_G * N);
     double *w;
-    AL(w, 5 * N);
+    AL(w, REC_W * N);
     m->W = w;
   }
   AL(d.Un, 5 * N);
@@ -306,9 +301,9 @@ int fv_mesh_load(const double *xyz, int64_t n_nodes, const int64_t *tets, int64_
   } else {
     AL(d.Us, 5 * N);
   }
-  AL(d.FA, 5 * F);
-  AL(d.ACC, 5 * F);
-  AL(d.BND, 5 * F);
+  AL(d.FA, REC_FA * F);
+  AL(d.ACC, REC_FA * F);
+  AL(d.BND, REC_FA * F);
   AL(d.lev, N);
   AL(d.lev_tmp, N);
   AL(d.flev, F);
@@ -325,7 +320,7 @@ int fv_mesh_load(const double *xyz, int64_t n_nodes, const int64_t *tets, int64_
   AL(d.counters, 3);
   AL(m->cnt_scratch, cnt_size);
   AL(m->new2old_dev, N);
-  AL(m->FAt, 5 * F);
+  AL(m->FAt, REC_FA * F);
 #undef AL
   std::vector<int> n2o(N);
   for (size_t i = 0; i < N; ++i) n2o[i] = (int)H.new2old[i];
@@ -337,38 +332,51 @@ int fv_mesh_load(const double *xyz, int64_t n_nodes, const int64_t *tets, int64_
     for (size_t i = 0; i < N; ++i) iv[i] = 1.0 / H.vol[i];
     urc |= upload(d.ivol, iv);
   }
-  urc |= upload(d.cf, H.cf);
-  urc |= upload(d.cnb, H.cnb);
-  urc |= upload(d.cown, H.cown);
-  urc |= upload(d.lsw, H.lsw);
-  urc |= upload(d.fown, H.fown);
-  urc |= upload(d.fnb, H.fnb);
-  urc |= upload(d.fn, H.fn);
-  urc |= upload(d.farea, H.farea);
-  urc |= upload(d.fr, H.fr);
-  if (f32) {
-    std::vector<float> iv32(N);
-    for (size_t i = 0; i < N; ++i) iv32[i] = (float)(1.0 / H.vol[i]);
-    urc |= upload(d.ivol32, iv32);
-    std::vector<float> w32(12 * N);
-    for (size_t q = 0; q < 12 * N; ++q) w32[q] = (float)H.lsw[q];
-    urc |= upload(d.lsw32, w32);
-    std::vector<float> tmp(3 * F);
-    for (size_t q = 0; q < 3 * F; ++q) tmp[q] = (float)H.fn[q];
-    urc |= upload(d.fn32, tmp);
-    for (size_t q = 0; q < 3 * F; ++q) tmp[q] = (float)H.fr[q];
-    urc |= upload(d.fr32, tmp);
-    tmp.resize(F);
-    for (size_t q = 0; q < F; ++q) tmp[q] = (float)H.farea[q];
-    urc |= upload(d.farea32, tmp);
+  {
+    // records: cell faces / neighbours as int4, weights as [N][12], faces as
+    // (owner, neighbour) pairs and [F][8] geometry (n, A, r, pad)
+    std::vector<int4> cf4(N), cnb4(N);
+    std::vector<double> lsw(REC_LSW * N);
+    for (size_t i = 0; i < N; ++i) {
+      cf4[i] = make_int4(H.cf[i], H.cf[N + i], H.cf[2 * N + i], H.cf[3 * N + i]);
+      cnb4[i] = make_int4(H.cnb[i], H.cnb[N + i], H.cnb[2 * N + i], H.cnb[3 * N + i]);
+      for (int q = 0; q < REC_LSW; ++q) lsw[REC_LSW * i + q] = H.lsw[q * N + i];
+    }
+    std::vector<int2> fcell(F);
+    std::vector<double> geo(REC_FG * F);
+    for (size_t f = 0; f < F; ++f) {
+      fcell[f] = make_int2(H.fown[f], H.fnb[f]);
+      double *g = &geo[REC_FG * f];
+      for (int e = 0; e < 3; ++e) {
+        g[e] = H.fn[e * F + f];
+        g[4 + e] = H.fr[e * F + f];
+      }
+      g[3] = H.farea[f];
+      g[7] = 0.0;
+    }
+    urc |= upload(d.cf4, cf4);
+    urc |= upload(d.cnb4, cnb4);
+    urc |= upload(d.cown, H.cown);
+    urc |= upload(d.lsw, lsw);
+    urc |= upload(d.fcell, fcell);
+    urc |= upload(d.fgeo, geo);
+    if (f32) {
+      std::vector<float> iv32(N);
+      for (size_t i = 0; i < N; ++i) iv32[i] = (float)(1.0 / H.vol[i]);
+      urc |= upload(d.ivol32, iv32);
+      std::vector<float> w32(lsw.begin(), lsw.end());
+      urc |= upload(d.lsw32, w32);
+      std::vector<float> g32(geo.begin(), geo.end());
+      urc |= upload(d.fgeo32, g32);
+    }
   }
   if (urc) {
     fv_mesh_free(m);
     return FV_ERR_CUDA;
   }
   cudaError_t e = cudaSuccess;
-  e = cudaMemset(d.ACC, 0, 5 * F * sizeof(double));
-  if (e == cudaSuccess) e = cudaMemset(d.BND, 0, 5 * F * sizeof(double));
+  e = cudaMemset(d.ACC, 0, REC_FA * F * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(d.BND, 0, REC_FA * F * sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(d.Un, 0, 5 * N * sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(d.tdev, 0, sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(d.status, 0, sizeof(int));
@@ -404,8 +412,8 @@ static int set_state_impl(fv_mesh *m, const double *src_host_or_dev, int on_devi
     CKL(fvk::launch_set_cons(m->d, src, m->new2old_dev, s));
   else
     CKL(fvk::launch_set_state(m->d, src, m->new2old_dev, s));
-  CK(cudaMemsetAsync(m->d.ACC, 0, 5 * (size_t)m->d.F * sizeof(double), s));
-  CK(cudaMemsetAsync(m->d.BND, 0, 5 * (size_t)m->d.F * sizeof(double), s));
+  CK(cudaMemsetAsync(m->d.ACC, 0, REC_FA * (size_t)m->d.F * sizeof(double), s));
+  CK(cudaMemsetAsync(m->d.BND, 0, REC_FA * (size_t)m->d.F * sizeof(double), s));
   CK(cudaMemsetAsync(m->d.counters, 0, 3 * sizeof(long long), s));
   if (!on_device) CK(cudaStreamSynchronize(s));
   m->in_cycle = false;
@@ -657,14 +665,14 @@ int fv_boundary_ledger(fv_mesh *m, double *out5) {
   if (!m || !out5) return fail(FV_ERR_INVALID_ARG, "fv_boundary_ledger: NULL argument");
   CK(cudaSetDevice(m->cfg.device));
   const size_t F = m->d.F;
-  std::vector<double> bnd(5 * F);
-  std::vector<int> fnb(F);
-  CK(cudaMemcpy(bnd.data(), m->d.BND, 5 * F * sizeof(double), cudaMemcpyDeviceToHost));
-  CK(cudaMemcpy(fnb.data(), m->d.fnb, F * sizeof(int), cudaMemcpyDeviceToHost));
+  std::vector<double> bnd(REC_FA * F);
+  std::vector<int2> fc(F);
+  CK(cudaMemcpy(bnd.data(), m->d.BND, REC_FA * F * sizeof(double), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(fc.data(), m->d.fcell, F * sizeof(int2), cudaMemcpyDeviceToHost));
   for (int c = 0; c < 5; ++c) {
     double sum = 0.0;
     for (size_t f = 0; f < F; ++f)
-      if (fnb[f] < 0) sum += bnd[c * F + f];
+      if (fc[f].y < 0) sum += bnd[REC_FA * f + c];
     out5[c] = sum;
   }
   return FV_OK;

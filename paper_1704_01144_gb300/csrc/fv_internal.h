@@ -2,21 +2,27 @@
 // GB300 library (not part of the C ABI).
 //
 // Layout in HBM (N cells after Morton renumbering, F faces numbered by owner
-// cell, all structure-of-arrays so a warp's loads of one component coalesce):
-//   cells  vol[N], cf[4][N] face of local face j, cnb[4][N] neighbour across
-//          local face j (-1 wall, -2 transmissive), cown[N] bit j set when
-//          the cell owns local face j, lsw[12][N] least-squares weights
-//          (3 per local face), lev[N] temporal level
-//   faces  fown[F], fnb[F] (same boundary encoding), fn[3][F] unit normal
-//          (owner -> outside), farea[F], fr[3][F] = x_R - x_L (ghost centroid
-//          on boundary faces), flev[F]; FP32 copies fn32/farea32/fr32 for the
-//          FP32-flux mode
+// cell).  Everything a kernel gathers through an index (a neighbour's or a
+// face's cell record, a cell's face records) is a padded record read with
+// 16-byte vector loads, so one gather touches one or two 32-byte sectors;
+// what is streamed in cell order (the conserved state) is
+// structure-of-arrays.
+//   cells  vol[N], ivol[N] (ivol32 in FP32 mode), cf4[N] faces of local faces
+//          0..3, cnb4[N] neighbours across them (-1 wall, -2 transmissive),
+//          cown[N] bit j set when the cell owns local face j, lsw[N][12]
+//          least-squares weights (3 per local face; lsw32 in FP32 mode),
+//          lev[N] temporal level
+//   faces  fcell[F] = (owner, neighbour or -bc), fgeo[F][8] = (unit normal
+//          owner -> outside, area, x_R - x_L (ghost centroid on boundary
+//          faces), pad) in FP64 and fgeo32 in FP32 mode, flev[F]
 //   state  Un[5][N] (FP64), Us[5][N] predicted (FP64 mode) or Un32/Us32
 //          (FP32-flux mode: FP32 shadow of U^n and the FP32 predicted
-//          state, which only ever feeds fluxes), G[15][N] gradients (FP64)
-//          or G32[15][N] (FP32 mode), FA[5][F] predictor flux x area, then the
-//          step's flux time integral, ACC[5][F] fine-side integral on level
-//          interfaces, BND[5][F] boundary ledger
+//          state, which only ever feeds fluxes)
+//   phase  W[N][8] primitives at the phase time, G[N][16] gradients (FP64 or
+//          FP32 by mode); FA[F][6] predictor flux x area (FP64 mode; FA32
+//          [F][8] in FP32 mode), then the step's flux time integral;
+//          ACC[F][6] fine-side integral on level interfaces; BND[F][6]
+//          boundary ledger
 //   lists  cl[N] cells sorted by (level, has-finer-neighbour), coff[2L+1];
 //          fl[F] faces sorted by face level, foff[L+1]
 #pragma once
@@ -30,6 +36,13 @@
 #include "../../include/fv.h"
 
 #define FV_MAXL 8
+// record strides (elements)
+#define REC_W 8     // primitives (5 used)
+#define REC_G 16    // gradients (15 used)
+#define REC_FG 8    // face geometry: n[3], A, r[3], pad
+#define REC_FA 6    // FP64 face values (5 used)
+#define REC_FA32 8  // FP32 face values (5 used)
+#define REC_LSW 12  // least-squares weights
 #define FV_STATUS_NONPHYS 1
 #define FV_STATUS_RIEMANN 2
 
@@ -38,14 +51,14 @@ struct DevMesh {
   // cells
   double *vol, *ivol;  // volume and its reciprocal
   float *ivol32;       // FP32 reciprocal volume (FP32-flux mode predictor)
-  int *cf, *cnb;
+  int4 *cf4, *cnb4;
   uint8_t *cown;
   double *lsw;
   float *lsw32;        // FP32 copy of the weights (FP32-flux mode)
   // faces
-  int *fown, *fnb;
-  double *fn, *farea, *fr;
-  float *fn32, *farea32, *fr32;
+  int2 *fcell;
+  double *fgeo;
+  float *fgeo32;
   // state
   double *Un, *Us, *G;  // Us: predicted state (FP64 mode only)
   float *Un32, *Us32;    // FP32-flux mode: FP32 shadow of U^n, predicted state

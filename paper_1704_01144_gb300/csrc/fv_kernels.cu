@@ -13,8 +13,9 @@
 // Every phase kernel grid-strides over a range of a level-sorted list whose
 // bounds are read from device memory, so inactive levels cost a few idle
 // blocks and the launch sequence of a cycle is fixed (graph-capturable).
-// All face and cell data are structure-of-arrays; cells follow a Morton
-// curve, faces their owner cell.
+// Gathered data (cell primitive/gradient records, face geometry and flux
+// records) are padded records read with 16-byte vector loads; the state is
+// structure-of-arrays.  Cells follow a Morton curve, faces their owner cell.
 #include <cuda_runtime.h>
 
 #include "fv_internal.h"
@@ -47,6 +48,44 @@ static inline int grid_for(int64_t items, int block, int per_sm) {
   } while (0)
 
 // ------------------------------------------------------------- helpers ---
+// N-element record loads/stores with 16-byte vector accesses (records are
+// 16-byte aligned: cudaMalloc bases and strides that are multiples of 16 B)
+template <int NE>
+__device__ __forceinline__ void ldrec(const float *p, float *o) {
+  static_assert(NE % 4 == 0, "record of float4");
+#pragma unroll
+  for (int k = 0; k < NE / 4; ++k) {
+    float4 v = reinterpret_cast<const float4 *>(p)[k];
+    o[4 * k] = v.x;
+    o[4 * k + 1] = v.y;
+    o[4 * k + 2] = v.z;
+    o[4 * k + 3] = v.w;
+  }
+}
+template <int NE>
+__device__ __forceinline__ void ldrec(const double *p, double *o) {
+  static_assert(NE % 2 == 0, "record of double2");
+#pragma unroll
+  for (int k = 0; k < NE / 2; ++k) {
+    double2 v = reinterpret_cast<const double2 *>(p)[k];
+    o[2 * k] = v.x;
+    o[2 * k + 1] = v.y;
+  }
+}
+template <int NE>
+__device__ __forceinline__ void strec(float *p, const float *o) {
+#pragma unroll
+  for (int k = 0; k < NE / 4; ++k)
+    reinterpret_cast<float4 *>(p)[k] = make_float4(o[4 * k], o[4 * k + 1], o[4 * k + 2], o[4 * k + 3]);
+}
+template <int NE>
+__device__ __forceinline__ void strec(double *p, const double *o) {
+#pragma unroll
+  for (int k = 0; k < NE / 2; ++k) reinterpret_cast<double2 *>(p)[k] = make_double2(o[2 * k], o[2 * k + 1]);
+}
+__device__ __forceinline__ int nbr_of(const int4 &v, int j) {
+  return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w;
+}
 template <typename T>
 __device__ __forceinline__ void cons_to_prim(const T U[5], T gm1, T W[5]) {
   T r = U[0];
@@ -95,7 +134,7 @@ __device__ __forceinline__ float minmod(float a, float b) {
 // the same number as a plain FP64 host evaluation of the same formula:
 // temporal levels are integer decisions taken on it.
 __global__ void __launch_bounds__(256) k_dt(DevMesh d) {
-  const size_t N = d.N, F = d.F;
+  const size_t N = d.N;
   double local_min = __longlong_as_double(0x7ff0000000000000LL);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x) {
     double r = d.Un[i];
@@ -104,12 +143,14 @@ __global__ void __launch_bounds__(256) k_dt(DevMesh d) {
     double p = __dmul_rn(d.gamma - 1.0, __dsub_rn(d.Un[4 * N + i], __ddiv_rn(__dmul_rn(0.5, mm), r)));
     double rc = __dsqrt_rn(__dmul_rn(__dmul_rn(d.gamma, p), r));
     double S = 0.0;
+    int4 cf = d.cf4[i];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      int f = d.cf[j * N + i];
-      double mn = __dadd_rn(__dadd_rn(__dmul_rn(mx, d.fn[f]), __dmul_rn(my, d.fn[F + f])),
-                            __dmul_rn(mz, d.fn[2 * F + f]));
-      S = __dadd_rn(S, __dmul_rn(d.farea[f], __dadd_rn(fabs(mn), rc)));
+      const double *g = d.fgeo + (size_t)nbr_of(cf, j) * REC_FG;
+      double2 n01 = reinterpret_cast<const double2 *>(g)[0];
+      double2 n2A = reinterpret_cast<const double2 *>(g)[1];
+      double mn = __dadd_rn(__dadd_rn(__dmul_rn(mx, n01.x), __dmul_rn(my, n01.y)), __dmul_rn(mz, n2A.x));
+      S = __dadd_rn(S, __dmul_rn(n2A.y, __dadd_rn(fabs(mn), rc)));
     }
     double dt = __ddiv_rn(__dmul_rn(__dmul_rn(__dmul_rn(2.0, d.cfl), d.vol[i]), r), S);
     if (!(p > 0.0) || !(r > 0.0) || !isfinite(dt)) {
@@ -149,12 +190,12 @@ __global__ void __launch_bounds__(256) k_levels0(DevMesh d, int L) {
 // fixed point (the result is min_j (k0_j + graph distance), and k0 <= L-1)
 __global__ void __launch_bounds__(256) k_smooth(DevMesh d, const int8_t *__restrict__ src,
                                                 int8_t *__restrict__ dst) {
-  const size_t N = d.N;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x) {
     int k = src[i];
+    int4 nb4 = d.cnb4[i];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      int nb = d.cnb[j * N + i];
+      int nb = nbr_of(nb4, j);
       if (nb >= 0) k = min(k, src[nb] + 1);
     }
     dst[i] = (int8_t)k;
@@ -165,13 +206,13 @@ __global__ void __launch_bounds__(256) k_smooth(DevMesh d, const int8_t *__restr
 // cells a phase touches are contiguous: levels <= tau followed by the
 // level-(tau+1) cells next to level tau
 __global__ void __launch_bounds__(256) k_cell_keys(DevMesh d) {
-  const size_t N = d.N;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x) {
     int k = d.lev[i];
     int finer = 0;
+    int4 nb4 = d.cnb4[i];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      int nb = d.cnb[j * N + i];
+      int nb = nbr_of(nb4, j);
       if (nb >= 0 && d.lev[nb] < k) finer = 1;
     }
     d.ckey[i] = (uint8_t)(2 * k + (finer ? 0 : 1));
@@ -181,9 +222,9 @@ __global__ void __launch_bounds__(256) k_cell_keys(DevMesh d) {
 // face level = min of the two cell levels; faces sort by it
 __global__ void __launch_bounds__(256) k_face_keys(DevMesh d) {
   for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < d.F; f += gridDim.x * blockDim.x) {
-    int a = d.lev[d.fown[f]];
-    int nb = d.fnb[f];
-    int k = nb >= 0 ? min(a, (int)d.lev[nb]) : a;
+    int2 fc = d.fcell[f];
+    int a = d.lev[fc.x];
+    int k = fc.y >= 0 ? min(a, (int)d.lev[fc.y]) : a;
     d.flev[f] = (int8_t)k;
     d.fkey[f] = (uint8_t)k;
   }
@@ -333,19 +374,20 @@ __device__ __forceinline__ void to_prim(const float U[5], double gm1, float W[5]
 }
 
 // primitives of the cells of list range [coff[b0], coff[b1]) at the phase
-// time: W[5][N] in FP64 (FP64 mode) or FP32 (FP32-flux mode, no FP64 work)
+// time into their W record: FP64 (FP64 mode) or FP32 (FP32-flux mode, no FP64
+// work)
 template <typename WT>
 __global__ void __launch_bounds__(256) k_prim(DevMesh d, const __grid_constant__ PhaseLevels pl, int b0, int b1, WT *W) {
-  const size_t N = d.N;
   int beg = d.coff[b0], end = d.coff[b1];
   double gm1 = d.gamma - 1.0;
   for (int idx = beg + blockIdx.x * blockDim.x + threadIdx.x; idx < end; idx += gridDim.x * blockDim.x) {
     int i = d.cl[idx];
-    WT U[5], Wt[5];
+    WT U[5], Wt[REC_W];
     load_state(d, pl, i, U);
     to_prim(U, gm1, Wt);
 #pragma unroll
-    for (int q = 0; q < 5; ++q) W[q * N + i] = Wt[q];
+    for (int q = 5; q < REC_W; ++q) Wt[q] = WT(0);
+    strec<REC_W>(W + (size_t)i * REC_W, Wt);
   }
 }
 
@@ -354,78 +396,81 @@ __global__ void __launch_bounds__(256) k_prim(DevMesh d, const __grid_constant__
 template <typename T>
 __global__ void __launch_bounds__(256) k_grad(DevMesh d, int b0, int b1, const T *__restrict__ W,
                                               T *__restrict__ G, const T *__restrict__ lsw,
-                                              const T *__restrict__ fn) {
-  const size_t N = d.N, F = d.F;
+                                              const T *__restrict__ fgeo) {
   int beg = d.coff[b0], end = d.coff[b1];
   for (int idx = beg + blockIdx.x * blockDim.x + threadIdx.x; idx < end; idx += gridDim.x * blockDim.x) {
     int i = d.cl[idx];
-    T Wi[5], g[15];
+    T Wi[REC_W], g[REC_G], w[REC_LSW];
+    ldrec<REC_W>(W + (size_t)i * REC_W, Wi);
+    ldrec<REC_LSW>(lsw + (size_t)i * REC_LSW, w);
+    int4 nb4 = d.cnb4[i];
 #pragma unroll
-    for (int q = 0; q < 5; ++q) Wi[q] = W[q * N + i];
-#pragma unroll
-    for (int q = 0; q < 15; ++q) g[q] = T(0);
+    for (int q = 0; q < REC_G; ++q) g[q] = T(0);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      int nb = d.cnb[j * N + i];
-      T Wn[5];
+      int nb = nbr_of(nb4, j);
+      T Wn[REC_W];
       if (nb >= 0) {
-#pragma unroll
-        for (int q = 0; q < 5; ++q) Wn[q] = W[q * N + nb];
+        ldrec<REC_W>(W + (size_t)nb * REC_W, Wn);
       } else {
 #pragma unroll
         for (int q = 0; q < 5; ++q) Wn[q] = Wi[q];
         if (nb == -FV_BC_WALL) {
-          int f = d.cf[j * N + i];
-          T n0 = fn[f], n1 = fn[F + f], n2 = fn[2 * F + f];
+          const T *gf = fgeo + (size_t)nbr_of(d.cf4[i], j) * REC_FG;
+          T n0 = gf[0], n1 = gf[1], n2 = gf[2];
           T un = (Wi[1] * n0 + Wi[2] * n1) + Wi[3] * n2;
           Wn[1] = Wi[1] - (T(2) * un) * n0;
           Wn[2] = Wi[2] - (T(2) * un) * n1;
           Wn[3] = Wi[3] - (T(2) * un) * n2;
         }
       }
-      T w0 = lsw[(3 * j) * N + i], w1 = lsw[(3 * j + 1) * N + i], w2 = lsw[(3 * j + 2) * N + i];
 #pragma unroll
       for (int c = 0; c < 5; ++c) {
         T dd = Wn[c] - Wi[c];
-        g[3 * c] += w0 * dd;
-        g[3 * c + 1] += w1 * dd;
-        g[3 * c + 2] += w2 * dd;
+        g[3 * c] += w[3 * j] * dd;
+        g[3 * c + 1] += w[3 * j + 1] * dd;
+        g[3 * c + 2] += w[3 * j + 2] * dd;
       }
     }
-#pragma unroll
-    for (int q = 0; q < 15; ++q) G[q * N + i] = g[q];
+    strec<REC_G>(G + (size_t)i * REC_G, g);
   }
 }
 
-// face flux of face f from the phase-time primitives W and gradients G:
-// F A in FA_out[5] (FP64).  Returns a nonzero status on Riemann failure.
+// face flux of face f from the phase-time primitive and gradient records:
+// F A in FA[5].  Returns a nonzero status on Riemann failure.
 template <typename T, bool G14>
 __device__ __forceinline__ int face_flux(const DevMesh &d, const GasT<T> &G, const T *__restrict__ W,
-                                         const T *__restrict__ Gr, const T *__restrict__ fn,
-                                         const T *__restrict__ fr, const T *__restrict__ farea, int f,
+                                         const T *__restrict__ Gr, const T *__restrict__ fgeo, int f,
                                          T FA[5]) {
-  const size_t N = d.N, Fn = d.F;
-  int L = d.fown[f], R = d.fnb[f];
-  T n[3] = {fn[f], fn[Fn + f], fn[2 * Fn + f]};
-  T r[3] = {fr[f], fr[Fn + f], fr[2 * Fn + f]};
-  T WL[5], WR[5], Fx[5];
+  int2 fc = d.fcell[f];
+  const int L = fc.x, R = fc.y;
+  T geo[REC_FG];
+  ldrec<REC_FG>(fgeo + (size_t)f * REC_FG, geo);
+  const T n[3] = {geo[0], geo[1], geo[2]};
+  const T A = geo[3];
+  const T r[3] = {geo[4], geo[5], geo[6]};
+  T Wi[REC_W], gi[REC_G], WL[5], WR[5], Fx[5];
+  ldrec<REC_W>(W + (size_t)L * REC_W, Wi);
+  ldrec<REC_G>(Gr + (size_t)L * REC_G, gi);
   int it, rc;
   if (R >= 0) {
+    T Wj[REC_W], gj[REC_G];
+    ldrec<REC_W>(W + (size_t)R * REC_W, Wj);
+    ldrec<REC_G>(Gr + (size_t)R * REC_G, gj);
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
-      T wi = W[c * N + L], wj = W[c * N + R];
-      T dW = wj - wi;
-      T gir = (Gr[(3 * c) * N + L] * r[0] + Gr[(3 * c + 1) * N + L] * r[1]) + Gr[(3 * c + 2) * N + L] * r[2];
-      T gjr = (Gr[(3 * c) * N + R] * r[0] + Gr[(3 * c + 1) * N + R] * r[1]) + Gr[(3 * c + 2) * N + R] * r[2];
-      WL[c] = wi + T(0.5) * minmod(T(2) * gir - dW, dW);
-      WR[c] = wj - T(0.5) * minmod(T(2) * gjr - dW, dW);
+      T dW = Wj[c] - Wi[c];
+      T gir = (gi[3 * c] * r[0] + gi[3 * c + 1] * r[1]) + gi[3 * c + 2] * r[2];
+      T gjr = (gj[3 * c] * r[0] + gj[3 * c + 1] * r[1]) + gj[3 * c + 2] * r[2];
+      WL[c] = Wi[c] + T(0.5) * minmod(T(2) * gir - dW, dW);
+      WR[c] = Wj[c] - T(0.5) * minmod(T(2) * gjr - dW, dW);
     }
     rc = godunov_flux<T, G14>(G, WL, WR, n, Fx, it);
   } else {
     // reconstruct toward the ghost (mirror image of the cell in the face)
-    T Wi[5], Wg[5];
+    T Wg[5];
 #pragma unroll
-    for (int c = 0; c < 5; ++c) Wi[c] = Wg[c] = W[c * N + L];
+    for (int c = 0; c < 5; ++c) Wg[c] = Wi[c];
     if (R == -FV_BC_WALL) {
       T un = (Wi[1] * n[0] + Wi[2] * n[1]) + Wi[3] * n[2];
 #pragma unroll
@@ -434,12 +479,11 @@ __device__ __forceinline__ int face_flux(const DevMesh &d, const GasT<T> &G, con
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
       T dW = Wg[c] - Wi[c];
-      T gir = (Gr[(3 * c) * N + L] * r[0] + Gr[(3 * c + 1) * N + L] * r[1]) + Gr[(3 * c + 2) * N + L] * r[2];
+      T gir = (gi[3 * c] * r[0] + gi[3 * c + 1] * r[1]) + gi[3 * c + 2] * r[2];
       WL[c] = Wi[c] + T(0.5) * minmod(T(2) * gir - dW, dW);
     }
     rc = boundary_flux<T, G14>(G, -R, WL, n, Fx, it);
   }
-  T A = farea[f];
 #pragma unroll
   for (int c = 0; c < 5; ++c) FA[c] = Fx[c] * A;
   return rc;
@@ -460,37 +504,49 @@ __device__ __forceinline__ float flip(float v, bool neg) {
 // a level interface Phi is added to ACC[f] (the coarse side's integral), on a
 // boundary face to BND[f] (the conservation ledger).
 template <typename T, bool G14>
-__global__ void __launch_bounds__(128) k_flux(DevMesh d, GasT<T> G, int stage, int level, int b0,
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 4) k_flux(DevMesh d, GasT<T> G, int stage, int level, int b0,
                                               int b1, const T *__restrict__ W, const T *__restrict__ Gr,
-                                              const T *__restrict__ fn, const T *__restrict__ fr,
-                                              const T *__restrict__ farea) {
-  const size_t F = d.F;
+                                              const T *__restrict__ fgeo) {
   const bool f32 = sizeof(T) == 4;
   int beg = d.foff[b0], end = d.foff[b1];
   double h = 0.5 * ldexp(__longlong_as_double((long long)*d.dtmin_bits), level);
   for (int idx = beg + blockIdx.x * blockDim.x + threadIdx.x; idx < end; idx += gridDim.x * blockDim.x) {
     int f = d.fl[idx];
     T FAt[5];
-    int rc = face_flux<T, G14>(d, G, W, Gr, fn, fr, farea, f, FAt);
+    int rc = face_flux<T, G14>(d, G, W, Gr, fgeo, f, FAt);
     if (rc) atomicOr(d.status, FV_STATUS_RIEMANN);
     if (stage == 1) {
-#pragma unroll
-      for (int c = 0; c < 5; ++c) {
-        if (f32)
-          d.FA32[c * F + f] = (float)FAt[c];
-        else
-          d.FA[c * F + f] = (double)FAt[c];
+      if (f32) {
+        float v[REC_FA32] = {(float)FAt[0], (float)FAt[1], (float)FAt[2], (float)FAt[3], (float)FAt[4], 0.f, 0.f, 0.f};
+        strec<REC_FA32>(d.FA32 + (size_t)f * REC_FA32, v);
+      } else {
+        double v[REC_FA] = {(double)FAt[0], (double)FAt[1], (double)FAt[2], (double)FAt[3], (double)FAt[4], 0.0};
+        strec<REC_FA>(d.FA + (size_t)f * REC_FA, v);
       }
     } else {
-      int R = d.fnb[f];
-      bool iface = R >= 0 && d.lev[d.fown[f]] != d.lev[R];
+      int2 fc = d.fcell[f];
+      bool iface = fc.y >= 0 && d.lev[fc.x] != d.lev[fc.y];
+      double phi[REC_FA];
+      if (f32) {
+        float a[REC_FA32];
+        ldrec<REC_FA32>(d.FA32 + (size_t)f * REC_FA32, a);
 #pragma unroll
-      for (int c = 0; c < 5; ++c) {
-        double sum = f32 ? (double)(d.FA32[c * F + f] + (float)FAt[c]) : d.FA[c * F + f] + (double)FAt[c];
-        double phi = h * sum;
-        d.FA[c * F + f] = phi;
-        if (iface) d.ACC[c * F + f] += phi;
-        if (R < 0) d.BND[c * F + f] += phi;
+        for (int c = 0; c < 5; ++c) phi[c] = h * (double)(a[c] + (float)FAt[c]);
+      } else {
+        double a[REC_FA];
+        ldrec<REC_FA>(d.FA + (size_t)f * REC_FA, a);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) phi[c] = h * (a[c] + (double)FAt[c]);
+      }
+      phi[5] = 0.0;
+      strec<REC_FA>(d.FA + (size_t)f * REC_FA, phi);
+      if (iface || fc.y < 0) {
+        double *dst = (iface ? d.ACC : d.BND) + (size_t)f * REC_FA;
+        double acc[REC_FA];
+        ldrec<REC_FA>(dst, acc);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) acc[c] += phi[c];
+        strec<REC_FA>(dst, acc);
       }
     }
   }
@@ -507,24 +563,23 @@ __global__ void __launch_bounds__(128) k_flux(DevMesh d, GasT<T> G, int stage, i
 // (fv_status), not here.
 template <bool F32>
 __global__ void __launch_bounds__(256) k_update(DevMesh d, int stage, int level, int b0, int b1) {
-  const size_t N = d.N, F = d.F;
+  const size_t N = d.N;
   int beg = d.coff[b0], end = d.coff[b1];
   double dtmin = __longlong_as_double((long long)*d.dtmin_bits);
   float dtmin32 = (float)dtmin;
   for (int idx = beg + blockIdx.x * blockDim.x + threadIdx.x; idx < end; idx += gridDim.x * blockDim.x) {
     int i = d.cl[idx];
     unsigned own = d.cown[i];
+    int4 cf = d.cf4[i];
     if (stage == 1 && F32) {
       float S[5];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        int f = d.cf[j * N + i];
         bool neg = !((own >> j) & 1u);
+        float v[REC_FA32];
+        ldrec<REC_FA32>(d.FA32 + (size_t)nbr_of(cf, j) * REC_FA32, v);
 #pragma unroll
-        for (int c = 0; c < 5; ++c) {
-          float v = flip(d.FA32[c * F + f], neg);
-          S[c] = j == 0 ? v : S[c] + v;
-        }
+        for (int c = 0; c < 5; ++c) S[c] = j == 0 ? flip(v[c], neg) : S[c] + flip(v[c], neg);
       }
       float cdt = -ldexpf(dtmin32, (int)d.lev[i]) * d.ivol32[i];
 #pragma unroll
@@ -534,21 +589,19 @@ __global__ void __launch_bounds__(256) k_update(DevMesh d, int stage, int level,
     double S[5];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      int f = d.cf[j * N + i];
+      int f = nbr_of(cf, j);
       bool neg = !((own >> j) & 1u);
-      bool acc = stage == 2 && d.flev[f] != level;
-#pragma unroll
-      for (int c = 0; c < 5; ++c) {
-        double v;
-        if (acc) {
-          v = d.ACC[c * F + f];
-          d.ACC[c * F + f] = 0.0;
-        } else {
-          v = d.FA[c * F + f];
-        }
-        v = flip(v, neg);
-        S[c] = j == 0 ? v : S[c] + v;
+      double v[REC_FA];
+      if (stage == 2 && d.flev[f] != level) {
+        double *a = d.ACC + (size_t)f * REC_FA;
+        ldrec<REC_FA>(a, v);
+        const double z[REC_FA] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        strec<REC_FA>(a, z);
+      } else {
+        ldrec<REC_FA>(d.FA + (size_t)f * REC_FA, v);
       }
+#pragma unroll
+      for (int c = 0; c < 5; ++c) S[c] = j == 0 ? flip(v[c], neg) : S[c] + flip(v[c], neg);
     }
     double iV = d.ivol[i];
     if (stage == 1) {
@@ -589,7 +642,7 @@ int launch_check_state(const DevMesh &d, cudaStream_t s) {
 // written in the caller's order
 __global__ void __launch_bounds__(256) k_residual(DevMesh d, int level, const double *__restrict__ FAt,
                                                   double *__restrict__ R, const int *__restrict__ new2old) {
-  const size_t N = d.N, F = d.F;
+  const size_t N = d.N;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x) {
     int o = new2old[i];
     if (d.lev[i] != level) {
@@ -598,13 +651,15 @@ __global__ void __launch_bounds__(256) k_residual(DevMesh d, int level, const do
       continue;
     }
     unsigned own = d.cown[i];
-    double S[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    int4 cf = d.cf4[i];
+    double S[5];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      int f = d.cf[j * N + i];
-      double s = ((own >> j) & 1u) ? 1.0 : -1.0;
+      bool neg = !((own >> j) & 1u);
+      double v[REC_FA];
+      ldrec<REC_FA>(FAt + (size_t)nbr_of(cf, j) * REC_FA, v);
 #pragma unroll
-      for (int c = 0; c < 5; ++c) S[c] += s * FAt[c * F + f];
+      for (int c = 0; c < 5; ++c) S[c] = j == 0 ? flip(v[c], neg) : S[c] + flip(v[c], neg);
     }
     double iV = d.ivol[i];
 #pragma unroll
@@ -615,37 +670,33 @@ __global__ void __launch_bounds__(256) k_residual(DevMesh d, int level, const do
 // F A of every face touching a level-`level` cell into FAt (residual hook)
 template <typename T, bool G14>
 __global__ void __launch_bounds__(128) k_flux_all(DevMesh d, GasT<T> G, int level, const T *__restrict__ W,
-                                                  const T *__restrict__ Gr, const T *__restrict__ fn,
-                                                  const T *__restrict__ fr, const T *__restrict__ farea,
+                                                  const T *__restrict__ Gr, const T *__restrict__ fgeo,
                                                   double *__restrict__ FAt) {
-  const size_t F = d.F;
   for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < d.F; f += gridDim.x * blockDim.x) {
-    int R = d.fnb[f];
-    bool touch = d.lev[d.fown[f]] == level || (R >= 0 && d.lev[R] == level);
+    int2 fc = d.fcell[f];
+    bool touch = d.lev[fc.x] == level || (fc.y >= 0 && d.lev[fc.y] == level);
     if (!touch) continue;
     T FAx[5];
-    if (face_flux<T, G14>(d, G, W, Gr, fn, fr, farea, f, FAx)) atomicOr(d.status, FV_STATUS_RIEMANN);
-#pragma unroll
-    for (int c = 0; c < 5; ++c) FAt[c * F + f] = (double)FAx[c];
+    if (face_flux<T, G14>(d, G, W, Gr, fgeo, f, FAx)) atomicOr(d.status, FV_STATUS_RIEMANN);
+    double v[REC_FA] = {(double)FAx[0], (double)FAx[1], (double)FAx[2], (double)FAx[3], (double)FAx[4], 0.0};
+    strec<REC_FA>(FAt + (size_t)f * REC_FA, v);
   }
 }
 
-// primitives / gradients of every cell (residual hook: a plain, unsorted pass)
+// primitives of every cell (residual hook: a plain, unsorted pass)
 template <typename WT>
 __global__ void __launch_bounds__(256) k_prim_all(DevMesh d, const __grid_constant__ PhaseLevels pl, WT *W) {
-  const size_t N = d.N;
   double gm1 = d.gamma - 1.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x) {
-    WT U[5], Wt[5];
+    WT U[5], Wt[REC_W];
     load_state(d, pl, i, U);
     to_prim(U, gm1, Wt);
 #pragma unroll
-    for (int q = 0; q < 5; ++q) W[q * N + i] = Wt[q];
+    for (int q = 5; q < REC_W; ++q) Wt[q] = WT(0);
+    strec<REC_W>(W + (size_t)i * REC_W, Wt);
   }
 }
 
-// end of a cycle: t += 2^theta dt_min, and the work counters of the cost
-// model: sum_k 2^(theta-k) |Omega_k| cell updates, twice that over faces
 __global__ void k_time_advance(DevMesh d, int theta) {
   d.tdev[0] += ldexp(__longlong_as_double((long long)*d.dtmin_bits), theta);
   long long cu = 0, fe = 0;
@@ -815,23 +866,23 @@ int launch_phase(const DevMesh &d, int precision, const PhaseLevels &pl, int sta
     double *W = (double *)Wbuf;
     GasT<double> G = GasT<double>::make(d.gamma, d.tol, d.maxit);
     { ProfScope sc(ph, FV_PROF_PRIM, s); k_prim<double><<<gc, 256, 0, s>>>(d, pl, pb0, pb1, W); }
-    { ProfScope sc(ph, FV_PROF_GRAD, s); k_grad<double><<<gc, 256, 0, s>>>(d, gb0, gb1, W, d.G, d.lsw, d.fn); }
+    { ProfScope sc(ph, FV_PROF_GRAD, s); k_grad<double><<<gc, 256, 0, s>>>(d, gb0, gb1, W, d.G, d.lsw, d.fgeo); }
     { ProfScope sc(ph, FV_PROF_FLUX, s);
       if (d.gamma == 1.4)
-        k_flux<double, true><<<gfx, 128, 0, s>>>(d, G, stage, level, fb0, fb1, W, d.G, d.fn, d.fr, d.farea);
+        k_flux<double, true><<<gfx, 128, 0, s>>>(d, G, stage, level, fb0, fb1, W, d.G, d.fgeo);
       else
-        k_flux<double, false><<<gfx, 128, 0, s>>>(d, G, stage, level, fb0, fb1, W, d.G, d.fn, d.fr, d.farea); }
+        k_flux<double, false><<<gfx, 128, 0, s>>>(d, G, stage, level, fb0, fb1, W, d.G, d.fgeo); }
   } else {
     float *W = (float *)Wbuf;
     double tol32 = d.tol > 2e-6 ? d.tol : 2e-6;
     GasT<float> G = GasT<float>::make(d.gamma, tol32, d.maxit);
     { ProfScope sc(ph, FV_PROF_PRIM, s); k_prim<float><<<gc, 256, 0, s>>>(d, pl, pb0, pb1, W); }
-    { ProfScope sc(ph, FV_PROF_GRAD, s); k_grad<float><<<gc, 256, 0, s>>>(d, gb0, gb1, W, d.G32, d.lsw32, d.fn32); }
+    { ProfScope sc(ph, FV_PROF_GRAD, s); k_grad<float><<<gc, 256, 0, s>>>(d, gb0, gb1, W, d.G32, d.lsw32, d.fgeo32); }
     { ProfScope sc(ph, FV_PROF_FLUX, s);
       if (d.gamma == 1.4)
-        k_flux<float, true><<<gfx, 128, 0, s>>>(d, G, stage, level, fb0, fb1, W, d.G32, d.fn32, d.fr32, d.farea32);
+        k_flux<float, true><<<gfx, 128, 0, s>>>(d, G, stage, level, fb0, fb1, W, d.G32, d.fgeo32);
       else
-        k_flux<float, false><<<gfx, 128, 0, s>>>(d, G, stage, level, fb0, fb1, W, d.G32, d.fn32, d.fr32, d.farea32); }
+        k_flux<float, false><<<gfx, 128, 0, s>>>(d, G, stage, level, fb0, fb1, W, d.G32, d.fgeo32); }
   }
   { ProfScope sc(ph, FV_PROF_UPDATE, s);
     if (precision == FV_FP64)
@@ -851,21 +902,21 @@ int launch_residual(const DevMesh &d, int precision, const PhaseLevels &pl, int 
     GasT<double> G = GasT<double>::make(d.gamma, d.tol, d.maxit);
     k_prim_all<double><<<gc, 256, 0, s>>>(d, pl, W);
     // gradients of every cell: the list range covering all cells
-    k_grad<double><<<gc, 256, 0, s>>>(d, 0, 2 * d.L, W, d.G, d.lsw, d.fn);
+    k_grad<double><<<gc, 256, 0, s>>>(d, 0, 2 * d.L, W, d.G, d.lsw, d.fgeo);
     if (d.gamma == 1.4)
-      k_flux_all<double, true><<<gfx, 128, 0, s>>>(d, G, level, W, d.G, d.fn, d.fr, d.farea, FAt);
+      k_flux_all<double, true><<<gfx, 128, 0, s>>>(d, G, level, W, d.G, d.fgeo, FAt);
     else
-      k_flux_all<double, false><<<gfx, 128, 0, s>>>(d, G, level, W, d.G, d.fn, d.fr, d.farea, FAt);
+      k_flux_all<double, false><<<gfx, 128, 0, s>>>(d, G, level, W, d.G, d.fgeo, FAt);
   } else {
     float *W = (float *)Wbuf;
     double tol32 = d.tol > 2e-6 ? d.tol : 2e-6;
     GasT<float> G = GasT<float>::make(d.gamma, tol32, d.maxit);
     k_prim_all<float><<<gc, 256, 0, s>>>(d, pl, W);
-    k_grad<float><<<gc, 256, 0, s>>>(d, 0, 2 * d.L, W, d.G32, d.lsw32, d.fn32);
+    k_grad<float><<<gc, 256, 0, s>>>(d, 0, 2 * d.L, W, d.G32, d.lsw32, d.fgeo32);
     if (d.gamma == 1.4)
-      k_flux_all<float, true><<<gfx, 128, 0, s>>>(d, G, level, W, d.G32, d.fn32, d.fr32, d.farea32, FAt);
+      k_flux_all<float, true><<<gfx, 128, 0, s>>>(d, G, level, W, d.G32, d.fgeo32, FAt);
     else
-      k_flux_all<float, false><<<gfx, 128, 0, s>>>(d, G, level, W, d.G32, d.fn32, d.fr32, d.farea32, FAt);
+      k_flux_all<float, false><<<gfx, 128, 0, s>>>(d, G, level, W, d.G32, d.fgeo32, FAt);
   }
   k_residual<<<gc, 256, 0, s>>>(d, level, FAt, R, new2old);
   FV_LAUNCH_CHECK();
