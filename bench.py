@@ -37,17 +37,69 @@ WORKLOADS = {
     "sod": (None, 1),
 }
 
-# Algorithmic bytes per face evaluation of the flux kernel (unique bytes the
-# method must move; each cell's primitives and gradients are shared by its 4
-# faces, so a face carries half a cell's worth):
-#   list index 4 + owner/neighbour 8 + geometry (n, r, A) + FA write 40
-#   + half a cell (W + G) ; corrector adds the FA read (40) and 2 level bytes.
+# Algorithmic bytes per unit of the two dominant kernels (unique bytes the
+# method must move, independent of record padding; each cell's primitives and
+# gradients are shared by its 4 faces, so a face carries half a cell's worth;
+# a face value is read by its 2 cells, so a cell carries half of each of its
+# 4 faces' values):
+#  k_flux, per face evaluation: list index 4 + face cells 8 + geometry
+#    (n, A, r) 28/56 + flux record write 20/40 + half a cell's W + G 40/80;
+#    the corrector adds the predictor flux read 20/40, the FP64 integral write
+#    40 (FP32 mode) and 2 level bytes.
+#  k_update, per cell update (predictor + corrector): list 4 + faces 16 +
+#    owner bits 1 + level 1 + face values 4 x 20/40 / 2 + reciprocal volume
+#    4/8 + U^n read 20/40 (FP32 shadow / FP64) + U* write 20/40; corrector:
+#    4 + 16 + 1 + 4 face levels + 4 x 40 / 2 + 8 + U^n 40 read + 40 write
+#    (+ 20 FP32 shadow write).
 def flux_bytes_per_eval(fp32: bool) -> float:
-    geom = 28 if fp32 else 56
-    cell = (20 + 60) if fp32 else (40 + 120)
-    predictor = 4 + 8 + geom + 40 + cell / 2
-    corrector = predictor + 40 + 2
+    if fp32:
+        predictor = 4 + 8 + 28 + 20 + 40
+        corrector = 4 + 8 + 28 + 20 + 40 + 40 + 2
+    else:
+        predictor = 4 + 8 + 56 + 40 + 80
+        corrector = 4 + 8 + 56 + 40 + 40 + 80 + 2
     return 0.5 * (predictor + corrector)
+
+
+def update_bytes_per_cell_update(fp32: bool) -> float:
+    if fp32:
+        predictor = 4 + 16 + 1 + 1 + 40 + 4 + 20 + 20
+        corrector = 4 + 16 + 1 + 4 + 80 + 8 + 40 + 40 + 20
+    else:
+        predictor = 4 + 16 + 1 + 1 + 80 + 8 + 40 + 40
+        corrector = 4 + 16 + 1 + 4 + 80 + 8 + 40 + 40
+    return predictor + corrector
+
+
+KERNEL_SOURCES = ["paper_1704_01144_gb300/csrc/fv_kernels.cu",
+                  "paper_1704_01144_gb300/csrc/fv_riemann.cuh",
+                  "paper_1704_01144_gb300/csrc/fv_internal.h"]
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic():
+    """DRAM bytes per unit from the committed ncu summary, when it was taken
+    on the current kernel sources (else None: the counters are stale)."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic_blast1m.md")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as fh:
+        for ln in fh:
+            if ln.startswith("    ") and ":" in ln:
+                k, v = ln.strip().split(":", 1)
+                vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha256_16") != kernel_source_hash():
+        return None
+    return vals
 
 
 def launches_per_cycle(L: int) -> int:
@@ -289,19 +341,51 @@ def main_ours(args):
             e2e["value"] = float(vals[:, 2].sum())
 
     peaks, peak_src = _load_peaks()
+    alu_peaks = {"fp64_tflops": fv.fv_probe_fma_peak(fv.FV_FP64, local),
+                 "fp32_tflops": fv.fv_probe_fma_peak(fv.FV_FP32_FLUX, local),
+                 "derived_fp64_tflops": 152 * 2 * 2 * 2.07e9 / 1e12,
+                 "derived_fp32_tflops": 152 * 128 * 2 * 2.07e9 / 1e12}
 
-    def roofline(r, fp32):
-        ms, n = r["prof"]["flux"]
+    traffic = measured_traffic()
+
+    def roofline(r, fp32, kernel):
+        ms, n = r["prof"][kernel]
         if n == 0 or ms <= 0:
             return None
-        bpe = flux_bytes_per_eval(fp32)
-        achieved = r["prof_face_evals"] * bpe / (ms * 1e-3) / 1e9
+        if kernel == "flux":
+            units, bpu, tkey = r["prof_face_evals"], flux_bytes_per_eval(fp32), "flux"
+        else:
+            units, bpu, tkey = r["prof_cell_updates"], update_bytes_per_cell_update(fp32), "update"
+        achieved = units * bpu / (ms * 1e-3) / 1e9
         peak = float(peaks["hbm_gbs"])
-        return {"bound": "hbm", "kernel": "k_flux", "achieved": round(achieved, 1),
-                "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
-                "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)",
-                "bytes_per_face_eval": bpe,
-                "avg_launch_ms": ms / n, "launches": n}
+        tr = None
+        if traffic is not None:
+            key = f"{tkey}_{'fp32' if fp32 else 'fp64'}_dram_bytes_per_unit"
+            if key in traffic:
+                tr = round(float(traffic[key]) * units / n)
+        return {"bound": "hbm", "kernel": f"k_{kernel}", "achieved": round(achieved, 1),
+                "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": tr, "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)",
+                "algorithmic_bytes_per_unit": bpu,
+                "unit_counted": "face evaluation" if kernel == "flux" else "cell update",
+                "units_per_launch": round(units / n, 1), "avg_launch_ms": ms / n, "launches": n}
+
+    def dominant(r, fp32):
+        k = max(("flux", "update"), key=lambda q: r["prof"][q][0])
+        return roofline(r, fp32, k)
+
+    def fp64_alu(r):
+        """FP64 flux kernel against the FP64 pipe: executed FP64 flops per face
+        evaluation from the committed ncu op counts (DFMA = 2, DADD/DMUL = 1)."""
+        if traffic is None or "flux_fp64_fp64_flops_per_unit" not in traffic:
+            return None
+        ms, n = r["prof"]["flux"]
+        fl = float(traffic["flux_fp64_fp64_flops_per_unit"]) * r["prof_face_evals"]
+        achieved = fl / (ms * 1e-3) / 1e12
+        return {"bound": "alu", "kernel": "k_flux (FP64)", "achieved": round(achieved, 4),
+                "peak": round(alu_peaks["fp64_tflops"], 4), "unit": "TFLOP/s",
+                "frac": round(achieved / alu_peaks["fp64_tflops"], 4),
+                "peak_source": "measured FP64 FMA probe (fv_probe_fma_peak)"}
 
     def kernel_shares(r):
         tot = sum(v[0] for v in r["prof"].values())
@@ -325,14 +409,18 @@ def main_ours(args):
             "dtype": "f32 flux / f64 state", "data": "synthetic (seeded graded tet mesh, blast wave)",
             "config": desc,
             "clocks": chosen["clocks"],
-            "roofline": roofline(chosen, "fp32flux" in res),
+            "roofline": dominant(chosen, "fp32flux" in res),
+            "roofline_kernels": {k: roofline(chosen, "fp32flux" in res, k) for k in ("flux", "update")},
+            "alu_peaks_measured": alu_peaks,
+            "kernel_source_sha256_16": kernel_source_hash(),
             "e2e": e2e,
             "gpu_launches": launches_per_cycle(L) * args.steps,
             "cpu_baseline": cpu,
             "plain_fp64": None if "fp64" not in res else {
                 "value": round(res["fp64"]["value"], 1), "unit": "cell-updates/s",
                 "ms_per_step": round(res["fp64"]["ms_per_step"], 4),
-                "roofline": roofline(res["fp64"], False),
+                "roofline": dominant(res["fp64"], False),
+                "roofline_alu": fp64_alu(res["fp64"]),
                 "kernels": kernel_shares(res["fp64"]),
                 "clocks": res["fp64"]["clocks"]},
             "kernels": kernel_shares(chosen),

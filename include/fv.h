@@ -260,6 +260,14 @@ int fv_godunov_flux_batch(const double *WL_dev, const double *WR_dev, const doub
                           int64_t count, const fv_config *cfg, int bc, double *F_dev,
                           int32_t *iters_dev, void *stream);
 
+/*
+ * Measured fused-multiply-add ceiling of the device in TFLOP/s (2 flops per
+ * FMA): precision FV_FP64 or FV_FP32_FLUX (FP32).  Runs a timed probe
+ * kernel (well under a second); synchronous.  The denominator of the
+ * roofline of ALU-bound kernels.
+ */
+int fv_probe_fma_peak(int device, int precision, double *tflops_out);
+
 /* Largest n_cells fv_assign_levels_noalloc accepts (its static scratch). */
 #define FV_NOALLOC_MAX_CELLS (1 << 22)
 

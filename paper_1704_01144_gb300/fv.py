@@ -57,7 +57,7 @@ EXPORTS = [
     "fv_cell_volumes", "fv_status", "fv_last_error", "fv_version", "fv_set_conserved",
     "fv_work_counters", "fv_use_graph", "fv_profile_enable", "fv_profile_read",
     "fv_get_level_lists", "fv_get_local_dt", "fv_assign_levels_noalloc",
-    "fv_godunov_flux_batch",
+    "fv_godunov_flux_batch", "fv_probe_fma_peak",
 ]
 
 FV_NOALLOC_MAX_CELLS = 1 << 22
@@ -112,6 +112,7 @@ def lib():
     L.fv_profile_enable.argtypes = [vp, C.c_int]
     L.fv_profile_read.argtypes = [vp, dp, C.POINTER(C.c_int64)]
     L.fv_get_local_dt.argtypes = [vp, dp]
+    L.fv_probe_fma_peak.argtypes = [C.c_int, C.c_int, dp]
     L.fv_godunov_flux_batch.argtypes = [vp, vp, vp, i64, C.POINTER(fv_config), C.c_int, vp, vp, vp]
     L.fv_assign_levels_noalloc.argtypes = [vp, vp, i64, C.c_int, vp, vp, vp]
     L.fv_get_level_lists.argtypes = [vp, C.POINTER(C.c_int64), i32p, i8p, i32p]
@@ -298,6 +299,13 @@ def fv_godunov_flux_batch(WL, WR, nrm, cfg: fv_config, bc=FV_BC_INTERIOR, F=None
                                        n, C.byref(cfg), int(bc), _dptr(F), _dptr(iters, "int32"),
                                        _stream(stream)), "fv_godunov_flux_batch")
     return F, iters
+
+
+def fv_probe_fma_peak(precision, device=0) -> float:
+    """Measured FMA ceiling (TFLOP/s) in FP64 (FV_FP64) or FP32."""
+    t = C.c_double()
+    _check(lib().fv_probe_fma_peak(int(device), int(precision), C.byref(t)), "fv_probe_fma_peak")
+    return t.value
 
 
 def fv_get_levels(h):
