@@ -246,6 +246,29 @@ int fv_profile_enable(fv_mesh *m, int enable);
 int fv_profile_read(fv_mesh *m, double ms_out[FV_PROF_N], int64_t launches_out[FV_PROF_N]);
 
 /*
+ * Batches: many meshes of uneven sizes and level counts advanced together.
+ * Each mesh keeps its own schedule (Alg. 2 with its own L, dt_min and
+ * levels); a batch cycle lasts 2^(Lmax-1) batch subiterations, during which a
+ * mesh with L levels completes 2^(Lmax-L) of its own cycles.  Every kernel
+ * launch covers all meshes (one per kernel kind and phase; level assignment
+ * batched over the meshes starting a cycle), and on a non-legacy stream the
+ * whole batch cycle is captured once and replayed as one CUDA graph.
+ * Results are bitwise those of each mesh advanced on its own.
+ *
+ * fv_batch_create: 1..64 distinct meshes sharing device, precision, gamma
+ * and Newton settings; the batch references (does not own) them and their
+ * states must be set.  fv_batch_advance: n_cycles batch cycles, asynchronous
+ * on `stream`; a mesh inside a cycle of its own is FV_ERR_INVALID_ARG.
+ * fv_batch_info: subiterations per batch cycle and kernels per batch cycle.
+ */
+typedef struct fv_batch fv_batch;
+int fv_batch_create(fv_mesh *const *meshes, int n, fv_batch **out);
+int fv_batch_advance(fv_batch *b, int n_cycles, void *stream);
+int fv_batch_info(fv_batch *b, int *subiterations, int *kernel_launches);
+int fv_batch_use_graph(fv_batch *b, int enable);
+void fv_batch_free(fv_batch *b);
+
+/*
  * The device Godunov flux (Sec. 2.1) on a batch of face states, for tests
  * and data harvesting: for i < count, with primitives WL_dev/WR_dev
  * [5*count] = (rho, u, v, w, p) and unit normals n_dev[3*count]

@@ -47,48 +47,10 @@ int cuda_fail(cudaError_t e, const char *what) {
                                          cudaGetErrorString(cudaGetLastError())); \
   } while (0)
 
-struct Phase {
-  int kind;   // 0 begin, 1 end
-  int level;  // tau(s) for begin, k for end
-  int64_t T;  // time in dt_min units from the cycle start
-};
-
-std::vector<Phase> make_phases(int theta) {
-  std::vector<Phase> out;
-  int nsub = 1 << theta;
-  for (int s = 1; s <= nsub; ++s) {
-    int tau = 0;
-    for (int tmp = 1; tmp <= theta; ++tmp)
-      if ((s - 1) % (1 << tmp) == 0) tau = tmp;
-    out.push_back({0, tau, (int64_t)(s - 1)});
-    for (int k = 0; k <= theta && s % (1 << k) == 0; ++k) out.push_back({1, k, (int64_t)s});
-  }
-  return out;
-}
-
 }  // namespace
 
 void fv_internal_set_error(const std::string &msg) { t_err = msg; }
 
-struct fv_mesh {
-  fv_config cfg;
-  DevMesh d;
-  int L = 1, theta = 0;
-  int *new2old_dev = nullptr;  // Morton index -> caller's index
-  void *W = nullptr;           // phase-time primitives (FP64 or FP32)
-  double *FAt = nullptr;       // residual-hook scratch (REC_FA x F; also host staging)
-  int *cnt_scratch = nullptr;  // level-sort counts
-  std::vector<Phase> phases;
-  bool in_cycle = false;
-  int next_phase = 0;
-  int64_t tn[FV_MAXL];
-  bool pred[FV_MAXL];
-  std::vector<void *> allocs;
-  ProfHook prof;
-  bool use_graph = true;
-  cudaGraphExec_t cycle_graph = nullptr;
-  bool have_dt = false;
-};
 
 namespace {
 
@@ -112,54 +74,11 @@ int upload(T *dst, const std::vector<T> &src) {
   return FV_OK;
 }
 
-PhaseLevels levels_at(const fv_mesh *m, int64_t T) {
-  PhaseLevels pl;
-  for (int j = 0; j < FV_MAXL; ++j) {
-    pl.w[j] = 0.0;
-    pl.mode[j] = 0;
-    if (j >= m->L) continue;
-    int64_t dd = T - m->tn[j];
-    int64_t span = (int64_t)1 << j;
-    if (dd <= 0 || dd > span || !m->pred[j]) continue;  // U^n (or not needed)
-    if (dd == span) {
-      pl.mode[j] = 1;
-    } else {
-      pl.mode[j] = 2;
-      pl.w[j] = (double)dd / (double)span;
-    }
-  }
-  return pl;
-}
-
-int run_phase(fv_mesh *m, const Phase &ph, cudaStream_t s) {
-  const int L = m->L;
-  const int nb = 2 * L;
-  auto cl = [nb](int b) { return b < 0 ? 0 : (b > nb ? nb : b); };
-  auto fclip = [L](int b) { return b < 0 ? 0 : (b > L ? L : b); };
-  PhaseLevels pl = levels_at(m, ph.T);
-  int rc;
-  if (ph.kind == 0) {
-    int tau = ph.level;
-    rc = fvk::launch_phase(m->d, m->cfg.precision, pl, 1, tau,
-                           0, cl(2 * (tau + 3)),          // prim: levels <= tau+2
-                           0, cl(2 * tau + 3),            // grad: levels <= tau + halo
-                           0, fclip(tau + 1),             // faces of level <= tau
-                           0, cl(2 * tau + 2),            // cells of level <= tau
-                           m->W, &m->prof, s);
-    if (rc) return fail(rc, "phase launch failed");
-    for (int j = 0; j <= tau; ++j) m->pred[j] = true;
-  } else {
-    int k = ph.level;
-    rc = fvk::launch_phase(m->d, m->cfg.precision, pl, 2, k,
-                           cl(2 * (k - 1)), cl(2 * (k + 3)),  // prim: levels k-1..k+2
-                           cl(2 * k), cl(2 * k + 3),          // grad: level k + halo of k+1
-                           fclip(k), fclip(k + 1),            // faces of level k
-                           cl(2 * k), cl(2 * k + 2),          // cells of level k
-                           m->W, &m->prof, s);
-    if (rc) return fail(rc, "phase launch failed");
-    m->tn[k] = ph.T;
-    m->pred[k] = false;
-  }
+int run_phase(fv_mesh *m, const SchedPhase &ph, cudaStream_t s) {
+  PhaseDesc pd = phase_desc(m->L, m->tn, m->pred, ph);
+  int rc = fvk::launch_phase(m->d, pd, &m->prof, s);
+  if (rc) return fail(rc, "phase launch failed");
+  phase_apply(m->tn, m->pred, ph);
   return FV_OK;
 }
 
@@ -250,6 +169,7 @@ int fv_mesh_load(const double *xyz, int64_t n_nodes, const int64_t *tets, int64_
   m->L = cfg->max_levels;
   m->theta = m->L - 1;
   m->phases = make_phases(m->theta);
+  m->d.sort_cnt = nullptr;
   DevMesh &d = m->d;
   memset(&d, 0, sizeof d);
   const size_t N = H.N, F = H.F;
@@ -260,6 +180,7 @@ int fv_mesh_load(const double *xyz, int64_t n_nodes, const int64_t *tets, int64_
   d.cfl = cfg->cfl;
   d.tol = cfg->newton_tol;
   d.maxit = cfg->newton_max_iter;
+  d.precision = cfg->precision;
   const bool f32 = cfg->precision == FV_FP32_FLUX;
   const int nblk_c = (int)((N + 1023) / 1024), nblk_f = (int)((F + 1023) / 1024);
   size_t cnt_size = (size_t)16 * (nblk_c > nblk_f ? nblk_c : nblk_f) + 16;
@@ -288,11 +209,13 @@ int fv_mesh_load(const double *xyz, int64_t n_nodes, const int64_t *tets, int64_
     float *w;
     AL(w, REC_W * N);
     m->W = w;
+    d.W = w;
   } else {
     AL(d.G, REC_G * N);
     double *w;
     AL(w, REC_W * N);
     m->W = w;
+    d.W = w;
   }
   AL(d.Un, 5 * N);
   if (f32) {
@@ -319,6 +242,7 @@ int fv_mesh_load(const double *xyz, int64_t n_nodes, const int64_t *tets, int64_
   AL(d.status, 1);
   AL(d.counters, 3);
   AL(m->cnt_scratch, cnt_size);
+  d.sort_cnt = m->cnt_scratch;
   AL(m->new2old_dev, N);
   AL(m->FAt, REC_FA * F);
 #undef AL
@@ -528,7 +452,7 @@ int fv_residual_level(fv_mesh *m, int level, int stage, double *R_soa_dev, void 
     if (dd < 0 || dd > ((int64_t)1 << j) || (dd > 0 && !m->pred[j]))
       return fail(FV_ERR_INVALID_ARG, "fv_residual_level: states not available at that time");
   }
-  PhaseLevels pl = levels_at(m, T);
+  PhaseLevels pl = levels_at(m->L, m->tn, m->pred, T);
   int rc = fvk::launch_residual(m->d, m->cfg.precision, pl, level, m->W, m->FAt, R_soa_dev,
                                 m->new2old_dev, s);
   if (rc) return fail(rc, "residual launch failed");

@@ -30,6 +30,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -75,6 +76,9 @@ struct DevMesh {
   double *tdev;           // physical time
   int *status;            // sticky status bits
   long long *counters;    // [0] cycles, [1] weighted cell updates, [2] face evaluations
+  // phase scratch: primitives at the phase time (FP64 or FP32 records)
+  void *W;
+  int precision;
   // physics
   double gamma, cfl, tol;
   int maxit;
@@ -86,6 +90,106 @@ struct PhaseLevels {
   double w[FV_MAXL];
   int mode[FV_MAXL];
 };
+
+// What one phase does on one mesh: the kind of update (stage 1 begins the
+// levels 0..level, stage 2 ends the step of `level`), the view of every level
+// at the phase time, and the bucket ranges of the level-sorted lists each
+// kernel covers (cells: coff buckets [b0, b1); faces: foff buckets).
+struct PhaseDesc {
+  PhaseLevels pl;
+  int stage, level;
+  int pb0, pb1;  // primitives
+  int gb0, gb1;  // gradients
+  int fb0, fb1;  // faces
+  int ub0, ub1;  // cell updates
+  int active;    // 0: the mesh sits this phase out (batches)
+  int end_cycle; // 1: the mesh's cycle ends with this phase (batches)
+};
+
+#define FV_MAXB 64  // instances per batch
+
+// ---- host schedule of one cycle (Alg. 2 lines 4-9) -------------------
+// kind 0: begin levels 0..level at T; kind 1: end the step of `level` at T
+struct SchedPhase {
+  int kind;
+  int level;
+  int64_t T;  // time in dt_min units from the cycle start
+};
+
+inline std::vector<SchedPhase> make_phases(int theta) {
+  std::vector<SchedPhase> out;
+  int nsub = 1 << theta;
+  for (int s = 1; s <= nsub; ++s) {
+    int tau = 0;
+    for (int tmp = 1; tmp <= theta; ++tmp)
+      if ((s - 1) % (1 << tmp) == 0) tau = tmp;
+    out.push_back({0, tau, (int64_t)(s - 1)});
+    for (int k = 0; k <= theta && s % (1 << k) == 0; ++k) out.push_back({1, k, (int64_t)s});
+  }
+  return out;
+}
+
+// the view of every level at time T from each level's step start tn and
+// whether its predicted state exists
+inline PhaseLevels levels_at(int L, const int64_t *tn, const bool *pred, int64_t T) {
+  PhaseLevels pl;
+  for (int j = 0; j < FV_MAXL; ++j) {
+    pl.w[j] = 0.0;
+    pl.mode[j] = 0;
+    if (j >= L) continue;
+    int64_t dd = T - tn[j];
+    int64_t span = (int64_t)1 << j;
+    if (dd <= 0 || dd > span || !pred[j]) continue;  // U^n (or not needed)
+    if (dd == span) {
+      pl.mode[j] = 1;
+    } else {
+      pl.mode[j] = 2;
+      pl.w[j] = (double)dd / (double)span;
+    }
+  }
+  return pl;
+}
+
+// what a phase covers: begin(tau) -> primitives of levels <= tau+2,
+// gradients of levels <= tau plus the level-(tau+1) cells next to level tau,
+// faces of level <= tau, updates of levels <= tau; end(k) -> primitives of
+// levels k-1..k+2, gradients of level k plus the halo of k+1, faces of level
+// k, updates of level k (cell buckets: 2 level + no-finer-neighbour)
+inline PhaseDesc phase_desc(int L, const int64_t *tn, const bool *pred, const SchedPhase &ph) {
+  const int nb = 2 * L;
+  auto cl = [nb](int b) { return b < 0 ? 0 : (b > nb ? nb : b); };
+  auto fclip = [L](int b) { return b < 0 ? 0 : (b > L ? L : b); };
+  PhaseDesc pd;
+  memset(&pd, 0, sizeof pd);
+  pd.pl = levels_at(L, tn, pred, ph.T);
+  pd.active = 1;
+  pd.level = ph.level;
+  if (ph.kind == 0) {
+    int tau = ph.level;
+    pd.stage = 1;
+    pd.pb0 = 0; pd.pb1 = cl(2 * (tau + 3));
+    pd.gb0 = 0; pd.gb1 = cl(2 * tau + 3);
+    pd.fb0 = 0; pd.fb1 = fclip(tau + 1);
+    pd.ub0 = 0; pd.ub1 = cl(2 * tau + 2);
+  } else {
+    int k = ph.level;
+    pd.stage = 2;
+    pd.pb0 = cl(2 * (k - 1)); pd.pb1 = cl(2 * (k + 3));
+    pd.gb0 = cl(2 * k); pd.gb1 = cl(2 * k + 3);
+    pd.fb0 = fclip(k); pd.fb1 = fclip(k + 1);
+    pd.ub0 = cl(2 * k); pd.ub1 = cl(2 * k + 2);
+  }
+  return pd;
+}
+
+inline void phase_apply(int64_t *tn, bool *pred, const SchedPhase &ph) {
+  if (ph.kind == 0) {
+    for (int j = 0; j <= ph.level; ++j) pred[j] = true;
+  } else {
+    tn[ph.level] = ph.T;
+    pred[ph.level] = false;
+  }
+}
 
 // host-side mesh preprocessing result (fv_host.cpp)
 struct HostMesh {
@@ -141,13 +245,40 @@ struct ProfScope {
   }
 };
 
+// a mesh handle (C ABI type fv_mesh)
+struct fv_mesh {
+  fv_config cfg;
+  DevMesh d;
+  int L = 1, theta = 0;
+  int *new2old_dev = nullptr;  // Morton index -> caller's index
+  void *W = nullptr;           // phase-time primitives (FP64 or FP32)
+  double *FAt = nullptr;       // residual-hook scratch (REC_FA x F; also host staging)
+  int *cnt_scratch = nullptr;  // level-sort counts
+  std::vector<SchedPhase> phases;
+  bool in_cycle = false;
+  int next_phase = 0;
+  int64_t tn[FV_MAXL];
+  bool pred[FV_MAXL];
+  std::vector<void *> allocs;
+  ProfHook prof;
+  bool use_graph = true;
+  cudaGraphExec_t cycle_graph = nullptr;
+  bool have_dt = false;
+  bool in_batch = false;       // owned by a batch's schedule while advancing
+};
+
 // kernels (fv_kernels.cu)
 namespace fvk {
 void init_device_info();
 int launch_assign_levels(const DevMesh &d, int L, int *cnt_scratch, ProfHook *ph, cudaStream_t s);
-int launch_phase(const DevMesh &d, int precision, const PhaseLevels &pl, int stage, int level,
-                 int pb0, int pb1, int gb0, int gb1, int fb0, int fb1, int ub0, int ub1, void *Wbuf,
-                 ProfHook *ph, cudaStream_t s);
+int launch_phase(const DevMesh &d, const PhaseDesc &pd, ProfHook *ph, cudaStream_t s);
+// batches: ms/pds are device arrays of n meshes / descriptors of one phase
+int launch_phase_multi(const DevMesh *ms, const PhaseDesc *pds, int n, const DevMesh &d0,
+                       int64_t max_cells, int64_t max_faces, cudaStream_t s);
+int launch_assign_multi(const DevMesh *ms, const int *active, int n, int Lmax, int64_t max_cells,
+                        int64_t max_faces, int64_t max_cell_blocks, int64_t max_face_blocks,
+                        int *cnt_scratch, const int *blk_pref_c, const int *blk_pref_f, cudaStream_t s);
+int launch_time_advance_multi(const DevMesh *ms, const PhaseDesc *pds, int n, cudaStream_t s);
 int launch_residual(const DevMesh &d, int precision, const PhaseLevels &pl, int level, void *Wbuf,
                     double *FAt, double *R, const int *new2old, cudaStream_t s);
 int launch_time_advance(const DevMesh &d, int theta, cudaStream_t s);

@@ -18,6 +18,8 @@
 // structure-of-arrays.  Cells follow a Morton curve, faces their owner cell.
 #include <cuda_runtime.h>
 
+#include <cstring>
+
 #include "fv_internal.h"
 #include "fv_riemann.cuh"
 
@@ -133,124 +135,150 @@ __device__ __forceinline__ float minmod(float a, float b) {
 // (no fused multiply-add) in the fixed order j = 0..3, so that it is bitwise
 // the same number as a plain FP64 host evaluation of the same formula:
 // temporal levels are integer decisions taken on it.
-__global__ void __launch_bounds__(256) k_dt(DevMesh d) {
+__device__ __forceinline__ double local_dt_of(const DevMesh &d, int i) {
   const size_t N = d.N;
-  double local_min = __longlong_as_double(0x7ff0000000000000LL);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x) {
-    double r = d.Un[i];
-    double mx = d.Un[N + i], my = d.Un[2 * N + i], mz = d.Un[3 * N + i];
-    double mm = __dadd_rn(__dadd_rn(__dmul_rn(mx, mx), __dmul_rn(my, my)), __dmul_rn(mz, mz));
-    double p = __dmul_rn(d.gamma - 1.0, __dsub_rn(d.Un[4 * N + i], __ddiv_rn(__dmul_rn(0.5, mm), r)));
-    double rc = __dsqrt_rn(__dmul_rn(__dmul_rn(d.gamma, p), r));
-    double S = 0.0;
-    int4 cf = d.cf4[i];
+  double r = d.Un[i];
+  double mx = d.Un[N + i], my = d.Un[2 * N + i], mz = d.Un[3 * N + i];
+  double mm = __dadd_rn(__dadd_rn(__dmul_rn(mx, mx), __dmul_rn(my, my)), __dmul_rn(mz, mz));
+  double p = __dmul_rn(d.gamma - 1.0, __dsub_rn(d.Un[4 * N + i], __ddiv_rn(__dmul_rn(0.5, mm), r)));
+  double rc = __dsqrt_rn(__dmul_rn(__dmul_rn(d.gamma, p), r));
+  double S = 0.0;
+  int4 cf = d.cf4[i];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const double *g = d.fgeo + (size_t)nbr_of(cf, j) * REC_FG;
-      double2 n01 = reinterpret_cast<const double2 *>(g)[0];
-      double2 n2A = reinterpret_cast<const double2 *>(g)[1];
-      double mn = __dadd_rn(__dadd_rn(__dmul_rn(mx, n01.x), __dmul_rn(my, n01.y)), __dmul_rn(mz, n2A.x));
-      S = __dadd_rn(S, __dmul_rn(n2A.y, __dadd_rn(fabs(mn), rc)));
-    }
-    double dt = __ddiv_rn(__dmul_rn(__dmul_rn(__dmul_rn(2.0, d.cfl), d.vol[i]), r), S);
-    if (!(p > 0.0) || !(r > 0.0) || !isfinite(dt)) {
-      atomicOr(d.status, FV_STATUS_NONPHYS);
-      dt = __longlong_as_double(0x7ff0000000000000LL);
-    }
-    d.dt[i] = dt;
-    local_min = fmin(local_min, dt);
+  for (int j = 0; j < 4; ++j) {
+    const double *g = d.fgeo + (size_t)nbr_of(cf, j) * REC_FG;
+    double2 n01 = reinterpret_cast<const double2 *>(g)[0];
+    double2 n2A = reinterpret_cast<const double2 *>(g)[1];
+    double mn = __dadd_rn(__dadd_rn(__dmul_rn(mx, n01.x), __dmul_rn(my, n01.y)), __dmul_rn(mz, n2A.x));
+    S = __dadd_rn(S, __dmul_rn(n2A.y, __dadd_rn(fabs(mn), rc)));
   }
-  // block minimum, then one atomic per block on the bit pattern (positive
-  // doubles order like their bit patterns): order-independent, exact
-  __shared__ double sm[8];
+  double dt = __ddiv_rn(__dmul_rn(__dmul_rn(__dmul_rn(2.0, d.cfl), d.vol[i]), r), S);
+  if (!(p > 0.0) || !(r > 0.0) || !isfinite(dt)) {
+    atomicOr(d.status, FV_STATUS_NONPHYS);
+    dt = __longlong_as_double(0x7ff0000000000000LL);
+  }
+  d.dt[i] = dt;
+  return dt;
+}
+
+// block minimum, then one atomic per block on the bit pattern (positive
+// doubles order like their bit patterns): order-independent, exact.  Every
+// thread of the block must call it.
+__device__ __forceinline__ void block_min_to(double local_min, unsigned long long *bits) {
+  __shared__ double sm[32];
   for (int o = 16; o > 0; o >>= 1) local_min = fmin(local_min, __shfl_xor_sync(0xffffffff, local_min, o));
   if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = local_min;
   __syncthreads();
   if (threadIdx.x < 32) {
     double v = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : __longlong_as_double(0x7ff0000000000000LL);
     for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffff, v, o));
-    if (threadIdx.x == 0) atomicMin(d.dtmin_bits, (unsigned long long)__double_as_longlong(v));
+    if (threadIdx.x == 0) atomicMin(bits, (unsigned long long)__double_as_longlong(v));
   }
+}
+
+__global__ void __launch_bounds__(256) k_dt(DevMesh d) {
+  double local_min = __longlong_as_double(0x7ff0000000000000LL);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x)
+    local_min = fmin(local_min, local_dt_of(d, i));
+  block_min_to(local_min, d.dtmin_bits);
 }
 
 __global__ void k_init_min(unsigned long long *bits) { *bits = 0x7ff0000000000000ULL; }
 
 // k_i = max{k <= L-1 : 2^k dt_min <= dt_i}
-__global__ void __launch_bounds__(256) k_levels0(DevMesh d, int L) {
+__device__ __forceinline__ int8_t level0_of(const DevMesh &d, double dtmin, int i) {
+  double dt = d.dt[i];
+  int k = 0;
+  while (k + 1 < d.L && ldexp(dtmin, k + 1) <= dt) ++k;
+  return (int8_t)k;
+}
+
+__global__ void __launch_bounds__(256) k_levels0(DevMesh d) {
   double dtmin = __longlong_as_double((long long)*d.dtmin_bits);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x) {
-    double dt = d.dt[i];
-    int k = 0;
-    while (k + 1 < L && ldexp(dtmin, k + 1) <= dt) ++k;
-    d.lev_tmp[i] = (int8_t)k;
-  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x)
+    d.lev_tmp[i] = level0_of(d, dtmin, i);
 }
 
 // one Jacobi sweep of k_i <- min(k_i, 1 + min_j k_j); L-1 sweeps reach the
 // fixed point (the result is min_j (k0_j + graph distance), and k0 <= L-1)
+__device__ __forceinline__ int8_t smooth_of(const DevMesh &d, const int8_t *src, int i) {
+  int k = src[i];
+  int4 nb4 = d.cnb4[i];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    int nb = nbr_of(nb4, j);
+    if (nb >= 0) k = min(k, src[nb] + 1);
+  }
+  return (int8_t)k;
+}
+
 __global__ void __launch_bounds__(256) k_smooth(DevMesh d, const int8_t *__restrict__ src,
                                                 int8_t *__restrict__ dst) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x) {
-    int k = src[i];
-    int4 nb4 = d.cnb4[i];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      int nb = nbr_of(nb4, j);
-      if (nb >= 0) k = min(k, src[nb] + 1);
-    }
-    dst[i] = (int8_t)k;
-  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x)
+    dst[i] = smooth_of(d, src, i);
 }
 
 // cell sort key: 2 level + (1 unless a neighbour is one level finer), so the
 // cells a phase touches are contiguous: levels <= tau followed by the
 // level-(tau+1) cells next to level tau
-__global__ void __launch_bounds__(256) k_cell_keys(DevMesh d) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x) {
-    int k = d.lev[i];
-    int finer = 0;
-    int4 nb4 = d.cnb4[i];
+__device__ __forceinline__ uint8_t cell_key_of(const DevMesh &d, int i) {
+  int k = d.lev[i];
+  int finer = 0;
+  int4 nb4 = d.cnb4[i];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      int nb = nbr_of(nb4, j);
-      if (nb >= 0 && d.lev[nb] < k) finer = 1;
-    }
-    d.ckey[i] = (uint8_t)(2 * k + (finer ? 0 : 1));
+  for (int j = 0; j < 4; ++j) {
+    int nb = nbr_of(nb4, j);
+    if (nb >= 0 && d.lev[nb] < k) finer = 1;
   }
+  return (uint8_t)(2 * k + (finer ? 0 : 1));
+}
+
+__global__ void __launch_bounds__(256) k_cell_keys(DevMesh d) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x)
+    d.ckey[i] = cell_key_of(d, i);
 }
 
 // face level = min of the two cell levels; faces sort by it
-__global__ void __launch_bounds__(256) k_face_keys(DevMesh d) {
-  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < d.F; f += gridDim.x * blockDim.x) {
-    int2 fc = d.fcell[f];
-    int a = d.lev[fc.x];
-    int k = fc.y >= 0 ? min(a, (int)d.lev[fc.y]) : a;
-    d.flev[f] = (int8_t)k;
-    d.fkey[f] = (uint8_t)k;
-  }
+__device__ __forceinline__ void face_key_of(const DevMesh &d, int f) {
+  int2 fc = d.fcell[f];
+  int a = d.lev[fc.x];
+  int k = fc.y >= 0 ? min(a, (int)d.lev[fc.y]) : a;
+  d.flev[f] = (int8_t)k;
+  d.fkey[f] = (uint8_t)k;
 }
 
-// ---- stable counting sort of small keys (< 16 buckets), 1024 items per block
+__global__ void __launch_bounds__(256) k_face_keys(DevMesh d) {
+  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < d.F; f += gridDim.x * blockDim.x)
+    face_key_of(d, f);
+}
+
+// ---- stable counting sort of small keys (< 16 buckets), 1024 items per tile
 #define SORT_TILE 1024
 #define SORT_THREADS 256
 
-__global__ void __launch_bounds__(SORT_THREADS) k_sort_hist(const uint8_t *__restrict__ key, int n,
-                                                            int nb, int *cnt) {
+// per-tile bucket counts -> cnt[bucket * nblk + tile]
+__device__ __forceinline__ void sort_hist_tile(const uint8_t *__restrict__ key, int n, int nb, int *cnt,
+                                               int tile, int nblk) {
   __shared__ int h[16];
   if (threadIdx.x < 16) h[threadIdx.x] = 0;
   __syncthreads();
-  int base = blockIdx.x * SORT_TILE;
+  int base = tile * SORT_TILE;
   for (int r = 0; r < SORT_TILE / SORT_THREADS; ++r) {
     int i = base + r * SORT_THREADS + threadIdx.x;
     if (i < n) atomicAdd(&h[key[i]], 1);
   }
   __syncthreads();
-  if (threadIdx.x < nb) cnt[threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
+  if (threadIdx.x < nb) cnt[threadIdx.x * nblk + tile] = h[threadIdx.x];
 }
 
-// exclusive scan over the bucket-major (bucket, block) counts; also writes
-// the bucket offsets off[0..nb]
-__global__ void __launch_bounds__(1024) k_sort_scan(int *cnt, int total, int nblk, int nb, int *off) {
+__global__ void __launch_bounds__(SORT_THREADS) k_sort_hist(const uint8_t *__restrict__ key, int n,
+                                                            int nb, int *cnt) {
+  sort_hist_tile(key, n, nb, cnt, blockIdx.x, gridDim.x);
+}
+
+// exclusive scan over the bucket-major (bucket, tile) counts by one block of
+// 1024 threads; also writes the bucket offsets off[0..nb]
+__device__ __forceinline__ void sort_scan_block(int *cnt, int total, int nblk, int nb, int *off) {
   __shared__ int warp_sums[32];
   __shared__ int carry;
   if (threadIdx.x == 0) carry = 0;
@@ -258,7 +286,6 @@ __global__ void __launch_bounds__(1024) k_sort_scan(int *cnt, int total, int nbl
   for (int base = 0; base < total; base += 1024) {
     int i = base + threadIdx.x;
     int v = i < total ? cnt[i] : 0;
-    // inclusive warp scan
     int x = v;
     for (int o = 1; o < 32; o <<= 1) {
       int y = __shfl_up_sync(0xffffffff, x, o);
@@ -288,20 +315,25 @@ __global__ void __launch_bounds__(1024) k_sort_scan(int *cnt, int total, int nbl
   if (threadIdx.x == 0) off[nb] = carry;
 }
 
-__global__ void __launch_bounds__(SORT_THREADS) k_sort_scatter(const uint8_t *__restrict__ key, int n,
-                                                               int nb, const int *__restrict__ cnt,
-                                                               int *__restrict__ out) {
+__global__ void __launch_bounds__(1024) k_sort_scan(int *cnt, int total, int nblk, int nb, int *off) {
+  sort_scan_block(cnt, total, nblk, nb, off);
+}
+
+// stable scatter of one tile: lanes with equal keys rank in lane (= item)
+// order, warps in order, earlier rounds first
+__device__ __forceinline__ void sort_scatter_tile(const uint8_t *__restrict__ key, int n, int nb,
+                                                  const int *__restrict__ cnt, int *__restrict__ out,
+                                                  int tile, int nblk) {
   __shared__ int wcount[SORT_THREADS / 32][16];
   __shared__ int run[16];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (threadIdx.x < 16) run[threadIdx.x] = threadIdx.x < nb ? cnt[threadIdx.x * gridDim.x + blockIdx.x] : 0;
-  int base = blockIdx.x * SORT_TILE;
+  if (threadIdx.x < 16) run[threadIdx.x] = threadIdx.x < nb ? cnt[threadIdx.x * nblk + tile] : 0;
+  int base = tile * SORT_TILE;
   for (int r = 0; r < SORT_TILE / SORT_THREADS; ++r) {
     int i = base + r * SORT_THREADS + threadIdx.x;
     int k = i < n ? (int)key[i] : -1;
     if (lane < 16) wcount[warp][lane] = 0;
     __syncthreads();
-    // lanes with equal keys: rank among them in lane (= item) order
     unsigned mask = __match_any_sync(0xffffffff, k);
     int rank = __popc(mask & ((1u << lane) - 1));
     if (k >= 0 && rank == 0) wcount[warp][k] = __popc(mask);
@@ -319,6 +351,106 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort_scatter(const uint8_t *__
     }
     __syncthreads();
   }
+}
+
+__global__ void __launch_bounds__(SORT_THREADS) k_sort_scatter(const uint8_t *__restrict__ key, int n,
+                                                               int nb, const int *__restrict__ cnt,
+                                                               int *__restrict__ out) {
+  sort_scatter_tile(key, n, nb, cnt, out, blockIdx.x, gridDim.x);
+}
+
+// ---- batched level assignment: block b of a grid covering every instance's
+// tiles maps to (instance, tile) through a prefix over per-instance tile
+// counts; blocks of instances that do not start a cycle return at once
+struct MultiTiles {
+  const DevMesh *ms;
+  const int *active;  // per instance
+  const int *tpref;   // n+1 prefix of tile counts (cells or faces, 1024 per tile)
+  int n;
+};
+
+__device__ __forceinline__ bool tile_of(const MultiTiles &a, int &inst, int &tile) {
+  __shared__ int s_inst, s_tile;
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = a.n;
+    while (hi - lo > 1) {
+      int mid = (lo + hi) >> 1;
+      if (a.tpref[mid] <= (int)blockIdx.x) lo = mid; else hi = mid;
+    }
+    s_inst = lo;
+    s_tile = (int)blockIdx.x - a.tpref[lo];
+  }
+  __syncthreads();
+  inst = s_inst;
+  tile = s_tile;
+  return a.active[inst] != 0 && (int)blockIdx.x < a.tpref[a.n];
+}
+
+__global__ void k_init_min_multi(const DevMesh *ms, const int *active, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && active[i]) *ms[i].dtmin_bits = 0x7ff0000000000000ULL;
+}
+
+__global__ void __launch_bounds__(256) k_dt_multi(MultiTiles a) {
+  int inst, tile;
+  if (!tile_of(a, inst, tile)) return;
+  const DevMesh &d = a.ms[inst];
+  double m = __longlong_as_double(0x7ff0000000000000LL);
+  for (int i = tile * SORT_TILE + threadIdx.x; i < min(d.N, (tile + 1) * SORT_TILE); i += blockDim.x)
+    m = fmin(m, local_dt_of(d, i));
+  block_min_to(m, d.dtmin_bits);
+}
+
+// op 0: levels0; 1: copy lev_tmp -> lev; 2: sweep lev_tmp -> lev;
+// 3: sweep lev -> lev_tmp; 4: cell keys
+__global__ void __launch_bounds__(256) k_cells_multi(MultiTiles a, int op) {
+  int inst, tile;
+  if (!tile_of(a, inst, tile)) return;
+  const DevMesh &d = a.ms[inst];
+  double dtmin = __longlong_as_double((long long)*d.dtmin_bits);
+  for (int i = tile * SORT_TILE + threadIdx.x; i < min(d.N, (tile + 1) * SORT_TILE); i += blockDim.x) {
+    if (op == 0) d.lev_tmp[i] = level0_of(d, dtmin, i);
+    else if (op == 1) d.lev[i] = d.lev_tmp[i];
+    else if (op == 2) d.lev[i] = smooth_of(d, d.lev_tmp, i);
+    else if (op == 3) d.lev_tmp[i] = smooth_of(d, d.lev, i);
+    else d.ckey[i] = cell_key_of(d, i);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_face_keys_multi(MultiTiles a) {
+  int inst, tile;
+  if (!tile_of(a, inst, tile)) return;
+  const DevMesh &d = a.ms[inst];
+  for (int f = tile * SORT_TILE + threadIdx.x; f < min(d.F, (tile + 1) * SORT_TILE); f += blockDim.x)
+    face_key_of(d, f);
+}
+
+// faces = 0: cell keys (2L buckets) into cl/coff; 1: face keys (L) into fl/foff
+__global__ void __launch_bounds__(SORT_THREADS) k_sort_hist_multi(MultiTiles a, int faces) {
+  int inst, tile;
+  if (!tile_of(a, inst, tile)) return;
+  const DevMesh &d = a.ms[inst];
+  int n = faces ? d.F : d.N;
+  sort_hist_tile(faces ? d.fkey : d.ckey, n, faces ? d.L : 2 * d.L, d.sort_cnt, tile,
+                 (n + SORT_TILE - 1) / SORT_TILE);
+}
+
+__global__ void __launch_bounds__(1024) k_sort_scan_multi(const DevMesh *ms, const int *active, int faces) {
+  if (!active[blockIdx.x]) return;
+  const DevMesh &d = ms[blockIdx.x];
+  int n = faces ? d.F : d.N;
+  int nb = faces ? d.L : 2 * d.L;
+  int nblk = (n + SORT_TILE - 1) / SORT_TILE;
+  sort_scan_block(d.sort_cnt, nb * nblk, nblk, nb, faces ? d.foff : d.coff);
+}
+
+__global__ void __launch_bounds__(SORT_THREADS) k_sort_scatter_multi(MultiTiles a, int faces) {
+  int inst, tile;
+  if (!tile_of(a, inst, tile)) return;
+  const DevMesh &d = a.ms[inst];
+  int n = faces ? d.F : d.N;
+  sort_scatter_tile(faces ? d.fkey : d.ckey, n, faces ? d.L : 2 * d.L, d.sort_cnt, faces ? d.fl : d.cl,
+                    tile, (n + SORT_TILE - 1) / SORT_TILE);
 }
 
 // ------------------------------------------------------ state at a time --
@@ -373,67 +505,70 @@ __device__ __forceinline__ void to_prim(const float U[5], double gm1, float W[5]
   cons_to_prim(U, (float)gm1, W);
 }
 
-// primitives of the cells of list range [coff[b0], coff[b1]) at the phase
-// time into their W record: FP64 (FP64 mode) or FP32 (FP32-flux mode, no FP64
-// work)
+// record arrays of the flux type
+__device__ __forceinline__ const double *grec(const DevMesh &d, double) { return d.G; }
+__device__ __forceinline__ const float *grec(const DevMesh &d, float) { return d.G32; }
+__device__ __forceinline__ double *grec_w(const DevMesh &d, double) { return d.G; }
+__device__ __forceinline__ float *grec_w(const DevMesh &d, float) { return d.G32; }
+__device__ __forceinline__ const double *lswrec(const DevMesh &d, double) { return d.lsw; }
+__device__ __forceinline__ const float *lswrec(const DevMesh &d, float) { return d.lsw32; }
+__device__ __forceinline__ const double *georec(const DevMesh &d, double) { return d.fgeo; }
+__device__ __forceinline__ const float *georec(const DevMesh &d, float) { return d.fgeo32; }
+
+// primitives of the cell at list position idx at the phase time into its W
+// record: FP64 (FP64 mode) or FP32 (FP32-flux mode, no FP64 work)
 template <typename WT>
-__global__ void __launch_bounds__(256) k_prim(DevMesh d, const __grid_constant__ PhaseLevels pl, int b0, int b1, WT *W) {
-  int beg = d.coff[b0], end = d.coff[b1];
-  double gm1 = d.gamma - 1.0;
-  for (int idx = beg + blockIdx.x * blockDim.x + threadIdx.x; idx < end; idx += gridDim.x * blockDim.x) {
-    int i = d.cl[idx];
-    WT U[5], Wt[REC_W];
-    load_state(d, pl, i, U);
-    to_prim(U, gm1, Wt);
+__device__ __forceinline__ void prim_item(const DevMesh &d, const PhaseLevels &pl, int idx) {
+  int i = d.cl[idx];
+  WT U[5], Wt[REC_W];
+  load_state(d, pl, i, U);
+  to_prim(U, d.gamma - 1.0, Wt);
 #pragma unroll
-    for (int q = 5; q < REC_W; ++q) Wt[q] = WT(0);
-    strec<REC_W>(W + (size_t)i * REC_W, Wt);
-  }
+  for (int q = 5; q < REC_W; ++q) Wt[q] = WT(0);
+  strec<REC_W>((WT *)d.W + (size_t)i * REC_W, Wt);
 }
 
-// least-squares gradients of the primitives: g = sum_j w_j (W_nb(j) - W_i),
-// ghost states on boundary faces
+// least-squares gradients of the primitives of the cell at list position
+// idx: g = sum_j w_j (W_nb(j) - W_i), ghost states on boundary faces
 template <typename T>
-__global__ void __launch_bounds__(256) k_grad(DevMesh d, int b0, int b1, const T *__restrict__ W,
-                                              T *__restrict__ G, const T *__restrict__ lsw,
-                                              const T *__restrict__ fgeo) {
-  int beg = d.coff[b0], end = d.coff[b1];
-  for (int idx = beg + blockIdx.x * blockDim.x + threadIdx.x; idx < end; idx += gridDim.x * blockDim.x) {
-    int i = d.cl[idx];
-    T Wi[REC_W], g[REC_G], w[REC_LSW];
-    ldrec<REC_W>(W + (size_t)i * REC_W, Wi);
-    ldrec<REC_LSW>(lsw + (size_t)i * REC_LSW, w);
-    int4 nb4 = d.cnb4[i];
+__device__ __forceinline__ void grad_item(const DevMesh &d, int idx) {
+  const T *W = (const T *)d.W;
+  const T *lsw = lswrec(d, T(0));
+  const T *fgeo = georec(d, T(0));
+  int i = d.cl[idx];
+  T Wi[REC_W], g[REC_G], w[REC_LSW];
+  ldrec<REC_W>(W + (size_t)i * REC_W, Wi);
+  ldrec<REC_LSW>(lsw + (size_t)i * REC_LSW, w);
+  int4 nb4 = d.cnb4[i];
 #pragma unroll
-    for (int q = 0; q < REC_G; ++q) g[q] = T(0);
+  for (int q = 0; q < REC_G; ++q) g[q] = T(0);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      int nb = nbr_of(nb4, j);
-      T Wn[REC_W];
-      if (nb >= 0) {
-        ldrec<REC_W>(W + (size_t)nb * REC_W, Wn);
-      } else {
+  for (int j = 0; j < 4; ++j) {
+    int nb = nbr_of(nb4, j);
+    T Wn[REC_W];
+    if (nb >= 0) {
+      ldrec<REC_W>(W + (size_t)nb * REC_W, Wn);
+    } else {
 #pragma unroll
-        for (int q = 0; q < 5; ++q) Wn[q] = Wi[q];
-        if (nb == -FV_BC_WALL) {
-          const T *gf = fgeo + (size_t)nbr_of(d.cf4[i], j) * REC_FG;
-          T n0 = gf[0], n1 = gf[1], n2 = gf[2];
-          T un = (Wi[1] * n0 + Wi[2] * n1) + Wi[3] * n2;
-          Wn[1] = Wi[1] - (T(2) * un) * n0;
-          Wn[2] = Wi[2] - (T(2) * un) * n1;
-          Wn[3] = Wi[3] - (T(2) * un) * n2;
-        }
-      }
-#pragma unroll
-      for (int c = 0; c < 5; ++c) {
-        T dd = Wn[c] - Wi[c];
-        g[3 * c] += w[3 * j] * dd;
-        g[3 * c + 1] += w[3 * j + 1] * dd;
-        g[3 * c + 2] += w[3 * j + 2] * dd;
+      for (int q = 0; q < 5; ++q) Wn[q] = Wi[q];
+      if (nb == -FV_BC_WALL) {
+        const T *gf = fgeo + (size_t)nbr_of(d.cf4[i], j) * REC_FG;
+        T n0 = gf[0], n1 = gf[1], n2 = gf[2];
+        T un = (Wi[1] * n0 + Wi[2] * n1) + Wi[3] * n2;
+        Wn[1] = Wi[1] - (T(2) * un) * n0;
+        Wn[2] = Wi[2] - (T(2) * un) * n1;
+        Wn[3] = Wi[3] - (T(2) * un) * n2;
       }
     }
-    strec<REC_G>(G + (size_t)i * REC_G, g);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      T dd = Wn[c] - Wi[c];
+      g[3 * c] += w[3 * j] * dd;
+      g[3 * c + 1] += w[3 * j + 1] * dd;
+      g[3 * c + 2] += w[3 * j + 2] * dd;
+    }
   }
+  strec<REC_G>(grec_w(d, T(0)) + (size_t)i * REC_G, g);
 }
 
 // face flux of face f from the phase-time primitive and gradient records:
@@ -504,50 +639,46 @@ __device__ __forceinline__ float flip(float v, bool neg) {
 // a level interface Phi is added to ACC[f] (the coarse side's integral), on a
 // boundary face to BND[f] (the conservation ledger).
 template <typename T, bool G14>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 4) k_flux(DevMesh d, GasT<T> G, int stage, int level, int b0,
-                                              int b1, const T *__restrict__ W, const T *__restrict__ Gr,
-                                              const T *__restrict__ fgeo) {
+__device__ __forceinline__ void flux_item(const DevMesh &d, const GasT<T> &G, int stage, int level,
+                                          int idx) {
   const bool f32 = sizeof(T) == 4;
-  int beg = d.foff[b0], end = d.foff[b1];
-  double h = 0.5 * ldexp(__longlong_as_double((long long)*d.dtmin_bits), level);
-  for (int idx = beg + blockIdx.x * blockDim.x + threadIdx.x; idx < end; idx += gridDim.x * blockDim.x) {
-    int f = d.fl[idx];
-    T FAt[5];
-    int rc = face_flux<T, G14>(d, G, W, Gr, fgeo, f, FAt);
-    if (rc) atomicOr(d.status, FV_STATUS_RIEMANN);
-    if (stage == 1) {
-      if (f32) {
-        float v[REC_FA32] = {(float)FAt[0], (float)FAt[1], (float)FAt[2], (float)FAt[3], (float)FAt[4], 0.f, 0.f, 0.f};
-        strec<REC_FA32>(d.FA32 + (size_t)f * REC_FA32, v);
-      } else {
-        double v[REC_FA] = {(double)FAt[0], (double)FAt[1], (double)FAt[2], (double)FAt[3], (double)FAt[4], 0.0};
-        strec<REC_FA>(d.FA + (size_t)f * REC_FA, v);
-      }
+  int f = d.fl[idx];
+  T FAt[5];
+  int rc = face_flux<T, G14>(d, G, (const T *)d.W, grec(d, T(0)), georec(d, T(0)), f, FAt);
+  if (rc) atomicOr(d.status, FV_STATUS_RIEMANN);
+  if (stage == 1) {
+    if (f32) {
+      float v[REC_FA32] = {(float)FAt[0], (float)FAt[1], (float)FAt[2], (float)FAt[3], (float)FAt[4], 0.f, 0.f, 0.f};
+      strec<REC_FA32>(d.FA32 + (size_t)f * REC_FA32, v);
     } else {
-      int2 fc = d.fcell[f];
-      bool iface = fc.y >= 0 && d.lev[fc.x] != d.lev[fc.y];
-      double phi[REC_FA];
-      if (f32) {
-        float a[REC_FA32];
-        ldrec<REC_FA32>(d.FA32 + (size_t)f * REC_FA32, a);
+      double v[REC_FA] = {(double)FAt[0], (double)FAt[1], (double)FAt[2], (double)FAt[3], (double)FAt[4], 0.0};
+      strec<REC_FA>(d.FA + (size_t)f * REC_FA, v);
+    }
+  } else {
+    double h = 0.5 * ldexp(__longlong_as_double((long long)*d.dtmin_bits), level);
+    int2 fc = d.fcell[f];
+    bool iface = fc.y >= 0 && d.lev[fc.x] != d.lev[fc.y];
+    double phi[REC_FA];
+    if (f32) {
+      float a[REC_FA32];
+      ldrec<REC_FA32>(d.FA32 + (size_t)f * REC_FA32, a);
 #pragma unroll
-        for (int c = 0; c < 5; ++c) phi[c] = h * (double)(a[c] + (float)FAt[c]);
-      } else {
-        double a[REC_FA];
-        ldrec<REC_FA>(d.FA + (size_t)f * REC_FA, a);
+      for (int c = 0; c < 5; ++c) phi[c] = h * (double)(a[c] + (float)FAt[c]);
+    } else {
+      double a[REC_FA];
+      ldrec<REC_FA>(d.FA + (size_t)f * REC_FA, a);
 #pragma unroll
-        for (int c = 0; c < 5; ++c) phi[c] = h * (a[c] + (double)FAt[c]);
-      }
-      phi[5] = 0.0;
-      strec<REC_FA>(d.FA + (size_t)f * REC_FA, phi);
-      if (iface || fc.y < 0) {
-        double *dst = (iface ? d.ACC : d.BND) + (size_t)f * REC_FA;
-        double acc[REC_FA];
-        ldrec<REC_FA>(dst, acc);
+      for (int c = 0; c < 5; ++c) phi[c] = h * (a[c] + (double)FAt[c]);
+    }
+    phi[5] = 0.0;
+    strec<REC_FA>(d.FA + (size_t)f * REC_FA, phi);
+    if (iface || fc.y < 0) {
+      double *dst = (iface ? d.ACC : d.BND) + (size_t)f * REC_FA;
+      double acc[REC_FA];
+      ldrec<REC_FA>(dst, acc);
 #pragma unroll
-        for (int c = 0; c < 5; ++c) acc[c] += phi[c];
-        strec<REC_FA>(dst, acc);
-      }
+      for (int c = 0; c < 5; ++c) acc[c] += phi[c];
+      strec<REC_FA>(dst, acc);
     }
   }
 }
@@ -562,60 +693,150 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 4) k_flux(DevMesh d,
 // Positivity is checked by the next level assignment and on demand
 // (fv_status), not here.
 template <bool F32>
-__global__ void __launch_bounds__(256) k_update(DevMesh d, int stage, int level, int b0, int b1) {
+__device__ __forceinline__ void update_item(const DevMesh &d, int stage, int level, int idx) {
   const size_t N = d.N;
-  int beg = d.coff[b0], end = d.coff[b1];
   double dtmin = __longlong_as_double((long long)*d.dtmin_bits);
-  float dtmin32 = (float)dtmin;
-  for (int idx = beg + blockIdx.x * blockDim.x + threadIdx.x; idx < end; idx += gridDim.x * blockDim.x) {
-    int i = d.cl[idx];
-    unsigned own = d.cown[i];
-    int4 cf = d.cf4[i];
-    if (stage == 1 && F32) {
-      float S[5];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        bool neg = !((own >> j) & 1u);
-        float v[REC_FA32];
-        ldrec<REC_FA32>(d.FA32 + (size_t)nbr_of(cf, j) * REC_FA32, v);
-#pragma unroll
-        for (int c = 0; c < 5; ++c) S[c] = j == 0 ? flip(v[c], neg) : S[c] + flip(v[c], neg);
-      }
-      float cdt = -ldexpf(dtmin32, (int)d.lev[i]) * d.ivol32[i];
-#pragma unroll
-      for (int c = 0; c < 5; ++c) d.Us32[c * N + i] = d.Un32[c * N + i] + cdt * S[c];
-      continue;
-    }
-    double S[5];
+  int i = d.cl[idx];
+  unsigned own = d.cown[i];
+  int4 cf = d.cf4[i];
+  if (stage == 1 && F32) {
+    float S[5];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      int f = nbr_of(cf, j);
       bool neg = !((own >> j) & 1u);
-      double v[REC_FA];
-      if (stage == 2 && d.flev[f] != level) {
-        double *a = d.ACC + (size_t)f * REC_FA;
-        ldrec<REC_FA>(a, v);
-        const double z[REC_FA] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-        strec<REC_FA>(a, z);
-      } else {
-        ldrec<REC_FA>(d.FA + (size_t)f * REC_FA, v);
-      }
+      float v[REC_FA32];
+      ldrec<REC_FA32>(d.FA32 + (size_t)nbr_of(cf, j) * REC_FA32, v);
 #pragma unroll
       for (int c = 0; c < 5; ++c) S[c] = j == 0 ? flip(v[c], neg) : S[c] + flip(v[c], neg);
     }
-    double iV = d.ivol[i];
-    if (stage == 1) {
-      double cdt = -ldexp(dtmin, (int)d.lev[i]) * iV;
+    float cdt = -ldexpf((float)dtmin, (int)d.lev[i]) * d.ivol32[i];
 #pragma unroll
-      for (int c = 0; c < 5; ++c) d.Us[c * N + i] = d.Un[c * N + i] + cdt * S[c];
+    for (int c = 0; c < 5; ++c) d.Us32[c * N + i] = d.Un32[c * N + i] + cdt * S[c];
+    return;
+  }
+  double S[5];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    int f = nbr_of(cf, j);
+    bool neg = !((own >> j) & 1u);
+    double v[REC_FA];
+    if (stage == 2 && d.flev[f] != level) {
+      double *a = d.ACC + (size_t)f * REC_FA;
+      ldrec<REC_FA>(a, v);
+      const double z[REC_FA] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+      strec<REC_FA>(a, z);
     } else {
+      ldrec<REC_FA>(d.FA + (size_t)f * REC_FA, v);
+    }
 #pragma unroll
-      for (int c = 0; c < 5; ++c) {
-        double u = d.Un[c * N + i] - iV * S[c];
-        d.Un[c * N + i] = u;
-        if (F32) d.Un32[c * N + i] = (float)u;
+    for (int c = 0; c < 5; ++c) S[c] = j == 0 ? flip(v[c], neg) : S[c] + flip(v[c], neg);
+  }
+  double iV = d.ivol[i];
+  if (stage == 1) {
+    double cdt = -ldexp(dtmin, (int)d.lev[i]) * iV;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) d.Us[c * N + i] = d.Un[c * N + i] + cdt * S[c];
+  } else {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      double u = d.Un[c * N + i] - iV * S[c];
+      d.Un[c * N + i] = u;
+      if (F32) d.Un32[c * N + i] = (float)u;
+    }
+  }
+}
+
+// ---- phase drivers: one kernel kind over the phase's list range of one
+// mesh (k_phase1), or over the concatenated ranges of a batch of meshes
+// (k_phaseN: a flattened work index, split by a per-block prefix over the
+// instances' range lengths)
+enum { K_PRIM = 0, K_GRAD = 1, K_FLUX = 2, K_UPD = 3 };
+
+__device__ __forceinline__ void kind_range(const DevMesh &d, const PhaseDesc &p, int kind, int &beg,
+                                           int &end) {
+  if (kind == K_FLUX) {
+    beg = d.foff[p.fb0];
+    end = d.foff[p.fb1];
+  } else {
+    int b0 = kind == K_PRIM ? p.pb0 : kind == K_GRAD ? p.gb0 : p.ub0;
+    int b1 = kind == K_PRIM ? p.pb1 : kind == K_GRAD ? p.gb1 : p.ub1;
+    beg = d.coff[b0];
+    end = d.coff[b1];
+  }
+}
+
+template <int KIND, typename T, bool G14>
+__device__ __forceinline__ void run_item(const DevMesh &d, const PhaseDesc &p, const GasT<T> &G,
+                                         int idx) {
+  if (KIND == K_PRIM)
+    prim_item<T>(d, p.pl, idx);
+  else if (KIND == K_GRAD)
+    grad_item<T>(d, idx);
+  else if (KIND == K_FLUX)
+    flux_item<T, G14>(d, G, p.stage, p.level, idx);
+  else
+    update_item<sizeof(T) == 4>(d, p.stage, p.level, idx);
+}
+
+// flux: 128 threads, 8 blocks per SM in FP32 (64 registers), 4 in FP64;
+// FP64 gradients need ~96 registers (2 blocks of 256); the rest fit in 64
+#define KBOUNDS(KIND, T)                                                                      \
+  __launch_bounds__((KIND) == K_FLUX ? 128 : 256,                                             \
+                    (KIND) == K_FLUX ? (sizeof(T) == 4 ? 8 : 4)                               \
+                                     : ((KIND) == K_GRAD && sizeof(T) == 8 ? 2 : 4))
+
+template <int KIND, typename T, bool G14>
+__global__ void KBOUNDS(KIND, T) k_phase1(DevMesh d, const __grid_constant__ PhaseDesc p, GasT<T> G) {
+  int beg, end;
+  kind_range(d, p, KIND, beg, end);
+  for (int idx = beg + blockIdx.x * blockDim.x + threadIdx.x; idx < end; idx += gridDim.x * blockDim.x)
+    run_item<KIND, T, G14>(d, p, G, idx);
+}
+
+template <int KIND, typename T, bool G14>
+__global__ void KBOUNDS(KIND, T) k_phaseN(const DevMesh *__restrict__ ms, const PhaseDesc *__restrict__ ps,
+                                          int n, GasT<T> G) {
+  __shared__ int pref[FV_MAXB + 1];
+  __shared__ int base[FV_MAXB];
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    int len[2], b[2];
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+      int i = lane + 32 * hh;
+      len[hh] = 0;
+      b[hh] = 0;
+      if (i < n && ps[i].active) {
+        int e;
+        kind_range(ms[i], ps[i], KIND, b[hh], e);
+        len[hh] = e - b[hh];
       }
     }
+    int x0 = len[0], x1 = len[1];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y0 = __shfl_up_sync(0xffffffff, x0, o), y1 = __shfl_up_sync(0xffffffff, x1, o);
+      if (lane >= o) {
+        x0 += y0;
+        x1 += y1;
+      }
+    }
+    int tot0 = __shfl_sync(0xffffffff, x0, 31);
+    pref[lane] = x0 - len[0];
+    pref[lane + 32] = tot0 + x1 - len[1];
+    if (lane == 31) pref[FV_MAXB] = tot0 + x1;
+    base[lane] = b[0];
+    base[lane + 32] = b[1];
+  }
+  __syncthreads();
+  const int total = pref[FV_MAXB];
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+      int mid = (lo + hi) >> 1;
+      if (pref[mid] <= g) lo = mid; else hi = mid;
+    }
+    run_item<KIND, T, G14>(ms[lo], ps[lo], G, base[lo] + (g - pref[lo]));
   }
 }
 
@@ -697,7 +918,9 @@ __global__ void __launch_bounds__(256) k_prim_all(DevMesh d, const __grid_consta
   }
 }
 
-__global__ void k_time_advance(DevMesh d, int theta) {
+// end of a cycle: t += 2^theta dt_min, and the work counters of the cost
+// model: sum_k 2^(theta-k) |Omega_k| cell updates, twice that over faces
+__device__ __forceinline__ void time_advance_of(const DevMesh &d, int theta) {
   d.tdev[0] += ldexp(__longlong_as_double((long long)*d.dtmin_bits), theta);
   long long cu = 0, fe = 0;
   for (int k = 0; k <= theta; ++k) {
@@ -707,6 +930,13 @@ __global__ void k_time_advance(DevMesh d, int theta) {
   d.counters[0] += 1;
   d.counters[1] += cu;
   d.counters[2] += fe;
+}
+
+__global__ void k_time_advance(DevMesh d, int theta) { time_advance_of(d, theta); }
+
+__global__ void k_time_advance_multi(const DevMesh *ms, const PhaseDesc *pds, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && pds[i].end_cycle) time_advance_of(ms[i], ms[i].L - 1);
 }
 
 // caller-order primitives -> Morton-order conserved state
@@ -819,7 +1049,7 @@ int launch_assign_levels(const DevMesh &d, int L, int *cnt_scratch, ProfHook *ph
   ProfScope scope(ph, FV_PROF_LEVELS, s);
   k_init_min<<<1, 1, 0, s>>>(d.dtmin_bits);
   k_dt<<<g, 256, 0, s>>>(d);
-  k_levels0<<<g, 256, 0, s>>>(d, L);
+  k_levels0<<<g, 256, 0, s>>>(d);
   // L-1 Jacobi sweeps between lev_tmp and lev; the result must land in lev
   const int8_t *src = d.lev_tmp;
   int8_t *dst = d.lev;
@@ -857,68 +1087,132 @@ int launch_assign_levels(const DevMesh &d, int L, int *cnt_scratch, ProfHook *ph
   return FV_OK;
 }
 
-int launch_phase(const DevMesh &d, int precision, const PhaseLevels &pl, int stage, int level,
-                 int pb0, int pb1, int gb0, int gb1, int fb0, int fb1, int ub0, int ub1,
-                 void *Wbuf, ProfHook *ph, cudaStream_t s) {
+template <typename T, bool G14>
+static void phase1_all(const DevMesh &d, const PhaseDesc &pd, const GasT<T> &G, int gc, int gfx,
+                       ProfHook *ph, cudaStream_t s) {
+  { ProfScope sc(ph, FV_PROF_PRIM, s); k_phase1<K_PRIM, T, G14><<<gc, 256, 0, s>>>(d, pd, G); }
+  { ProfScope sc(ph, FV_PROF_GRAD, s); k_phase1<K_GRAD, T, G14><<<gc, 256, 0, s>>>(d, pd, G); }
+  { ProfScope sc(ph, FV_PROF_FLUX, s); k_phase1<K_FLUX, T, G14><<<gfx, 128, 0, s>>>(d, pd, G); }
+  { ProfScope sc(ph, FV_PROF_UPDATE, s); k_phase1<K_UPD, T, G14><<<gc, 256, 0, s>>>(d, pd, G); }
+}
+
+static GasT<double> gas64(const DevMesh &d) { return GasT<double>::make(d.gamma, d.tol, d.maxit); }
+static GasT<float> gas32(const DevMesh &d) {
+  return GasT<float>::make(d.gamma, d.tol > 2e-6 ? d.tol : 2e-6, d.maxit);
+}
+
+int launch_phase(const DevMesh &d, const PhaseDesc &pd, ProfHook *ph, cudaStream_t s) {
   int gc = grid_for(d.N, 256, 8);
   int gfx = grid_for(d.F, 128, 16);
-  if (precision == FV_FP64) {
-    double *W = (double *)Wbuf;
-    GasT<double> G = GasT<double>::make(d.gamma, d.tol, d.maxit);
-    { ProfScope sc(ph, FV_PROF_PRIM, s); k_prim<double><<<gc, 256, 0, s>>>(d, pl, pb0, pb1, W); }
-    { ProfScope sc(ph, FV_PROF_GRAD, s); k_grad<double><<<gc, 256, 0, s>>>(d, gb0, gb1, W, d.G, d.lsw, d.fgeo); }
-    { ProfScope sc(ph, FV_PROF_FLUX, s);
-      if (d.gamma == 1.4)
-        k_flux<double, true><<<gfx, 128, 0, s>>>(d, G, stage, level, fb0, fb1, W, d.G, d.fgeo);
-      else
-        k_flux<double, false><<<gfx, 128, 0, s>>>(d, G, stage, level, fb0, fb1, W, d.G, d.fgeo); }
+  const bool g14 = d.gamma == 1.4;
+  if (d.precision == FV_FP64) {
+    if (g14) phase1_all<double, true>(d, pd, gas64(d), gc, gfx, ph, s);
+    else phase1_all<double, false>(d, pd, gas64(d), gc, gfx, ph, s);
   } else {
-    float *W = (float *)Wbuf;
-    double tol32 = d.tol > 2e-6 ? d.tol : 2e-6;
-    GasT<float> G = GasT<float>::make(d.gamma, tol32, d.maxit);
-    { ProfScope sc(ph, FV_PROF_PRIM, s); k_prim<float><<<gc, 256, 0, s>>>(d, pl, pb0, pb1, W); }
-    { ProfScope sc(ph, FV_PROF_GRAD, s); k_grad<float><<<gc, 256, 0, s>>>(d, gb0, gb1, W, d.G32, d.lsw32, d.fgeo32); }
-    { ProfScope sc(ph, FV_PROF_FLUX, s);
-      if (d.gamma == 1.4)
-        k_flux<float, true><<<gfx, 128, 0, s>>>(d, G, stage, level, fb0, fb1, W, d.G32, d.fgeo32);
-      else
-        k_flux<float, false><<<gfx, 128, 0, s>>>(d, G, stage, level, fb0, fb1, W, d.G32, d.fgeo32); }
+    if (g14) phase1_all<float, true>(d, pd, gas32(d), gc, gfx, ph, s);
+    else phase1_all<float, false>(d, pd, gas32(d), gc, gfx, ph, s);
   }
-  { ProfScope sc(ph, FV_PROF_UPDATE, s);
-    if (precision == FV_FP64)
-      k_update<false><<<gc, 256, 0, s>>>(d, stage, level, ub0, ub1);
-    else
-      k_update<true><<<gc, 256, 0, s>>>(d, stage, level, ub0, ub1); }
+  FV_LAUNCH_CHECK();
+  return FV_OK;
+}
+
+template <typename T, bool G14>
+static void phaseN_all(const DevMesh *ms, const PhaseDesc *pds, int n, const GasT<T> &G, int gc,
+                       int gfx, cudaStream_t s) {
+  k_phaseN<K_PRIM, T, G14><<<gc, 256, 0, s>>>(ms, pds, n, G);
+  k_phaseN<K_GRAD, T, G14><<<gc, 256, 0, s>>>(ms, pds, n, G);
+  k_phaseN<K_FLUX, T, G14><<<gfx, 128, 0, s>>>(ms, pds, n, G);
+  k_phaseN<K_UPD, T, G14><<<gc, 256, 0, s>>>(ms, pds, n, G);
+}
+
+int launch_phase_multi(const DevMesh *ms, const PhaseDesc *pds, int n, const DevMesh &d0,
+                       int64_t max_cells, int64_t max_faces, cudaStream_t s) {
+  int gc = grid_for(max_cells, 256, 8);
+  int gfx = grid_for(max_faces, 128, 16);
+  const bool g14 = d0.gamma == 1.4;
+  if (d0.precision == FV_FP64) {
+    if (g14) phaseN_all<double, true>(ms, pds, n, gas64(d0), gc, gfx, s);
+    else phaseN_all<double, false>(ms, pds, n, gas64(d0), gc, gfx, s);
+  } else {
+    if (g14) phaseN_all<float, true>(ms, pds, n, gas32(d0), gc, gfx, s);
+    else phaseN_all<float, false>(ms, pds, n, gas32(d0), gc, gfx, s);
+  }
   FV_LAUNCH_CHECK();
   return FV_OK;
 }
 
 int launch_residual(const DevMesh &d, int precision, const PhaseLevels &pl, int level, void *Wbuf,
                     double *FAt, double *R, const int *new2old, cudaStream_t s) {
+  (void)Wbuf;
   int gc = grid_for(d.N, 256, 8);
   int gfx = grid_for(d.F, 128, 16);
+  PhaseDesc all;  // gradients of every cell: the list range covering all cells
+  memset(&all, 0, sizeof all);
+  all.gb0 = 0;
+  all.gb1 = 2 * d.L;
+  all.active = 1;
+  const bool g14 = d.gamma == 1.4;
   if (precision == FV_FP64) {
-    double *W = (double *)Wbuf;
-    GasT<double> G = GasT<double>::make(d.gamma, d.tol, d.maxit);
+    double *W = (double *)d.W;
+    GasT<double> G = gas64(d);
     k_prim_all<double><<<gc, 256, 0, s>>>(d, pl, W);
-    // gradients of every cell: the list range covering all cells
-    k_grad<double><<<gc, 256, 0, s>>>(d, 0, 2 * d.L, W, d.G, d.lsw, d.fgeo);
-    if (d.gamma == 1.4)
+    k_phase1<K_GRAD, double, true><<<gc, 256, 0, s>>>(d, all, G);
+    if (g14)
       k_flux_all<double, true><<<gfx, 128, 0, s>>>(d, G, level, W, d.G, d.fgeo, FAt);
     else
       k_flux_all<double, false><<<gfx, 128, 0, s>>>(d, G, level, W, d.G, d.fgeo, FAt);
   } else {
-    float *W = (float *)Wbuf;
-    double tol32 = d.tol > 2e-6 ? d.tol : 2e-6;
-    GasT<float> G = GasT<float>::make(d.gamma, tol32, d.maxit);
+    float *W = (float *)d.W;
+    GasT<float> G = gas32(d);
     k_prim_all<float><<<gc, 256, 0, s>>>(d, pl, W);
-    k_grad<float><<<gc, 256, 0, s>>>(d, 0, 2 * d.L, W, d.G32, d.lsw32, d.fgeo32);
-    if (d.gamma == 1.4)
+    k_phase1<K_GRAD, float, true><<<gc, 256, 0, s>>>(d, all, G);
+    if (g14)
       k_flux_all<float, true><<<gfx, 128, 0, s>>>(d, G, level, W, d.G32, d.fgeo32, FAt);
     else
       k_flux_all<float, false><<<gfx, 128, 0, s>>>(d, G, level, W, d.G32, d.fgeo32, FAt);
   }
   k_residual<<<gc, 256, 0, s>>>(d, level, FAt, R, new2old);
+  FV_LAUNCH_CHECK();
+  return FV_OK;
+}
+
+int launch_assign_multi(const DevMesh *ms, const int *active, int n, int Lmax, int64_t max_cells,
+                        int64_t max_faces, int64_t max_cell_blocks, int64_t max_face_blocks,
+                        int *cnt_scratch, const int *blk_pref_c, const int *blk_pref_f, cudaStream_t s) {
+  (void)max_cells;
+  (void)max_faces;
+  (void)cnt_scratch;
+  MultiTiles ac{ms, active, blk_pref_c, n}, af{ms, active, blk_pref_f, n};
+  const int gc = (int)max_cell_blocks, gf = (int)max_face_blocks;
+  k_init_min_multi<<<1, FV_MAXB, 0, s>>>(ms, active, n);
+  k_dt_multi<<<gc, 256, 0, s>>>(ac);
+  k_cells_multi<<<gc, 256, 0, s>>>(ac, 0);
+  // Lmax-1 sweeps for every instance (extra sweeps keep the fixed point); the
+  // last one must write lev
+  int sweeps = Lmax - 1;
+  bool from_tmp = true;
+  if (sweeps % 2 == 0) {
+    k_cells_multi<<<gc, 256, 0, s>>>(ac, 1);
+    from_tmp = false;
+  }
+  for (int sw = 0; sw < sweeps; ++sw) {
+    k_cells_multi<<<gc, 256, 0, s>>>(ac, from_tmp ? 2 : 3);
+    from_tmp = !from_tmp;
+  }
+  k_cells_multi<<<gc, 256, 0, s>>>(ac, 4);
+  k_sort_hist_multi<<<gc, SORT_THREADS, 0, s>>>(ac, 0);
+  k_sort_scan_multi<<<n, 1024, 0, s>>>(ms, active, 0);
+  k_sort_scatter_multi<<<gc, SORT_THREADS, 0, s>>>(ac, 0);
+  k_face_keys_multi<<<gf, 256, 0, s>>>(af);
+  k_sort_hist_multi<<<gf, SORT_THREADS, 0, s>>>(af, 1);
+  k_sort_scan_multi<<<n, 1024, 0, s>>>(ms, active, 1);
+  k_sort_scatter_multi<<<gf, SORT_THREADS, 0, s>>>(af, 1);
+  FV_LAUNCH_CHECK();
+  return FV_OK;
+}
+
+int launch_time_advance_multi(const DevMesh *ms, const PhaseDesc *pds, int n, cudaStream_t s) {
+  k_time_advance_multi<<<1, FV_MAXB, 0, s>>>(ms, pds, n);
   FV_LAUNCH_CHECK();
   return FV_OK;
 }

@@ -57,7 +57,8 @@ EXPORTS = [
     "fv_cell_volumes", "fv_status", "fv_last_error", "fv_version", "fv_set_conserved",
     "fv_work_counters", "fv_use_graph", "fv_profile_enable", "fv_profile_read",
     "fv_get_level_lists", "fv_get_local_dt", "fv_assign_levels_noalloc",
-    "fv_godunov_flux_batch", "fv_probe_fma_peak",
+    "fv_godunov_flux_batch", "fv_probe_fma_peak", "fv_batch_create", "fv_batch_advance",
+    "fv_batch_info", "fv_batch_use_graph", "fv_batch_free",
 ]
 
 FV_NOALLOC_MAX_CELLS = 1 << 22
@@ -113,6 +114,12 @@ def lib():
     L.fv_profile_read.argtypes = [vp, dp, C.POINTER(C.c_int64)]
     L.fv_get_local_dt.argtypes = [vp, dp]
     L.fv_probe_fma_peak.argtypes = [C.c_int, C.c_int, dp]
+    L.fv_batch_create.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(vp)]
+    L.fv_batch_advance.argtypes = [vp, C.c_int, vp]
+    L.fv_batch_info.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.fv_batch_use_graph.argtypes = [vp, C.c_int]
+    L.fv_batch_free.argtypes = [vp]
+    L.fv_batch_free.restype = None
     L.fv_godunov_flux_batch.argtypes = [vp, vp, vp, i64, C.POINTER(fv_config), C.c_int, vp, vp, vp]
     L.fv_assign_levels_noalloc.argtypes = [vp, vp, i64, C.c_int, vp, vp, vp]
     L.fv_get_level_lists.argtypes = [vp, C.POINTER(C.c_int64), i32p, i8p, i32p]
@@ -378,6 +385,31 @@ def fv_status(h) -> int:
     return int(lib().fv_status(h))
 
 
+def fv_batch_create(handles):
+    arr = (C.c_void_p * len(handles))(*[h.value if isinstance(h, C.c_void_p) else h for h in handles])
+    out = C.c_void_p()
+    _check(lib().fv_batch_create(arr, len(handles), C.byref(out)), "fv_batch_create")
+    return out
+
+
+def fv_batch_advance(b, n_cycles, stream=None):
+    _check(lib().fv_batch_advance(b, int(n_cycles), _stream(stream)), "fv_batch_advance")
+
+
+def fv_batch_info(b):
+    s, k = C.c_int(), C.c_int()
+    _check(lib().fv_batch_info(b, C.byref(s), C.byref(k)), "fv_batch_info")
+    return s.value, k.value
+
+
+def fv_batch_use_graph(b, enable):
+    _check(lib().fv_batch_use_graph(b, int(bool(enable))), "fv_batch_use_graph")
+
+
+def fv_batch_free(b):
+    lib().fv_batch_free(b)
+
+
 # ------------------------------------------------------------ convenience
 class Mesh:
     """Owns one fv_mesh handle."""
@@ -454,3 +486,31 @@ class Mesh:
 
     def status(self):
         return fv_status(self.h)
+
+
+class Batch:
+    """A batch over existing Mesh objects (kept alive by the batch)."""
+
+    def __init__(self, meshes):
+        self.meshes = list(meshes)
+        self.h = fv_batch_create([m.h for m in self.meshes])
+
+    def advance(self, n_cycles=1, stream=None):
+        fv_batch_advance(self.h, n_cycles, stream)
+
+    def info(self):
+        return fv_batch_info(self.h)
+
+    def use_graph(self, enable):
+        fv_batch_use_graph(self.h, enable)
+
+    def close(self):
+        if getattr(self, "h", None):
+            fv_batch_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
