@@ -228,6 +228,15 @@ int fv_work_counters(fv_mesh *m, int64_t *cycles, int64_t *cell_updates, int64_t
  */
 int fv_use_graph(fv_mesh *m, int enable);
 
+/*
+ * Grid sizes of the four phase kernels (primitives, gradients, fluxes,
+ * updates) in blocks per SM (1..64; defaults 8, 8, 16, 8).  Results do not
+ * depend on them; the autotuner in paper_1704_01144_gb300/autotune.py picks
+ * them by timing and caches its choice.  Setting them drops a captured graph.
+ */
+int fv_set_launch(fv_mesh *m, const int32_t per_sm[4]);
+int fv_get_launch(fv_mesh *m, int32_t per_sm[4]);
+
 /* kernel classes of the profiler */
 #define FV_PROF_LEVELS 0 /* level assignment: dt, levels, sorts */
 #define FV_PROF_PRIM 1   /* primitives at the phase time */
@@ -266,6 +275,9 @@ int fv_batch_create(fv_mesh *const *meshes, int n, fv_batch **out);
 int fv_batch_advance(fv_batch *b, int n_cycles, void *stream);
 int fv_batch_info(fv_batch *b, int *subiterations, int *kernel_launches);
 int fv_batch_use_graph(fv_batch *b, int enable);
+/* grid sizes of a batch's phase kernels, as fv_set_launch */
+int fv_batch_set_launch(fv_batch *b, const int32_t per_sm[4]);
+int fv_batch_get_launch(fv_batch *b, int32_t per_sm[4]);
 void fv_batch_free(fv_batch *b);
 
 /*

@@ -76,7 +76,7 @@ int upload(T *dst, const std::vector<T> &src) {
 
 int run_phase(fv_mesh *m, const SchedPhase &ph, cudaStream_t s) {
   PhaseDesc pd = phase_desc(m->L, m->tn, m->pred, ph);
-  int rc = fvk::launch_phase(m->d, pd, &m->prof, s);
+  int rc = fvk::launch_phase(m->d, pd, m->launch, &m->prof, s);
   if (rc) return fail(rc, "phase launch failed");
   phase_apply(m->tn, m->pred, ph);
   return FV_OK;
@@ -512,6 +512,24 @@ int fv_advance(fv_mesh *m, int n_cycles, double *t_out, void *stream) {
     CK(cudaMemcpyAsync(t_out, m->d.tdev, sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
   }
+  return FV_OK;
+}
+
+int fv_set_launch(fv_mesh *m, const int32_t per_sm[4]) {
+  if (!m || !per_sm) return fail(FV_ERR_INVALID_ARG, "fv_set_launch: NULL argument");
+  for (int k = 0; k < 4; ++k)
+    if (per_sm[k] < 1 || per_sm[k] > 64) return fail(FV_ERR_INVALID_ARG, "fv_set_launch: 1..64 blocks per SM");
+  for (int k = 0; k < 4; ++k) m->launch.per_sm[k] = per_sm[k];
+  if (m->cycle_graph) {
+    cudaGraphExecDestroy(m->cycle_graph);
+    m->cycle_graph = nullptr;
+  }
+  return FV_OK;
+}
+
+int fv_get_launch(fv_mesh *m, int32_t per_sm[4]) {
+  if (!m || !per_sm) return fail(FV_ERR_INVALID_ARG, "fv_get_launch: NULL argument");
+  for (int k = 0; k < 4; ++k) per_sm[k] = m->launch.per_sm[k];
   return FV_OK;
 }
 

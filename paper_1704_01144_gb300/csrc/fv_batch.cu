@@ -36,6 +36,7 @@ struct fv_batch {
   bool use_graph = true;
   cudaGraphExec_t graph = nullptr;
   std::vector<void *> allocs;
+  LaunchCfg launch = default_launch();
 };
 
 namespace {
@@ -72,7 +73,7 @@ int run_steps(fv_batch *b, cudaStream_t s) {
                                     b->d_tpref_f, s);
     } else if (st.type == 1) {
       rc = fvk::launch_phase_multi(b->d_ms, b->d_pds + (size_t)st.idx * b->n, b->n,
-                                   b->meshes[0]->d, b->cells, b->faces, s);
+                                   b->meshes[0]->d, b->cells, b->faces, b->launch, s);
     } else {
       rc = fvk::launch_time_advance_multi(b->d_ms, b->d_pds + (size_t)st.idx * b->n, b->n, s);
     }
@@ -292,6 +293,25 @@ int fv_batch_info(fv_batch *b, int *subiterations, int *kernel_launches) {
     for (const auto &st : b->steps) k += st.type == 0 ? (11 + (b->Lmax - 1) + ((b->Lmax - 1) % 2 == 0)) : st.type == 1 ? 4 : 1;
     *kernel_launches = k;
   }
+  return FV_OK;
+}
+
+int fv_batch_set_launch(fv_batch *b, const int32_t per_sm[4]) {
+  if (!b || !per_sm) return bfail(FV_ERR_INVALID_ARG, "fv_batch_set_launch: NULL argument");
+  for (int k = 0; k < 4; ++k)
+    if (per_sm[k] < 1 || per_sm[k] > 64)
+      return bfail(FV_ERR_INVALID_ARG, "fv_batch_set_launch: 1..64 blocks per SM");
+  for (int k = 0; k < 4; ++k) b->launch.per_sm[k] = per_sm[k];
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  return FV_OK;
+}
+
+int fv_batch_get_launch(fv_batch *b, int32_t per_sm[4]) {
+  if (!b || !per_sm) return bfail(FV_ERR_INVALID_ARG, "fv_batch_get_launch: NULL argument");
+  for (int k = 0; k < 4; ++k) per_sm[k] = b->launch.per_sm[k];
   return FV_OK;
 }
 

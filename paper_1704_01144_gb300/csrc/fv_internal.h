@@ -108,6 +108,14 @@ struct PhaseDesc {
 
 #define FV_MAXB 64  // instances per batch
 
+// grid sizes of the phase kernels, in blocks per SM (256 threads for
+// primitives / gradients / updates, 128 for fluxes); results do not depend
+// on them (items are independent), so an autotuner may pick any
+struct LaunchCfg {
+  int per_sm[4];  // prim, grad, flux, update
+};
+inline LaunchCfg default_launch() { return LaunchCfg{{8, 8, 16, 8}}; }
+
 // ---- host schedule of one cycle (Alg. 2 lines 4-9) -------------------
 // kind 0: begin levels 0..level at T; kind 1: end the step of `level` at T
 struct SchedPhase {
@@ -265,16 +273,18 @@ struct fv_mesh {
   cudaGraphExec_t cycle_graph = nullptr;
   bool have_dt = false;
   bool in_batch = false;       // owned by a batch's schedule while advancing
+  LaunchCfg launch = default_launch();
 };
 
 // kernels (fv_kernels.cu)
 namespace fvk {
 void init_device_info();
 int launch_assign_levels(const DevMesh &d, int L, int *cnt_scratch, ProfHook *ph, cudaStream_t s);
-int launch_phase(const DevMesh &d, const PhaseDesc &pd, ProfHook *ph, cudaStream_t s);
+int launch_phase(const DevMesh &d, const PhaseDesc &pd, const LaunchCfg &lc, ProfHook *ph,
+                 cudaStream_t s);
 // batches: ms/pds are device arrays of n meshes / descriptors of one phase
 int launch_phase_multi(const DevMesh *ms, const PhaseDesc *pds, int n, const DevMesh &d0,
-                       int64_t max_cells, int64_t max_faces, cudaStream_t s);
+                       int64_t max_cells, int64_t max_faces, const LaunchCfg &lc, cudaStream_t s);
 int launch_assign_multi(const DevMesh *ms, const int *active, int n, int Lmax, int64_t max_cells,
                         int64_t max_faces, int64_t max_cell_blocks, int64_t max_face_blocks,
                         int *cnt_scratch, const int *blk_pref_c, const int *blk_pref_f, cudaStream_t s);

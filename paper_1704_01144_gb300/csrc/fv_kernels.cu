@@ -1088,12 +1088,14 @@ int launch_assign_levels(const DevMesh &d, int L, int *cnt_scratch, ProfHook *ph
 }
 
 template <typename T, bool G14>
-static void phase1_all(const DevMesh &d, const PhaseDesc &pd, const GasT<T> &G, int gc, int gfx,
+static void phase1_all(const DevMesh &d, const PhaseDesc &pd, const GasT<T> &G, const LaunchCfg &lc,
                        ProfHook *ph, cudaStream_t s) {
-  { ProfScope sc(ph, FV_PROF_PRIM, s); k_phase1<K_PRIM, T, G14><<<gc, 256, 0, s>>>(d, pd, G); }
-  { ProfScope sc(ph, FV_PROF_GRAD, s); k_phase1<K_GRAD, T, G14><<<gc, 256, 0, s>>>(d, pd, G); }
-  { ProfScope sc(ph, FV_PROF_FLUX, s); k_phase1<K_FLUX, T, G14><<<gfx, 128, 0, s>>>(d, pd, G); }
-  { ProfScope sc(ph, FV_PROF_UPDATE, s); k_phase1<K_UPD, T, G14><<<gc, 256, 0, s>>>(d, pd, G); }
+  const int g0 = grid_for(d.N, 256, lc.per_sm[0]), g1 = grid_for(d.N, 256, lc.per_sm[1]);
+  const int g2 = grid_for(d.F, 128, lc.per_sm[2]), g3 = grid_for(d.N, 256, lc.per_sm[3]);
+  { ProfScope sc(ph, FV_PROF_PRIM, s); k_phase1<K_PRIM, T, G14><<<g0, 256, 0, s>>>(d, pd, G); }
+  { ProfScope sc(ph, FV_PROF_GRAD, s); k_phase1<K_GRAD, T, G14><<<g1, 256, 0, s>>>(d, pd, G); }
+  { ProfScope sc(ph, FV_PROF_FLUX, s); k_phase1<K_FLUX, T, G14><<<g2, 128, 0, s>>>(d, pd, G); }
+  { ProfScope sc(ph, FV_PROF_UPDATE, s); k_phase1<K_UPD, T, G14><<<g3, 256, 0, s>>>(d, pd, G); }
 }
 
 static GasT<double> gas64(const DevMesh &d) { return GasT<double>::make(d.gamma, d.tol, d.maxit); }
@@ -1101,41 +1103,40 @@ static GasT<float> gas32(const DevMesh &d) {
   return GasT<float>::make(d.gamma, d.tol > 2e-6 ? d.tol : 2e-6, d.maxit);
 }
 
-int launch_phase(const DevMesh &d, const PhaseDesc &pd, ProfHook *ph, cudaStream_t s) {
-  int gc = grid_for(d.N, 256, 8);
-  int gfx = grid_for(d.F, 128, 16);
+int launch_phase(const DevMesh &d, const PhaseDesc &pd, const LaunchCfg &lc, ProfHook *ph,
+                 cudaStream_t s) {
   const bool g14 = d.gamma == 1.4;
   if (d.precision == FV_FP64) {
-    if (g14) phase1_all<double, true>(d, pd, gas64(d), gc, gfx, ph, s);
-    else phase1_all<double, false>(d, pd, gas64(d), gc, gfx, ph, s);
+    if (g14) phase1_all<double, true>(d, pd, gas64(d), lc, ph, s);
+    else phase1_all<double, false>(d, pd, gas64(d), lc, ph, s);
   } else {
-    if (g14) phase1_all<float, true>(d, pd, gas32(d), gc, gfx, ph, s);
-    else phase1_all<float, false>(d, pd, gas32(d), gc, gfx, ph, s);
+    if (g14) phase1_all<float, true>(d, pd, gas32(d), lc, ph, s);
+    else phase1_all<float, false>(d, pd, gas32(d), lc, ph, s);
   }
   FV_LAUNCH_CHECK();
   return FV_OK;
 }
 
 template <typename T, bool G14>
-static void phaseN_all(const DevMesh *ms, const PhaseDesc *pds, int n, const GasT<T> &G, int gc,
-                       int gfx, cudaStream_t s) {
-  k_phaseN<K_PRIM, T, G14><<<gc, 256, 0, s>>>(ms, pds, n, G);
-  k_phaseN<K_GRAD, T, G14><<<gc, 256, 0, s>>>(ms, pds, n, G);
-  k_phaseN<K_FLUX, T, G14><<<gfx, 128, 0, s>>>(ms, pds, n, G);
-  k_phaseN<K_UPD, T, G14><<<gc, 256, 0, s>>>(ms, pds, n, G);
+static void phaseN_all(const DevMesh *ms, const PhaseDesc *pds, int n, const GasT<T> &G,
+                       int64_t cells, int64_t faces, const LaunchCfg &lc, cudaStream_t s) {
+  const int g0 = grid_for(cells, 256, lc.per_sm[0]), g1 = grid_for(cells, 256, lc.per_sm[1]);
+  const int g2 = grid_for(faces, 128, lc.per_sm[2]), g3 = grid_for(cells, 256, lc.per_sm[3]);
+  k_phaseN<K_PRIM, T, G14><<<g0, 256, 0, s>>>(ms, pds, n, G);
+  k_phaseN<K_GRAD, T, G14><<<g1, 256, 0, s>>>(ms, pds, n, G);
+  k_phaseN<K_FLUX, T, G14><<<g2, 128, 0, s>>>(ms, pds, n, G);
+  k_phaseN<K_UPD, T, G14><<<g3, 256, 0, s>>>(ms, pds, n, G);
 }
 
 int launch_phase_multi(const DevMesh *ms, const PhaseDesc *pds, int n, const DevMesh &d0,
-                       int64_t max_cells, int64_t max_faces, cudaStream_t s) {
-  int gc = grid_for(max_cells, 256, 8);
-  int gfx = grid_for(max_faces, 128, 16);
+                       int64_t max_cells, int64_t max_faces, const LaunchCfg &lc, cudaStream_t s) {
   const bool g14 = d0.gamma == 1.4;
   if (d0.precision == FV_FP64) {
-    if (g14) phaseN_all<double, true>(ms, pds, n, gas64(d0), gc, gfx, s);
-    else phaseN_all<double, false>(ms, pds, n, gas64(d0), gc, gfx, s);
+    if (g14) phaseN_all<double, true>(ms, pds, n, gas64(d0), max_cells, max_faces, lc, s);
+    else phaseN_all<double, false>(ms, pds, n, gas64(d0), max_cells, max_faces, lc, s);
   } else {
-    if (g14) phaseN_all<float, true>(ms, pds, n, gas32(d0), gc, gfx, s);
-    else phaseN_all<float, false>(ms, pds, n, gas32(d0), gc, gfx, s);
+    if (g14) phaseN_all<float, true>(ms, pds, n, gas32(d0), max_cells, max_faces, lc, s);
+    else phaseN_all<float, false>(ms, pds, n, gas32(d0), max_cells, max_faces, lc, s);
   }
   FV_LAUNCH_CHECK();
   return FV_OK;

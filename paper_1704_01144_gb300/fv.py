@@ -58,7 +58,8 @@ EXPORTS = [
     "fv_work_counters", "fv_use_graph", "fv_profile_enable", "fv_profile_read",
     "fv_get_level_lists", "fv_get_local_dt", "fv_assign_levels_noalloc",
     "fv_godunov_flux_batch", "fv_probe_fma_peak", "fv_batch_create", "fv_batch_advance",
-    "fv_batch_info", "fv_batch_use_graph", "fv_batch_free",
+    "fv_batch_info", "fv_batch_use_graph", "fv_batch_free", "fv_set_launch", "fv_get_launch",
+    "fv_batch_set_launch", "fv_batch_get_launch",
 ]
 
 FV_NOALLOC_MAX_CELLS = 1 << 22
@@ -120,6 +121,8 @@ def lib():
     L.fv_batch_use_graph.argtypes = [vp, C.c_int]
     L.fv_batch_free.argtypes = [vp]
     L.fv_batch_free.restype = None
+    for nm in ("fv_set_launch", "fv_get_launch", "fv_batch_set_launch", "fv_batch_get_launch"):
+        getattr(L, nm).argtypes = [vp, i32p]
     L.fv_godunov_flux_batch.argtypes = [vp, vp, vp, i64, C.POINTER(fv_config), C.c_int, vp, vp, vp]
     L.fv_assign_levels_noalloc.argtypes = [vp, vp, i64, C.c_int, vp, vp, vp]
     L.fv_get_level_lists.argtypes = [vp, C.POINTER(C.c_int64), i32p, i8p, i32p]
@@ -406,6 +409,31 @@ def fv_batch_use_graph(b, enable):
     _check(lib().fv_batch_use_graph(b, int(bool(enable))), "fv_batch_use_graph")
 
 
+def _launch4(per_sm):
+    a = (C.c_int32 * 4)(*[int(x) for x in per_sm])
+    return a
+
+
+def fv_set_launch(h, per_sm):
+    _check(lib().fv_set_launch(h, _launch4(per_sm)), "fv_set_launch")
+
+
+def fv_get_launch(h):
+    a = (C.c_int32 * 4)()
+    _check(lib().fv_get_launch(h, a), "fv_get_launch")
+    return list(a)
+
+
+def fv_batch_set_launch(b, per_sm):
+    _check(lib().fv_batch_set_launch(b, _launch4(per_sm)), "fv_batch_set_launch")
+
+
+def fv_batch_get_launch(b):
+    a = (C.c_int32 * 4)()
+    _check(lib().fv_batch_get_launch(b, a), "fv_batch_get_launch")
+    return list(a)
+
+
 def fv_batch_free(b):
     lib().fv_batch_free(b)
 
@@ -443,6 +471,12 @@ class Mesh:
 
     def use_graph(self, enable):
         fv_use_graph(self.h, enable)
+
+    def set_launch(self, per_sm):
+        fv_set_launch(self.h, per_sm)
+
+    def get_launch(self):
+        return fv_get_launch(self.h)
 
     def profile_enable(self, enable):
         fv_profile_enable(self.h, enable)
@@ -503,6 +537,12 @@ class Batch:
 
     def use_graph(self, enable):
         fv_batch_use_graph(self.h, enable)
+
+    def set_launch(self, per_sm):
+        fv_batch_set_launch(self.h, per_sm)
+
+    def get_launch(self):
+        return fv_batch_get_launch(self.h)
 
     def close(self):
         if getattr(self, "h", None):

@@ -82,3 +82,29 @@ def test_batch_rejects_bad_input(fvmod):
     m.advance_phases(1)                            # mesh inside its own cycle
     with pytest.raises(fvmod.FvError):
         b.advance(1)
+
+
+def test_launch_config_does_not_change_results(fvmod, tmp_path):
+    """Grid sizes are free parameters: any choice (here the autotuner's and
+    an extreme one) gives bitwise the same state."""
+    import torch
+    from paper_1704_01144_gb300 import autotune as AT
+    mesh, prim = I.blast_case(n=10, ratio=8.0)
+    out = []
+    for per_sm in ([1, 2, 1, 3], [16, 16, 32, 16], None):
+        g = fvmod.Mesh(mesh, max_levels=4, precision=1)
+        g.set_state(prim)
+        if per_sm is None:
+            per_sm, info = AT.autotune(g, "test", cache_path=str(tmp_path / "at.json"), reps=1)
+            assert not info["cached"] and len(info["tried"]) >= 4
+            g.set_state(prim)
+        else:
+            g.set_launch(per_sm)
+        assert g.get_launch() == list(per_sm)
+        g.advance(2, stream=torch.cuda.Stream())
+        torch.cuda.synchronize()
+        out.append(g.get_state())
+    assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
+    g2 = fvmod.Mesh(mesh, max_levels=4, precision=1)
+    per_sm2, info2 = AT.autotune(g2, "test", cache_path=str(tmp_path / "at.json"))
+    assert info2["cached"] and per_sm2 == per_sm
