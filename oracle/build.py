@@ -1,4 +1,4 @@
-"""Compile the CPU oracle (``fv_oracle.c``) into ``oracle/_build/liboracle.so``.
+"""Compile the CPU oracle (``fv_oracle.c``, ``mlp_oracle.c``) into ``oracle/_build/liboracle.so``.
 
 Test infrastructure: the oracle is built with ``-ffp-contract=off`` so that no
 multiply-add is fused behind the source's back (on aarch64 GCC fuses by
@@ -11,7 +11,7 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SRC = os.path.join(HERE, "fv_oracle.c")
+SRCS = [os.path.join(HERE, "fv_oracle.c"), os.path.join(HERE, "mlp_oracle.c")]
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liboracle.so")
 
@@ -19,10 +19,10 @@ LIB = os.path.join(OUT_DIR, "liboracle.so")
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
     if (not force and os.path.exists(LIB)
-            and os.path.getmtime(LIB) >= os.path.getmtime(SRC)):
+            and os.path.getmtime(LIB) >= max(os.path.getmtime(s) for s in SRCS)):
         return LIB
     base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-            SRC, "-o", LIB + ".tmp", "-lm"]
+            *SRCS, "-o", LIB + ".tmp", "-lm"]
     for extra in (["-fopenmp"], []):
         cmd = base[:1] + extra + base[1:]
         r = subprocess.run(cmd, capture_output=True, text=True)

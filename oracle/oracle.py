@@ -67,6 +67,19 @@ def lib():
         L.orc_phase_info.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                      C.POINTER(C.c_int64)]
         L.orc_set_threads.argtypes = [C.c_int]
+        fp = C.POINTER(C.c_float)
+        L.orc_mlp_n_params.restype = C.c_int
+        for name in ("orc_gelu", "orc_gelu_grad", "orc_bf16_round"):
+            getattr(L, name).argtypes = [C.c_double]
+            getattr(L, name).restype = C.c_double
+        L.orc_tr_guess.argtypes = [C.c_double] * 7
+        L.orc_tr_guess.restype = C.c_double
+        L.orc_mlp_features.argtypes = [C.c_double, dp, dp, dp, dp]
+        L.orc_mlp_forward.argtypes = [dp, dp, C.c_int64, dp]
+        L.orc_mlp_forward_bf16.argtypes = [fp, fp, C.c_int64, dp]
+        L.orc_mlp_loss_grad.argtypes = [dp, dp, dp, C.c_int64, dp, dp]
+        L.orc_adam_step.argtypes = [dp, dp, dp, dp, C.c_int64, C.c_int, C.c_double, C.c_double,
+                                    C.c_double, C.c_double]
         _lib = L
     return _lib
 
@@ -302,3 +315,79 @@ def cons_to_prim(cons, gamma=1.4):
     u, v, w = cons[1] / r, cons[2] / r, cons[3] / r
     p = (gamma - 1.0) * (cons[4] - 0.5 * r * (u * u + v * v + w * w))
     return np.stack([r, u, v, w, p])
+
+
+# ------------------------------------------------------------------ MLP guess
+# (mlp_oracle.c: the learned star-pressure guess, FP64 reference)
+
+def mlp_n_params():
+    return int(lib().orc_mlp_n_params())
+
+
+def gelu(x):
+    return float(lib().orc_gelu(float(x)))
+
+
+def gelu_grad(x):
+    return float(lib().orc_gelu_grad(float(x)))
+
+
+def bf16_round(x):
+    return float(lib().orc_bf16_round(float(x)))
+
+
+def tr_guess(pair, gamma=1.4):
+    return float(lib().orc_tr_guess(gamma, *[float(v) for v in pair]))
+
+
+def mlp_features(pairs, gamma=1.4):
+    """pairs [n, 6] = (rL, uL, pL, rR, uR, pR) -> (x [n, 6], pbar [n], p_TR [n])."""
+    pairs = np.ascontiguousarray(np.atleast_2d(pairs), dtype=np.float64)
+    n = pairs.shape[0]
+    x = np.zeros((n, 6))
+    pb = np.zeros(n)
+    ptr = np.zeros(n)
+    L = lib()
+    for s in range(n):
+        xs = np.zeros(6)
+        a, b = C.c_double(), C.c_double()
+        L.orc_mlp_features(gamma, _dp(pairs[s]), _dp(xs), C.byref(a), C.byref(b))
+        x[s] = xs
+        pb[s] = a.value
+        ptr[s] = b.value
+    return x, pb, ptr
+
+
+def mlp_forward(theta, x):
+    theta = np.ascontiguousarray(theta, dtype=np.float64)
+    x = np.ascontiguousarray(np.atleast_2d(x), dtype=np.float64)
+    y = np.zeros(x.shape[0])
+    lib().orc_mlp_forward(_dp(theta), _dp(x), x.shape[0], _dp(y))
+    return y
+
+
+def mlp_forward_bf16(theta, x):
+    theta = np.ascontiguousarray(theta, dtype=np.float32)
+    x = np.ascontiguousarray(np.atleast_2d(x), dtype=np.float32)
+    y = np.zeros(x.shape[0])
+    fp = C.POINTER(C.c_float)
+    lib().orc_mlp_forward_bf16(theta.ctypes.data_as(fp), x.ctypes.data_as(fp), x.shape[0], _dp(y))
+    return y
+
+
+def mlp_loss_grad(theta, x, t):
+    theta = np.ascontiguousarray(theta, dtype=np.float64)
+    x = np.ascontiguousarray(np.atleast_2d(x), dtype=np.float64)
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    g = np.zeros(theta.shape[0])
+    loss = C.c_double()
+    _check(lib().orc_mlp_loss_grad(_dp(theta), _dp(x), _dp(t), x.shape[0], _dp(g), C.byref(loss)),
+           "orc_mlp_loss_grad")
+    return loss.value, g
+
+
+def adam_step(theta, m, v, grad, step, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """In place on float64 arrays theta, m, v."""
+    grad = np.ascontiguousarray(grad, dtype=np.float64)
+    _check(lib().orc_adam_step(_dp(theta), _dp(m), _dp(v), _dp(grad), theta.shape[0], int(step),
+                               lr, b1, b2, eps), "orc_adam_step")
