@@ -69,7 +69,7 @@ typedef struct fv_config {
   int max_levels;      /* L: number of temporal levels, 1..8 */
   int newton_max_iter; /* Newton iterations before FV_ERR_RIEMANN (50) */
   int precision;       /* FV_FP64 or FV_FP32_FLUX */
-  int guess;           /* FV_GUESS_TWO_RAREFACTION or FV_GUESS_MLP */
+  int guess;           /* FV_GUESS_TWO_RAREFACTION at load; fv_mlp_load selects FV_GUESS_MLP */
   int device;          /* CUDA device ordinal */
 } fv_config;
 
@@ -334,6 +334,117 @@ int fv_probe_fma_peak(int device, int precision, double *tflops_out);
 int fv_assign_levels_noalloc(const double *dt_dev, const int32_t *nbr_dev, int64_t n_cells,
                              int max_levels, int8_t *levels_dev, double *dt_min_dev,
                              void *stream);
+
+/* ---------------------------------------------------------------------
+ * Learned starting guess of the exact Riemann solver's Newton iteration.
+ * Sec. 2.1 computes face fluxes from the exact Riemann problem; the paper
+ * has no learned component, so the network and its inputs are readings:
+ * a 6 -> 64 -> 64 -> 1 perceptron with tanh-form GELU activations whose
+ * inputs are the face-frame primitives normalised by the pair's mean state,
+ * x = ((rL-rb)/rb, (uL-ub)/ab, (pL-pb)/pb, (rR-rb)/rb, (uR-ub)/ab, (pR-pb)/pb)
+ * (u: normal velocities; rb, ub, pb: means; ab = sqrt(gamma pb / rb)), and
+ * whose output is y = log(p* / pb) (FV_MLP_TARGET_PBAR) or
+ * y = log(p* / p_TR) / s(q) (FV_MLP_TARGET_TR), with p_TR the two-rarefaction
+ * guess, q = p_TR / min(pL, pR) - 1 and s(q) = (q / (1 + q))^3 for q > 0
+ * (0 otherwise: the two-rarefaction guess is then exact).
+ * Newton keeps its stopping rule (newton_tol), so the converged flux does
+ * not depend on the guess beyond that tolerance; a non-finite or
+ * non-positive guess falls back to the two-rarefaction guess.
+ * Parameters (FP32, FV_MLP_PARAMS values, rows = output units):
+ * W1[64][6], b1[64], W2[64][64], b2[64], w3[64], b3.
+ * ------------------------------------------------------------------- */
+#define FV_MLP_PARAMS 4673
+#define FV_MLP_PACKED_BYTES 10240 /* bfloat16 weight fragments + FP32 biases */
+#define FV_MLP_TARGET_PBAR 0
+#define FV_MLP_TARGET_TR 1
+
+typedef struct fv_train_config {
+  int epochs;     /* passes over the selected samples */
+  int batch;      /* samples per Adam step (1 .. 2^20) */
+  double lr0;     /* learning rate of the first step ... */
+  double lr1;     /* ... decayed along a half cosine to this one */
+  double beta1;   /* Adam moment decay rates and epsilon (0.9, 0.999, 1e-8) */
+  double beta2;
+  double eps;
+  uint64_t seed;  /* shuffle seed (splitmix64 stream) */
+} fv_train_config;
+
+/* Glorot-uniform weights, zero biases, from a splitmix64 stream seeded by
+ * `seed`, into host memory params[FV_MLP_PARAMS]. */
+int fv_mlp_init(float *params, int n_params, uint64_t seed);
+
+/* Packs device FP32 parameters into the fused kernels' layout (bfloat16
+ * B-fragments of W1 and W2, FP32 biases and output weights, the target
+ * mode, the gate) in packed_dev (FV_MLP_PACKED_BYTES, 16-byte aligned,
+ * caller-owned).  gate: a face takes the learned guess only where the
+ * two-rarefaction estimate shows a shock, q = p_TR / min(pL, pR) - 1 > gate
+ * (that estimate is exact for two rarefactions and third-order accurate for
+ * weak shocks); a negative gate consults the network on every face.  A warp
+ * evaluates the network when any of its faces passes the gate.
+ * Asynchronous on `stream`. */
+int fv_mlp_pack(const float *params_dev, int n_params, int target, double gate, void *packed_dev,
+                void *stream);
+
+/* The bfloat16 tensor-core inference the flux kernel fuses, on its own:
+ * y_dev[i] = network(x_dev[6*i .. 6*i+5]) for i < count.  Device pointers;
+ * asynchronous. */
+int fv_mlp_infer(const void *packed_dev, const float *x_dev, int64_t count, float *y_dev, void *stream);
+
+/* Training data from harvested pairs pairs_dev[6*count] = (rL, uL, pL, rR,
+ * uR, pR) in the face frame: the exact star pressure pstar_dev[count] (FP64
+ * Newton to a relative change of 1e-14), the features x_dev[6*count], the
+ * targets y_dev[count] (FP32) and, if q_dev is not NULL, the shock strength
+ * of the two-rarefaction estimate q_dev[count] (see fv_mlp_pack's gate).
+ * Synchronous.  FV_ERR_RIEMANN if a pair has no star state (its entries are
+ * NaN). */
+int fv_mlp_label(const double *pairs_dev, int64_t count, double gamma, int target, float *x_dev,
+                 float *y_dev, double *pstar_dev, float *q_dev, void *stream);
+
+/* Mean squared loss over samples sel_dev[0..count-1] (NULL: 0..count-1) and
+ * its gradient grad_dev[FV_MLP_PARAMS] (NULL: loss only), by the FP32
+ * training kernels; sums in a fixed order.  Synchronous. */
+int fv_mlp_loss_grad(const float *params_dev, const float *x_dev, const float *y_dev,
+                     const int32_t *sel_dev, int64_t count, float *grad_dev, double *loss_out,
+                     void *stream);
+
+/* One Adam step (step = 1, 2, ...) on device arrays params, m, v (FP32,
+ * FV_MLP_PARAMS each) from grad_dev.  Asynchronous. */
+int fv_mlp_adam(float *params_dev, float *m_dev, float *v_dev, const float *grad_dev, int step,
+                double lr, double beta1, double beta2, double eps, void *stream);
+
+/* Trains params_dev in place: tc->epochs passes over the samples listed in
+ * sel_host[n_sel] (host; NULL: 0..n_sel-1), each pass in a fresh
+ * Fisher-Yates order, one Adam step per minibatch of tc->batch samples.
+ * loss_hist_dev (NULL or fv_mlp_train_steps() floats) receives each step's
+ * minibatch loss.  Deterministic for a given seed.  Synchronous. */
+int fv_mlp_train(float *params_dev, const float *x_dev, const float *y_dev, const int32_t *sel_host,
+                 int64_t n_sel, const fv_train_config *tc, float *loss_hist_dev, void *stream);
+int fv_mlp_train_steps(const fv_train_config *tc, int64_t n_sel);
+
+/* Installs the network in the mesh (packed into mesh-owned device memory,
+ * with target and gate as in fv_mlp_pack) and selects FV_GUESS_MLP: the
+ * flux kernel then evaluates it on the tensor cores for the faces the gate
+ * passes and starts Newton from its guess there.  Synchronous.  Not
+ * inside a cycle; batches (fv_batch_create) take only meshes with the
+ * two-rarefaction guess. */
+int fv_mlp_load(fv_mesh *m, const float *params_dev, int n_params, int target, double gate);
+
+/* FV_GUESS_TWO_RAREFACTION, or FV_GUESS_MLP after fv_mlp_load. */
+int fv_set_guess(fv_mesh *m, int guess);
+
+/* Riemann pairs of the mesh's current state U^n (the reconstructed face
+ * states the flux kernel sees, in its precision): pair j of face
+ * (a j + b) mod F, with a coprime to F and a, b drawn from `seed`, so a call
+ * repeats no face; written as pairs_dev[6*j ..] = (rL, uL, pL, rR, uR, pR)
+ * in the face frame (a wall face: its mirrored problem).  count <= faces.
+ * Asynchronous on `stream`; not inside a cycle. */
+int fv_harvest_pairs(fv_mesh *m, double *pairs_dev, int64_t count, uint64_t seed, void *stream);
+
+/* fv_godunov_flux_batch for interior faces with the learned guess of the
+ * packed network (fv_mlp_pack); iters_dev shows what the guess saves. */
+int fv_godunov_flux_batch_mlp(const double *WL_dev, const double *WR_dev, const double *n_dev,
+                              int64_t count, const fv_config *cfg, const void *packed_dev,
+                              double *F_dev, int32_t *iters_dev, void *stream);
 
 /* Message of the calling thread's last failed call ("" if none). */
 const char *fv_last_error(void);

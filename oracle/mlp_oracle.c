@@ -9,11 +9,18 @@
  * and the CPU legs of the benchmark load it.  It shares no code with the CUDA
  * path.  The paper fixes none of this (it has no learned component); the
  * definitions below are the stated readings:
- *   features  pbar = (pL+pR)/2, rbar = (rL+rR)/2, abar = sqrt(g pbar / rbar),
- *             x = (rL/rbar, uL/abar, pL/pbar, rR/rbar, uR/abar, pR/pbar)
- *             with u the face-normal velocities;
- *   targets   log(p* / pbar) (target 0) or log(p* / p_TR) (target 1), p_TR the
- *             two-rarefaction guess (Toro ch. 4);
+ *   features  the left and right states normalised by the pair's mean state:
+ *             rbar, ubar, pbar the means of density, face-normal velocity and
+ *             pressure, abar = sqrt(g pbar / rbar);
+ *             x = ((rL-rbar)/rbar, (uL-ubar)/abar, (pL-pbar)/pbar,
+ *                  (rR-rbar)/rbar, (uR-ubar)/abar, (pR-pbar)/pbar)
+ *             (deviations, so that bfloat16 keeps 2^-9 of a small jump);
+ *   targets   log(p* / pbar) (target 0), or log(p* / p_TR) / s(q) (target 1)
+ *             with p_TR the two-rarefaction guess (Toro ch. 4), q = p_TR /
+ *             min(pL, pR) - 1 its shock strength and s(q) = q^3 / (1 + q)^3
+ *             for q > 0 (the guess is exact for two rarefactions, q <= 0,
+ *             where the target is 0; its error is third order in a weak
+ *             shock's strength and bounded for strong ones);
  *   GELU      tanh form, gelu(x) = x/2 (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3)));
  *   loss      mean over the samples of (y - t)^2;
  *   Adam      Kingma & Ba, bias-corrected moments.
@@ -24,7 +31,9 @@
  * the derivative against differences; a network built from mirrored unit
  * pairs computes a known affine map exactly; gradients against central
  * differences; the first two Adam steps against their closed forms;
- * features of mirrored states; the Sod star pressure of Toro's table.
+ * features of mirrored states; the Sod star pressure of Toro's table; the
+ * target of two rarefactions is 0 and the weak-shock scaling keeps the
+ * target bounded as the shock vanishes.
  */
 #include <math.h>
 #include <stdint.h>
@@ -70,17 +79,38 @@ double orc_tr_guess(double gamma, double rL, double uL, double pL, double rR, do
 /* pair = (rL, uL, pL, rR, uR, pR), face-normal velocities */
 int orc_mlp_features(double gamma, const double *pair, double *x, double *pbar, double *ptr) {
   double rb = 0.5 * (pair[0] + pair[3]);
+  double ub = 0.5 * (pair[1] + pair[4]);
   double pb = 0.5 * (pair[2] + pair[5]);
   double ab = sqrt(gamma * pb / rb);
-  x[0] = pair[0] / rb;
-  x[1] = pair[1] / ab;
-  x[2] = pair[2] / pb;
-  x[3] = pair[3] / rb;
-  x[4] = pair[4] / ab;
-  x[5] = pair[5] / pb;
+  x[0] = (pair[0] - rb) / rb;
+  x[1] = (pair[1] - ub) / ab;
+  x[2] = (pair[2] - pb) / pb;
+  x[3] = (pair[3] - rb) / rb;
+  x[4] = (pair[4] - ub) / ab;
+  x[5] = (pair[5] - pb) / pb;
   *pbar = pb;
   *ptr = orc_tr_guess(gamma, pair[0], pair[1], pair[2], pair[3], pair[4], pair[5]);
   return 0;
+}
+
+/* scale of the two-rarefaction guess's error: s(q) = (q / (1 + q))^3 for
+ * q > 0, else 0 */
+double orc_shock_scale(double q) {
+  if (!(q > 0.0)) return 0.0;
+  double r = q / (1.0 + q);
+  return r * r * r;
+}
+
+/* training target of a pair with exact star pressure ps; *q_out the shock
+ * strength of the two-rarefaction estimate */
+double orc_mlp_target(double gamma, const double *pair, int target, double ps, double *q_out) {
+  double x[NIN], pb, ptr;
+  orc_mlp_features(gamma, pair, x, &pb, &ptr);
+  double q = ptr / fmin(pair[2], pair[5]) - 1.0;
+  if (q_out) *q_out = q;
+  if (target == 0) return log(ps / pb);
+  double sc = orc_shock_scale(q);
+  return sc > 0.0 ? log(ps / ptr) / sc : 0.0;
 }
 
 /* one sample, FP64; keeps the pre-activations for the backward pass */

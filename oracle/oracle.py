@@ -75,6 +75,10 @@ def lib():
         L.orc_tr_guess.argtypes = [C.c_double] * 7
         L.orc_tr_guess.restype = C.c_double
         L.orc_mlp_features.argtypes = [C.c_double, dp, dp, dp, dp]
+        L.orc_shock_scale.argtypes = [C.c_double]
+        L.orc_shock_scale.restype = C.c_double
+        L.orc_mlp_target.argtypes = [C.c_double, dp, C.c_int, C.c_double, dp]
+        L.orc_mlp_target.restype = C.c_double
         L.orc_mlp_forward.argtypes = [dp, dp, C.c_int64, dp]
         L.orc_mlp_forward_bf16.argtypes = [fp, fp, C.c_int64, dp]
         L.orc_mlp_loss_grad.argtypes = [dp, dp, dp, C.c_int64, dp, dp]
@@ -356,6 +360,18 @@ def mlp_features(pairs, gamma=1.4):
         pb[s] = a.value
         ptr[s] = b.value
     return x, pb, ptr
+
+
+def shock_scale(q):
+    return float(lib().orc_shock_scale(float(q)))
+
+
+def mlp_target(pair, target, pstar, gamma=1.4):
+    """(training target, shock strength q) of one pair with star pressure pstar."""
+    pair = np.ascontiguousarray(pair, dtype=np.float64)
+    q = C.c_double()
+    y = lib().orc_mlp_target(gamma, _dp(pair), int(target), float(pstar), C.byref(q))
+    return float(y), q.value
 
 
 def mlp_forward(theta, x):

@@ -646,7 +646,7 @@ int fv_godunov_flux_batch(const double *WL_dev, const double *WR_dev, const doub
   fvk::init_device_info();
   int rc = fvk::launch_flux_batch(WL_dev, WR_dev ? WR_dev : WL_dev, n_dev, (int)count, cfg->gamma,
                                   cfg->newton_tol, cfg->newton_max_iter, cfg->precision, bc, F_dev,
-                                  iters_dev, (cudaStream_t)stream);
+                                  iters_dev, nullptr, (cudaStream_t)stream);
   if (rc) return fail(rc, "fv_godunov_flux_batch: launch failed");
   return FV_OK;
 }

@@ -79,6 +79,10 @@ struct DevMesh {
   // phase scratch: primitives at the phase time (FP64 or FP32 records)
   void *W;
   int precision;
+  // starting guess of the Riemann solver's Newton iteration: FV_GUESS_TR or
+  // FV_GUESS_MLP with the packed network weights (device, PK_WORDS words)
+  int guess;
+  const uint32_t *mlp;
   // physics
   double gamma, cfl, tol;
   int maxit;
@@ -299,5 +303,6 @@ int launch_get_levels(const DevMesh &d, int8_t *lev, const int *new2old, cudaStr
 int launch_check_state(const DevMesh &d, cudaStream_t s);
 int launch_flux_batch(const double *WL, const double *WR, const double *nrm, int n, double gamma,
                       double tol, int maxit, int precision, int bc, double *F, int *iters,
-                      cudaStream_t s);
+                      const uint32_t *mlp, cudaStream_t s);
+int launch_harvest(const DevMesh &d, double *out, int m, long long a, long long b, cudaStream_t s);
 }  // namespace fvk

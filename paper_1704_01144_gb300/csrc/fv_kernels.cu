@@ -22,6 +22,7 @@
 
 #include "fv_internal.h"
 #include "fv_riemann.cuh"
+#include "fv_mlp.cuh"
 
 namespace fvk {
 
@@ -571,23 +572,58 @@ __device__ __forceinline__ void grad_item(const DevMesh &d, int idx) {
   strec<REC_G>(grec_w(d, T(0)) + (size_t)i * REC_G, g);
 }
 
-// face flux of face f from the phase-time primitive and gradient records:
-// F A in FA[5].  Returns a nonzero status on Riemann failure.
-template <typename T, bool G14>
-__device__ __forceinline__ int face_flux(const DevMesh &d, const GasT<T> &G, const T *__restrict__ W,
-                                         const T *__restrict__ Gr, const T *__restrict__ fgeo, int f,
-                                         T FA[5]) {
+// the learned starting guess of one face (warp-collective): where the
+// two-rarefaction estimate shows a shock stronger than the packed gate, the
+// network (on the tensor cores, run by the warp if any of its lanes needs it)
+// gives either an absolute guess pbar e^y (target 0) or a factor e^(s(q) y)
+// on the two-rarefaction guess (target 1).
+// Elsewhere, and for invalid values, the solver keeps the two-rarefaction
+// guess.
+template <typename T>
+__device__ __forceinline__ void mlp_guess(const uint32_t *__restrict__ sw, float gamma, const T WL[5],
+                                          const T WR[5], const T n[3], T &gabs, T &gmul) {
+  T unL = (WL[1] * n[0] + WL[2] * n[1]) + WL[3] * n[2];
+  T unR = (WR[1] * n[0] + WR[2] * n[1]) + WR[3] * n[2];
+  const float rL = (float)WL[0], uL = (float)unL, pL = (float)WL[4];
+  const float rR = (float)WR[0], uR = (float)unR, pR = (float)WR[4];
+  const float gate = __uint_as_float(sw[PK_GATE]);
+  const float q = shock_strength(gamma, rL, uL, pL, rR, uR, pR);
+  const bool use = gate < 0.0f || q > gate;
+  gabs = T(0);
+  gmul = T(1);
+  if (!__any_sync(0xffffffffu, use)) return;
+  float x[6];
+  float pb = mlp_features<T>((T)gamma, WL[0], unL, WL[4], WR[0], unR, WR[4], x);
+  float y = mlp_eval_warp(sw, x);
+  if (!use) return;
+  if (sw[PK_TARGET] == 0u) {
+    gabs = (T)(pb * __expf(y));
+  } else {
+    float e = __expf(shock_scale(q) * y);
+    if (e > 0.0f && e < 3.0e38f) gmul = (T)e;
+  }
+}
+
+// the reconstructed inputs of face f's Riemann problem from the phase-time
+// primitive and gradient records: WL, WR (a boundary face copies WL into WR),
+// unit normal n and area A.  Returns fcell.y: the right cell, or minus the
+// boundary tag.
+template <typename T>
+__device__ __forceinline__ int face_states(const DevMesh &d, const T *__restrict__ W,
+                                           const T *__restrict__ Gr, const T *__restrict__ fgeo, int f,
+                                           T WL[5], T WR[5], T n[3], T &A) {
   int2 fc = d.fcell[f];
   const int L = fc.x, R = fc.y;
   T geo[REC_FG];
   ldrec<REC_FG>(fgeo + (size_t)f * REC_FG, geo);
-  const T n[3] = {geo[0], geo[1], geo[2]};
-  const T A = geo[3];
+  n[0] = geo[0];
+  n[1] = geo[1];
+  n[2] = geo[2];
+  A = geo[3];
   const T r[3] = {geo[4], geo[5], geo[6]};
-  T Wi[REC_W], gi[REC_G], WL[5], WR[5], Fx[5];
+  T Wi[REC_W], gi[REC_G];
   ldrec<REC_W>(W + (size_t)L * REC_W, Wi);
   ldrec<REC_G>(Gr + (size_t)L * REC_G, gi);
-  int it, rc;
   if (R >= 0) {
     T Wj[REC_W], gj[REC_G];
     ldrec<REC_W>(W + (size_t)R * REC_W, Wj);
@@ -600,7 +636,6 @@ __device__ __forceinline__ int face_flux(const DevMesh &d, const GasT<T> &G, con
       WL[c] = Wi[c] + T(0.5) * minmod(T(2) * gir - dW, dW);
       WR[c] = Wj[c] - T(0.5) * minmod(T(2) * gjr - dW, dW);
     }
-    rc = godunov_flux<T, G14>(G, WL, WR, n, Fx, it);
   } else {
     // reconstruct toward the ghost (mirror image of the cell in the face)
     T Wg[5];
@@ -617,8 +652,42 @@ __device__ __forceinline__ int face_flux(const DevMesh &d, const GasT<T> &G, con
       T gir = (gi[3 * c] * r[0] + gi[3 * c + 1] * r[1]) + gi[3 * c + 2] * r[2];
       WL[c] = Wi[c] + T(0.5) * minmod(T(2) * gir - dW, dW);
     }
-    rc = boundary_flux<T, G14>(G, -R, WL, n, Fx, it);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) WR[c] = WL[c];
   }
+  return R;
+}
+
+// face flux of face f: F A in FA[5].  Returns a nonzero status on Riemann
+// failure.  With MLP the whole warp calls it together (the learned guess is
+// warp-collective); a lane without a face passes f < 0 and gets nothing.
+template <typename T, bool G14, bool MLP = false>
+__device__ __forceinline__ int face_flux(const DevMesh &d, const GasT<T> &G, const T *__restrict__ W,
+                                         const T *__restrict__ Gr, const T *__restrict__ fgeo, int f,
+                                         T FA[5], const uint32_t *sw = nullptr) {
+  T WL[5], WR[5], n[3], A;
+  int R = 0;
+  if (!MLP || f >= 0) {
+    R = face_states<T>(d, W, Gr, fgeo, f, WL, WR, n, A);
+  } else {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) WL[c] = WR[c] = c == 0 || c == 4 ? T(1) : T(0);
+    n[0] = T(1);
+    n[1] = n[2] = T(0);
+    A = T(0);
+  }
+  T gabs = T(0), gmul = T(1);
+  if (MLP) {
+    __syncwarp();
+    mlp_guess<T>(sw, (float)G.g, WL, WR, n, gabs, gmul);
+    if (f < 0) return 0;
+  }
+  int it, rc;
+  T Fx[5];
+  if (R >= 0)
+    rc = godunov_flux<T, G14, MLP>(G, WL, WR, n, Fx, it, gabs, gmul);
+  else
+    rc = boundary_flux<T, G14>(G, -R, WL, n, Fx, it);
 #pragma unroll
   for (int c = 0; c < 5; ++c) FA[c] = Fx[c] * A;
   return rc;
@@ -638,13 +707,14 @@ __device__ __forceinline__ float flip(float v, bool neg) {
 // (in the FP32-flux mode from the FP32 sum of the two fluxes) and stored; on
 // a level interface Phi is added to ACC[f] (the coarse side's integral), on a
 // boundary face to BND[f] (the conservation ledger).
-template <typename T, bool G14>
+template <typename T, bool G14, bool MLP = false>
 __device__ __forceinline__ void flux_item(const DevMesh &d, const GasT<T> &G, int stage, int level,
-                                          int idx) {
+                                          int idx, const uint32_t *sw = nullptr) {
   const bool f32 = sizeof(T) == 4;
-  int f = d.fl[idx];
+  int f = (!MLP || idx >= 0) ? d.fl[idx] : -1;
   T FAt[5];
-  int rc = face_flux<T, G14>(d, G, (const T *)d.W, grec(d, T(0)), georec(d, T(0)), f, FAt);
+  int rc = face_flux<T, G14, MLP>(d, G, (const T *)d.W, grec(d, T(0)), georec(d, T(0)), f, FAt, sw);
+  if (MLP && f < 0) return;
   if (rc) atomicOr(d.status, FV_STATUS_RIEMANN);
   if (stage == 1) {
     if (f32) {
@@ -791,6 +861,23 @@ __global__ void KBOUNDS(KIND, T) k_phase1(DevMesh d, const __grid_constant__ Pha
   kind_range(d, p, KIND, beg, end);
   for (int idx = beg + blockIdx.x * blockDim.x + threadIdx.x; idx < end; idx += gridDim.x * blockDim.x)
     run_item<KIND, T, G14>(d, p, G, idx);
+}
+
+// flux with the learned guess: the packed network staged in shared memory,
+// the loop warp-uniform (lanes past the end ride along without a face)
+template <typename T, bool G14>
+__global__ void __launch_bounds__(128, 4) k_flux_mlp1(DevMesh d, const __grid_constant__ PhaseDesc p,
+                                                      GasT<T> G) {
+  __shared__ __align__(16) uint32_t sw[PK_WORDS];
+  mlp_stage(sw, d.mlp);
+  int beg, end;
+  kind_range(d, p, K_FLUX, beg, end);
+  const int lane = threadIdx.x & 31;
+  for (int base = beg + blockIdx.x * blockDim.x + (threadIdx.x - lane); base < end;
+       base += gridDim.x * blockDim.x) {
+    const int idx = base + lane;
+    flux_item<T, G14, true>(d, G, p.stage, p.level, idx < end ? idx : -1, sw);
+  }
 }
 
 template <int KIND, typename T, bool G14>
@@ -1019,11 +1106,65 @@ __global__ void __launch_bounds__(128) k_flux_batch(const double *__restrict__ W
   }
 }
 
+// the same with the learned starting guess (interior faces; warp-uniform
+// loop, packed network staged in shared memory)
+template <typename T, bool G14>
+__global__ void __launch_bounds__(128, 4) k_flux_batch_mlp(const double *__restrict__ WL,
+                                                           const double *__restrict__ WR,
+                                                           const double *__restrict__ nrm, int n,
+                                                           GasT<T> G, const uint32_t *__restrict__ mlp,
+                                                           double *__restrict__ F,
+                                                           int *__restrict__ iters) {
+  __shared__ __align__(16) uint32_t sw[PK_WORDS];
+  mlp_stage(sw, mlp);
+  const int lane = threadIdx.x & 31;
+  for (int base = blockIdx.x * blockDim.x + (threadIdx.x - lane); base < n;
+       base += gridDim.x * blockDim.x) {
+    const int i = base + lane;
+    const bool ok = i < n;
+    T wl[5], wr[5], nn[3], Fx[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      wl[c] = ok ? (T)WL[(size_t)c * n + i] : T(c == 0 || c == 4);
+      wr[c] = ok ? (T)WR[(size_t)c * n + i] : T(c == 0 || c == 4);
+    }
+#pragma unroll
+    for (int e = 0; e < 3; ++e) nn[e] = ok ? (T)nrm[(size_t)e * n + i] : T(e == 0);
+    T gabs, gmul;
+    __syncwarp();
+    mlp_guess<T>(sw, (float)G.g, wl, wr, nn, gabs, gmul);
+    if (!ok) continue;
+    int it = 0;
+    int rc = godunov_flux<T, G14, true>(G, wl, wr, nn, Fx, it, gabs, gmul);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) F[(size_t)c * n + i] = rc ? 0.0 : (double)Fx[c];
+    iters[i] = rc ? -1 : it;
+  }
+}
+
 int launch_flux_batch(const double *WL, const double *WR, const double *nrm, int n, double gamma,
                       double tol, int maxit, int precision, int bc, double *F, int *iters,
-                      cudaStream_t s) {
+                      const uint32_t *mlp, cudaStream_t s) {
   int g = grid_for(n, 128, 16);
   bool g14 = gamma == 1.4;
+  if (mlp) {
+    int gm = grid_for(n, 128, 4);
+    if (precision == FV_FP64) {
+      GasT<double> G = GasT<double>::make(gamma, tol, maxit);
+      if (g14)
+        k_flux_batch_mlp<double, true><<<gm, 128, 0, s>>>(WL, WR, nrm, n, G, mlp, F, iters);
+      else
+        k_flux_batch_mlp<double, false><<<gm, 128, 0, s>>>(WL, WR, nrm, n, G, mlp, F, iters);
+    } else {
+      GasT<float> G = GasT<float>::make(gamma, tol > 2e-6 ? tol : 2e-6, maxit);
+      if (g14)
+        k_flux_batch_mlp<float, true><<<gm, 128, 0, s>>>(WL, WR, nrm, n, G, mlp, F, iters);
+      else
+        k_flux_batch_mlp<float, false><<<gm, 128, 0, s>>>(WL, WR, nrm, n, G, mlp, F, iters);
+    }
+    FV_LAUNCH_CHECK();
+    return FV_OK;
+  }
   if (precision == FV_FP64) {
     GasT<double> G = GasT<double>::make(gamma, tol, maxit);
     if (g14)
@@ -1094,7 +1235,13 @@ static void phase1_all(const DevMesh &d, const PhaseDesc &pd, const GasT<T> &G, 
   const int g2 = grid_for(d.F, 128, lc.per_sm[2]), g3 = grid_for(d.N, 256, lc.per_sm[3]);
   { ProfScope sc(ph, FV_PROF_PRIM, s); k_phase1<K_PRIM, T, G14><<<g0, 256, 0, s>>>(d, pd, G); }
   { ProfScope sc(ph, FV_PROF_GRAD, s); k_phase1<K_GRAD, T, G14><<<g1, 256, 0, s>>>(d, pd, G); }
-  { ProfScope sc(ph, FV_PROF_FLUX, s); k_phase1<K_FLUX, T, G14><<<g2, 128, 0, s>>>(d, pd, G); }
+  {
+    ProfScope sc(ph, FV_PROF_FLUX, s);
+    if (d.guess == FV_GUESS_MLP)
+      k_flux_mlp1<T, G14><<<grid_for(d.F, 128, lc.per_sm[2] < 4 ? lc.per_sm[2] : 4), 128, 0, s>>>(d, pd, G);
+    else
+      k_phase1<K_FLUX, T, G14><<<g2, 128, 0, s>>>(d, pd, G);
+  }
   { ProfScope sc(ph, FV_PROF_UPDATE, s); k_phase1<K_UPD, T, G14><<<g3, 256, 0, s>>>(d, pd, G); }
 }
 
@@ -1173,6 +1320,56 @@ int launch_residual(const DevMesh &d, int precision, const PhaseLevels &pl, int 
       k_flux_all<float, false><<<gfx, 128, 0, s>>>(d, G, level, W, d.G32, d.fgeo32, FAt);
   }
   k_residual<<<gc, 256, 0, s>>>(d, level, FAt, R, new2old);
+  FV_LAUNCH_CHECK();
+  return FV_OK;
+}
+
+// Riemann pairs of the current state U^n for training the learned guess:
+// pair j is face (a j + b) mod F (a coprime with F, so no face repeats within
+// a call), written as (rho, u_n, p) left and right in the face frame; a wall
+// face gives its mirrored problem
+template <typename T>
+__global__ void __launch_bounds__(128) k_harvest(DevMesh d, const T *__restrict__ W, const T *__restrict__ Gr,
+                                                 const T *__restrict__ fgeo, double *__restrict__ out,
+                                                 int m, long long a, long long b) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) {
+    int f = (int)((a * (long long)j + b) % (long long)d.F);
+    T WL[5], WR[5], n[3], A;
+    int R = face_states<T>(d, W, Gr, fgeo, f, WL, WR, n, A);
+    T unL = (WL[1] * n[0] + WL[2] * n[1]) + WL[3] * n[2];
+    T unR = (WR[1] * n[0] + WR[2] * n[1]) + WR[3] * n[2];
+    if (R == -FV_BC_WALL) unR = -unL;
+    double *o = out + 6 * (size_t)j;
+    o[0] = (double)WL[0];
+    o[1] = (double)unL;
+    o[2] = (double)WL[4];
+    o[3] = (double)WR[0];
+    o[4] = (double)unR;
+    o[5] = (double)WR[4];
+  }
+}
+
+int launch_harvest(const DevMesh &d, double *out, int m, long long a, long long b, cudaStream_t s) {
+  int gc = grid_for(d.N, 256, 8);
+  PhaseLevels pl;  // every level at U^n
+  memset(&pl, 0, sizeof pl);
+  PhaseDesc all;
+  memset(&all, 0, sizeof all);
+  all.gb0 = 0;
+  all.gb1 = 2 * d.L;
+  all.active = 1;
+  int gh = grid_for(m, 128, 8);
+  if (d.precision == FV_FP64) {
+    double *W = (double *)d.W;
+    k_prim_all<double><<<gc, 256, 0, s>>>(d, pl, W);
+    k_phase1<K_GRAD, double, true><<<gc, 256, 0, s>>>(d, all, gas64(d));
+    k_harvest<double><<<gh, 128, 0, s>>>(d, W, d.G, d.fgeo, out, m, a, b);
+  } else {
+    float *W = (float *)d.W;
+    k_prim_all<float><<<gc, 256, 0, s>>>(d, pl, W);
+    k_phase1<K_GRAD, float, true><<<gc, 256, 0, s>>>(d, all, gas32(d));
+    k_harvest<float><<<gh, 128, 0, s>>>(d, W, d.G32, d.fgeo32, out, m, a, b);
+  }
   FV_LAUNCH_CHECK();
   return FV_OK;
 }

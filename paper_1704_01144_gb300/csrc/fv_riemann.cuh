@@ -7,8 +7,9 @@
 // exact solver follows the published construction (Toro, "Riemann Solvers
 // and Numerical Methods for Fluid Dynamics", ch. 4): pressure functions f_K
 // (shock branch for p > p_K, rarefaction branch otherwise), Newton on
-// f_L(p) + f_R(p) + (u_R - u_L) = 0 from the two-rarefaction guess, the
-// solution sampled on the face (x/t = 0).  Written from the equations.
+// f_L(p) + f_R(p) + (u_R - u_L) = 0 from the two-rarefaction guess (or a
+// learned guess, see fv_mlp.cuh), the solution sampled on the face
+// (x/t = 0).  Written from the equations.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -81,15 +82,25 @@ __device__ __forceinline__ bool at_rounding_floor(float f, float a, float b, flo
 }
 
 // Star pressure/velocity.  Returns 0, or 1 (vacuum), 2 (no convergence).
-template <typename T>
+// Newton starts from the two-rarefaction guess, or with GUESS from gabs when
+// that is a positive finite pressure, else from the two-rarefaction guess
+// times gmul (a learned correction factor, 1 when there is none).
+template <typename T, bool GUESS = false>
 __device__ __forceinline__ int riemann_star(const GasT<T> &G, T rL, T uL, T pL, T rR, T uR, T pR,
-                                            T &ps, T &us, int &iters) {
+                                            T &ps, T &us, int &iters, T gabs = T(0),
+                                            T gmul = T(1)) {
   T aL = fsqrt(G.g * pL / rL), aR = fsqrt(G.g * pR / rR);
   T du = uR - uL;
   if (G.two_gm1 * (aL + aR) <= du) return 1;
-  T num = aL + aR - T(0.5) * G.gm1 * du;
-  T den = aL / fpow(pL, G.z) + aR / fpow(pR, G.z);
-  T p = fpow(num / den, G.inv_z);
+  T p;
+  if (GUESS && gabs > T(0) && isfinite(gabs)) {
+    p = gabs;
+  } else {
+    T num = aL + aR - T(0.5) * G.gm1 * du;
+    T den = aL / fpow(pL, G.z) + aR / fpow(pR, G.z);
+    p = fpow(num / den, G.inv_z);
+    if (GUESS) p *= gmul;
+  }
   T pfloor = T(1e-6) * (pL < pR ? pL : pR);
   if (p < pfloor) p = pfloor;
   int it;
@@ -295,14 +306,20 @@ __device__ __forceinline__ void roots_of(T p, T &p17, T &rp6) {
   p17 = p * rp6;
 }
 
-template <typename T>
+template <typename T, bool GUESS = false>
 __device__ __forceinline__ int riemann_star14(const GasT<T> &G, const Side14<T> &L, T uL,
                                               const Side14<T> &R, T uR, T &ps, T &us, T &ps17,
-                                              int &iters) {
+                                              int &iters, T gabs = T(0), T gmul = T(1)) {
   T du = uR - uL;
   if (G.two_gm1 * (L.a + R.a) <= du) return 1;
-  T num = L.a + R.a - T(0.5) * G.gm1 * du;
-  T p = ipow7(num / (L.a * L.iq + R.a * R.iq));
+  T p;
+  if (GUESS && gabs > T(0) && isfinite(gabs)) {
+    p = gabs;
+  } else {
+    T num = L.a + R.a - T(0.5) * G.gm1 * du;
+    p = ipow7(num / (L.a * L.iq + R.a * R.iq));
+    if (GUESS) p *= gmul;
+  }
   T pfloor = T(1e-6) * (L.p < R.p ? L.p : R.p);
   if (p < pfloor) p = pfloor;
   int it;
@@ -408,9 +425,10 @@ __device__ __forceinline__ void sample_face14(const GasT<T> &G, const Side14<T> 
 // Godunov flux per unit area through an interior face with unit normal n;
 // the tangential velocity comes from the upwind side of the contact.
 // Returns 0 or the riemann_star error.
-template <typename T, bool G14>
+template <typename T, bool G14, bool GUESS = false>
 __device__ __forceinline__ int godunov_flux(const GasT<T> &G, const T WL[5], const T WR[5],
-                                            const T n[3], T F[5], int &iters) {
+                                            const T n[3], T F[5], int &iters, T gabs = T(0),
+                                            T gmul = T(1)) {
   T unL = (WL[1] * n[0] + WL[2] * n[1]) + WL[3] * n[2];
   T unR = (WR[1] * n[0] + WR[2] * n[1]) + WR[3] * n[2];
   T ps, us;
@@ -419,11 +437,12 @@ __device__ __forceinline__ int godunov_flux(const GasT<T> &G, const T WL[5], con
   if (G14) {
     Side14<T> L = make_side14(G, WL[0], WL[4]), R = make_side14(G, WR[0], WR[4]);
     T p17;
-    int rc = riemann_star14(G, L, unL, R, unR, ps, us, p17, iters);
+    int rc = riemann_star14<T, GUESS>(G, L, unL, R, unR, ps, us, p17, iters, gabs, gmul);
     if (rc) return rc;
     sample_face14(G, L, unL, R, unR, ps, us, p17, r0, un0, p0, side);
   } else {
-    int rc = riemann_star(G, WL[0], unL, WL[4], WR[0], unR, WR[4], ps, us, iters);
+    int rc = riemann_star<T, GUESS>(G, WL[0], unL, WL[4], WR[0], unR, WR[4], ps, us, iters, gabs,
+                                    gmul);
     if (rc) return rc;
     sample_face(G, WL[0], unL, WL[4], WR[0], unR, WR[4], ps, us, r0, un0, p0, side);
   }

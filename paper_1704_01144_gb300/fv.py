@@ -41,6 +41,12 @@ class FvError(RuntimeError):
         super().__init__(f"{what}: {_ERR_NAMES.get(code, code)}: {fv_last_error()}")
 
 
+class fv_train_config(C.Structure):
+    _fields_ = [("epochs", C.c_int), ("batch", C.c_int), ("lr0", C.c_double), ("lr1", C.c_double),
+                ("beta1", C.c_double), ("beta2", C.c_double), ("eps", C.c_double),
+                ("seed", C.c_uint64)]
+
+
 class fv_config(C.Structure):
     _fields_ = [("gamma", C.c_double), ("cfl", C.c_double), ("newton_tol", C.c_double),
                 ("max_levels", C.c_int), ("newton_max_iter", C.c_int), ("precision", C.c_int),
@@ -59,8 +65,14 @@ EXPORTS = [
     "fv_get_level_lists", "fv_get_local_dt", "fv_assign_levels_noalloc",
     "fv_godunov_flux_batch", "fv_probe_fma_peak", "fv_batch_create", "fv_batch_advance",
     "fv_batch_info", "fv_batch_use_graph", "fv_batch_free", "fv_set_launch", "fv_get_launch",
-    "fv_batch_set_launch", "fv_batch_get_launch",
+    "fv_batch_set_launch", "fv_batch_get_launch", "fv_mlp_init", "fv_mlp_pack", "fv_mlp_infer",
+    "fv_mlp_label", "fv_mlp_loss_grad", "fv_mlp_adam", "fv_mlp_train", "fv_mlp_train_steps",
+    "fv_mlp_load", "fv_set_guess", "fv_harvest_pairs", "fv_godunov_flux_batch_mlp",
 ]
+
+FV_MLP_PARAMS = 4673
+FV_MLP_PACKED_BYTES = 10240
+FV_MLP_TARGET_PBAR, FV_MLP_TARGET_TR = 0, 1
 
 FV_NOALLOC_MAX_CELLS = 1 << 22
 
@@ -126,6 +138,20 @@ def lib():
     L.fv_godunov_flux_batch.argtypes = [vp, vp, vp, i64, C.POINTER(fv_config), C.c_int, vp, vp, vp]
     L.fv_assign_levels_noalloc.argtypes = [vp, vp, i64, C.c_int, vp, vp, vp]
     L.fv_get_level_lists.argtypes = [vp, C.POINTER(C.c_int64), i32p, i8p, i32p]
+    fp = C.POINTER(C.c_float)
+    L.fv_mlp_init.argtypes = [fp, C.c_int, C.c_uint64]
+    L.fv_mlp_pack.argtypes = [vp, C.c_int, C.c_int, C.c_double, vp, vp]
+    L.fv_mlp_infer.argtypes = [vp, vp, i64, vp, vp]
+    L.fv_mlp_label.argtypes = [vp, i64, C.c_double, C.c_int, vp, vp, vp, vp, vp]
+    L.fv_mlp_loss_grad.argtypes = [vp, vp, vp, vp, i64, vp, dp, vp]
+    L.fv_mlp_adam.argtypes = [vp, vp, vp, vp, C.c_int, C.c_double, C.c_double, C.c_double,
+                              C.c_double, vp]
+    L.fv_mlp_train.argtypes = [vp, vp, vp, i32p, i64, C.POINTER(fv_train_config), vp, vp]
+    L.fv_mlp_train_steps.argtypes = [C.POINTER(fv_train_config), i64]
+    L.fv_mlp_load.argtypes = [vp, vp, C.c_int, C.c_int, C.c_double]
+    L.fv_set_guess.argtypes = [vp, C.c_int]
+    L.fv_harvest_pairs.argtypes = [vp, vp, i64, C.c_uint64, vp]
+    L.fv_godunov_flux_batch_mlp.argtypes = [vp, vp, vp, i64, C.POINTER(fv_config), vp, vp, vp, vp]
     L.fv_last_error.restype = C.c_char_p
     L.fv_version.restype = C.c_char_p
     _lib = L
@@ -311,6 +337,125 @@ def fv_godunov_flux_batch(WL, WR, nrm, cfg: fv_config, bc=FV_BC_INTERIOR, F=None
     return F, iters
 
 
+# ------------------------------------------------------------ learned guess
+def fv_mlp_init(seed) -> np.ndarray:
+    """Glorot-uniform initial parameters (host float32, FV_MLP_PARAMS)."""
+    p = np.zeros(FV_MLP_PARAMS, dtype=np.float32)
+    _check(lib().fv_mlp_init(p.ctypes.data_as(C.POINTER(C.c_float)), FV_MLP_PARAMS, int(seed)),
+           "fv_mlp_init")
+    return p
+
+
+def fv_mlp_pack(params, target, gate=-1.0, packed=None, stream=None):
+    """Pack a float32 CUDA tensor of parameters; returns the uint8 packed
+    buffer (FV_MLP_PACKED_BYTES).  gate < 0: the network on every face."""
+    import torch
+    if packed is None:
+        packed = torch.empty(FV_MLP_PACKED_BYTES, dtype=torch.uint8, device=params.device)
+    _check(lib().fv_mlp_pack(_dptr(params, "float32"), FV_MLP_PARAMS, int(target), float(gate),
+                             _dptr(packed, "uint8"), _stream(stream)), "fv_mlp_pack")
+    return packed
+
+
+def fv_mlp_infer(packed, x, y=None, stream=None):
+    """Network outputs of features x (n, 6) float32 CUDA -> y (n,) float32."""
+    import torch
+    n = int(x.shape[0])
+    if y is None:
+        y = torch.empty(n, dtype=torch.float32, device=x.device)
+    _check(lib().fv_mlp_infer(_dptr(packed, "uint8"), _dptr(x, "float32"), n, _dptr(y, "float32"),
+                              _stream(stream)), "fv_mlp_infer")
+    return y
+
+
+def fv_mlp_label(pairs, target, gamma=1.4, stream=None, want_q=False):
+    """pairs (n, 6) float64 CUDA -> (x (n, 6) float32, y (n,) float32,
+    p* (n,) float64[, q (n,) float32 shock strength])."""
+    import torch
+    n = int(pairs.shape[0])
+    x = torch.empty((n, 6), dtype=torch.float32, device=pairs.device)
+    y = torch.empty(n, dtype=torch.float32, device=pairs.device)
+    ps = torch.empty(n, dtype=torch.float64, device=pairs.device)
+    q = torch.empty(n, dtype=torch.float32, device=pairs.device) if want_q else None
+    _check(lib().fv_mlp_label(_dptr(pairs), n, float(gamma), int(target), _dptr(x, "float32"),
+                              _dptr(y, "float32"), _dptr(ps),
+                              _dptr(q, "float32") if q is not None else None, _stream(stream)),
+           "fv_mlp_label")
+    return (x, y, ps, q) if want_q else (x, y, ps)
+
+
+def fv_mlp_loss_grad(params, x, y, sel=None, want_grad=True, stream=None):
+    """(loss, grad float32 CUDA tensor or None) over the samples sel (int32
+    CUDA tensor) or all."""
+    import torch
+    n = int(sel.shape[0]) if sel is not None else int(x.shape[0])
+    g = torch.empty(FV_MLP_PARAMS, dtype=torch.float32, device=x.device) if want_grad else None
+    loss = C.c_double()
+    _check(lib().fv_mlp_loss_grad(_dptr(params, "float32"), _dptr(x, "float32"), _dptr(y, "float32"),
+                                  _dptr(sel, "int32") if sel is not None else None, n,
+                                  _dptr(g, "float32") if g is not None else None, C.byref(loss),
+                                  _stream(stream)), "fv_mlp_loss_grad")
+    return loss.value, g
+
+
+def fv_mlp_adam(params, m, v, grad, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(lib().fv_mlp_adam(_dptr(params, "float32"), _dptr(m, "float32"), _dptr(v, "float32"),
+                             _dptr(grad, "float32"), int(step), float(lr), float(beta1), float(beta2),
+                             float(eps), _stream(stream)), "fv_mlp_adam")
+
+
+def fv_mlp_train(params, x, y, sel=None, epochs=4, batch=8192, lr0=2e-3, lr1=2e-5, seed=1,
+                 beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    """Train params (float32 CUDA tensor) in place on samples sel (host int
+    array; None: all).  Returns the per-step minibatch losses (numpy)."""
+    import torch
+    tc = fv_train_config(int(epochs), int(batch), float(lr0), float(lr1), float(beta1), float(beta2),
+                         float(eps), int(seed))
+    if sel is not None:
+        sel = np.ascontiguousarray(sel, dtype=np.int32)
+        n = sel.shape[0]
+        selp = sel.ctypes.data_as(C.POINTER(C.c_int32))
+    else:
+        n = int(x.shape[0])
+        selp = None
+    steps = lib().fv_mlp_train_steps(C.byref(tc), n)
+    hist = torch.zeros(max(steps, 1), dtype=torch.float32, device=x.device)
+    _check(lib().fv_mlp_train(_dptr(params, "float32"), _dptr(x, "float32"), _dptr(y, "float32"),
+                              selp, n, C.byref(tc), _dptr(hist, "float32"), _stream(stream)),
+           "fv_mlp_train")
+    return hist[:steps].cpu().numpy()
+
+
+def fv_mlp_load(h, params, target, gate=-1.0):
+    _check(lib().fv_mlp_load(h, _dptr(params, "float32"), FV_MLP_PARAMS, int(target), float(gate)),
+           "fv_mlp_load")
+
+
+def fv_set_guess(h, guess):
+    _check(lib().fv_set_guess(h, int(guess)), "fv_set_guess")
+
+
+def fv_harvest_pairs(h, count, seed, out=None, stream=None):
+    """(count, 6) float64 CUDA tensor of face-frame Riemann pairs of U^n."""
+    import torch
+    if out is None:
+        out = torch.empty((int(count), 6), dtype=torch.float64, device="cuda")
+    _check(lib().fv_harvest_pairs(h, _dptr(out), int(count), int(seed), _stream(stream)),
+           "fv_harvest_pairs")
+    return out
+
+
+def fv_godunov_flux_batch_mlp(WL, WR, nrm, cfg: fv_config, packed, stream=None):
+    import torch
+    n = int(WL.shape[1])
+    F = torch.empty((5, n), dtype=torch.float64, device=WL.device)
+    iters = torch.empty(n, dtype=torch.int32, device=WL.device)
+    _check(lib().fv_godunov_flux_batch_mlp(_dptr(WL), _dptr(WR), _dptr(nrm), n, C.byref(cfg),
+                                           _dptr(packed, "uint8"), _dptr(F), _dptr(iters, "int32"),
+                                           _stream(stream)), "fv_godunov_flux_batch_mlp")
+    return F, iters
+
+
 def fv_probe_fma_peak(precision, device=0) -> float:
     """Measured FMA ceiling (TFLOP/s) in FP64 (FV_FP64) or FP32."""
     t = C.c_double()
@@ -474,6 +619,15 @@ class Mesh:
 
     def set_launch(self, per_sm):
         fv_set_launch(self.h, per_sm)
+
+    def mlp_load(self, params, target=FV_MLP_TARGET_TR, gate=-1.0):
+        fv_mlp_load(self.h, params, target, gate)
+
+    def set_guess(self, guess):
+        fv_set_guess(self.h, guess)
+
+    def harvest_pairs(self, count, seed, out=None, stream=None):
+        return fv_harvest_pairs(self.h, count, seed, out, stream)
 
     def get_launch(self):
         return fv_get_launch(self.h)

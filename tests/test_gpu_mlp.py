@@ -1,0 +1,332 @@
+"""GPU tests of the learned starting guess (fv_mlp_*): the bfloat16
+tensor-core inference against the oracle's quantised forward pass, the FP32
+training kernels' loss, gradient and Adam step against the oracle's FP64
+ones, labels against the oracle's exact solver, harvest coverage, and the
+solver with the guess switched on against the oracle run with the
+two-rarefaction guess (Newton's stopping rule is unchanged, so the results
+agree within the path's tolerance)."""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+NP = 4673
+
+
+@pytest.fixture(scope="module")
+def fv():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1704_01144_gb300 import build, fv as F
+    build.build()
+    return F
+
+
+def features(rng, n):
+    """Normalised inputs with the spread of face pairs: deviations of density,
+    velocity and pressure from the pair's mean, opposite on the two sides,
+    from tiny jumps to strong ones."""
+    x = np.empty((n, 6), dtype=np.float32)
+    mag = 10.0 ** rng.uniform(-4, 0, (n, 3))
+    d = np.sign(rng.normal(size=(n, 3))) * mag * np.array([0.95, 1.5, 0.98])
+    x[:, 0:3] = d
+    x[:, 3:6] = -d
+    return x
+
+
+def theta_random(fv, seed, noise=0.3):
+    th = fv.fv_mlp_init(seed).astype(np.float64)
+    rng = np.random.default_rng(seed)
+    th[384:448] = rng.normal(0, noise, 64)          # biases too, so every term is exercised
+    th[4544:4608] = rng.normal(0, noise, 64)
+    th[4672] = 0.3
+    return th.astype(np.float32)
+
+
+def random_pairs(rng, n):
+    r = rng.uniform(0.2, 2.0, (n, 2))
+    p = np.exp(rng.uniform(np.log(0.1), np.log(10.0), (n, 2)))
+    u = rng.uniform(-1.0, 1.0, (n, 2))
+    return np.stack([r[:, 0], u[:, 0], p[:, 0], r[:, 1], u[:, 1], p[:, 1]], axis=1)
+
+
+@pytest.mark.parametrize("n", [1, 31, 1037, 20000])
+def test_infer_matches_quantised_oracle(fv, oracle_mod, n):
+    import torch
+    rng = np.random.default_rng(100 + n)
+    th = theta_random(fv, 7)
+    x = features(rng, n)
+    thd = torch.from_numpy(th).cuda()
+    for target in (0, 1):
+        pk = fv.fv_mlp_pack(thd, target)
+        y = fv.fv_mlp_infer(pk, torch.from_numpy(x).cuda()).cpu().numpy().astype(np.float64)
+        ref = oracle_mod.mlp_forward_bf16(th, x)
+        err = np.abs(y - ref)
+        # FP32 accumulation order, the hardware tanh (relative error ~2^-11)
+        # and an occasional one-ulp bfloat16 flip of a hidden activation
+        assert err.max() <= 2e-2, err.max()
+        assert err.mean() <= 2e-3, err.mean()
+    full = oracle_mod.mlp_forward(th.astype(np.float64), x.astype(np.float64))
+    assert np.abs(y - full).max() < 0.1
+
+
+def test_loss_grad_matches_oracle(fv, oracle_mod):
+    import torch
+    rng = np.random.default_rng(3)
+    n = 300                                      # two full tiles and a ragged one
+    th = theta_random(fv, 11)
+    x = features(rng, n)
+    t = rng.normal(0, 0.5, n).astype(np.float32)
+    loss, g = fv.fv_mlp_loss_grad(torch.from_numpy(th).cuda(), torch.from_numpy(x).cuda(),
+                                  torch.from_numpy(t).cuda())
+    lo, go = oracle_mod.mlp_loss_grad(th.astype(np.float64), x.astype(np.float64), t.astype(np.float64))
+    assert loss == pytest.approx(lo, rel=1e-5)
+    g = g.cpu().numpy().astype(np.float64)
+    assert np.abs(g - go).max() <= 1e-4 * np.abs(go).max()
+    # a selection of samples, in a scrambled order
+    sel = rng.permutation(n)[:173].astype(np.int32)
+    loss2, g2 = fv.fv_mlp_loss_grad(torch.from_numpy(th).cuda(), torch.from_numpy(x).cuda(),
+                                    torch.from_numpy(t).cuda(), sel=torch.from_numpy(sel).cuda())
+    lo2, go2 = oracle_mod.mlp_loss_grad(th.astype(np.float64), x[sel].astype(np.float64),
+                                        t[sel].astype(np.float64))
+    assert loss2 == pytest.approx(lo2, rel=1e-5)
+    assert np.abs(g2.cpu().numpy() - go2).max() <= 1e-4 * np.abs(go2).max()
+
+
+def test_adam_matches_oracle(fv, oracle_mod):
+    import torch
+    rng = np.random.default_rng(4)
+    th = rng.normal(size=NP).astype(np.float32)
+    g1 = rng.normal(size=NP).astype(np.float32)
+    g2 = rng.normal(size=NP).astype(np.float32)
+    p = torch.from_numpy(th.copy()).cuda()
+    m = torch.zeros(NP, dtype=torch.float32, device="cuda")
+    v = torch.zeros(NP, dtype=torch.float32, device="cuda")
+    tho, mo, vo = th.astype(np.float64), np.zeros(NP), np.zeros(NP)
+    for step, g in ((1, g1), (2, g2)):
+        fv.fv_mlp_adam(p, m, v, torch.from_numpy(g).cuda(), step, 1e-3)
+        oracle_mod.adam_step(tho, mo, vo, g.astype(np.float64), step, 1e-3)
+    torch.cuda.synchronize()
+    assert np.abs(p.cpu().numpy() - tho).max() <= 1e-6
+
+
+def test_label_matches_oracle(fv, oracle_mod):
+    import torch
+    rng = np.random.default_rng(5)
+    pairs = random_pairs(rng, 2000)
+    x, y, ps = fv.fv_mlp_label(torch.from_numpy(pairs).cuda(), 0)
+    x, y, ps = x.cpu().numpy(), y.cpu().numpy(), ps.cpu().numpy()
+    _, y1, _, q = fv.fv_mlp_label(torch.from_numpy(pairs).cuda(), 1, want_q=True)
+    y1, q = y1.cpu().numpy(), q.cpu().numpy()
+    xo, pbo, ptro = oracle_mod.mlp_features(pairs)
+    for i in range(0, 2000, 7):
+        pso, _, _ = oracle_mod.riemann(pairs[i, 0:3], pairs[i, 3:6], tol=1e-14, maxit=100)
+        assert ps[i] == pytest.approx(pso, rel=1e-12)
+        assert y[i] == pytest.approx(math.log(pso / pbo[i]), abs=2e-6)
+        yo1, qo = oracle_mod.mlp_target(pairs[i], 1, pso)
+        assert y1[i] == pytest.approx(yo1, rel=1e-5, abs=2e-6)
+        assert q[i] == pytest.approx(qo, rel=1e-6, abs=1e-7)
+    assert np.allclose(x, xo, rtol=2e-6, atol=2e-7)
+
+
+def test_label_reports_vacuum(fv):
+    import torch
+    pairs = np.array([[1.0, -10.0, 0.1, 1.0, 10.0, 0.1]])
+    with pytest.raises(fv.FvError) as e:
+        fv.fv_mlp_label(torch.from_numpy(pairs).cuda(), 0)
+    assert e.value.code == fv.FV_ERR_RIEMANN
+
+
+def test_harvest_covers_every_face_once(fv, oracle_mod):
+    """Free stream: every pair is (rho, u.n, p | rho, u.n, p) (a wall face:
+    u.n mirrored), and harvesting F pairs visits each face exactly once --
+    the multiset of |u.n| equals the one over the oracle's face normals."""
+    import torch
+    from paper_1704_01144_gb300 import inputs as I
+    mesh, prim = I.uniform_flow_case(n=5)
+    rho0, u0, p0 = prim[0][0], np.array([prim[c][0] for c in (1, 2, 3)]), prim[4][0]
+    o = oracle_mod.Oracle(mesh, max_levels=1)
+    own, nb, bc, area, nrm = o.face_data()
+    want = np.sort(np.abs(nrm.reshape(3, -1).T @ u0))
+    for prec in (fv.FV_FP64, fv.FV_FP32_FLUX):
+        m = fv.Mesh(mesh, max_levels=1, precision=prec)
+        m.set_state(prim)
+        F = m.nf
+        pr = m.harvest_pairs(F, seed=9).cpu().numpy()
+        tol = 1e-14 if prec == fv.FV_FP64 else 1e-6
+        assert np.allclose(pr[:, [0, 3]], rho0, rtol=tol)
+        assert np.allclose(pr[:, [2, 5]], p0, rtol=tol)
+        wall = np.isclose(pr[:, 4], -pr[:, 1], atol=1e-15) & ~np.isclose(pr[:, 1], 0.0, atol=1e-15)
+        inter = np.isclose(pr[:, 4], pr[:, 1], rtol=tol, atol=tol)
+        assert np.all(wall | inter)
+        assert np.allclose(np.sort(np.abs(pr[:, 1])), want, rtol=tol, atol=tol)
+        again = m.harvest_pairs(F, seed=9).cpu().numpy()
+        assert np.array_equal(pr, again)
+        other = m.harvest_pairs(F // 3, seed=10).cpu().numpy()
+        assert not np.array_equal(other, pr[:F // 3])
+
+
+GATE = 0.02
+
+
+def trained_net(fv, seed=1, n_cells=16, cycles=8, target=1, epochs=30, gate=GATE):
+    """Harvest, label and train on a small blast run (the pipeline of the
+    learned guess at test size); trains on the pairs past the gate."""
+    import torch
+    from paper_1704_01144_gb300 import inputs as I
+    mesh, prim = I.blast_case(n=n_cells)
+    m = fv.Mesh(mesh, max_levels=3, precision=fv.FV_FP64)
+    m.set_state(prim)
+    chunks = []
+    per = m.nf // 2
+    for c in range(cycles):
+        m.advance(1, want_time=False)
+        chunks.append(m.harvest_pairs(per, seed=seed * 1000 + c))
+    pairs = torch.cat(chunks)
+    x, y, ps, q = fv.fv_mlp_label(pairs, target, want_q=True)
+    n = pairs.shape[0]
+    perm = np.random.default_rng(seed).permutation(n)
+    tr, te = perm[: n * 9 // 10], perm[n * 9 // 10:]
+    qh = q.cpu().numpy()
+    trg = tr[qh[tr] > gate]
+    th = torch.from_numpy(fv.fv_mlp_init(seed)).cuda()
+    hist = fv.fv_mlp_train(th, x, y, sel=trg, epochs=epochs, batch=1024, lr0=3e-3, lr1=3e-5, seed=seed)
+    return th, hist, pairs, x, y, ps, qh, trg, te
+
+
+def test_training_learns_and_is_deterministic(fv, oracle_mod):
+    import torch
+    th, hist, pairs, x, y, ps, q, tr, te = trained_net(fv)
+    assert np.all(np.isfinite(hist))
+    k = max(1, len(hist) // 10)
+    assert hist[-k:].mean() < 0.5 * hist[:k].mean()
+    th2, hist2, *_ = trained_net(fv)
+    assert torch.equal(th, th2)
+    assert np.array_equal(hist, hist2)
+    # held-out loss close to the training loss (no memorisation at this size)
+    sel = torch.from_numpy(te[q[te] > GATE].astype(np.int32)).cuda()
+    lte, _ = fv.fv_mlp_loss_grad(th, x, y, sel=sel, want_grad=False)
+    ltr, _ = fv.fv_mlp_loss_grad(th, x, y, sel=torch.from_numpy(tr.astype(np.int32)).cuda(),
+                                 want_grad=False)
+    assert lte < 3 * ltr + 1e-6
+
+
+def face_frame(pairs):
+    """Face-frame pairs -> 3-D primitives with normal (1, 0, 0)."""
+    import torch
+    n = pairs.shape[0]
+    WL = torch.zeros((5, n), dtype=torch.float64, device="cuda")
+    WR = torch.zeros_like(WL)
+    WL[0], WL[1], WL[4] = pairs[:, 0], pairs[:, 1], pairs[:, 2]
+    WR[0], WR[1], WR[4] = pairs[:, 3], pairs[:, 4], pairs[:, 5]
+    nrm = torch.zeros((3, n), dtype=torch.float64, device="cuda")
+    nrm[0] = 1.0
+    return WL, WR, nrm
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_flux_with_learned_guess_matches_oracle(fv, oracle_mod, precision):
+    """Even an untrained network's guess leaves the converged flux within the
+    path's tolerance of the oracle's (which starts from the two-rarefaction
+    guess)."""
+    import torch
+    rng = np.random.default_rng(21)
+    n = 3001
+    pairs = random_pairs(rng, n)
+    WL, WR, _ = face_frame(torch.from_numpy(pairs).cuda())
+    nrm = torch.from_numpy(rng.normal(size=(3, n))).cuda()
+    nrm /= torch.linalg.norm(nrm, dim=0)
+    # rotate the 1-D states into the random normals
+    for W in (WL, WR):
+        un = W[1].clone()
+        W[1:4] = un * nrm
+    cfg = fv.fv_config_default(precision=precision)
+    for target in (0, 1):
+        pk = fv.fv_mlp_pack(torch.from_numpy(theta_random(fv, 30 + target)).cuda(), target)
+        F, it = fv.fv_godunov_flux_batch_mlp(WL, WR, nrm, cfg, pk)
+        F, it = F.cpu().numpy(), it.cpu().numpy()
+        assert np.all(it > 0)
+        wl, wr, nn = WL.cpu().numpy(), WR.cpu().numpy(), nrm.cpu().numpy()
+        tol = 1e-12 if precision == 0 else 5e-5
+        for i in range(0, n, 11):
+            ref = oracle_mod.godunov_flux(wl[:, i], wr[:, i], nn[:, i])
+            scale = max(np.abs(ref).max(), 1e-300)
+            assert np.abs(F[:, i] - ref).max() <= tol * scale, (i, F[:, i], ref)
+
+
+@pytest.mark.parametrize("precision,target", [(0, 0), (0, 1), (1, 1)])
+def test_solver_with_learned_guess_matches_oracle(fv, oracle_mod, precision, target):
+    import torch
+    from paper_1704_01144_gb300 import inputs as I
+    mesh, prim = I.blast_case(n=8)
+    L = 3
+    m = fv.Mesh(mesh, max_levels=L, precision=precision)
+    m.set_state(prim)
+    th = torch.from_numpy(theta_random(fv, 40 + target)).cuda()
+    m.mlp_load(th, target)
+    o = oracle_mod.Oracle(mesh, max_levels=L)
+    o.set_prim(prim)
+    for _ in range(3):
+        m.advance(1, want_time=False)
+        o.advance(1)
+    assert m.status() == 0
+    U, Uo = m.get_state(), o.get_cons()
+    rel = np.abs(U - Uo).max(axis=1) / np.abs(Uo).max(axis=1)
+    tol = 1e-12 if precision == 0 else 1e-5
+    assert rel.max() <= tol, rel
+    # switching back to the two-rarefaction guess is allowed, and the batch
+    # refuses a mesh with the learned guess until then
+    with pytest.raises(fv.FvError):
+        fv.Batch([m])
+    m.set_guess(fv.FV_GUESS_TWO_RAREFACTION)
+    m.advance(1, want_time=False)
+    assert m.status() == 0
+
+
+def test_guess_requires_a_network(fv):
+    from paper_1704_01144_gb300 import inputs as I
+    mesh, _ = I.blast_case(n=6)
+    m = fv.Mesh(mesh, max_levels=2)
+    with pytest.raises(fv.FvError):
+        m.set_guess(fv.FV_GUESS_MLP)
+
+
+def test_learned_guess_gain(fv, oracle_mod):
+    """What the trained network gains over the two-rarefaction guess on
+    held-out harvested pairs: the error of the starting guess where the gate
+    passes, and the Newton iterations to the same tolerance there and over
+    all pairs (all printed); the fluxes agree within the FP64 tolerance."""
+    import torch
+    th, hist, pairs, x, y, ps, q, tr, te = trained_net(fv, target=1)
+    cfg = fv.fv_config_default(precision=0)
+    pk = fv.fv_mlp_pack(th, 1, gate=GATE)
+    gated = te[q[te] > GATE]
+    out = {}
+    for name, idx in (("gated", gated), ("all", te)):
+        it_t = torch.from_numpy(idx).cuda()
+        WL, WR, nrm = face_frame(pairs[it_t])
+        F_tr, it_tr = fv.fv_godunov_flux_batch(WL, WR, nrm, cfg)
+        F_ml, it_ml = fv.fv_godunov_flux_batch_mlp(WL, WR, nrm, cfg, pk)
+        assert torch.all(it_tr > 0) and torch.all(it_ml > 0)
+        scale = F_tr.abs().max(dim=0).values
+        assert ((F_ml - F_tr).abs().max(dim=0).values <= 1e-12 * scale + 1e-300).all()
+        out[name] = (it_tr.double().mean().item(), it_ml.double().mean().item())
+    g_t = torch.from_numpy(gated).cuda()
+    yte = y[g_t]
+    pred = fv.fv_mlp_infer(pk, x[g_t].contiguous())
+    # target = log(p*/p_TR) / s(q): guess errors |log(p_guess/p*)| are s(q)
+    # times the target's error
+    qg = torch.from_numpy(q[gated]).cuda().double()
+    sc = (qg / (1 + qg)) ** 3
+    err_tr = (sc * yte.double()).abs().mean().item()
+    err_ml = (sc * (pred - yte).double()).abs().mean().item()
+    print(f"\nheld-out pairs {len(te)}, {len(gated)} past the gate q > {GATE}: "
+          f"mean |log(p_guess/p*)| there: two-rarefaction {err_tr:.3e}, learned {err_ml:.3e}; "
+          f"mean Newton iterations there {out['gated'][0]:.3f} -> {out['gated'][1]:.3f}, "
+          f"over all pairs {out['all'][0]:.4f} -> {out['all'][1]:.4f}")
+    assert err_ml < err_tr
+    assert out["gated"][1] < out["gated"][0]
+    assert out["all"][1] <= out["all"][0]

@@ -171,8 +171,14 @@ def test_features_of_mirrored_states(oracle_mod):
     r, u, p, g = 1.3, 0.4, 2.0, 1.4
     x, pb, ptr = oracle_mod.mlp_features([[r, u, p, r, -u, p]], gamma=g)
     a = math.sqrt(g * p / r)
-    assert np.allclose(x[0], [1, u / a, 1, 1, -u / a, 1], rtol=1e-15, atol=0)
+    assert np.allclose(x[0], [0, u / a, 0, 0, -u / a, 0], rtol=1e-15, atol=0)
     assert pb[0] == p
+    # a common velocity drops out (the star pressure is Galilean invariant)
+    x2, _, _ = oracle_mod.mlp_features([[r, u + 5.0, p, r, -u + 5.0, p]], gamma=g)
+    assert np.allclose(x2, x, rtol=1e-14, atol=1e-15)
+    # left/right deviations are opposite; Sod's are the relative jumps
+    x3, _, _ = oracle_mod.mlp_features([[1.0, 0.0, 1.0, 0.125, 0.0, 0.1]])
+    assert np.allclose(x3[0], [0.875 / 1.125, 0, 0.9 / 1.1, -0.875 / 1.125, 0, -0.9 / 1.1], rtol=1e-15)
     # identical states at rest: the two-rarefaction guess is exact
     _, _, ptr = oracle_mod.mlp_features([[r, 0.0, p, r, 0.0, p]], gamma=g)
     assert ptr[0] == pytest.approx(p, rel=1e-14)
@@ -192,3 +198,34 @@ def test_tr_guess_exact_for_two_rarefactions_and_sod_target(oracle_mod):
     ps, _, _ = oracle_mod.riemann(t1[0:3], t1[3:6], tol=1e-14, maxit=100)
     assert math.log(ps / pb[0]) == pytest.approx(math.log(t1[6] / 0.55), abs=2e-5)
     assert ptr[0] > t1[6] * 1.005
+
+
+def test_target_scaling(oracle_mod):
+    rows = [[float(v) for v in ln.split()] for ln in read_golden("toro_table_4_3.txt")]
+    # two rarefactions (Toro test 2): q <= 0 and the target is exactly 0
+    t2 = rows[1]
+    y, q = oracle_mod.mlp_target(t2[:6], 1, t2[6])
+    assert q <= 0 and y == 0.0
+    # s(q) = (q/(1+q))^3: q^3 for weak shocks, bounded by 1 for strong ones
+    assert oracle_mod.shock_scale(1e-2) == pytest.approx(1e-6 / 1.01 ** 3, rel=1e-14)
+    assert oracle_mod.shock_scale(1.0) == 0.125
+    assert oracle_mod.shock_scale(1e6) == pytest.approx(1.0, rel=4e-6)
+    assert oracle_mod.shock_scale(-0.5) == 0.0
+    # Toro test 3 (q ~ 9e4): the target is log(p*/p_TR) itself, of order one
+    t3 = rows[2]
+    y3, q3 = oracle_mod.mlp_target(t3[:6], 1, t3[6])
+    assert q3 > 1e4 and -1.0 < y3 < -0.3
+    # a weak shock: log(p*/p_TR) shrinks like q^3, so the scaled target stays
+    # of order one as the jump vanishes
+    ys = []
+    for eps in (0.2, 0.1, 0.05):
+        pair = [1.0, 0.0, 1.0 + eps, 1.0, 0.0, 1.0]
+        ps, _, _ = oracle_mod.riemann(pair[:3], pair[3:], tol=1e-15, maxit=100)
+        y, q = oracle_mod.mlp_target(pair, 1, ps)
+        assert q > 0
+        ys.append(y)
+    assert all(abs(v) < 1.0 for v in ys) and abs(ys[2] - ys[1]) < abs(ys[1] - ys[0])
+    # target 0 is log(p*/pbar)
+    t1 = rows[0]
+    y0, _ = oracle_mod.mlp_target(t1[:6], 0, t1[6])
+    assert y0 == pytest.approx(math.log(t1[6] / 0.55), rel=1e-14)
