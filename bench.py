@@ -203,12 +203,15 @@ def describe(name, mesh, L):
 
 
 # ------------------------------------------------------------------ ours ---
-def run_mode(fv, torch, mesh, prim, L, precision, steps, warmup, stream, flush, gpu_index):
+def run_mode(fv, torch, mesh, prim, L, precision, steps, warmup, stream, flush, gpu_index,
+             setup=None, tag=""):
     from paper_1704_01144_gb300 import autotune as AT
     g = fv.Mesh(mesh, max_levels=L, precision=precision)
+    if setup is not None:
+        setup(g)
     g.set_state(prim)
     # grid sizes picked by the project's autotuner (cached per GPU and workload)
-    per_sm, tune = AT.autotune(g, f"mesh|N{g.n}|F{g.nf}|L{L}|prec{precision}", stream=stream,
+    per_sm, tune = AT.autotune(g, f"mesh|N{g.n}|F{g.nf}|L{L}|prec{precision}{tag}", stream=stream,
                                reset=lambda: g.set_state(prim))
     g.set_state(prim)
     with torch.cuda.stream(stream):
@@ -298,6 +301,74 @@ def cpu_baseline(mesh, prim, L, budget_s=15.0, max_cycles=4):
                       f"({O.num_threads()} OpenMP threads), {dt:.1f} s"}
 
 
+def replica_stats(local, device):
+    """all_gather of this rank's [cell updates, ms per step, e2e value] over
+    the job's process group (any backend); returns a (world, 3) array."""
+    import torch
+    t = torch.tensor([float(v) for v in local], dtype=torch.float64, device=device)
+    vals = [torch.zeros_like(t) for _ in range(torch.distributed.get_world_size())]
+    torch.distributed.all_gather(vals, t)
+    return torch.stack(vals).cpu().numpy()
+
+
+def aggregate_replicas(vals, steps):
+    """(whole-job cell-updates/s, ms per step, summed e2e) from the gathered
+    per-rank stats: every rank's updates over the slowest rank's time."""
+    ms_max = float(vals[:, 1].max())
+    return float(vals[:, 0].sum() / (ms_max * steps * 1e-3)), ms_max, float(vals[:, 2].sum())
+
+
+def train_learned_guess(fv, torch, mesh, prim, L, cycles=40, per_cycle=250_000, seed=1):
+    """The learned guess for this workload: ~10M Riemann pairs harvested
+    between cycles of its own FP32-flux run, labelled, split 90/10, the
+    network trained on the training pairs past the gate (all on the GPU)."""
+    from paper_1704_01144_gb300 import learned_guess as LG
+    t0 = time.perf_counter()
+    h = fv.Mesh(mesh, max_levels=L, precision=fv.FV_FP32_FLUX)
+    pairs = LG.harvest(h, prim, cycles, min(per_cycle, h.nf), seed)
+    h.close()
+    params, data = LG.train(pairs, gate=LG.DEFAULT_GATE, epochs=20, batch=4096, seed=seed)
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    ev = {"fp32": LG.evaluate(params, pairs, data, gate=LG.DEFAULT_GATE, precision=fv.FV_FP32_FLUX),
+          "fp64": LG.evaluate(params, pairs, data, gate=LG.DEFAULT_GATE, precision=fv.FV_FP64)}
+    info = data["info"]
+    del pairs, data
+    torch.cuda.empty_cache()
+    return {"params": params, "gate": LG.DEFAULT_GATE, "info": info, "eval": ev, "seconds": secs}
+
+
+def gate_sweep(fv, torch, g, prim, guess, stream, flush, gates=(0.1, 0.3, 1.0, 1e30), cycles=5):
+    """Throughput of the learned-guess mesh at other gates (1e30: the network
+    never fires, which leaves the fixed cost of the gate test), 5 timed
+    cycles each after 3 warm-up cycles."""
+    out = {}
+    for gate in gates:
+        g.mlp_load(guess["params"], fv.FV_MLP_TARGET_TR, gate)
+        g.set_state(prim)
+        for _ in range(3):
+            g.advance(1, stream=stream, want_time=False)
+        torch.cuda.synchronize()
+        c0 = g.work_counters()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(cycles)]
+        with torch.cuda.stream(stream):
+            for k in range(cycles):
+                flush.add_(1.0)
+                ev[k][0].record(stream)
+                g.advance(1, stream=stream, want_time=False)
+                ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        c1 = g.work_counters()
+        if g.status() != 0:
+            raise RuntimeError(f"gate sweep: {fv.fv_last_error()}")
+        out[f"{gate:g}"] = {"value": round((c1[1] - c0[1]) / (ms * 1e-3), 1),
+                            "ms_per_step": round(ms / cycles, 4)}
+    g.mlp_load(guess["params"], fv.FV_MLP_TARGET_TR, guess["gate"])
+    return out
+
+
 def main_ours(args):
     import torch
     ws, rank, local = _dist()
@@ -320,31 +391,34 @@ def main_ours(args):
 
     res = {}
     modes = [m for m in args.modes.split(",") if m]
-    for name, prec in (("fp64", fv.FV_FP64), ("fp32flux", fv.FV_FP32_FLUX)):
+    guess = None
+    if "fp32mlp" in modes:
+        guess = train_learned_guess(fv, torch, mesh, prim, L)
+    for name, prec in (("fp64", fv.FV_FP64), ("fp32flux", fv.FV_FP32_FLUX),
+                       ("fp32mlp", fv.FV_FP32_FLUX)):
         if name not in modes:
             continue
+        setup, tag = None, ""
+        if name == "fp32mlp":
+            setup = lambda g: g.mlp_load(guess["params"], fv.FV_MLP_TARGET_TR, guess["gate"])
+            tag = f"|mlp{guess['gate']}"
         g, r = run_mode(fv, torch, mesh, prim, L, prec, args.steps, args.warmup, stream, flush,
-                        gpu_index)
+                        gpu_index, setup=setup, tag=tag)
         r["g"] = g
         res[name] = r
     chosen = res["fp32flux"] if "fp32flux" in res else res["fp64"]
     e2e = None if args.no_e2e else run_e2e(fv, torch, chosen["g"], max(3, min(args.steps, 10)), 1,
                                            stream)
 
-    # whole-job aggregate over ranks (replicas): sum of values, max of times
+    # whole-job aggregate over ranks (independent replicas, no data-path
+    # collective): the work of all ranks over the slowest rank's time
     value = chosen["value"]
     ms_step = chosen["ms_per_step"]
     if ws > 1:
-        t = torch.tensor([value, ms_step, e2e["value"] if e2e else 0.0], dtype=torch.float64,
-                         device="cuda")
-        vals = [torch.zeros_like(t) for _ in range(ws)]
-        torch.distributed.all_gather(vals, t)
-        vals = torch.stack(vals).cpu().numpy()
-        # every rank ran the same work: total = sum of per-rank work / max time
-        value = float(chosen["cell_updates"] * ws / (vals[:, 1].max() * args.steps * 1e-3))
-        ms_step = float(vals[:, 1].max())
+        vals = replica_stats([chosen["cell_updates"], ms_step, e2e["value"] if e2e else 0.0], "cuda")
+        value, ms_step, e2e_total = aggregate_replicas(vals, args.steps)
         if e2e:
-            e2e["value"] = float(vals[:, 2].sum())
+            e2e["value"] = e2e_total
 
     peaks, peak_src = _load_peaks()
     alu_peaks = {"fp64_tflops": fv.fv_probe_fma_peak(fv.FV_FP64, local),
@@ -435,6 +509,23 @@ def main_ours(args):
             "cell_updates_per_step": chosen["cell_updates"] / args.steps,
             "face_evals_per_step": chosen["face_evals"] / args.steps,
         }
+        if "fp32mlp" in res:
+            r = res["fp32mlp"]
+            fl = lambda rr: rr["prof"]["flux"][0] / max(1, rr["prof_face_evals"]) * 1e6
+            sweep = gate_sweep(fv, torch, r["g"], prim, guess, stream, flush)
+            line["learned_guess"] = {
+                "what": "FP32-flux mode with the learned p* guess (bf16 tensor-core MLP fused "
+                        "into the flux kernel, gated by the two-rarefaction shock strength), "
+                        "same workload, graph and timing as the line's value",
+                "value": round(r["value"], 1), "unit": "cell-updates/s",
+                "ms_per_step": round(r["ms_per_step"], 4),
+                "vs_two_rarefaction_guess": round(r["value"] / chosen["value"], 4),
+                "flux_ns_per_face_eval": {"learned": round(fl(r), 4),
+                                          "two_rarefaction": round(fl(chosen), 4)},
+                "kernels": kernel_shares(r), "clocks": r["clocks"],
+                "training": guess["info"], "heldout": guess["eval"],
+                "train_s": round(guess["seconds"], 2),
+                "gate_sweep": sweep}
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.barrier()
@@ -585,8 +676,8 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch64"], default="blast1m")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--modes", default="fp64,fp32flux",
-                    help="comma list of fp64,fp32flux (the last is the chosen form)")
+    ap.add_argument("--modes", default="fp64,fp32flux,fp32mlp",
+                    help="comma list of fp64, fp32flux (the line's value) and fp32mlp (FP32 flux with the learned guess)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

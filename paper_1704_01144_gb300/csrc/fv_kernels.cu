@@ -865,8 +865,11 @@ __global__ void KBOUNDS(KIND, T) k_phase1(DevMesh d, const __grid_constant__ Pha
 
 // flux with the learned guess: the packed network staged in shared memory,
 // the loop warp-uniform (lanes past the end ride along without a face)
+#ifndef FV_MLP_FLUX_BLOCKS
+#define FV_MLP_FLUX_BLOCKS 8  // resident 128-thread blocks per SM (64 registers)
+#endif
 template <typename T, bool G14>
-__global__ void __launch_bounds__(128, 4) k_flux_mlp1(DevMesh d, const __grid_constant__ PhaseDesc p,
+__global__ void __launch_bounds__(128, FV_MLP_FLUX_BLOCKS) k_flux_mlp1(DevMesh d, const __grid_constant__ PhaseDesc p,
                                                       GasT<T> G) {
   __shared__ __align__(16) uint32_t sw[PK_WORDS];
   mlp_stage(sw, d.mlp);
@@ -1238,7 +1241,9 @@ static void phase1_all(const DevMesh &d, const PhaseDesc &pd, const GasT<T> &G, 
   {
     ProfScope sc(ph, FV_PROF_FLUX, s);
     if (d.guess == FV_GUESS_MLP)
-      k_flux_mlp1<T, G14><<<grid_for(d.F, 128, lc.per_sm[2] < 4 ? lc.per_sm[2] : 4), 128, 0, s>>>(d, pd, G);
+      k_flux_mlp1<T, G14><<<grid_for(d.F, 128, lc.per_sm[2] < FV_MLP_FLUX_BLOCKS ? lc.per_sm[2]
+                                                                                  : FV_MLP_FLUX_BLOCKS),
+                            128, 0, s>>>(d, pd, G);
     else
       k_phase1<K_FLUX, T, G14><<<g2, 128, 0, s>>>(d, pd, G);
   }

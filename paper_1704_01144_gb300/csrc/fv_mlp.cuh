@@ -125,74 +125,74 @@ __device__ __forceinline__ float shock_strength(float gamma, float rL, float uL,
 
 // the network output for this lane's features; every lane of the warp must
 // call it together (mma.sync and full-mask shuffles).  sw: packed weights.
+// The two 16-face tiles go one after the other, which halves the live
+// fragments (the weights are read from shared memory once per tile).
 __device__ __forceinline__ float mlp_eval_warp(const uint32_t *__restrict__ sw, const float x[6]) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   const uint32_t q0 = pack_bf16x2(x[0], x[1]), q1 = pack_bf16x2(x[2], x[3]),
                  q2 = pack_bf16x2(x[4], x[5]);
-  // layer-1 A fragments (m16n8k8): rows g and g+8 of each 16-face tile hold
-  // the features of faces 16 mt + g and 16 mt + 8 + g, columns 2t, 2t+1
-  uint32_t a1f[2][2];
-#pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
+  const float *b1 = reinterpret_cast<const float *>(sw + PK_B1);
+  const float *b2 = reinterpret_cast<const float *>(sw + PK_B2);
+  const float *w3 = reinterpret_cast<const float *>(sw + PK_W3);
+  const uint2 *w2 = reinterpret_cast<const uint2 *>(sw + PK_W2);
+  float yr00 = 0.f, yr01 = 0.f, yr10 = 0.f, yr11 = 0.f;  // [tile][row g / g+8]
+#pragma unroll 1
+  for (int mt = 0; mt < 2; ++mt) {
+    // layer-1 A fragment (m16n8k8): rows g and g+8 of the tile hold the
+    // features of faces 16 mt + g and 16 mt + 8 + g, columns 2t, 2t+1
+    uint32_t a1f[2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int src = 16 * mt + 8 * h + g;
       uint32_t s0 = __shfl_sync(FULL, q0, src), s1 = __shfl_sync(FULL, q1, src),
                s2 = __shfl_sync(FULL, q2, src);
-      a1f[mt][h] = t == 0 ? s0 : t == 1 ? s1 : t == 2 ? s2 : 0u;
+      a1f[h] = t == 0 ? s0 : t == 1 ? s1 : t == 2 ? s2 : 0u;
     }
-  const float *b1 = reinterpret_cast<const float *>(sw + PK_B1);
-  const float *b2 = reinterpret_cast<const float *>(sw + PK_B2);
-  const float *w3 = reinterpret_cast<const float *>(sw + PK_W3);
-  // layer 1 + GELU, re-packed as the A fragments of layer 2: n-tile j
-  // (hidden units 8j..8j+7) fills k-step j/2, registers 0/1 (j even) or
-  // 2/3 (j odd), low/high rows g / g+8
-  uint32_t a2f[2][4][4];
+    // layer 1 + GELU, re-packed as the A fragments of layer 2: n-tile j
+    // (hidden units 8j..8j+7) fills k-step j/2, registers 0/1 (j even) or
+    // 2/3 (j odd), rows g / g+8
+    uint32_t a2f[4][4];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const uint32_t bw = sw[PK_W1 + j * 32 + lane];
-    const float c0 = b1[8 * j + 2 * t], c1 = b1[8 * j + 2 * t + 1];
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
+    for (int j = 0; j < 8; ++j) {
+      const float c0 = b1[8 * j + 2 * t], c1 = b1[8 * j + 2 * t + 1];
       float c[4] = {c0, c1, c0, c1};
-      mma_k8(c, a1f[mt][0], a1f[mt][1], bw);
-      a2f[mt][j >> 1][(j & 1) * 2 + 0] = pack_bf16x2(gelu_infer(c[0]), gelu_infer(c[1]));
-      a2f[mt][j >> 1][(j & 1) * 2 + 1] = pack_bf16x2(gelu_infer(c[2]), gelu_infer(c[3]));
+      mma_k8(c, a1f[0], a1f[1], sw[PK_W1 + j * 32 + lane]);
+      a2f[j >> 1][(j & 1) * 2 + 0] = pack_bf16x2(gelu_infer(c[0]), gelu_infer(c[1]));
+      a2f[j >> 1][(j & 1) * 2 + 1] = pack_bf16x2(gelu_infer(c[2]), gelu_infer(c[3]));
+    }
+    // layer 2 + GELU + the output layer's partial dot products
+    float y0 = 0.f, y1 = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const float c0 = b2[8 * j + 2 * t], c1 = b2[8 * j + 2 * t + 1];
+      float c[4] = {c0, c1, c0, c1};
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        const uint2 bw = w2[(kk * 8 + j) * 32 + lane];
+        mma_k16(c, a2f[kk], bw.x, bw.y);
+      }
+      const float v0 = w3[8 * j + 2 * t], v1 = w3[8 * j + 2 * t + 1];
+      y0 += gelu_infer(c[0]) * v0 + gelu_infer(c[1]) * v1;
+      y1 += gelu_infer(c[2]) * v0 + gelu_infer(c[3]) * v1;
+    }
+    y0 += __shfl_xor_sync(FULL, y0, 1);
+    y0 += __shfl_xor_sync(FULL, y0, 2);
+    y1 += __shfl_xor_sync(FULL, y1, 1);
+    y1 += __shfl_xor_sync(FULL, y1, 2);
+    if (mt == 0) {
+      yr00 = y0;
+      yr01 = y1;
+    } else {
+      yr10 = y0;
+      yr11 = y1;
     }
   }
-  // layer 2 + GELU + the output layer's partial dot products
-  float yp[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
-  const uint2 *w2 = reinterpret_cast<const uint2 *>(sw + PK_W2);
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const float c0 = b2[8 * j + 2 * t], c1 = b2[8 * j + 2 * t + 1];
-    float c[2][4] = {{c0, c1, c0, c1}, {c0, c1, c0, c1}};
-#pragma unroll
-    for (int kk = 0; kk < 4; ++kk) {
-      const uint2 bw = w2[(kk * 8 + j) * 32 + lane];
-      mma_k16(c[0], a2f[0][kk], bw.x, bw.y);
-      mma_k16(c[1], a2f[1][kk], bw.x, bw.y);
-    }
-    const float v0 = w3[8 * j + 2 * t], v1 = w3[8 * j + 2 * t + 1];
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-      yp[mt][0] += gelu_infer(c[mt][0]) * v0 + gelu_infer(c[mt][1]) * v1;
-      yp[mt][1] += gelu_infer(c[mt][2]) * v0 + gelu_infer(c[mt][3]) * v1;
-    }
-  }
-#pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      yp[mt][h] += __shfl_xor_sync(FULL, yp[mt][h], 1);
-      yp[mt][h] += __shfl_xor_sync(FULL, yp[mt][h], 2);
-    }
   // face `lane` is row 16 mt + 8 h + g with (mt, h) = (lane >> 4, (lane >> 3) & 1),
   // held by lane 4 (lane & 7)
   const int src = 4 * (lane & 7), which = lane >> 3;
-  float v0 = __shfl_sync(FULL, yp[0][0], src), v1 = __shfl_sync(FULL, yp[0][1], src),
-        v2 = __shfl_sync(FULL, yp[1][0], src), v3 = __shfl_sync(FULL, yp[1][1], src);
+  float v0 = __shfl_sync(FULL, yr00, src), v1 = __shfl_sync(FULL, yr01, src),
+        v2 = __shfl_sync(FULL, yr10, src), v3 = __shfl_sync(FULL, yr11, src);
   float y = which == 0 ? v0 : which == 1 ? v1 : which == 2 ? v2 : v3;
   return y + __int_as_float((int)sw[PK_B3]);
 }

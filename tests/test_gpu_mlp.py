@@ -173,43 +173,30 @@ GATE = 0.02
 
 
 def trained_net(fv, seed=1, n_cells=16, cycles=8, target=1, epochs=30, gate=GATE):
-    """Harvest, label and train on a small blast run (the pipeline of the
-    learned guess at test size); trains on the pairs past the gate."""
-    import torch
+    """The package's pipeline (harvest from a small blast run, label, train
+    on the pairs past the gate) at test size."""
     from paper_1704_01144_gb300 import inputs as I
+    from paper_1704_01144_gb300 import learned_guess as LG
     mesh, prim = I.blast_case(n=n_cells)
     m = fv.Mesh(mesh, max_levels=3, precision=fv.FV_FP64)
-    m.set_state(prim)
-    chunks = []
-    per = m.nf // 2
-    for c in range(cycles):
-        m.advance(1, want_time=False)
-        chunks.append(m.harvest_pairs(per, seed=seed * 1000 + c))
-    pairs = torch.cat(chunks)
-    x, y, ps, q = fv.fv_mlp_label(pairs, target, want_q=True)
-    n = pairs.shape[0]
-    perm = np.random.default_rng(seed).permutation(n)
-    tr, te = perm[: n * 9 // 10], perm[n * 9 // 10:]
-    qh = q.cpu().numpy()
-    trg = tr[qh[tr] > gate]
-    th = torch.from_numpy(fv.fv_mlp_init(seed)).cuda()
-    hist = fv.fv_mlp_train(th, x, y, sel=trg, epochs=epochs, batch=1024, lr0=3e-3, lr1=3e-5, seed=seed)
-    return th, hist, pairs, x, y, ps, qh, trg, te
+    pairs = LG.harvest(m, prim, cycles, m.nf // 2, seed)
+    th, data = LG.train(pairs, target=target, gate=gate, epochs=epochs, batch=1024, seed=seed)
+    return th, data, pairs
 
 
 def test_training_learns_and_is_deterministic(fv, oracle_mod):
     import torch
-    th, hist, pairs, x, y, ps, q, tr, te = trained_net(fv)
-    assert np.all(np.isfinite(hist))
-    k = max(1, len(hist) // 10)
-    assert hist[-k:].mean() < 0.5 * hist[:k].mean()
-    th2, hist2, *_ = trained_net(fv)
+    th, data, pairs = trained_net(fv)
+    info = data["info"]
+    assert info["loss_last"] < 0.5 * info["loss_first"]
+    th2, data2, pairs2 = trained_net(fv)
+    assert torch.equal(pairs, pairs2)
     assert torch.equal(th, th2)
-    assert np.array_equal(hist, hist2)
     # held-out loss close to the training loss (no memorisation at this size)
+    te, q, x, y = data["heldout"], data["q"], data["x"], data["y"]
     sel = torch.from_numpy(te[q[te] > GATE].astype(np.int32)).cuda()
     lte, _ = fv.fv_mlp_loss_grad(th, x, y, sel=sel, want_grad=False)
-    ltr, _ = fv.fv_mlp_loss_grad(th, x, y, sel=torch.from_numpy(tr.astype(np.int32)).cuda(),
+    ltr, _ = fv.fv_mlp_loss_grad(th, x, y, sel=torch.from_numpy(data["train"].astype(np.int32)).cuda(),
                                  want_grad=False)
     assert lte < 3 * ltr + 1e-6
 
@@ -298,35 +285,21 @@ def test_learned_guess_gain(fv, oracle_mod):
     """What the trained network gains over the two-rarefaction guess on
     held-out harvested pairs: the error of the starting guess where the gate
     passes, and the Newton iterations to the same tolerance there and over
-    all pairs (all printed); the fluxes agree within the FP64 tolerance."""
+    all pairs (printed); the fluxes agree within the FP64 tolerance."""
     import torch
-    th, hist, pairs, x, y, ps, q, tr, te = trained_net(fv, target=1)
+    from paper_1704_01144_gb300 import learned_guess as LG
+    th, data, pairs = trained_net(fv, target=1)
+    te = torch.from_numpy(data["heldout"]).cuda()
+    WL, WR, nrm = LG.face_frame(pairs[te])
     cfg = fv.fv_config_default(precision=0)
-    pk = fv.fv_mlp_pack(th, 1, gate=GATE)
-    gated = te[q[te] > GATE]
-    out = {}
-    for name, idx in (("gated", gated), ("all", te)):
-        it_t = torch.from_numpy(idx).cuda()
-        WL, WR, nrm = face_frame(pairs[it_t])
-        F_tr, it_tr = fv.fv_godunov_flux_batch(WL, WR, nrm, cfg)
-        F_ml, it_ml = fv.fv_godunov_flux_batch_mlp(WL, WR, nrm, cfg, pk)
-        assert torch.all(it_tr > 0) and torch.all(it_ml > 0)
-        scale = F_tr.abs().max(dim=0).values
-        assert ((F_ml - F_tr).abs().max(dim=0).values <= 1e-12 * scale + 1e-300).all()
-        out[name] = (it_tr.double().mean().item(), it_ml.double().mean().item())
-    g_t = torch.from_numpy(gated).cuda()
-    yte = y[g_t]
-    pred = fv.fv_mlp_infer(pk, x[g_t].contiguous())
-    # target = log(p*/p_TR) / s(q): guess errors |log(p_guess/p*)| are s(q)
-    # times the target's error
-    qg = torch.from_numpy(q[gated]).cuda().double()
-    sc = (qg / (1 + qg)) ** 3
-    err_tr = (sc * yte.double()).abs().mean().item()
-    err_ml = (sc * (pred - yte).double()).abs().mean().item()
-    print(f"\nheld-out pairs {len(te)}, {len(gated)} past the gate q > {GATE}: "
-          f"mean |log(p_guess/p*)| there: two-rarefaction {err_tr:.3e}, learned {err_ml:.3e}; "
-          f"mean Newton iterations there {out['gated'][0]:.3f} -> {out['gated'][1]:.3f}, "
-          f"over all pairs {out['all'][0]:.4f} -> {out['all'][1]:.4f}")
-    assert err_ml < err_tr
-    assert out["gated"][1] < out["gated"][0]
-    assert out["all"][1] <= out["all"][0]
+    F_tr, _ = fv.fv_godunov_flux_batch(WL, WR, nrm, cfg)
+    F_ml, _ = fv.fv_godunov_flux_batch_mlp(WL, WR, nrm, cfg, fv.fv_mlp_pack(th, 1, gate=GATE))
+    scale = F_tr.abs().max(dim=0).values
+    assert ((F_ml - F_tr).abs().max(dim=0).values <= 1e-12 * scale + 1e-300).all()
+    r = LG.evaluate(th, pairs, data, target=1, gate=GATE)
+    print("\n", r)
+    e = r["guess_log_err_past_gate"]
+    it_g, it_a = r["newton_iters_past_gate"], r["newton_iters_all"]
+    assert e["learned"] < 0.5 * e["two_rarefaction"]
+    assert it_g["learned"] < it_g["two_rarefaction"]
+    assert it_a["learned"] <= it_a["two_rarefaction"]
