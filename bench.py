@@ -73,7 +73,8 @@ def update_bytes_per_cell_update(fp32: bool) -> float:
 
 KERNEL_SOURCES = ["paper_1704_01144_gb300/csrc/fv_kernels.cu",
                   "paper_1704_01144_gb300/csrc/fv_riemann.cuh",
-                  "paper_1704_01144_gb300/csrc/fv_internal.h"]
+                  "paper_1704_01144_gb300/csrc/fv_internal.h",
+                  "paper_1704_01144_gb300/csrc/fv_mlp.cuh"]
 
 
 def kernel_source_hash() -> str:
@@ -406,7 +407,7 @@ def main_ours(args):
                         gpu_index, setup=setup, tag=tag)
         r["g"] = g
         res[name] = r
-    chosen = res["fp32flux"] if "fp32flux" in res else res["fp64"]
+    chosen = next(res[k] for k in ("fp32flux", "fp64", "fp32mlp") if k in res)
     e2e = None if args.no_e2e else run_e2e(fv, torch, chosen["g"], max(3, min(args.steps, 10)), 1,
                                            stream)
 

@@ -19,9 +19,7 @@
 #include "fv_mlp.cuh"
 #include "fv_riemann.cuh"
 
-using namespace fvk;
-
-namespace {
+namespace fvk {
 
 constexpr int TILE = 128;        // samples per block tile (one per thread)
 constexpr int TS = TILE + 1;     // padded row stride of the per-sample arrays
@@ -295,7 +293,9 @@ __global__ void __launch_bounds__(128) k_mlp_label(const double *__restrict__ pa
   }
 }
 
-}  // namespace
+}  // namespace fvk
+
+using namespace fvk;
 
 // ===================================================================== C ABI
 namespace {
@@ -383,7 +383,7 @@ int fv_mlp_init(float *params, int n_params, uint64_t seed) {
 int fv_mlp_pack(const float *params_dev, int n_params, int target, double gate, void *packed_dev,
                 void *stream) {
   if (!params_dev || !packed_dev || n_params != MLP_NPARAM || (target != 0 && target != 1) ||
-      !(gate < 1e30))
+      !std::isfinite(gate) || gate > 1e38)
     return mfail(FV_ERR_INVALID_ARG, "fv_mlp_pack: bad argument");
   if ((uintptr_t)packed_dev % 16) return mfail(FV_ERR_INVALID_ARG, "fv_mlp_pack: packed buffer not 16-byte aligned");
   k_mlp_pack<<<1, 256, 0, (cudaStream_t)stream>>>(params_dev, target, (float)gate, (uint32_t *)packed_dev);
@@ -535,7 +535,7 @@ int fv_mlp_train_steps(const fv_train_config *tc, int64_t n_sel) {
 }
 
 int fv_mlp_load(fv_mesh *m, const float *params_dev, int n_params, int target, double gate) {
-  if (!m || !params_dev || n_params != MLP_NPARAM || (target != 0 && target != 1) || !(gate < 1e30))
+  if (!m || !params_dev || n_params != MLP_NPARAM || (target != 0 && target != 1) || !std::isfinite(gate) || gate > 1e38)
     return mfail(FV_ERR_INVALID_ARG, "fv_mlp_load: bad argument");
   if (m->in_batch || (m->in_cycle && m->next_phase > 0))
     return mfail(FV_ERR_INVALID_ARG, "fv_mlp_load: mesh is inside a cycle or a batch");
