@@ -162,7 +162,10 @@ int fv_mesh_load(const double *xyz, int64_t n_nodes, const int64_t *tets, int64_
   std::string err;
   int rc = fv_host_build(xyz, n_nodes, tets, n_tets, face_bc, H, &err);
   if (rc) return fail(rc, err);
-  if (H.F > (int64_t)0x7fffffff / 16) return fail(FV_ERR_INVALID_ARG, "fv_mesh_load: mesh too large");
+  // cell and face ids are int32 on the device, and grid-stride loops step up
+  // to ~2^21 past the end of a range
+  if (H.F > FV_MAX_ITEMS || H.N > FV_MAX_ITEMS)
+    return fail(FV_ERR_INVALID_ARG, "fv_mesh_load: mesh too large (more than 2^31 - 2^22 faces)");
 
   fv_mesh *m = new fv_mesh();
   m->cfg = *cfg;

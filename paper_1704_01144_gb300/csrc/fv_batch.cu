@@ -227,6 +227,11 @@ int fv_batch_create(fv_mesh *const *meshes, int n, fv_batch **out) {
   b->tiles_c = tpc[n];
   b->tiles_f = tpf[n];
   int rc = FV_OK;
+  // the batched kernels index the concatenated ranges with int32
+  if (b->cells > FV_MAX_ITEMS || b->faces > FV_MAX_ITEMS) {
+    delete b;
+    return bfail(FV_ERR_INVALID_ARG, "fv_batch_create: more than 2^31 - 2^22 cells or faces in all");
+  }
   rc = rc ? rc : balloc(b, &b->d_ms, n);
   rc = rc ? rc : balloc(b, &b->d_pds, pds.size());
   rc = rc ? rc : balloc(b, &b->d_active, actives.size());

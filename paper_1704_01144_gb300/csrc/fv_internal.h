@@ -47,6 +47,10 @@
 #define FV_STATUS_NONPHYS 1
 #define FV_STATUS_RIEMANN 2
 
+// largest cell or face count (ids are int32; grid-stride loops overshoot a
+// range end by less than 2^22)
+#define FV_MAX_ITEMS ((int64_t)0x7fffffff - ((int64_t)1 << 22))
+
 struct DevMesh {
   int N, F, L;
   // cells

@@ -1,0 +1,195 @@
+"""Parity at the benchmark's full sizes, in the launch configuration the
+benchmark times (autotuned blocks per SM, one CUDA graph per cycle):
+
+- the 998,250-tet 4-level blast against the FP64 oracle on the whole mesh:
+  plain FP64 within 1e-12, FP32 flux within 1e-5, FP32 flux with the learned
+  guess within 1e-5;
+- the 64-instance batch: sampled instances against the oracle run alone;
+- the 79.9M-tet 6-level ground-plane blast, which the oracle cannot run in
+  reasonable time: properties that hold at any size (conservation with the
+  boundary ledger, the level rule against the local time steps, positivity,
+  the FP32-flux path against the FP64 path within 1e-5);
+- the breakdown of a strong ground blast at 6 levels: the GPU and the
+  oracle fail in the same cycle.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fv():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1704_01144_gb300 import build, fv as F
+    build.build()
+    return F
+
+
+def scales(U):
+    """Per-quantity scales: density, momentum magnitude, energy."""
+    return np.array([np.abs(U[0]).max(), np.sqrt((U[1:4] ** 2).sum(axis=0)).max(),
+                     np.abs(U[4]).max()])
+
+
+def rel_err(U, Uo):
+    s = scales(Uo)
+    d = np.abs(U - Uo)
+    return np.array([d[0].max() / s[0], d[1:4].max() / s[1], d[4].max() / s[2]])
+
+
+def tuned(fv, mesh, prim, L, precision, tag=""):
+    import torch
+    from paper_1704_01144_gb300 import autotune as AT
+    g = fv.Mesh(mesh, max_levels=L, precision=precision)
+    g.set_state(prim)
+    AT.autotune(g, f"mesh|N{g.n}|F{g.nf}|L{L}|prec{precision}{tag}",
+                stream=torch.cuda.Stream(), reset=lambda: g.set_state(prim))
+    g.set_state(prim)
+    return g
+
+
+def test_blast1m_full_size_against_oracle(fv, oracle_mod):
+    from paper_1704_01144_gb300 import inputs as I
+    from paper_1704_01144_gb300 import learned_guess as LG
+    mesh, prim = I.blast_case(n=55, ratio=8.0)
+    L, cycles = 4, 2
+    o = oracle_mod.Oracle(mesh, max_levels=L)
+    o.set_prim(prim)
+    o.advance(cycles)
+    Uo = o.get_cons()
+    # learned guess trained as the benchmark trains it (fewer pairs)
+    h = fv.Mesh(mesh, max_levels=L, precision=fv.FV_FP32_FLUX)
+    pairs = LG.harvest(h, prim, 8, 250_000, seed=1)
+    h.close()
+    params, _ = LG.train(pairs, epochs=10, seed=1)
+    del pairs
+    for precision, tol, learned in ((fv.FV_FP64, 1e-12, False), (fv.FV_FP32_FLUX, 1e-5, False),
+                                    (fv.FV_FP32_FLUX, 1e-5, True)):
+        tag = f"|mlp{LG.DEFAULT_GATE}" if learned else ""
+        g = tuned(fv, mesh, prim, L, precision, tag)
+        if learned:
+            g.mlp_load(params, fv.FV_MLP_TARGET_TR, LG.DEFAULT_GATE)
+            g.set_state(prim)
+        g.advance(cycles, want_time=False)
+        assert g.status() == 0
+        err = rel_err(g.get_state(), Uo)
+        assert err.max() <= tol, (precision, learned, err)
+        g.close()
+
+
+def test_batch64_sampled_instances_against_oracle(fv, oracle_mod):
+    import torch
+    from paper_1704_01144_gb300 import autotune as AT
+    from paper_1704_01144_gb300 import inputs as I
+    insts = I.batch_cases(64)
+    meshes = []
+    for b in insts:
+        m = fv.Mesh(b.mesh, max_levels=b.max_levels, precision=fv.FV_FP32_FLUX)
+        m.set_state(b.prim)
+        meshes.append(m)
+    Lmax = max(b.max_levels for b in insts)
+    batch = fv.Batch(meshes)
+    cells = sum(m.n for m in meshes)
+
+    def reset():
+        for m, b in zip(meshes, insts):
+            m.set_state(b.prim)
+
+    AT.autotune(batch, f"batch64|cells{cells}|Lmax{Lmax}|fp32", stream=torch.cuda.Stream(), reps=1,
+                reset=reset)
+    reset()
+    batch.advance(1)
+    torch.cuda.synchronize()
+    assert all(m.status() == 0 for m in meshes)
+    # the three smallest instances of different level counts
+    order = sorted(range(64), key=lambda i: meshes[i].n)
+    picked, seen = [], set()
+    for i in order:
+        if insts[i].max_levels not in seen:
+            picked.append(i)
+            seen.add(insts[i].max_levels)
+        if len(picked) == 3:
+            break
+    for i in picked:
+        b = insts[i]
+        o = oracle_mod.Oracle(b.mesh, max_levels=b.max_levels)
+        o.set_prim(b.prim)
+        o.advance(2 ** (Lmax - b.max_levels))
+        err = rel_err(meshes[i].get_state(), o.get_cons())
+        assert err.max() <= 1e-5, (i, b.max_levels, err)
+
+
+def test_ground80m_full_size_properties(fv):
+    from paper_1704_01144_gb300 import inputs as I
+    mesh, prim = I.ground_blast_case(n=237)
+    L = 6
+    g = tuned(fv, mesh, prim, L, fv.FV_FP32_FLUX)
+    vol = g.volumes()
+    U0 = g.get_state()
+    g.advance(1, want_time=False)
+    assert g.status() == 0
+    # levels of the cycle against its local steps: never above the level the
+    # step allows (k <= L-1 with 2^k dt_min <= dt_i), every level in 0..L-1
+    dt = g.local_dt()
+    lev = g.levels().astype(np.int64)
+    dtmin = dt.min()
+    kdt = np.zeros(dt.shape, dtype=np.int64)
+    for k in range(1, L):
+        kdt += (np.ldexp(dtmin, k) <= dt)
+    assert lev.min() == 0 and lev.max() <= L - 1
+    assert np.all(lev <= kdt)
+    counts = np.bincount(lev, minlength=L)
+    assert np.all(counts > 0), counts
+    # conservation with the boundary ledger (walls everywhere: no mass or
+    # energy crosses them)
+    U1 = g.get_state()
+    M0, M1 = (U0 * vol).sum(axis=1), (U1 * vol).sum(axis=1)
+    led = g.boundary_ledger()
+    scale = np.abs(U1 * vol).sum(axis=1).max()
+    assert np.abs(M1 - M0 + led).max() <= 1e-12 * scale
+    assert led[0] == 0.0 and led[4] == 0.0
+    # positivity
+    rho = U1[0]
+    p = 0.4 * (U1[4] - 0.5 * (U1[1] ** 2 + U1[2] ** 2 + U1[3] ** 2) / rho)
+    assert rho.min() > 0 and p.min() > 0
+    g.close()
+    del U0
+    # the FP64 path from the same state, one cycle: the FP32-flux result
+    # within its stated tolerance
+    g64 = fv.Mesh(mesh, max_levels=L, precision=fv.FV_FP64)
+    g64.set_state(prim)
+    g64.advance(1, want_time=False)
+    assert g64.status() == 0
+    err = rel_err(U1, g64.get_state())
+    assert err.max() <= 1e-5, err
+    g64.close()
+
+
+def test_ground_blast_breakdown_matches_oracle(fv, oracle_mod):
+    """A degenerate case of the method as read: levels are fixed for a whole
+    cycle (32 subiterations at L = 6) and neighbours differ by at most one
+    level, so a strong blast front can outrun the fine-level buffer and reach
+    coarse cells in the middle of their step, where the CFL condition of the
+    cycle start no longer holds.  On the 1.3M-tet ground blast the FP64 GPU
+    path and the oracle agree up to that point and both report the
+    non-physical state in the same cycle."""
+    from paper_1704_01144_gb300 import inputs as I
+    mesh, prim = I.ground_blast_case(n=60)
+    L = 6
+    o = oracle_mod.Oracle(mesh, max_levels=L)
+    o.set_prim(prim)
+    g = fv.Mesh(mesh, max_levels=L, precision=fv.FV_FP64)
+    g.set_state(prim)
+    for c in range(19):
+        o.advance(1)
+        g.advance(1, want_time=False)
+    assert g.status() == 0
+    err = rel_err(g.get_state(), o.get_cons())
+    assert err.max() <= 1e-12, err
+    with pytest.raises(RuntimeError, match="non-physical"):
+        o.advance(1)
+    g.advance(1, want_time=False)
+    assert g.status() == fv.FV_ERR_NONPHYSICAL
