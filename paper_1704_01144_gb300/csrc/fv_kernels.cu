@@ -849,11 +849,14 @@ __device__ __forceinline__ void run_item(const DevMesh &d, const PhaseDesc &p, c
 }
 
 // flux: 128 threads, 8 blocks per SM in FP32 (64 registers), 4 in FP64;
-// FP64 gradients need ~96 registers (2 blocks of 256); the rest fit in 64
+// FP64 gradients need ~96 registers (2 blocks of 256); the update (a gather
+// waiting on memory) fits in 40 registers for 6 resident blocks of 256; the
+// rest fit in 64
 #define KBOUNDS(KIND, T)                                                                      \
   __launch_bounds__((KIND) == K_FLUX ? 128 : 256,                                             \
                     (KIND) == K_FLUX ? (sizeof(T) == 4 ? 8 : 4)                               \
-                                     : ((KIND) == K_GRAD && sizeof(T) == 8 ? 2 : 4))
+                    : (KIND) == K_UPD ? 6                                                     \
+                                      : ((KIND) == K_GRAD && sizeof(T) == 8 ? 2 : 4))
 
 template <int KIND, typename T, bool G14>
 __global__ void KBOUNDS(KIND, T) k_phase1(DevMesh d, const __grid_constant__ PhaseDesc p, GasT<T> G) {
