@@ -346,6 +346,30 @@ def train_learned_guess(fv, torch, mesh, prim, L, cycles=40, per_cycle=250_000, 
     return {"params": params, "gate": LG.DEFAULT_GATE, "info": info, "eval": ev, "seconds": secs}
 
 
+def time_cycles(fv, torch, g, prim, stream, flush, cycles=5, warmup=3):
+    """{value, ms_per_step} of `cycles` timed cycles from `prim` after
+    `warmup` cycles (L2 flushed between timed cycles, CUDA events)."""
+    g.set_state(prim)
+    for _ in range(warmup):
+        g.advance(1, stream=stream, want_time=False)
+    torch.cuda.synchronize()
+    c0 = g.work_counters()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(cycles)]
+    with torch.cuda.stream(stream):
+        for k in range(cycles):
+            flush.add_(1.0)
+            ev[k][0].record(stream)
+            g.advance(1, stream=stream, want_time=False)
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    c1 = g.work_counters()
+    if g.status() != 0:
+        raise RuntimeError(f"timed cycles: {fv.fv_last_error()}")
+    return {"value": round((c1[1] - c0[1]) / (ms * 1e-3), 1), "ms_per_step": round(ms / cycles, 4)}
+
+
 def gate_sweep(fv, torch, g, prim, guess, stream, flush, gates=(0.1, 0.3, 1.0, 1e30), cycles=5):
     """Throughput of the learned-guess mesh at other gates (1e30: the network
     never fires, which leaves the fixed cost of the gate test), 5 timed
@@ -353,26 +377,7 @@ def gate_sweep(fv, torch, g, prim, guess, stream, flush, gates=(0.1, 0.3, 1.0, 1
     out = {}
     for gate in gates:
         g.mlp_load(guess["params"], fv.FV_MLP_TARGET_TR, gate)
-        g.set_state(prim)
-        for _ in range(3):
-            g.advance(1, stream=stream, want_time=False)
-        torch.cuda.synchronize()
-        c0 = g.work_counters()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(cycles)]
-        with torch.cuda.stream(stream):
-            for k in range(cycles):
-                flush.add_(1.0)
-                ev[k][0].record(stream)
-                g.advance(1, stream=stream, want_time=False)
-                ev[k][1].record(stream)
-        torch.cuda.synchronize()
-        ms = sum(a.elapsed_time(b) for a, b in ev)
-        c1 = g.work_counters()
-        if g.status() != 0:
-            raise RuntimeError(f"gate sweep: {fv.fv_last_error()}")
-        out[f"{gate:g}"] = {"value": round((c1[1] - c0[1]) / (ms * 1e-3), 1),
-                            "ms_per_step": round(ms / cycles, 4)}
+        out[f"{gate:g}"] = time_cycles(fv, torch, g, prim, stream, flush, cycles)
     g.mlp_load(guess["params"], fv.FV_MLP_TARGET_TR, guess["gate"])
     return out
 
@@ -421,6 +426,14 @@ def main_ours(args):
         r["g"] = g
         res[name] = r
     chosen = next(res[k] for k in ("fp32flux", "fp64", "fp32mlp") if k in res)
+    # the same cycles as one persistent cooperative launch (grid barriers
+    # between kernel kinds) instead of the graph of per-kind launches
+    persistent = None
+    if chosen["g"] is not None:
+        chosen["g"].use_persistent(True)
+        persistent = time_cycles(fv, torch, chosen["g"], prim, stream, flush)
+        chosen["g"].use_persistent(False)
+        persistent["vs_graph"] = round(persistent["value"] / chosen["value"], 4)
     e2e = None if args.no_e2e else run_e2e(fv, torch, chosen["g"], max(3, min(args.steps, 10)), 1,
                                            stream)
 
@@ -520,6 +533,7 @@ def main_ours(args):
             "kernels": kernel_shares(chosen),
             "autotuned_blocks_per_sm": {"prim_grad_flux_update": chosen["launch_per_sm"],
                                         "cached": chosen["autotune_cached"]},
+            "persistent_cycle": persistent,
             "cell_updates_per_step": chosen["cell_updates"] / args.steps,
             "face_evals_per_step": chosen["face_evals"] / args.steps,
         }

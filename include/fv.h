@@ -446,6 +446,27 @@ int fv_godunov_flux_batch_mlp(const double *WL_dev, const double *WR_dev, const 
                               int64_t count, const fv_config *cfg, const void *packed_dev,
                               double *F_dev, int32_t *iters_dev, void *stream);
 
+/*
+ * Runs each whole cycle of fv_advance as one cooperative (persistent)
+ * launch: after the level assignment, every phase of Alg. 2's cycle runs in
+ * a single kernel whose blocks stay resident and separate the kernel kinds
+ * of each phase (primitives, gradients, fluxes, updates) by a grid barrier,
+ * instead of four launches per phase.  Results are bitwise those of the
+ * per-kernel path.  The barrier waits a bounded time; if it gives up, the
+ * cycle stops and fv_status reports FV_ERR_TIMEOUT.  Applies to the
+ * two-rarefaction guess and unprofiled runs (others use the per-kernel
+ * path).  Not inside a cycle.
+ */
+int fv_use_persistent(fv_mesh *m, int enable);
+
+/* Failure detection of the persistent cycle's grid barrier: `rounds`
+ * barriers over one block per SM; with `unreachable` nonzero each barrier
+ * waits for one block more than exists, so every wait runs out (about a
+ * second at most) and the kernel returns.  *status_out gets the device
+ * status bits (4 = a barrier timed out).  Returns FV_OK, FV_ERR_TIMEOUT or
+ * FV_ERR_CUDA.  Synchronous. */
+int fv_barrier_selftest(int device, int rounds, int unreachable, int *status_out);
+
 /* Message of the calling thread's last failed call ("" if none). */
 const char *fv_last_error(void);
 

@@ -95,6 +95,53 @@ int start_cycle(fv_mesh *m, cudaStream_t s) {
   return FV_OK;
 }
 
+// the cycle's phase descriptors, uploaded once (a cycle always starts from
+// t_k^n = 0 and no predicted level, so they do not change between cycles)
+int persistent_tables(fv_mesh *m) {
+  if (m->pds_dev) return FV_OK;
+  const int nph = (int)m->phases.size();
+  std::vector<PhaseDesc> pds(nph);
+  int64_t tn[FV_MAXL];
+  bool pred[FV_MAXL];
+  for (int j = 0; j < FV_MAXL; ++j) {
+    tn[j] = 0;
+    pred[j] = false;
+  }
+  for (int q = 0; q < nph; ++q) {
+    pds[q] = phase_desc(m->L, tn, pred, m->phases[q]);
+    phase_apply(tn, pred, m->phases[q]);
+  }
+  PhaseDesc *p = nullptr;
+  GridBar *b = nullptr;
+  int rc = dalloc(m, &p, (size_t)nph);
+  if (rc == FV_OK) rc = dalloc(m, &b, 1);
+  if (rc) return rc;
+  CK(cudaMemcpy(p, pds.data(), sizeof(PhaseDesc) * nph, cudaMemcpyHostToDevice));
+  m->pds_dev = p;
+  m->bar = b;
+  return FV_OK;
+}
+
+bool persistent_on(const fv_mesh *m) {
+  return m->use_persistent && !m->prof.on && m->d.guess == FV_GUESS_TWO_RAREFACTION;
+}
+
+// a whole cycle: level assignment, every phase in one cooperative launch,
+// the end-of-cycle counters
+int run_cycle_persistent(fv_mesh *m, cudaStream_t s) {
+  int rc = persistent_tables(m);
+  if (rc) return rc;
+  rc = start_cycle(m, s);
+  if (rc) return rc;
+  rc = fvk::launch_persistent_cycle(m->d, m->pds_dev, (int)m->phases.size(), m->bar, s);
+  if (rc) return fail(rc, std::string("persistent cycle launch failed: ") + cudaGetErrorString(cudaGetLastError()));
+  rc = fvk::launch_time_advance(m->d, m->theta, s);
+  if (rc) return fail(rc, "time advance launch failed");
+  m->in_cycle = false;
+  m->next_phase = 0;
+  return FV_OK;
+}
+
 int run_phases(fv_mesh *m, int n, cudaStream_t s) {
   for (int q = 0; q < n; ++q) {
     if (!m->in_cycle || m->next_phase >= (int)m->phases.size())
@@ -470,9 +517,15 @@ int fv_advance_phases(fv_mesh *m, int n_phases, void *stream) {
 
 static int capture_cycle(fv_mesh *m, cudaStream_t s) {
   cudaGraph_t g = nullptr;
+  int rc = persistent_on(m) ? persistent_tables(m) : FV_OK;
+  if (rc) return rc;
   CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-  int rc = start_cycle(m, s);
-  if (rc == FV_OK) rc = run_phases(m, (int)m->phases.size(), s);
+  if (persistent_on(m)) {
+    rc = run_cycle_persistent(m, s);
+  } else {
+    rc = start_cycle(m, s);
+    if (rc == FV_OK) rc = run_phases(m, (int)m->phases.size(), s);
+  }
   cudaError_t e = cudaStreamEndCapture(s, &g);
   if (rc) {
     if (g) cudaGraphDestroy(g);
@@ -502,6 +555,11 @@ int fv_advance(fv_mesh *m, int n_cycles, double *t_out, void *stream) {
         if (rc) return rc;
       }
       CK(cudaGraphLaunch(m->cycle_graph, s));
+      continue;
+    }
+    if (!m->in_cycle && persistent_on(m)) {
+      rc = run_cycle_persistent(m, s);
+      if (rc) return rc;
       continue;
     }
     if (!m->in_cycle) {
@@ -534,6 +592,36 @@ int fv_get_launch(fv_mesh *m, int32_t per_sm[4]) {
   if (!m || !per_sm) return fail(FV_ERR_INVALID_ARG, "fv_get_launch: NULL argument");
   for (int k = 0; k < 4; ++k) per_sm[k] = m->launch.per_sm[k];
   return FV_OK;
+}
+
+int fv_use_persistent(fv_mesh *m, int enable) {
+  if (!m) return fail(FV_ERR_INVALID_ARG, "fv_use_persistent: NULL mesh");
+  if (m->in_cycle && m->next_phase > 0) return fail(FV_ERR_INVALID_ARG, "fv_use_persistent: inside a cycle");
+  m->use_persistent = enable != 0;
+  if (m->cycle_graph) {
+    cudaGraphExecDestroy(m->cycle_graph);
+    m->cycle_graph = nullptr;
+  }
+  return FV_OK;
+}
+
+int fv_barrier_selftest(int device, int rounds, int unreachable, int *status_out) {
+  if (!status_out || rounds < 1 || rounds > 1000000) return fail(FV_ERR_INVALID_ARG, "fv_barrier_selftest: bad argument");
+  CK(cudaSetDevice(device));
+  fvk::init_device_info();
+  GridBar *bar = nullptr;
+  int *st = nullptr;
+  CK(cudaMalloc(&bar, sizeof(GridBar)));
+  cudaError_t e = cudaMalloc(&st, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(st, 0, sizeof(int));
+  if (e == cudaSuccess && fvk::launch_barrier_probe(bar, st, rounds, unreachable ? 1u : 0u, 0) != FV_OK)
+    e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(status_out, st, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(bar);
+  cudaFree(st);
+  if (e != cudaSuccess) return cuda_fail(e, "fv_barrier_selftest");
+  return (*status_out & FV_STATUS_TIMEOUT) ? fail(FV_ERR_TIMEOUT, "grid barrier timed out") : FV_OK;
 }
 
 int fv_use_graph(fv_mesh *m, int enable) {
@@ -664,6 +752,7 @@ int fv_status(fv_mesh *m) {
   if (e != cudaSuccess) return cuda_fail(e, "fv_status");
   if (st & FV_STATUS_NONPHYS) return fail(FV_ERR_NONPHYSICAL, "non-physical state (rho or p <= 0)");
   if (st & FV_STATUS_RIEMANN) return fail(FV_ERR_RIEMANN, "Riemann solver failed (vacuum or no convergence)");
+  if (st & FV_STATUS_TIMEOUT) return fail(FV_ERR_TIMEOUT, "a grid barrier of the persistent cycle timed out");
   return FV_OK;
 }
 

@@ -46,6 +46,12 @@
 #define REC_LSW 12  // least-squares weights
 #define FV_STATUS_NONPHYS 1
 #define FV_STATUS_RIEMANN 2
+#define FV_STATUS_TIMEOUT 4  // a bounded grid barrier gave up
+
+// state of the persistent kernel's grid barrier (reset before each launch)
+struct GridBar {
+  unsigned count, gen;
+};
 
 // largest cell or face count (ids are int32; grid-stride loops overshoot a
 // range end by less than 2^22)
@@ -282,6 +288,9 @@ struct fv_mesh {
   bool have_dt = false;
   bool in_batch = false;       // owned by a batch's schedule while advancing
   LaunchCfg launch = default_launch();
+  bool use_persistent = false;    // whole cycles as one cooperative launch
+  PhaseDesc *pds_dev = nullptr;   // the cycle's phase descriptors (persistent mode)
+  GridBar *bar = nullptr;
 };
 
 // kernels (fv_kernels.cu)
@@ -309,4 +318,9 @@ int launch_flux_batch(const double *WL, const double *WR, const double *nrm, int
                       double tol, int maxit, int precision, int bc, double *F, int *iters,
                       const uint32_t *mlp, cudaStream_t s);
 int launch_harvest(const DevMesh &d, double *out, int m, long long a, long long b, cudaStream_t s);
+// every phase of a cycle in one cooperative launch (pds: the cycle's nph
+// phase descriptors in device memory; bar: barrier state, reset here)
+int launch_persistent_cycle(const DevMesh &d, const PhaseDesc *pds, int nph, GridBar *bar,
+                            cudaStream_t s);
+int launch_barrier_probe(GridBar *bar, int *status, int rounds, unsigned extra, cudaStream_t s);
 }  // namespace fvk

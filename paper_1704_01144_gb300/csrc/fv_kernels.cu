@@ -933,6 +933,124 @@ __global__ void KBOUNDS(KIND, T) k_phaseN(const DevMesh *__restrict__ ms, const 
   }
 }
 
+// ---- persistent cycle: every phase of a cycle in one cooperative launch,
+// the kernel kinds of a phase separated by a grid barrier.  The blocks all
+// run the same sequence (phase by phase, prim -> grad -> flux -> update, a
+// barrier after each), so every block meets every barrier.  The barrier is a
+// counter and a generation number; waiting is bounded: after 2^21 polls of
+// the generation (each an L2 round trip, about a second in all) a block
+// records FV_STATUS_TIMEOUT and every block leaves at its next barrier.
+#define FV_BAR_SPIN_LIMIT (1u << 21)
+
+__device__ __forceinline__ bool grid_barrier(GridBar *b, int *status, unsigned expected) {
+  __shared__ int go;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned *vgen = &b->gen;
+    volatile int *vst = status;
+    const unsigned g = *vgen;
+    __threadfence();
+    if (atomicAdd(&b->count, 1u) == expected - 1) {
+      b->count = 0;
+      __threadfence();
+      atomicAdd(&b->gen, 1u);
+    } else {
+      unsigned spins = 0;
+      while (*vgen == g) {
+        if (++spins > FV_BAR_SPIN_LIMIT) {
+          atomicOr(status, FV_STATUS_TIMEOUT);
+          break;
+        }
+        if ((spins & 1023u) == 0 && (*vst & FV_STATUS_TIMEOUT)) break;  // another block gave up
+      }
+    }
+    __threadfence();
+    go = (*(volatile int *)status & FV_STATUS_TIMEOUT) == 0;
+  }
+  __syncthreads();
+  return go != 0;
+}
+
+// the barrier on its own, for failure-detection tests: `rounds` barriers
+// over the grid, each expecting gridDim.x + extra arrivals (extra > 0: a
+// count that is never reached, so every wait runs out)
+__global__ void k_barrier_probe(GridBar *bar, int *status, int rounds, unsigned extra) {
+  for (int r = 0; r < rounds; ++r)
+    if (!grid_barrier(bar, status, gridDim.x + extra)) return;
+}
+
+int launch_barrier_probe(GridBar *bar, int *status, int rounds, unsigned extra, cudaStream_t s) {
+  if (cudaMemsetAsync(bar, 0, sizeof(GridBar), s) != cudaSuccess) return FV_ERR_CUDA;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(num_sms());
+  cfg.blockDim = dim3(64);
+  cfg.stream = s;
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeCooperative;
+  attr.val.cooperative = 1;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, k_barrier_probe, bar, status, rounds, extra) != cudaSuccess) return FV_ERR_CUDA;
+  return FV_OK;
+}
+
+// 256-thread blocks, 4 per SM at 64 registers (FP32), 2 at 128 (FP64)
+template <typename T>
+struct PersistThreads {
+  static constexpr int value = 256;
+  static constexpr int blocks = sizeof(T) == 4 ? 4 : 2;
+};
+
+template <typename T, bool G14>
+__global__ void __launch_bounds__(PersistThreads<T>::value, PersistThreads<T>::blocks)
+    k_persist(DevMesh d, const PhaseDesc *__restrict__ pds, int nph, GasT<T> G, GridBar *bar) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int p = 0; p < nph; ++p) {
+    const PhaseDesc &pd = pds[p];
+    int beg, end;
+    kind_range(d, pd, K_PRIM, beg, end);
+    for (int idx = beg + blockIdx.x * blockDim.x + threadIdx.x; idx < end; idx += stride)
+      prim_item<T>(d, pd.pl, idx);
+    if (!grid_barrier(bar, d.status, gridDim.x)) return;
+    kind_range(d, pd, K_GRAD, beg, end);
+    for (int idx = beg + blockIdx.x * blockDim.x + threadIdx.x; idx < end; idx += stride)
+      grad_item<T>(d, idx);
+    if (!grid_barrier(bar, d.status, gridDim.x)) return;
+    kind_range(d, pd, K_FLUX, beg, end);
+    for (int idx = beg + blockIdx.x * blockDim.x + threadIdx.x; idx < end; idx += stride)
+      flux_item<T, G14>(d, G, pd.stage, pd.level, idx);
+    if (!grid_barrier(bar, d.status, gridDim.x)) return;
+    kind_range(d, pd, K_UPD, beg, end);
+    for (int idx = beg + blockIdx.x * blockDim.x + threadIdx.x; idx < end; idx += stride)
+      update_item<sizeof(T) == 4>(d, pd.stage, pd.level, idx);
+    if (!grid_barrier(bar, d.status, gridDim.x)) return;
+  }
+}
+
+template <typename T, bool G14>
+static int persist_launch(const DevMesh &d, const PhaseDesc *pds, int nph, const GasT<T> &G,
+                          GridBar *bar, cudaStream_t s) {
+  static int per_sm[2][2] = {{0, 0}, {0, 0}};
+  int &bps = per_sm[sizeof(T) == 4][G14];
+  if (!bps) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_persist<T, G14>, PersistThreads<T>::value,
+                                                      0) != cudaSuccess ||
+        bps < 1)
+      return FV_ERR_CUDA;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(num_sms() * bps);
+  cfg.blockDim = dim3(PersistThreads<T>::value);
+  cfg.stream = s;
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeCooperative;
+  attr.val.cooperative = 1;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, k_persist<T, G14>, d, pds, nph, G, bar) != cudaSuccess) return FV_ERR_CUDA;
+  return FV_OK;
+}
+
 // positivity and finiteness of U^n (rho > 0, 2 rho E > |rho u|^2)
 __global__ void __launch_bounds__(256) k_check_state(DevMesh d) {
   const size_t N = d.N;
@@ -1256,6 +1374,20 @@ static void phase1_all(const DevMesh &d, const PhaseDesc &pd, const GasT<T> &G, 
 static GasT<double> gas64(const DevMesh &d) { return GasT<double>::make(d.gamma, d.tol, d.maxit); }
 static GasT<float> gas32(const DevMesh &d) {
   return GasT<float>::make(d.gamma, d.tol > 2e-6 ? d.tol : 2e-6, d.maxit);
+}
+
+int launch_persistent_cycle(const DevMesh &d, const PhaseDesc *pds, int nph, GridBar *bar,
+                            cudaStream_t s) {
+  if (cudaMemsetAsync(bar, 0, sizeof(GridBar), s) != cudaSuccess) return FV_ERR_CUDA;
+  const bool g14 = d.gamma == 1.4;
+  int rc;
+  if (d.precision == FV_FP64)
+    rc = g14 ? persist_launch<double, true>(d, pds, nph, gas64(d), bar, s)
+             : persist_launch<double, false>(d, pds, nph, gas64(d), bar, s);
+  else
+    rc = g14 ? persist_launch<float, true>(d, pds, nph, gas32(d), bar, s)
+             : persist_launch<float, false>(d, pds, nph, gas32(d), bar, s);
+  return rc;
 }
 
 int launch_phase(const DevMesh &d, const PhaseDesc &pd, const LaunchCfg &lc, ProfHook *ph,

@@ -68,6 +68,7 @@ EXPORTS = [
     "fv_batch_set_launch", "fv_batch_get_launch", "fv_mlp_init", "fv_mlp_pack", "fv_mlp_infer",
     "fv_mlp_label", "fv_mlp_loss_grad", "fv_mlp_adam", "fv_mlp_train", "fv_mlp_train_steps",
     "fv_mlp_load", "fv_set_guess", "fv_harvest_pairs", "fv_godunov_flux_batch_mlp",
+    "fv_use_persistent", "fv_barrier_selftest",
 ]
 
 FV_MLP_PARAMS = 4673
@@ -123,6 +124,8 @@ def lib():
     L.fv_work_counters.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                    C.POINTER(C.c_int64)]
     L.fv_use_graph.argtypes = [vp, C.c_int]
+    L.fv_use_persistent.argtypes = [vp, C.c_int]
+    L.fv_barrier_selftest.argtypes = [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int)]
     L.fv_profile_enable.argtypes = [vp, C.c_int]
     L.fv_profile_read.argtypes = [vp, dp, C.POINTER(C.c_int64)]
     L.fv_get_local_dt.argtypes = [vp, dp]
@@ -259,6 +262,17 @@ def fv_work_counters(h):
     a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
     _check(lib().fv_work_counters(h, C.byref(a), C.byref(b), C.byref(c)), "fv_work_counters")
     return a.value, b.value, c.value
+
+
+def fv_use_persistent(h, enable):
+    _check(lib().fv_use_persistent(h, int(bool(enable))), "fv_use_persistent")
+
+
+def fv_barrier_selftest(rounds, unreachable, device=0):
+    """(return code, device status bits) of the grid-barrier self-test."""
+    st = C.c_int(0)
+    rc = lib().fv_barrier_selftest(int(device), int(rounds), int(bool(unreachable)), C.byref(st))
+    return rc, st.value
 
 
 def fv_use_graph(h, enable):
@@ -616,6 +630,9 @@ class Mesh:
 
     def use_graph(self, enable):
         fv_use_graph(self.h, enable)
+
+    def use_persistent(self, enable):
+        fv_use_persistent(self.h, enable)
 
     def set_launch(self, per_sm):
         fv_set_launch(self.h, per_sm)
