@@ -104,12 +104,13 @@ def measured_traffic():
     return vals
 
 
-def launches_per_cycle(L: int) -> int:
+def launches_per_cycle(L: int, fp32: bool = True) -> int:
     """Kernels the library launches in one cycle: level assignment
     (init, dt, levels, L-1 smoothing sweeps, 2 x (keys, hist, scan, scatter)),
-    4 per phase (prim, grad, flux, update) x (3 * 2^(L-1) - 1) phases, and
-    the end-of-cycle time advance."""
-    return (11 + (L - 1)) + 4 * (3 * 2 ** (L - 1) - 1) + 1
+    per phase prim, grad, flux, update (FP64) or grad (with the primitives),
+    flux, update (FP32 flux) x (3 * 2^(L-1) - 1) phases, and the end-of-cycle
+    time advance."""
+    return (11 + (L - 1)) + (3 if fp32 else 4) * (3 * 2 ** (L - 1) - 1) + 1
 
 
 def _dist():
@@ -521,7 +522,7 @@ def main_ours(args):
             "alu_peaks_measured": alu_peaks,
             "kernel_source_sha256_16": kernel_source_hash(),
             "e2e": e2e,
-            "gpu_launches": launches_per_cycle(L) * args.steps,
+            "gpu_launches": launches_per_cycle(L, "fp32flux" in res) * args.steps,
             "cpu_baseline": cpu,
             "plain_fp64": None if "fp64" not in res else {
                 "value": round(res["fp64"]["value"], 1), "unit": "cell-updates/s",

@@ -269,8 +269,8 @@ int fv_mesh_load(const double *xyz, int64_t n_nodes, const int64_t *tets, int64_
   }
   AL(d.Un, 5 * N);
   if (f32) {
-    AL(d.Un32, 5 * N);
-    AL(d.Us32, 5 * N);
+    AL(d.Un32, REC_U32 * N);
+    AL(d.Us32, REC_U32 * N);
   } else {
     AL(d.Us, 5 * N);
   }

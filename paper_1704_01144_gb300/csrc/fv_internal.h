@@ -44,6 +44,7 @@
 #define REC_FA 6    // FP64 face values (5 used)
 #define REC_FA32 8  // FP32 face values (5 used)
 #define REC_LSW 12  // least-squares weights
+#define REC_U32 8   // FP32 shadow state: 5 conserved values, the cell's level, pad
 #define FV_STATUS_NONPHYS 1
 #define FV_STATUS_RIEMANN 2
 #define FV_STATUS_TIMEOUT 4  // a bounded grid barrier gave up
@@ -72,7 +73,7 @@ struct DevMesh {
   float *fgeo32;
   // state
   double *Un, *Us, *G;  // Us: predicted state (FP64 mode only)
-  float *Un32, *Us32;    // FP32-flux mode: FP32 shadow of U^n, predicted state
+  float *Un32, *Us32;    // FP32-flux mode: FP32 shadow of U^n, predicted state ([N][REC_U32])
   float *G32;
   double *FA, *ACC, *BND;
   float *FA32;         // FP32-flux mode: predictor flux x area

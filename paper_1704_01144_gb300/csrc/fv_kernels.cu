@@ -234,9 +234,17 @@ __device__ __forceinline__ uint8_t cell_key_of(const DevMesh &d, int i) {
   return (uint8_t)(2 * k + (finer ? 0 : 1));
 }
 
+// the cell's sort key; in the FP32-flux mode the cycle's level is also
+// stamped into the cell's FP32 state record (read with the state, so the
+// phase kernels need no separate level lookup)
+__device__ __forceinline__ void cell_key_store(const DevMesh &d, int i) {
+  d.ckey[i] = cell_key_of(d, i);
+  if (d.Un32) d.Un32[(size_t)i * REC_U32 + 5] = (float)d.lev[i];
+}
+
 __global__ void __launch_bounds__(256) k_cell_keys(DevMesh d) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x)
-    d.ckey[i] = cell_key_of(d, i);
+    cell_key_store(d, i);
 }
 
 // face level = min of the two cell levels; faces sort by it
@@ -414,7 +422,7 @@ __global__ void __launch_bounds__(256) k_cells_multi(MultiTiles a, int op) {
     else if (op == 1) d.lev[i] = d.lev_tmp[i];
     else if (op == 2) d.lev[i] = smooth_of(d, d.lev_tmp, i);
     else if (op == 3) d.lev_tmp[i] = smooth_of(d, d.lev, i);
-    else d.ckey[i] = cell_key_of(d, i);
+    else cell_key_store(d, i);
   }
 }
 
@@ -476,25 +484,27 @@ __device__ __forceinline__ void load_state(const DevMesh &d, const PhaseLevels &
   }
 }
 
-// FP32-flux mode: the state at the phase time from the FP32 shadow of U^n
-// and the FP32 predicted state
+// FP32-flux mode: the state at the phase time from the FP32 records of U^n
+// and of the predicted state; the record of U^n carries the cell's level
 __device__ __forceinline__ void load_state(const DevMesh &d, const PhaseLevels &pl, int c,
                                            float U[5]) {
-  const size_t N = d.N;
-  int k = d.lev[c];
-  int mode = pl.mode[k];
+  float a[REC_U32];
+  ldrec<REC_U32>(d.Un32 + (size_t)c * REC_U32, a);
+  const int k = (int)a[5];
+  const int mode = pl.mode[k];
   if (mode == 0) {
 #pragma unroll
-    for (int q = 0; q < 5; ++q) U[q] = d.Un32[q * N + c];
-  } else if (mode == 1) {
-#pragma unroll
-    for (int q = 0; q < 5; ++q) U[q] = d.Us32[q * N + c];
+    for (int q = 0; q < 5; ++q) U[q] = a[q];
   } else {
-    float w = (float)pl.w[k];
+    float b[REC_U32];
+    ldrec<REC_U32>(d.Us32 + (size_t)c * REC_U32, b);
+    if (mode == 1) {
 #pragma unroll
-    for (int q = 0; q < 5; ++q) {
-      float a = d.Un32[q * N + c], b = d.Us32[q * N + c];
-      U[q] = a + w * (b - a);
+      for (int q = 0; q < 5; ++q) U[q] = b[q];
+    } else {
+      float w = (float)pl.w[k];
+#pragma unroll
+      for (int q = 0; q < 5; ++q) U[q] = a[q] + w * (b[q] - a[q]);
     }
   }
 }
@@ -530,15 +540,31 @@ __device__ __forceinline__ void prim_item(const DevMesh &d, const PhaseLevels &p
 }
 
 // least-squares gradients of the primitives of the cell at list position
-// idx: g = sum_j w_j (W_nb(j) - W_i), ghost states on boundary faces
+// idx: g = sum_j w_j (W_nb(j) - W_i), ghost states on boundary faces.
+// FP64 mode: from the W records the primitives kernel wrote.  FP32-flux
+// mode (INLINE_W): the primitives of the cell and of its neighbours are
+// computed here from their states at the phase time, and the cell's own
+// primitives are stored in its W record for the flux kernel; there is no
+// separate primitives kernel.
 template <typename T>
-__device__ __forceinline__ void grad_item(const DevMesh &d, int idx) {
+__device__ __forceinline__ void grad_item(const DevMesh &d, const PhaseLevels &pl, int idx) {
+  constexpr bool INLINE_W = sizeof(T) == 4;
   const T *W = (const T *)d.W;
   const T *lsw = lswrec(d, T(0));
   const T *fgeo = georec(d, T(0));
+  const double gm1 = d.gamma - 1.0;
   int i = d.cl[idx];
   T Wi[REC_W], g[REC_G], w[REC_LSW];
-  ldrec<REC_W>(W + (size_t)i * REC_W, Wi);
+  if (INLINE_W) {
+    T U[5];
+    load_state(d, pl, i, U);
+    to_prim(U, gm1, Wi);
+#pragma unroll
+    for (int q = 5; q < REC_W; ++q) Wi[q] = T(0);
+    strec<REC_W>((T *)d.W + (size_t)i * REC_W, Wi);
+  } else {
+    ldrec<REC_W>(W + (size_t)i * REC_W, Wi);
+  }
   ldrec<REC_LSW>(lsw + (size_t)i * REC_LSW, w);
   int4 nb4 = d.cnb4[i];
 #pragma unroll
@@ -548,7 +574,13 @@ __device__ __forceinline__ void grad_item(const DevMesh &d, int idx) {
     int nb = nbr_of(nb4, j);
     T Wn[REC_W];
     if (nb >= 0) {
-      ldrec<REC_W>(W + (size_t)nb * REC_W, Wn);
+      if (INLINE_W) {
+        T U[5];
+        load_state(d, pl, nb, U);
+        to_prim(U, gm1, Wn);
+      } else {
+        ldrec<REC_W>(W + (size_t)nb * REC_W, Wn);
+      }
     } else {
 #pragma unroll
       for (int q = 0; q < 5; ++q) Wn[q] = Wi[q];
@@ -779,9 +811,12 @@ __device__ __forceinline__ void update_item(const DevMesh &d, int stage, int lev
 #pragma unroll
       for (int c = 0; c < 5; ++c) S[c] = j == 0 ? flip(v[c], neg) : S[c] + flip(v[c], neg);
     }
-    float cdt = -ldexpf((float)dtmin, (int)d.lev[i]) * d.ivol32[i];
+    float a[REC_U32];
+    ldrec<REC_U32>(d.Un32 + (size_t)i * REC_U32, a);
+    float cdt = -ldexpf((float)dtmin, (int)a[5]) * d.ivol32[i];
 #pragma unroll
-    for (int c = 0; c < 5; ++c) d.Us32[c * N + i] = d.Un32[c * N + i] + cdt * S[c];
+    for (int c = 0; c < 5; ++c) a[c] = a[c] + cdt * S[c];
+    strec<REC_U32>(d.Us32 + (size_t)i * REC_U32, a);
     return;
   }
   double S[5];
@@ -807,11 +842,17 @@ __device__ __forceinline__ void update_item(const DevMesh &d, int stage, int lev
 #pragma unroll
     for (int c = 0; c < 5; ++c) d.Us[c * N + i] = d.Un[c * N + i] + cdt * S[c];
   } else {
+    float r[REC_U32];
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
       double u = d.Un[c * N + i] - iV * S[c];
       d.Un[c * N + i] = u;
-      if (F32) d.Un32[c * N + i] = (float)u;
+      r[c] = (float)u;
+    }
+    if (F32) {
+      r[5] = (float)level;  // the cell ends the step of its own level
+      r[6] = r[7] = 0.0f;
+      strec<REC_U32>(d.Un32 + (size_t)i * REC_U32, r);
     }
   }
 }
@@ -841,7 +882,7 @@ __device__ __forceinline__ void run_item(const DevMesh &d, const PhaseDesc &p, c
   if (KIND == K_PRIM)
     prim_item<T>(d, p.pl, idx);
   else if (KIND == K_GRAD)
-    grad_item<T>(d, idx);
+    grad_item<T>(d, p.pl, idx);
   else if (KIND == K_FLUX)
     flux_item<T, G14>(d, G, p.stage, p.level, idx);
   else
@@ -1008,13 +1049,15 @@ __global__ void __launch_bounds__(PersistThreads<T>::value, PersistThreads<T>::b
   for (int p = 0; p < nph; ++p) {
     const PhaseDesc &pd = pds[p];
     int beg, end;
-    kind_range(d, pd, K_PRIM, beg, end);
-    for (int idx = beg + blockIdx.x * blockDim.x + threadIdx.x; idx < end; idx += stride)
-      prim_item<T>(d, pd.pl, idx);
-    if (!grid_barrier(bar, d.status, gridDim.x)) return;
+    if (sizeof(T) == 8) {  // the FP32-flux mode computes primitives in the gradient step
+      kind_range(d, pd, K_PRIM, beg, end);
+      for (int idx = beg + blockIdx.x * blockDim.x + threadIdx.x; idx < end; idx += stride)
+        prim_item<T>(d, pd.pl, idx);
+      if (!grid_barrier(bar, d.status, gridDim.x)) return;
+    }
     kind_range(d, pd, K_GRAD, beg, end);
     for (int idx = beg + blockIdx.x * blockDim.x + threadIdx.x; idx < end; idx += stride)
-      grad_item<T>(d, idx);
+      grad_item<T>(d, pd.pl, idx);
     if (!grid_barrier(bar, d.status, gridDim.x)) return;
     kind_range(d, pd, K_FLUX, beg, end);
     for (int idx = beg + blockIdx.x * blockDim.x + threadIdx.x; idx < end; idx += stride)
@@ -1166,8 +1209,11 @@ __global__ void __launch_bounds__(256) k_set_state(DevMesh d, const double *__re
     double uu = __dadd_rn(__dadd_rn(__dmul_rn(u, u), __dmul_rn(v, v)), __dmul_rn(w, w));
     d.Un[4 * N + i] = __dadd_rn(__ddiv_rn(p, gm1), __dmul_rn(__dmul_rn(0.5, r), uu));
     if (d.Un32) {
+      float r[REC_U32];
 #pragma unroll
-      for (int c = 0; c < 5; ++c) d.Un32[c * N + i] = (float)d.Un[c * N + i];
+      for (int c = 0; c < 5; ++c) r[c] = (float)d.Un[c * N + i];
+      r[5] = r[6] = r[7] = 0.0f;  // level: stamped by the next level assignment
+      strec<REC_U32>(d.Un32 + (size_t)i * REC_U32, r);
     }
   }
 }
@@ -1180,8 +1226,11 @@ __global__ void __launch_bounds__(256) k_set_cons(DevMesh d, const double *__res
 #pragma unroll
     for (int c = 0; c < 5; ++c) d.Un[c * N + i] = cons[c * N + o];
     if (d.Un32) {
+      float r[REC_U32];
 #pragma unroll
-      for (int c = 0; c < 5; ++c) d.Un32[c * N + i] = (float)cons[c * N + o];
+      for (int c = 0; c < 5; ++c) r[c] = (float)cons[c * N + o];
+      r[5] = r[6] = r[7] = 0.0f;  // level: stamped by the next level assignment
+      strec<REC_U32>(d.Un32 + (size_t)i * REC_U32, r);
     }
     if (!(cons[o] > 0.0)) atomicOr(d.status, FV_STATUS_NONPHYS);
   }
@@ -1357,7 +1406,10 @@ static void phase1_all(const DevMesh &d, const PhaseDesc &pd, const GasT<T> &G, 
                        ProfHook *ph, cudaStream_t s) {
   const int g0 = grid_for(d.N, 256, lc.per_sm[0]), g1 = grid_for(d.N, 256, lc.per_sm[1]);
   const int g2 = grid_for(d.F, 128, lc.per_sm[2]), g3 = grid_for(d.N, 256, lc.per_sm[3]);
-  { ProfScope sc(ph, FV_PROF_PRIM, s); k_phase1<K_PRIM, T, G14><<<g0, 256, 0, s>>>(d, pd, G); }
+  if (sizeof(T) == 8) {  // FP32-flux mode: primitives computed inside the gradient kernel
+    ProfScope sc(ph, FV_PROF_PRIM, s);
+    k_phase1<K_PRIM, T, G14><<<g0, 256, 0, s>>>(d, pd, G);
+  }
   { ProfScope sc(ph, FV_PROF_GRAD, s); k_phase1<K_GRAD, T, G14><<<g1, 256, 0, s>>>(d, pd, G); }
   {
     ProfScope sc(ph, FV_PROF_FLUX, s);
@@ -1409,7 +1461,7 @@ static void phaseN_all(const DevMesh *ms, const PhaseDesc *pds, int n, const Gas
                        int64_t cells, int64_t faces, const LaunchCfg &lc, cudaStream_t s) {
   const int g0 = grid_for(cells, 256, lc.per_sm[0]), g1 = grid_for(cells, 256, lc.per_sm[1]);
   const int g2 = grid_for(faces, 128, lc.per_sm[2]), g3 = grid_for(cells, 256, lc.per_sm[3]);
-  k_phaseN<K_PRIM, T, G14><<<g0, 256, 0, s>>>(ms, pds, n, G);
+  if (sizeof(T) == 8) k_phaseN<K_PRIM, T, G14><<<g0, 256, 0, s>>>(ms, pds, n, G);
   k_phaseN<K_GRAD, T, G14><<<g1, 256, 0, s>>>(ms, pds, n, G);
   k_phaseN<K_FLUX, T, G14><<<g2, 128, 0, s>>>(ms, pds, n, G);
   k_phaseN<K_UPD, T, G14><<<g3, 256, 0, s>>>(ms, pds, n, G);
@@ -1436,6 +1488,7 @@ int launch_residual(const DevMesh &d, int precision, const PhaseLevels &pl, int 
   int gfx = grid_for(d.F, 128, 16);
   PhaseDesc all;  // gradients of every cell: the list range covering all cells
   memset(&all, 0, sizeof all);
+  all.pl = pl;    // the view the FP32-flux gradient step computes its primitives in
   all.gb0 = 0;
   all.gb1 = 2 * d.L;
   all.active = 1;
@@ -1495,6 +1548,7 @@ int launch_harvest(const DevMesh &d, double *out, int m, long long a, long long 
   memset(&pl, 0, sizeof pl);
   PhaseDesc all;
   memset(&all, 0, sizeof all);
+  all.pl = pl;
   all.gb0 = 0;
   all.gb1 = 2 * d.L;
   all.active = 1;
