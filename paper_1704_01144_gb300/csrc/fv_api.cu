@@ -287,6 +287,8 @@ int fv_mesh_load(const double *xyz, int64_t n_nodes, const int64_t *tets, int64_
   AL(d.coff, 2 * FV_MAXL + 1);
   AL(d.foff, FV_MAXL + 1);
   AL(d.dt, N);
+  AL(d.dteps, N);
+  AL(d.dthi_bits, 1);
   AL(d.dtmin_bits, 1);
   AL(d.tdev, 1);
   AL(d.status, 1);

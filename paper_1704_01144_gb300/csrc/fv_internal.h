@@ -82,7 +82,9 @@ struct DevMesh {
   uint8_t *ckey, *fkey;
   int *cl, *fl, *coff, *foff;
   int *sort_cnt;          // bucket x block counts, scratch of the level sort
-  double *dt;             // local time steps
+  double *dt;             // local time steps (see k_dt32: exact where a decision needs it)
+  float *dteps;           // relative bound of dt's FP32 estimate (0: dt is exact)
+  unsigned long long *dthi_bits;  // smallest upper bound of the estimates (bit pattern)
   unsigned long long *dtmin_bits;  // bit pattern of dt_min (positive double)
   double *tdev;           // physical time
   int *status;            // sticky status bits

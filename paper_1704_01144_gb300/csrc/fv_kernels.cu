@@ -185,6 +185,116 @@ __global__ void __launch_bounds__(256) k_dt(DevMesh d) {
 }
 
 __global__ void k_init_min(unsigned long long *bits) { *bits = 0x7ff0000000000000ULL; }
+__global__ void k_init_min2(unsigned long long *a, unsigned long long *b) {
+  *a = 0x7ff0000000000000ULL;
+  *b = 0x7ff0000000000000ULL;
+}
+
+// ---- certified FP32 estimate of the local step.  The estimate dt~ comes
+// with a relative bound e such that the exact FP64 value of local_dt_of lies
+// in [dt~ (1 - e), dt~ (1 + e)]; the bound is built from first-order error
+// propagation (u = 2^-24 per rounding of the state, the geometry and every
+// operation; the cancellation in E - |m|^2/(2 rho) enters as
+// u (E + 8 ke) / (E - ke)), then widened by 1.25 plus 16 u and a 1e-13 term
+// for the FP64 evaluation's own rounding.  A cell whose bound exceeds 2^-12,
+// or whose pressure is not clearly positive, gets the exact FP64 value
+// (which also raises the non-physical status as before).  The exact minimum
+// and every level decision an estimate cannot settle are then taken on exact
+// FP64 values, so levels and dt_min are bit for bit those of the all-FP64
+// evaluation.
+__device__ __forceinline__ void local_dt32(const DevMesh &d, int i, double &dt, float &eps) {
+  const float u = 5.9604645e-8f;  // 2^-24
+  float r, mx, my, mz, E, iv;
+  if (d.Un32) {
+    float a[REC_U32];
+    ldrec<REC_U32>(d.Un32 + (size_t)i * REC_U32, a);
+    r = a[0]; mx = a[1]; my = a[2]; mz = a[3]; E = a[4];
+    iv = d.ivol32[i];
+  } else {
+    const size_t N = d.N;
+    r = (float)d.Un[i]; mx = (float)d.Un[N + i]; my = (float)d.Un[2 * N + i];
+    mz = (float)d.Un[3 * N + i]; E = (float)d.Un[4 * N + i];
+    iv = (float)d.ivol[i];
+  }
+  const float g = (float)d.gamma, gm1 = (float)(d.gamma - 1.0);
+  const float mm = mx * mx + my * my + mz * mz;
+  const float ke = 0.5f * mm / r;
+  const float P = E - ke;
+  const float eP = u * (E + 8.0f * ke + P);              // |P~ - P| to first order
+  if (!(r > 0.0f) || !(P > 4.0f * eP) || !isfinite(E + mm)) {
+    dt = local_dt_of(d, i);
+    eps = 0.0f;
+    return;
+  }
+  const float relP = eP / (P - eP);
+  const float p = gm1 * P;
+  const float relq = relP + 6.0f * u;                     // gamma p rho
+  const float rc = sqrtf(g * p * r);
+  const float relc = 0.5f * relq + u;
+  float S = 0.0f, eS = 0.0f;
+  int4 cf = d.cf4[i];
+  const float *fg = d.fgeo32;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    float n0, n1, n2, A;
+    const int f = nbr_of(cf, j);
+    if (fg) {
+      float4 q = *reinterpret_cast<const float4 *>(fg + (size_t)f * REC_FG);
+      n0 = q.x; n1 = q.y; n2 = q.z; A = q.w;
+    } else {
+      const double *gd = d.fgeo + (size_t)f * REC_FG;
+      n0 = (float)gd[0]; n1 = (float)gd[1]; n2 = (float)gd[2]; A = (float)gd[3];
+    }
+    const float amn = fabsf(mx * n0) + fabsf(my * n1) + fabsf(mz * n2);
+    const float mn = fabsf(mx * n0 + my * n1 + mz * n2);
+    const float t = mn + rc;
+    S += A * t;
+    eS += A * (6.0f * u * amn + relc * rc + 4.0f * u * t);
+  }
+  const float val = 2.0f * (float)d.cfl * r / (iv * S);
+  float e = eS / S + 3.0f * u + 10.0f * u;
+  e = 1.25f * e + 16.0f * u + 1e-13f;
+  if (!(e <= 2.44140625e-4f) || !isfinite(val) || !(val > 0.0f)) {  // 2^-12
+    dt = local_dt_of(d, i);
+    eps = 0.0f;
+    return;
+  }
+  dt = (double)val;
+  eps = e;
+  d.dt[i] = dt;
+}
+
+// pass 1: estimates and the smallest upper bound
+__global__ void __launch_bounds__(256) k_dt32(DevMesh d) {
+  double local_hi = __longlong_as_double(0x7ff0000000000000LL);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x) {
+    double dt;
+    float e;
+    local_dt32(d, i, dt, e);
+    d.dteps[i] = e;
+    local_hi = fmin(local_hi, dt * (1.0 + (double)e));
+  }
+  block_min_to(local_hi, d.dthi_bits);
+}
+
+// pass 2: every cell that can hold the minimum (lower bound <= the smallest
+// upper bound) is made exact; dt_min = the exact minimum over them
+__global__ void __launch_bounds__(256) k_dt_min_exact(DevMesh d) {
+  const double hi = __longlong_as_double((long long)*d.dthi_bits);
+  double local_min = __longlong_as_double(0x7ff0000000000000LL);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x) {
+    const float e = d.dteps[i];
+    double dt = d.dt[i];
+    if (e > 0.0f && dt * (1.0 - (double)e) <= hi) {
+      dt = local_dt_of(d, i);
+      d.dteps[i] = 0.0f;
+      local_min = fmin(local_min, dt);
+    } else if (e == 0.0f && dt <= hi) {
+      local_min = fmin(local_min, dt);
+    }
+  }
+  block_min_to(local_min, d.dtmin_bits);
+}
 
 // k_i = max{k <= L-1 : 2^k dt_min <= dt_i}
 __device__ __forceinline__ int8_t level0_of(const DevMesh &d, double dtmin, int i) {
@@ -198,6 +308,28 @@ __global__ void __launch_bounds__(256) k_levels0(DevMesh d) {
   double dtmin = __longlong_as_double((long long)*d.dtmin_bits);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x)
     d.lev_tmp[i] = level0_of(d, dtmin, i);
+}
+
+// the same decision from an estimate: certain when no threshold 2^k dt_min
+// falls inside (lo, hi]; otherwise taken on the exact value
+__global__ void __launch_bounds__(256) k_levels0_certified(DevMesh d) {
+  const double dtmin = __longlong_as_double((long long)*d.dtmin_bits);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x) {
+    const float e = d.dteps[i];
+    if (e > 0.0f) {
+      const double dt = d.dt[i], lo = dt * (1.0 - (double)e), hi = dt * (1.0 + (double)e);
+      int klo = 0, khi = 0;
+      while (klo + 1 < d.L && ldexp(dtmin, klo + 1) <= lo) ++klo;
+      while (khi + 1 < d.L && ldexp(dtmin, khi + 1) <= hi) ++khi;
+      if (klo == khi) {
+        d.lev_tmp[i] = (int8_t)klo;
+        continue;
+      }
+      local_dt_of(d, i);
+      d.dteps[i] = 0.0f;
+    }
+    d.lev_tmp[i] = level0_of(d, dtmin, i);
+  }
 }
 
 // one Jacobi sweep of k_i <- min(k_i, 1 + min_j k_j); L-1 sweeps reach the
@@ -1361,9 +1493,10 @@ void init_device_info() { num_sms(); }
 int launch_assign_levels(const DevMesh &d, int L, int *cnt_scratch, ProfHook *ph, cudaStream_t s) {
   int g = grid_for(d.N, 256, 8);
   ProfScope scope(ph, FV_PROF_LEVELS, s);
-  k_init_min<<<1, 1, 0, s>>>(d.dtmin_bits);
-  k_dt<<<g, 256, 0, s>>>(d);
-  k_levels0<<<g, 256, 0, s>>>(d);
+  k_init_min2<<<1, 1, 0, s>>>(d.dtmin_bits, d.dthi_bits);
+  k_dt32<<<g, 256, 0, s>>>(d);
+  k_dt_min_exact<<<g, 256, 0, s>>>(d);
+  k_levels0_certified<<<g, 256, 0, s>>>(d);
   // L-1 Jacobi sweeps between lev_tmp and lev; the result must land in lev
   const int8_t *src = d.lev_tmp;
   int8_t *dst = d.lev;
