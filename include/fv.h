@@ -128,12 +128,12 @@ int fv_get_state(fv_mesh *m, double *cons_soa, int on_device, void *stream);
 int fv_assign_levels(fv_mesh *m, double *dt_min_out, int32_t *level_counts_out, void *stream);
 
 /* Local explicit time step dt_i of every cell (caller's order) computed by
- * the last level assignment (Alg. 2 line 1): host dt_out[n_tets].  A
- * single mesh's assignment evaluates dt_i in FP32 with a certified relative
- * bound (at most 2^-12, typically ~3e-6) and in FP64 wherever the minimum or
- * a level decision needs the exact value: those entries, dt_min and every
- * level are bit for bit the all-FP64 evaluation; the other entries are the
- * FP32 estimates.  (Batches evaluate every cell in FP64.)  Synchronous.
+ * the last level assignment (Alg. 2 line 1): host dt_out[n_tets].  The
+ * assignment evaluates dt_i in FP32 with a certified relative bound (at
+ * most 2^-12, typically ~3e-6) and in FP64 wherever the minimum or a level
+ * decision needs the exact value: those entries, dt_min and every level are
+ * bit for bit the all-FP64 evaluation; the other entries are the FP32
+ * estimates.  Synchronous.
  * Errors: FV_ERR_INVALID_ARG before any level assignment. */
 int fv_get_local_dt(fv_mesh *m, double *dt_out);
 

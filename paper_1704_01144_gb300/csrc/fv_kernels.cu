@@ -177,13 +177,6 @@ __device__ __forceinline__ void block_min_to(double local_min, unsigned long lon
   }
 }
 
-__global__ void __launch_bounds__(256) k_dt(DevMesh d) {
-  double local_min = __longlong_as_double(0x7ff0000000000000LL);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x)
-    local_min = fmin(local_min, local_dt_of(d, i));
-  block_min_to(local_min, d.dtmin_bits);
-}
-
 __global__ void k_init_min(unsigned long long *bits) { *bits = 0x7ff0000000000000ULL; }
 __global__ void k_init_min2(unsigned long long *a, unsigned long long *b) {
   *a = 0x7ff0000000000000ULL;
@@ -264,16 +257,34 @@ __device__ __forceinline__ void local_dt32(const DevMesh &d, int i, double &dt, 
   d.dt[i] = dt;
 }
 
+// pass 1 of one cell: its estimate; returns its upper bound
+__device__ __forceinline__ double dt32_cell(const DevMesh &d, int i) {
+  double dt;
+  float e;
+  local_dt32(d, i, dt, e);
+  d.dteps[i] = e;
+  return dt * (1.0 + (double)e);
+}
+
+// pass 2 of one cell: exact if its lower bound reaches the smallest upper
+// bound hi (it can hold the minimum); returns its exact value then, else +inf
+__device__ __forceinline__ double dt_min_exact_cell(const DevMesh &d, int i, double hi) {
+  const float e = d.dteps[i];
+  double dt = d.dt[i];
+  if (e > 0.0f && dt * (1.0 - (double)e) <= hi) {
+    dt = local_dt_of(d, i);
+    d.dteps[i] = 0.0f;
+    return dt;
+  }
+  if (e == 0.0f && dt <= hi) return dt;
+  return __longlong_as_double(0x7ff0000000000000LL);
+}
+
 // pass 1: estimates and the smallest upper bound
 __global__ void __launch_bounds__(256) k_dt32(DevMesh d) {
   double local_hi = __longlong_as_double(0x7ff0000000000000LL);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x) {
-    double dt;
-    float e;
-    local_dt32(d, i, dt, e);
-    d.dteps[i] = e;
-    local_hi = fmin(local_hi, dt * (1.0 + (double)e));
-  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x)
+    local_hi = fmin(local_hi, dt32_cell(d, i));
   block_min_to(local_hi, d.dthi_bits);
 }
 
@@ -282,17 +293,8 @@ __global__ void __launch_bounds__(256) k_dt32(DevMesh d) {
 __global__ void __launch_bounds__(256) k_dt_min_exact(DevMesh d) {
   const double hi = __longlong_as_double((long long)*d.dthi_bits);
   double local_min = __longlong_as_double(0x7ff0000000000000LL);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x) {
-    const float e = d.dteps[i];
-    double dt = d.dt[i];
-    if (e > 0.0f && dt * (1.0 - (double)e) <= hi) {
-      dt = local_dt_of(d, i);
-      d.dteps[i] = 0.0f;
-      local_min = fmin(local_min, dt);
-    } else if (e == 0.0f && dt <= hi) {
-      local_min = fmin(local_min, dt);
-    }
-  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x)
+    local_min = fmin(local_min, dt_min_exact_cell(d, i, hi));
   block_min_to(local_min, d.dtmin_bits);
 }
 
@@ -312,24 +314,24 @@ __global__ void __launch_bounds__(256) k_levels0(DevMesh d) {
 
 // the same decision from an estimate: certain when no threshold 2^k dt_min
 // falls inside (lo, hi]; otherwise taken on the exact value
+__device__ __forceinline__ int8_t level0_certified_of(const DevMesh &d, double dtmin, int i) {
+  const float e = d.dteps[i];
+  if (e > 0.0f) {
+    const double dt = d.dt[i], lo = dt * (1.0 - (double)e), hi = dt * (1.0 + (double)e);
+    int klo = 0, khi = 0;
+    while (klo + 1 < d.L && ldexp(dtmin, klo + 1) <= lo) ++klo;
+    while (khi + 1 < d.L && ldexp(dtmin, khi + 1) <= hi) ++khi;
+    if (klo == khi) return (int8_t)klo;
+    local_dt_of(d, i);
+    d.dteps[i] = 0.0f;
+  }
+  return level0_of(d, dtmin, i);
+}
+
 __global__ void __launch_bounds__(256) k_levels0_certified(DevMesh d) {
   const double dtmin = __longlong_as_double((long long)*d.dtmin_bits);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x) {
-    const float e = d.dteps[i];
-    if (e > 0.0f) {
-      const double dt = d.dt[i], lo = dt * (1.0 - (double)e), hi = dt * (1.0 + (double)e);
-      int klo = 0, khi = 0;
-      while (klo + 1 < d.L && ldexp(dtmin, klo + 1) <= lo) ++klo;
-      while (khi + 1 < d.L && ldexp(dtmin, khi + 1) <= hi) ++khi;
-      if (klo == khi) {
-        d.lev_tmp[i] = (int8_t)klo;
-        continue;
-      }
-      local_dt_of(d, i);
-      d.dteps[i] = 0.0f;
-    }
-    d.lev_tmp[i] = level0_of(d, dtmin, i);
-  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x)
+    d.lev_tmp[i] = level0_certified_of(d, dtmin, i);
 }
 
 // one Jacobi sweep of k_i <- min(k_i, 1 + min_j k_j); L-1 sweeps reach the
@@ -529,17 +531,29 @@ __device__ __forceinline__ bool tile_of(const MultiTiles &a, int &inst, int &til
 
 __global__ void k_init_min_multi(const DevMesh *ms, const int *active, int n) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n && active[i]) *ms[i].dtmin_bits = 0x7ff0000000000000ULL;
+  if (i < n && active[i]) {
+    *ms[i].dtmin_bits = 0x7ff0000000000000ULL;
+    *ms[i].dthi_bits = 0x7ff0000000000000ULL;
+  }
 }
 
-__global__ void __launch_bounds__(256) k_dt_multi(MultiTiles a) {
+// the certified local step of a batch: pass 1 (op 0) and pass 2 (op 1) per
+// instance, as k_dt32 and k_dt_min_exact do for one mesh
+__global__ void __launch_bounds__(256) k_dt_multi(MultiTiles a, int op) {
   int inst, tile;
   if (!tile_of(a, inst, tile)) return;
   const DevMesh &d = a.ms[inst];
   double m = __longlong_as_double(0x7ff0000000000000LL);
-  for (int i = tile * SORT_TILE + threadIdx.x; i < min(d.N, (tile + 1) * SORT_TILE); i += blockDim.x)
-    m = fmin(m, local_dt_of(d, i));
-  block_min_to(m, d.dtmin_bits);
+  const int end = min(d.N, (tile + 1) * SORT_TILE);
+  if (op == 0) {
+    for (int i = tile * SORT_TILE + threadIdx.x; i < end; i += blockDim.x) m = fmin(m, dt32_cell(d, i));
+    block_min_to(m, d.dthi_bits);
+  } else {
+    const double hi = __longlong_as_double((long long)*d.dthi_bits);
+    for (int i = tile * SORT_TILE + threadIdx.x; i < end; i += blockDim.x)
+      m = fmin(m, dt_min_exact_cell(d, i, hi));
+    block_min_to(m, d.dtmin_bits);
+  }
 }
 
 // op 0: levels0; 1: copy lev_tmp -> lev; 2: sweep lev_tmp -> lev;
@@ -550,7 +564,7 @@ __global__ void __launch_bounds__(256) k_cells_multi(MultiTiles a, int op) {
   const DevMesh &d = a.ms[inst];
   double dtmin = __longlong_as_double((long long)*d.dtmin_bits);
   for (int i = tile * SORT_TILE + threadIdx.x; i < min(d.N, (tile + 1) * SORT_TILE); i += blockDim.x) {
-    if (op == 0) d.lev_tmp[i] = level0_of(d, dtmin, i);
+    if (op == 0) d.lev_tmp[i] = level0_certified_of(d, dtmin, i);
     else if (op == 1) d.lev[i] = d.lev_tmp[i];
     else if (op == 2) d.lev[i] = smooth_of(d, d.lev_tmp, i);
     else if (op == 3) d.lev_tmp[i] = smooth_of(d, d.lev, i);
@@ -1710,7 +1724,8 @@ int launch_assign_multi(const DevMesh *ms, const int *active, int n, int Lmax, i
   MultiTiles ac{ms, active, blk_pref_c, n}, af{ms, active, blk_pref_f, n};
   const int gc = (int)max_cell_blocks, gf = (int)max_face_blocks;
   k_init_min_multi<<<1, FV_MAXB, 0, s>>>(ms, active, n);
-  k_dt_multi<<<gc, 256, 0, s>>>(ac);
+  k_dt_multi<<<gc, 256, 0, s>>>(ac, 0);
+  k_dt_multi<<<gc, 256, 0, s>>>(ac, 1);
   k_cells_multi<<<gc, 256, 0, s>>>(ac, 0);
   // Lmax-1 sweeps for every instance (extra sweeps keep the fixed point); the
   // last one must write lev
