@@ -252,6 +252,7 @@ def run_mode(fv, torch, mesh, prim, L, precision, steps, warmup, stream, flush, 
         raise RuntimeError(f"device status {st}: {fv.fv_last_error()}")
     cell_updates = c1[1] - c0[1]
     face_evals = c1[2] - c0[2]
+    history = level_history_summary(g, L)
     # per-kernel-class timing (CUDA events on the launching stream), 2 cycles
     g.profile_enable(True)
     p0 = g.work_counters()
@@ -265,6 +266,7 @@ def run_mode(fv, torch, mesh, prim, L, precision, steps, warmup, stream, flush, 
         "value": cell_updates / (ms * 1e-3), "clocks": clk.summary(),
         "prof": prof, "prof_face_evals": p1[2] - p0[2], "prof_cell_updates": p1[1] - p0[1],
         "launch_per_sm": per_sm, "autotune_cached": tune["cached"],
+        "level_history": history,
     }
     return g, out
 
@@ -308,6 +310,29 @@ def cpu_baseline(mesh, prim, L, budget_s=15.0, max_cycles=4):
             "kind": "oracle",
             "sample": f"first {cycles} cycle(s) of the same workload, FP64 CPU oracle "
                       f"({O.num_threads()} OpenMP threads), {dt:.1f} s"}
+
+
+def level_history_summary(g, L):
+    """The level distribution of the first and last cycles the chosen mesh
+    ran (the paper's Sec. 5 tables): share of cells and of the cost C(tau)
+    per level, and the adaptive-vs-global cost ratio 2^theta N / sum C."""
+    if g is None:
+        return None
+    counts, dtm = g.level_history()
+    if len(counts) == 0:
+        return None
+    theta = L - 1
+
+    def row(c, dt):
+        c = c[:L].astype(float)
+        cost = c * 2.0 ** (theta - np.arange(L))
+        return {"cells_share": [round(x, 5) for x in c / c.sum()],
+                "cost_share": [round(x, 5) for x in cost / cost.sum()],
+                "global_over_adaptive_cost": round(2 ** theta * c.sum() / cost.sum(), 4),
+                "dt_min": dt}
+
+    return {"cycles_recorded": int(len(counts)), "first": row(counts[0], float(dtm[0])),
+            "last": row(counts[-1], float(dtm[-1]))}
 
 
 def replica_stats(local, device):
@@ -535,6 +560,7 @@ def main_ours(args):
             "autotuned_blocks_per_sm": {"prim_grad_flux_update": chosen["launch_per_sm"],
                                         "cached": chosen["autotune_cached"]},
             "persistent_cycle": persistent,
+            "level_history": chosen["level_history"],
             "cell_updates_per_step": chosen["cell_updates"] / args.steps,
             "face_evals_per_step": chosen["face_evals"] / args.steps,
         }

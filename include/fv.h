@@ -137,6 +137,14 @@ int fv_assign_levels(fv_mesh *m, double *dt_min_out, int32_t *level_counts_out, 
  * Errors: FV_ERR_INVALID_ARG before any level assignment. */
 int fv_get_local_dt(fv_mesh *m, double *dt_out);
 
+/* The evolving level distribution (the paper follows it in Sec. 5: the
+ * share of cells and of the cost C(tau) per level, iteration by iteration):
+ * for the last n = min(cycles run since the state was set, 4096,
+ * max_cycles) cycles, oldest first, counts_out[q*8 + k] = cells of level k
+ * in cycle q (k < 8; 0 above the mesh's levels) and dtmin_out[q] = its
+ * dt_min; *n_out = n.  Host arrays; synchronous. */
+int fv_level_history(fv_mesh *m, int max_cycles, int32_t *counts_out, double *dtmin_out, int *n_out);
+
 /* Level of every cell (caller's order) of the current cycle: host int8
  * array levels_out[n_tets].  Synchronous. */
 int fv_get_levels(fv_mesh *m, int8_t *levels_out);

@@ -293,6 +293,8 @@ int fv_mesh_load(const double *xyz, int64_t n_nodes, const int64_t *tets, int64_
   AL(d.tdev, 1);
   AL(d.status, 1);
   AL(d.counters, 3);
+  AL(d.hist, (size_t)FV_HIST_CAP * FV_MAXL);
+  AL(d.hist_dt, FV_HIST_CAP);
   AL(m->cnt_scratch, cnt_size);
   d.sort_cnt = m->cnt_scratch;
   AL(m->new2old_dev, N);
@@ -629,6 +631,29 @@ int fv_barrier_selftest(int device, int rounds, int unreachable, int *status_out
 int fv_use_graph(fv_mesh *m, int enable) {
   if (!m) return fail(FV_ERR_INVALID_ARG, "fv_use_graph: NULL mesh");
   m->use_graph = enable != 0;
+  return FV_OK;
+}
+
+int fv_level_history(fv_mesh *m, int max_cycles, int32_t *counts_out, double *dtmin_out, int *n_out) {
+  if (!m || max_cycles < 0 || !n_out || (max_cycles > 0 && (!counts_out || !dtmin_out)))
+    return fail(FV_ERR_INVALID_ARG, "fv_level_history: bad argument");
+  CK(cudaSetDevice(m->cfg.device));
+  CK(cudaDeviceSynchronize());
+  long long c[3];
+  CK(cudaMemcpy(c, m->d.counters, sizeof c, cudaMemcpyDeviceToHost));
+  const long long have = c[0] < FV_HIST_CAP ? c[0] : FV_HIST_CAP;
+  const int n = (int)(have < max_cycles ? have : max_cycles);
+  std::vector<int> h((size_t)FV_HIST_CAP * FV_MAXL);
+  std::vector<double> hd(FV_HIST_CAP);
+  CK(cudaMemcpy(h.data(), m->d.hist, h.size() * sizeof(int), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(hd.data(), m->d.hist_dt, hd.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  for (int q = 0; q < n; ++q) {
+    const long long cyc = c[0] - n + q;  // oldest first
+    const long long slot = cyc % FV_HIST_CAP;
+    for (int k = 0; k < FV_MAXL; ++k) counts_out[(size_t)q * FV_MAXL + k] = h[slot * FV_MAXL + k];
+    dtmin_out[q] = hd[slot];
+  }
+  *n_out = n;
   return FV_OK;
 }
 

@@ -54,6 +54,8 @@ struct GridBar {
   unsigned count, gen;
 };
 
+#define FV_HIST_CAP 4096  // cycles kept by the level history
+
 // largest cell or face count (ids are int32; grid-stride loops overshoot a
 // range end by less than 2^22)
 #define FV_MAX_ITEMS ((int64_t)0x7fffffff - ((int64_t)1 << 22))
@@ -89,6 +91,8 @@ struct DevMesh {
   double *tdev;           // physical time
   int *status;            // sticky status bits
   long long *counters;    // [0] cycles, [1] weighted cell updates, [2] face evaluations
+  int *hist;              // per cycle (ring of FV_HIST_CAP): cells per level [FV_MAXL]
+  double *hist_dt;        // per cycle: dt_min
   // phase scratch: primitives at the phase time (FP64 or FP32 records)
   void *W;
   int precision;

@@ -1320,13 +1320,22 @@ __global__ void __launch_bounds__(256) k_prim_all(DevMesh d, const __grid_consta
 
 // end of a cycle: t += 2^theta dt_min, and the work counters of the cost
 // model: sum_k 2^(theta-k) |Omega_k| cell updates, twice that over faces
+// The cycle's level distribution also goes into the level history (cells
+// per level and dt_min, a ring of FV_HIST_CAP cycles).
 __device__ __forceinline__ void time_advance_of(const DevMesh &d, int theta) {
-  d.tdev[0] += ldexp(__longlong_as_double((long long)*d.dtmin_bits), theta);
+  const double dtmin = __longlong_as_double((long long)*d.dtmin_bits);
+  d.tdev[0] += ldexp(dtmin, theta);
   long long cu = 0, fe = 0;
-  for (int k = 0; k <= theta; ++k) {
-    cu += (long long)(d.coff[2 * k + 2] - d.coff[2 * k]) << (theta - k);
-    fe += (long long)(d.foff[k + 1] - d.foff[k]) << (theta - k + 1);
+  const long long slot = d.counters[0] % FV_HIST_CAP;
+  for (int k = 0; k < FV_MAXL; ++k) {
+    const int nk = k <= theta ? d.coff[2 * k + 2] - d.coff[2 * k] : 0;
+    d.hist[slot * FV_MAXL + k] = nk;
+    if (k <= theta) {
+      cu += (long long)nk << (theta - k);
+      fe += (long long)(d.foff[k + 1] - d.foff[k]) << (theta - k + 1);
+    }
   }
+  d.hist_dt[slot] = dtmin;
   d.counters[0] += 1;
   d.counters[1] += cu;
   d.counters[2] += fe;

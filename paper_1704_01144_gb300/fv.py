@@ -68,7 +68,7 @@ EXPORTS = [
     "fv_batch_set_launch", "fv_batch_get_launch", "fv_mlp_init", "fv_mlp_pack", "fv_mlp_infer",
     "fv_mlp_label", "fv_mlp_loss_grad", "fv_mlp_adam", "fv_mlp_train", "fv_mlp_train_steps",
     "fv_mlp_load", "fv_set_guess", "fv_harvest_pairs", "fv_godunov_flux_batch_mlp",
-    "fv_use_persistent", "fv_barrier_selftest",
+    "fv_use_persistent", "fv_barrier_selftest", "fv_level_history",
 ]
 
 FV_MLP_PARAMS = 4673
@@ -125,6 +125,7 @@ def lib():
                                    C.POINTER(C.c_int64)]
     L.fv_use_graph.argtypes = [vp, C.c_int]
     L.fv_use_persistent.argtypes = [vp, C.c_int]
+    L.fv_level_history.argtypes = [vp, C.c_int, i32p, dp, C.POINTER(C.c_int)]
     L.fv_barrier_selftest.argtypes = [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int)]
     L.fv_profile_enable.argtypes = [vp, C.c_int]
     L.fv_profile_read.argtypes = [vp, dp, C.POINTER(C.c_int64)]
@@ -262,6 +263,18 @@ def fv_work_counters(h):
     a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
     _check(lib().fv_work_counters(h, C.byref(a), C.byref(b), C.byref(c)), "fv_work_counters")
     return a.value, b.value, c.value
+
+
+def fv_level_history(h, max_cycles=4096):
+    """(counts [n, 8] int32: cells per level, dtmin [n]) of the last n cycles,
+    oldest first."""
+    counts = np.zeros((max_cycles, 8), dtype=np.int32)
+    dtm = np.zeros(max_cycles)
+    n = C.c_int()
+    _check(lib().fv_level_history(h, int(max_cycles), counts.ctypes.data_as(C.POINTER(C.c_int32)),
+                                  dtm.ctypes.data_as(C.POINTER(C.c_double)), C.byref(n)),
+           "fv_level_history")
+    return counts[:n.value], dtm[:n.value]
 
 
 def fv_use_persistent(h, enable):
@@ -633,6 +646,9 @@ class Mesh:
 
     def use_persistent(self, enable):
         fv_use_persistent(self.h, enable)
+
+    def level_history(self, max_cycles=4096):
+        return fv_level_history(self.h, max_cycles)
 
     def set_launch(self, per_sm):
         fv_set_launch(self.h, per_sm)
