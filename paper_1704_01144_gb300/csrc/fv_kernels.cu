@@ -693,13 +693,12 @@ __device__ __forceinline__ void prim_item(const DevMesh &d, const PhaseLevels &p
 // primitives are stored in its W record for the flux kernel; there is no
 // separate primitives kernel.
 template <typename T>
-__device__ __forceinline__ void grad_item(const DevMesh &d, const PhaseLevels &pl, int idx) {
+__device__ __forceinline__ void grad_cell(const DevMesh &d, const PhaseLevels &pl, int i) {
   constexpr bool INLINE_W = sizeof(T) == 4;
   const T *W = (const T *)d.W;
   const T *lsw = lswrec(d, T(0));
   const T *fgeo = georec(d, T(0));
   const double gm1 = d.gamma - 1.0;
-  int i = d.cl[idx];
   T Wi[REC_W], g[REC_G], w[REC_LSW];
   if (INLINE_W) {
     T U[5];
@@ -748,6 +747,19 @@ __device__ __forceinline__ void grad_item(const DevMesh &d, const PhaseLevels &p
     }
   }
   strec<REC_G>(grec_w(d, T(0)) + (size_t)i * REC_G, g);
+}
+
+template <typename T>
+__device__ __forceinline__ void grad_item(const DevMesh &d, const PhaseLevels &pl, int idx) {
+  grad_cell<T>(d, pl, d.cl[idx]);
+}
+
+// gradients (and, FP32-flux mode, primitives) of every cell by plain index:
+// the hooks' pass, independent of the level-sorted lists
+template <typename T>
+__global__ void __launch_bounds__(256, 2) k_grad_all(DevMesh d, const __grid_constant__ PhaseLevels pl) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x)
+    grad_cell<T>(d, pl, i);
 }
 
 // the learned starting guess of one face (warp-collective): where the
@@ -1642,18 +1654,12 @@ int launch_residual(const DevMesh &d, int precision, const PhaseLevels &pl, int 
   (void)Wbuf;
   int gc = grid_for(d.N, 256, 8);
   int gfx = grid_for(d.F, 128, 16);
-  PhaseDesc all;  // gradients of every cell: the list range covering all cells
-  memset(&all, 0, sizeof all);
-  all.pl = pl;    // the view the FP32-flux gradient step computes its primitives in
-  all.gb0 = 0;
-  all.gb1 = 2 * d.L;
-  all.active = 1;
   const bool g14 = d.gamma == 1.4;
   if (precision == FV_FP64) {
     double *W = (double *)d.W;
     GasT<double> G = gas64(d);
     k_prim_all<double><<<gc, 256, 0, s>>>(d, pl, W);
-    k_phase1<K_GRAD, double, true><<<gc, 256, 0, s>>>(d, all, G);
+    k_grad_all<double><<<gc, 256, 0, s>>>(d, pl);
     if (g14)
       k_flux_all<double, true><<<gfx, 128, 0, s>>>(d, G, level, W, d.G, d.fgeo, FAt);
     else
@@ -1661,8 +1667,8 @@ int launch_residual(const DevMesh &d, int precision, const PhaseLevels &pl, int 
   } else {
     float *W = (float *)d.W;
     GasT<float> G = gas32(d);
-    k_prim_all<float><<<gc, 256, 0, s>>>(d, pl, W);
-    k_phase1<K_GRAD, float, true><<<gc, 256, 0, s>>>(d, all, G);
+    // the FP32 gradient pass writes every cell's primitives too (view pl)
+    k_grad_all<float><<<gc, 256, 0, s>>>(d, pl);
     if (g14)
       k_flux_all<float, true><<<gfx, 128, 0, s>>>(d, G, level, W, d.G32, d.fgeo32, FAt);
     else
@@ -1702,22 +1708,15 @@ int launch_harvest(const DevMesh &d, double *out, int m, long long a, long long 
   int gc = grid_for(d.N, 256, 8);
   PhaseLevels pl;  // every level at U^n
   memset(&pl, 0, sizeof pl);
-  PhaseDesc all;
-  memset(&all, 0, sizeof all);
-  all.pl = pl;
-  all.gb0 = 0;
-  all.gb1 = 2 * d.L;
-  all.active = 1;
   int gh = grid_for(m, 128, 8);
   if (d.precision == FV_FP64) {
     double *W = (double *)d.W;
     k_prim_all<double><<<gc, 256, 0, s>>>(d, pl, W);
-    k_phase1<K_GRAD, double, true><<<gc, 256, 0, s>>>(d, all, gas64(d));
+    k_grad_all<double><<<gc, 256, 0, s>>>(d, pl);
     k_harvest<double><<<gh, 128, 0, s>>>(d, W, d.G, d.fgeo, out, m, a, b);
   } else {
     float *W = (float *)d.W;
-    k_prim_all<float><<<gc, 256, 0, s>>>(d, pl, W);
-    k_phase1<K_GRAD, float, true><<<gc, 256, 0, s>>>(d, all, gas32(d));
+    k_grad_all<float><<<gc, 256, 0, s>>>(d, pl);
     k_harvest<float><<<gh, 128, 0, s>>>(d, W, d.G32, d.fgeo32, out, m, a, b);
   }
   FV_LAUNCH_CHECK();
