@@ -439,11 +439,17 @@ int fv_mlp_train_steps(const fv_train_config *tc, int64_t n_sel);
  * flux kernel then evaluates it on the tensor cores for the faces the gate
  * passes and starts Newton from its guess there.  Synchronous.  Not
  * inside a cycle; batches (fv_batch_create) take only meshes with the
- * two-rarefaction guess. */
+ * two-rarefaction guess and get their network from fv_batch_mlp_load. */
 int fv_mlp_load(fv_mesh *m, const float *params_dev, int n_params, int target, double gate);
 
 /* FV_GUESS_TWO_RAREFACTION, or FV_GUESS_MLP after fv_mlp_load. */
 int fv_set_guess(fv_mesh *m, int guess);
+
+/* The same for a batch: one network (packed into batch-owned memory) for
+ * every instance, evaluated in the batched flux kernel; results equal each
+ * mesh advanced alone with the same network.  Synchronous. */
+int fv_batch_mlp_load(fv_batch *b, const float *params_dev, int n_params, int target, double gate);
+int fv_batch_set_guess(fv_batch *b, int guess);
 
 /* Riemann pairs of the mesh's current state U^n (the reconstructed face
  * states the flux kernel sees, in its precision): pair j of face

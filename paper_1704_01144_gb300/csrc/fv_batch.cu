@@ -15,6 +15,8 @@
 // CUDA graph.  Results equal each mesh advanced on its own, bit for bit.
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 #include <string>
 #include <vector>
 
@@ -37,6 +39,8 @@ struct fv_batch {
   cudaGraphExec_t graph = nullptr;
   std::vector<void *> allocs;
   LaunchCfg launch = default_launch();
+  uint32_t *mlp = nullptr;  // the batch's learned guess (packed), shared by every instance
+  bool use_mlp = false;
 };
 
 namespace {
@@ -73,7 +77,8 @@ int run_steps(fv_batch *b, cudaStream_t s) {
                                     b->d_tpref_f, s);
     } else if (st.type == 1) {
       rc = fvk::launch_phase_multi(b->d_ms, b->d_pds + (size_t)st.idx * b->n, b->n,
-                                   b->meshes[0]->d, b->cells, b->faces, b->launch, s);
+                                   b->meshes[0]->d, b->cells, b->faces, b->launch,
+                                   b->use_mlp ? b->mlp : nullptr, s);
     } else {
       rc = fvk::launch_time_advance_multi(b->d_ms, b->d_pds + (size_t)st.idx * b->n, b->n, s);
     }
@@ -319,6 +324,39 @@ int fv_batch_set_launch(fv_batch *b, const int32_t per_sm[4]) {
 int fv_batch_get_launch(fv_batch *b, int32_t per_sm[4]) {
   if (!b || !per_sm) return bfail(FV_ERR_INVALID_ARG, "fv_batch_get_launch: NULL argument");
   for (int k = 0; k < 4; ++k) per_sm[k] = b->launch.per_sm[k];
+  return FV_OK;
+}
+
+int fv_batch_mlp_load(fv_batch *b, const float *params_dev, int n_params, int target, double gate) {
+  if (!b || !params_dev || n_params != 4673 || (target != 0 && target != 1) || !std::isfinite(gate) ||
+      gate > 1e38)
+    return bfail(FV_ERR_INVALID_ARG, "fv_batch_mlp_load: bad argument");
+  BCK(cudaSetDevice(b->device));
+  if (!b->mlp) {
+    int rc = balloc(b, &b->mlp, (size_t)2560);
+    if (rc) return rc;
+  }
+  if (fvk::launch_mlp_pack(params_dev, target, (float)gate, b->mlp, 0) != FV_OK)
+    return bfail(FV_ERR_CUDA, "fv_batch_mlp_load: pack launch failed");
+  BCK(cudaDeviceSynchronize());
+  b->use_mlp = true;
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  return FV_OK;
+}
+
+int fv_batch_set_guess(fv_batch *b, int guess) {
+  if (!b || (guess != FV_GUESS_TWO_RAREFACTION && guess != FV_GUESS_MLP))
+    return bfail(FV_ERR_INVALID_ARG, "fv_batch_set_guess: bad argument");
+  if (guess == FV_GUESS_MLP && !b->mlp)
+    return bfail(FV_ERR_INVALID_ARG, "fv_batch_set_guess: no network loaded (fv_batch_mlp_load)");
+  b->use_mlp = guess == FV_GUESS_MLP;
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
   return FV_OK;
 }
 

@@ -308,7 +308,8 @@ int launch_phase(const DevMesh &d, const PhaseDesc &pd, const LaunchCfg &lc, Pro
                  cudaStream_t s);
 // batches: ms/pds are device arrays of n meshes / descriptors of one phase
 int launch_phase_multi(const DevMesh *ms, const PhaseDesc *pds, int n, const DevMesh &d0,
-                       int64_t max_cells, int64_t max_faces, const LaunchCfg &lc, cudaStream_t s);
+                       int64_t max_cells, int64_t max_faces, const LaunchCfg &lc, const uint32_t *mlp,
+                       cudaStream_t s);
 int launch_assign_multi(const DevMesh *ms, const int *active, int n, int Lmax, int64_t max_cells,
                         int64_t max_faces, int64_t max_cell_blocks, int64_t max_face_blocks,
                         int *cnt_scratch, const int *blk_pref_c, const int *blk_pref_f, cudaStream_t s);
@@ -330,4 +331,6 @@ int launch_harvest(const DevMesh &d, double *out, int m, long long a, long long 
 int launch_persistent_cycle(const DevMesh &d, const PhaseDesc *pds, int nph, GridBar *bar,
                             cudaStream_t s);
 int launch_barrier_probe(GridBar *bar, int *status, int rounds, unsigned extra, cudaStream_t s);
+// fv_mlp.cu: FP32 parameters -> packed bf16 fragments (PK_WORDS words)
+int launch_mlp_pack(const float *params, int target, float gate, uint32_t *packed, cudaStream_t s);
 }  // namespace fvk

@@ -1085,11 +1085,12 @@ __global__ void __launch_bounds__(128, FV_MLP_FLUX_BLOCKS) k_flux_mlp1(DevMesh d
   }
 }
 
-template <int KIND, typename T, bool G14>
-__global__ void KBOUNDS(KIND, T) k_phaseN(const DevMesh *__restrict__ ms, const PhaseDesc *__restrict__ ps,
-                                          int n, GasT<T> G) {
-  __shared__ int pref[FV_MAXB + 1];
-  __shared__ int base[FV_MAXB];
+// a batch's flattened work index: the first warp of the block writes the
+// exclusive prefix of the active instances' range lengths (pref[0..n], total
+// in pref[FV_MAXB]) and their range starts (base) to shared memory
+__device__ __forceinline__ void batch_prefix(const DevMesh *__restrict__ ms,
+                                             const PhaseDesc *__restrict__ ps, int n, int kind,
+                                             int *pref, int *base) {
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
     int len[2], b[2];
@@ -1100,7 +1101,7 @@ __global__ void KBOUNDS(KIND, T) k_phaseN(const DevMesh *__restrict__ ms, const 
       b[hh] = 0;
       if (i < n && ps[i].active) {
         int e;
-        kind_range(ms[i], ps[i], KIND, b[hh], e);
+        kind_range(ms[i], ps[i], kind, b[hh], e);
         len[hh] = e - b[hh];
       }
     }
@@ -1121,13 +1122,52 @@ __global__ void KBOUNDS(KIND, T) k_phaseN(const DevMesh *__restrict__ ms, const 
     base[lane + 32] = b[1];
   }
   __syncthreads();
+}
+
+// the instance of flattened index g (binary search of the prefix)
+__device__ __forceinline__ int batch_instance(const int *pref, int n, int g) {
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (pref[mid] <= g) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// the batch's flux with the learned guess: one packed network for every
+// instance, the warp-uniform loop over the flattened face index
+template <typename T, bool G14>
+__global__ void __launch_bounds__(128, FV_MLP_FLUX_BLOCKS) k_flux_mlpN(const DevMesh *__restrict__ ms,
+                                                                       const PhaseDesc *__restrict__ ps,
+                                                                       int n, GasT<T> G,
+                                                                       const uint32_t *__restrict__ mlp) {
+  __shared__ __align__(16) uint32_t sw[PK_WORDS];
+  __shared__ int pref[FV_MAXB + 1];
+  __shared__ int base[FV_MAXB];
+  mlp_stage(sw, mlp);
+  batch_prefix(ms, ps, n, K_FLUX, pref, base);
+  const int total = pref[FV_MAXB];
+  const int lane = threadIdx.x & 31;
+  for (int gb = blockIdx.x * blockDim.x + (threadIdx.x - lane); gb < total; gb += gridDim.x * blockDim.x) {
+    // one call for every lane (the guess inside is warp-collective): lanes
+    // past the end pass no face
+    const int g = gb + lane;
+    const bool ok = g < total;
+    const int lo = ok ? batch_instance(pref, n, g) : 0;
+    const int idx = ok ? base[lo] + (g - pref[lo]) : -1;
+    flux_item<T, G14, true>(ms[lo], G, ps[lo].stage, ps[lo].level, idx, sw);
+  }
+}
+
+template <int KIND, typename T, bool G14>
+__global__ void KBOUNDS(KIND, T) k_phaseN(const DevMesh *__restrict__ ms, const PhaseDesc *__restrict__ ps,
+                                          int n, GasT<T> G) {
+  __shared__ int pref[FV_MAXB + 1];
+  __shared__ int base[FV_MAXB];
+  batch_prefix(ms, ps, n, KIND, pref, base);
   const int total = pref[FV_MAXB];
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
-    int lo = 0, hi = n;
-    while (hi - lo > 1) {
-      int mid = (lo + hi) >> 1;
-      if (pref[mid] <= g) lo = mid; else hi = mid;
-    }
+    const int lo = batch_instance(pref, n, g);
     run_item<KIND, T, G14>(ms[lo], ps[lo], G, base[lo] + (g - pref[lo]));
   }
 }
@@ -1626,24 +1666,31 @@ int launch_phase(const DevMesh &d, const PhaseDesc &pd, const LaunchCfg &lc, Pro
 
 template <typename T, bool G14>
 static void phaseN_all(const DevMesh *ms, const PhaseDesc *pds, int n, const GasT<T> &G,
-                       int64_t cells, int64_t faces, const LaunchCfg &lc, cudaStream_t s) {
+                       int64_t cells, int64_t faces, const LaunchCfg &lc, const uint32_t *mlp,
+                       cudaStream_t s) {
   const int g0 = grid_for(cells, 256, lc.per_sm[0]), g1 = grid_for(cells, 256, lc.per_sm[1]);
   const int g2 = grid_for(faces, 128, lc.per_sm[2]), g3 = grid_for(cells, 256, lc.per_sm[3]);
   if (sizeof(T) == 8) k_phaseN<K_PRIM, T, G14><<<g0, 256, 0, s>>>(ms, pds, n, G);
   k_phaseN<K_GRAD, T, G14><<<g1, 256, 0, s>>>(ms, pds, n, G);
-  k_phaseN<K_FLUX, T, G14><<<g2, 128, 0, s>>>(ms, pds, n, G);
+  if (mlp)
+    k_flux_mlpN<T, G14><<<grid_for(faces, 128, lc.per_sm[2] < FV_MLP_FLUX_BLOCKS ? lc.per_sm[2]
+                                                                                  : FV_MLP_FLUX_BLOCKS),
+                          128, 0, s>>>(ms, pds, n, G, mlp);
+  else
+    k_phaseN<K_FLUX, T, G14><<<g2, 128, 0, s>>>(ms, pds, n, G);
   k_phaseN<K_UPD, T, G14><<<g3, 256, 0, s>>>(ms, pds, n, G);
 }
 
 int launch_phase_multi(const DevMesh *ms, const PhaseDesc *pds, int n, const DevMesh &d0,
-                       int64_t max_cells, int64_t max_faces, const LaunchCfg &lc, cudaStream_t s) {
+                       int64_t max_cells, int64_t max_faces, const LaunchCfg &lc, const uint32_t *mlp,
+                       cudaStream_t s) {
   const bool g14 = d0.gamma == 1.4;
   if (d0.precision == FV_FP64) {
-    if (g14) phaseN_all<double, true>(ms, pds, n, gas64(d0), max_cells, max_faces, lc, s);
-    else phaseN_all<double, false>(ms, pds, n, gas64(d0), max_cells, max_faces, lc, s);
+    if (g14) phaseN_all<double, true>(ms, pds, n, gas64(d0), max_cells, max_faces, lc, mlp, s);
+    else phaseN_all<double, false>(ms, pds, n, gas64(d0), max_cells, max_faces, lc, mlp, s);
   } else {
-    if (g14) phaseN_all<float, true>(ms, pds, n, gas32(d0), max_cells, max_faces, lc, s);
-    else phaseN_all<float, false>(ms, pds, n, gas32(d0), max_cells, max_faces, lc, s);
+    if (g14) phaseN_all<float, true>(ms, pds, n, gas32(d0), max_cells, max_faces, lc, mlp, s);
+    else phaseN_all<float, false>(ms, pds, n, gas32(d0), max_cells, max_faces, lc, mlp, s);
   }
   FV_LAUNCH_CHECK();
   return FV_OK;

@@ -293,6 +293,11 @@ __global__ void __launch_bounds__(128) k_mlp_label(const double *__restrict__ pa
   }
 }
 
+int launch_mlp_pack(const float *params, int target, float gate, uint32_t *packed, cudaStream_t s) {
+  k_mlp_pack<<<1, 256, 0, s>>>(params, target, gate, packed);
+  return cudaGetLastError() == cudaSuccess ? FV_OK : FV_ERR_CUDA;
+}
+
 }  // namespace fvk
 
 using namespace fvk;

@@ -68,7 +68,8 @@ EXPORTS = [
     "fv_batch_set_launch", "fv_batch_get_launch", "fv_mlp_init", "fv_mlp_pack", "fv_mlp_infer",
     "fv_mlp_label", "fv_mlp_loss_grad", "fv_mlp_adam", "fv_mlp_train", "fv_mlp_train_steps",
     "fv_mlp_load", "fv_set_guess", "fv_harvest_pairs", "fv_godunov_flux_batch_mlp",
-    "fv_use_persistent", "fv_barrier_selftest", "fv_level_history",
+    "fv_use_persistent", "fv_barrier_selftest", "fv_level_history", "fv_batch_mlp_load",
+    "fv_batch_set_guess",
 ]
 
 FV_MLP_PARAMS = 4673
@@ -126,6 +127,8 @@ def lib():
     L.fv_use_graph.argtypes = [vp, C.c_int]
     L.fv_use_persistent.argtypes = [vp, C.c_int]
     L.fv_level_history.argtypes = [vp, C.c_int, i32p, dp, C.POINTER(C.c_int)]
+    L.fv_batch_mlp_load.argtypes = [vp, vp, C.c_int, C.c_int, C.c_double]
+    L.fv_batch_set_guess.argtypes = [vp, C.c_int]
     L.fv_barrier_selftest.argtypes = [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int)]
     L.fv_profile_enable.argtypes = [vp, C.c_int]
     L.fv_profile_read.argtypes = [vp, dp, C.POINTER(C.c_int64)]
@@ -581,6 +584,15 @@ def fv_batch_use_graph(b, enable):
     _check(lib().fv_batch_use_graph(b, int(bool(enable))), "fv_batch_use_graph")
 
 
+def fv_batch_mlp_load(b, params, target, gate=-1.0):
+    _check(lib().fv_batch_mlp_load(b, _dptr(params, "float32"), FV_MLP_PARAMS, int(target), float(gate)),
+           "fv_batch_mlp_load")
+
+
+def fv_batch_set_guess(b, guess):
+    _check(lib().fv_batch_set_guess(b, int(guess)), "fv_batch_set_guess")
+
+
 def _launch4(per_sm):
     a = (C.c_int32 * 4)(*[int(x) for x in per_sm])
     return a
@@ -724,6 +736,12 @@ class Batch:
 
     def use_graph(self, enable):
         fv_batch_use_graph(self.h, enable)
+
+    def mlp_load(self, params, target=FV_MLP_TARGET_TR, gate=-1.0):
+        fv_batch_mlp_load(self.h, params, target, gate)
+
+    def set_guess(self, guess):
+        fv_batch_set_guess(self.h, guess)
 
     def set_launch(self, per_sm):
         fv_batch_set_launch(self.h, per_sm)

@@ -303,3 +303,36 @@ def test_learned_guess_gain(fv, oracle_mod):
     assert e["learned"] < 0.5 * e["two_rarefaction"]
     assert it_g["learned"] < it_g["two_rarefaction"]
     assert it_a["learned"] <= it_a["two_rarefaction"]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_with_learned_guess_equals_meshes_alone(fv, precision):
+    """One network for every instance of a batch: bitwise the same as each
+    mesh advanced alone with it (a face's network output depends on its own
+    row of the tensor-core tile only)."""
+    import torch
+    from paper_1704_01144_gb300 import inputs as I
+    th = torch.from_numpy(theta_random(fv, 77)).cuda()
+    cases = [(6, 2, 1704), (8, 3, 1705), (7, 1, 1706)]
+    batch_meshes, alone = [], []
+    for n, L, seed in cases:
+        mesh, prim = I.blast_case(n=n, ratio=8.0, seed=seed)
+        mb = fv.Mesh(mesh, max_levels=L, precision=precision)
+        mb.set_state(prim)
+        batch_meshes.append(mb)
+        ma = fv.Mesh(mesh, max_levels=L, precision=precision)
+        ma.set_state(prim)
+        ma.mlp_load(th, 1, 0.0)
+        alone.append(ma)
+    b = fv.Batch(batch_meshes)
+    b.mlp_load(th, 1, 0.0)
+    b.advance(2)
+    for m, a, (n, L, seed) in zip(batch_meshes, alone, cases):
+        a.advance(2 * 2 ** (3 - L), want_time=False)
+        assert m.status() == 0 and a.status() == 0
+        assert np.array_equal(m.get_state(), a.get_state())
+    # back to the two-rarefaction guess
+    b.set_guess(fv.FV_GUESS_TWO_RAREFACTION)
+    b.advance(1)
+    with pytest.raises(fv.FvError):
+        fv.Batch([alone[0]])    # a mesh with its own learned guess is refused
