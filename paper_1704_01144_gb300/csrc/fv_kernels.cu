@@ -1,21 +1,27 @@
 // fv_kernels.cu -- the hot path of one temporally adaptive cycle (Alg. 2)
 // as CUDA kernels for sm_103a.
 //
-// Per cycle:  k_dt -> k_levels0 -> k_smooth x (L-1) -> cell/face keys ->
-//             counting sort (hist, scan, scatter) for cells and faces.
-// Per phase:  k_prim (states at the phase time, time-interpolated) ->
-//             k_grad (least-squares gradients) ->
-//             k_flux (MUSCL-minmod + exact Riemann; predictor stash or
-//                     corrector time integral + interface accumulation) ->
-//             k_update (per-cell gather over the 4 faces in fixed order, no
-//                       atomics; predictor U* or corrector U^{n+1}).
+// Per cycle:  k_dt32 (certified FP32 local steps) -> k_dt_min_exact (exact
+//             FP64 minimum) -> k_levels0_certified -> k_smooth x (L-1) ->
+//             cell/face keys -> counting sort (hist, scan, scatter) for
+//             cells and faces.
+// Per phase:  [FP64 mode: k_prim (states at the phase time, time-
+//             interpolated)] ->
+//             gradients (least squares; the FP32-flux mode computes the
+//                        primitives of the cell and its neighbours here) ->
+//             flux (MUSCL-minmod + exact Riemann, optionally the learned
+//                   starting guess; predictor stash or corrector time
+//                   integral + interface accumulation) ->
+//             update (per-cell gather over the 4 faces in fixed order, no
+//                     atomics; predictor U* or corrector U^{n+1}).
 //
 // Every phase kernel grid-strides over a range of a level-sorted list whose
 // bounds are read from device memory, so inactive levels cost a few idle
 // blocks and the launch sequence of a cycle is fixed (graph-capturable).
-// Gathered data (cell primitive/gradient records, face geometry and flux
-// records) are padded records read with 16-byte vector loads; the state is
-// structure-of-arrays.  Cells follow a Morton curve, faces their owner cell.
+// Gathered data (cell state, primitive and gradient records, face geometry
+// and flux records) are padded records read with 16-byte vector loads; the
+// FP64 state is structure-of-arrays.  Cells follow a Morton curve, faces
+// their owner cell.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -177,7 +183,6 @@ __device__ __forceinline__ void block_min_to(double local_min, unsigned long lon
   }
 }
 
-__global__ void k_init_min(unsigned long long *bits) { *bits = 0x7ff0000000000000ULL; }
 __global__ void k_init_min2(unsigned long long *a, unsigned long long *b) {
   *a = 0x7ff0000000000000ULL;
   *b = 0x7ff0000000000000ULL;
@@ -304,12 +309,6 @@ __device__ __forceinline__ int8_t level0_of(const DevMesh &d, double dtmin, int 
   int k = 0;
   while (k + 1 < d.L && ldexp(dtmin, k + 1) <= dt) ++k;
   return (int8_t)k;
-}
-
-__global__ void __launch_bounds__(256) k_levels0(DevMesh d) {
-  double dtmin = __longlong_as_double((long long)*d.dtmin_bits);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x)
-    d.lev_tmp[i] = level0_of(d, dtmin, i);
 }
 
 // the same decision from an estimate: certain when no threshold 2^k dt_min

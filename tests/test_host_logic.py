@@ -1,0 +1,59 @@
+"""Host-side logic of the benchmark and the learned-guess pipeline that runs
+without a GPU: the level-history summary (the paper's Sec. 5 shares), the
+launch count against the schedule, and the face-frame marshalling."""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+
+sys.path.insert(0, ROOT)
+
+
+class FakeMesh:
+    def __init__(self, counts, dtm):
+        self._c, self._d = np.asarray(counts, dtype=np.int32), np.asarray(dtm)
+
+    def level_history(self):
+        return self._c, self._d
+
+
+def test_level_history_summary_shares_and_cost_ratio():
+    import bench
+    # Table 1 of the paper, theta = 3: cells per level 5 / 5 / 10 / 80 (of
+    # 100), cost 2^(3-k) |Omega_k| = 40 + 20 + 20 + 80 = 160 against 800
+    counts = np.zeros((2, 8), dtype=np.int32)
+    counts[0, :4] = [5, 5, 10, 80]
+    counts[1, :4] = [10, 10, 20, 60]
+    s = bench.level_history_summary(FakeMesh(counts, [1e-3, 9e-4]), 4)
+    assert s["cycles_recorded"] == 2
+    f = s["first"]
+    assert f["cells_share"] == [0.05, 0.05, 0.1, 0.8]
+    assert f["cost_share"] == [0.25, 0.125, 0.125, 0.5]
+    assert f["global_over_adaptive_cost"] == 5.0
+    assert s["last"]["global_over_adaptive_cost"] == round(800 / (80 + 40 + 40 + 60), 4)
+    assert bench.level_history_summary(FakeMesh(np.zeros((0, 8)), []), 4) is None
+    assert bench.level_history_summary(None, 4) is None
+
+
+@pytest.mark.parametrize("L", [1, 2, 4, 6])
+def test_launch_count_matches_the_schedule(L):
+    import bench
+    from paper_1704_01144_gb300 import schedule as S
+    nph = len(S.phases(L - 1))
+    assert nph == 3 * 2 ** (L - 1) - 1
+    level_assignment = 11 + (L - 1)
+    assert bench.launches_per_cycle(L, fp32=True) == level_assignment + 3 * nph + 1
+    assert bench.launches_per_cycle(L, fp32=False) == level_assignment + 4 * nph + 1
+
+
+def test_face_frame_marshalling():
+    torch = pytest.importorskip("torch")
+    from paper_1704_01144_gb300 import learned_guess as LG
+    pairs = torch.tensor([[1.0, 0.5, 2.0, 0.5, -0.25, 1.0]], dtype=torch.float64)
+    WL, WR, n = LG.face_frame(pairs)
+    assert WL[:, 0].tolist() == [1.0, 0.5, 0.0, 0.0, 2.0]
+    assert WR[:, 0].tolist() == [0.5, -0.25, 0.0, 0.0, 1.0]
+    assert n[:, 0].tolist() == [1.0, 0.0, 0.0]
