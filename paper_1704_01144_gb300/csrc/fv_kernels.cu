@@ -1020,6 +1020,14 @@ __device__ __forceinline__ void update_item(const DevMesh &d, int stage, int lev
 // instances' range lengths)
 enum { K_PRIM = 0, K_GRAD = 1, K_FLUX = 2, K_UPD = 3 };
 
+// Programmatic dependent launch: a phase kernel waits (in hardware) for the
+// kernel before it to finish and flush before it reads anything, and lets
+// the next one be launched once its own items are done, so launch and
+// ramp-up of the next kernel overlap the drain of this one.  Without a
+// programmatic predecessor the wait returns at once.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ void kind_range(const DevMesh &d, const PhaseDesc &p, int kind, int &beg,
                                            int &end) {
   if (kind == K_FLUX) {
@@ -1058,10 +1066,12 @@ __device__ __forceinline__ void run_item(const DevMesh &d, const PhaseDesc &p, c
 
 template <int KIND, typename T, bool G14>
 __global__ void KBOUNDS(KIND, T) k_phase1(DevMesh d, const __grid_constant__ PhaseDesc p, GasT<T> G) {
+  pdl_wait();
   int beg, end;
   kind_range(d, p, KIND, beg, end);
   for (int idx = beg + blockIdx.x * blockDim.x + threadIdx.x; idx < end; idx += gridDim.x * blockDim.x)
     run_item<KIND, T, G14>(d, p, G, idx);
+  pdl_trigger();
 }
 
 // flux with the learned guess: the packed network staged in shared memory,
@@ -1073,7 +1083,8 @@ template <typename T, bool G14>
 __global__ void __launch_bounds__(128, FV_MLP_FLUX_BLOCKS) k_flux_mlp1(DevMesh d, const __grid_constant__ PhaseDesc p,
                                                       GasT<T> G) {
   __shared__ __align__(16) uint32_t sw[PK_WORDS];
-  mlp_stage(sw, d.mlp);
+  mlp_stage(sw, d.mlp);  // the weights do not depend on the previous kernel
+  pdl_wait();
   int beg, end;
   kind_range(d, p, K_FLUX, beg, end);
   const int lane = threadIdx.x & 31;
@@ -1082,6 +1093,7 @@ __global__ void __launch_bounds__(128, FV_MLP_FLUX_BLOCKS) k_flux_mlp1(DevMesh d
     const int idx = base + lane;
     flux_item<T, G14, true>(d, G, p.stage, p.level, idx < end ? idx : -1, sw);
   }
+  pdl_trigger();
 }
 
 // a batch's flattened work index: the first warp of the block writes the
@@ -1144,6 +1156,7 @@ __global__ void __launch_bounds__(128, FV_MLP_FLUX_BLOCKS) k_flux_mlpN(const Dev
   __shared__ int pref[FV_MAXB + 1];
   __shared__ int base[FV_MAXB];
   mlp_stage(sw, mlp);
+  pdl_wait();
   batch_prefix(ms, ps, n, K_FLUX, pref, base);
   const int total = pref[FV_MAXB];
   const int lane = threadIdx.x & 31;
@@ -1156,6 +1169,7 @@ __global__ void __launch_bounds__(128, FV_MLP_FLUX_BLOCKS) k_flux_mlpN(const Dev
     const int idx = ok ? base[lo] + (g - pref[lo]) : -1;
     flux_item<T, G14, true>(ms[lo], G, ps[lo].stage, ps[lo].level, idx, sw);
   }
+  pdl_trigger();
 }
 
 template <int KIND, typename T, bool G14>
@@ -1163,12 +1177,14 @@ __global__ void KBOUNDS(KIND, T) k_phaseN(const DevMesh *__restrict__ ms, const 
                                           int n, GasT<T> G) {
   __shared__ int pref[FV_MAXB + 1];
   __shared__ int base[FV_MAXB];
+  pdl_wait();
   batch_prefix(ms, ps, n, KIND, pref, base);
   const int total = pref[FV_MAXB];
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
     const int lo = batch_instance(pref, n, g);
     run_item<KIND, T, G14>(ms[lo], ps[lo], G, base[lo] + (g - pref[lo]));
   }
+  pdl_trigger();
 }
 
 // ---- persistent cycle: every phase of a cycle in one cooperative launch,
@@ -1608,6 +1624,21 @@ int launch_assign_levels(const DevMesh &d, int L, int *cnt_scratch, ProfHook *ph
   return FV_OK;
 }
 
+// launch with a programmatic dependency on the previous kernel of the stream
+template <typename... KArgs, typename... Args>
+static void launch_pdl(void (*kernel)(KArgs...), int grid, int block, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.stream = s;
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr.val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 template <typename T, bool G14>
 static void phase1_all(const DevMesh &d, const PhaseDesc &pd, const GasT<T> &G, const LaunchCfg &lc,
                        ProfHook *ph, cudaStream_t s) {
@@ -1615,19 +1646,19 @@ static void phase1_all(const DevMesh &d, const PhaseDesc &pd, const GasT<T> &G, 
   const int g2 = grid_for(d.F, 128, lc.per_sm[2]), g3 = grid_for(d.N, 256, lc.per_sm[3]);
   if (sizeof(T) == 8) {  // FP32-flux mode: primitives computed inside the gradient kernel
     ProfScope sc(ph, FV_PROF_PRIM, s);
-    k_phase1<K_PRIM, T, G14><<<g0, 256, 0, s>>>(d, pd, G);
+    launch_pdl(k_phase1<K_PRIM, T, G14>, g0, 256, s, d, pd, G);
   }
-  { ProfScope sc(ph, FV_PROF_GRAD, s); k_phase1<K_GRAD, T, G14><<<g1, 256, 0, s>>>(d, pd, G); }
+  { ProfScope sc(ph, FV_PROF_GRAD, s); launch_pdl(k_phase1<K_GRAD, T, G14>, g1, 256, s, d, pd, G); }
   {
     ProfScope sc(ph, FV_PROF_FLUX, s);
     if (d.guess == FV_GUESS_MLP)
-      k_flux_mlp1<T, G14><<<grid_for(d.F, 128, lc.per_sm[2] < FV_MLP_FLUX_BLOCKS ? lc.per_sm[2]
-                                                                                  : FV_MLP_FLUX_BLOCKS),
-                            128, 0, s>>>(d, pd, G);
+      launch_pdl(k_flux_mlp1<T, G14>,
+                 grid_for(d.F, 128, lc.per_sm[2] < FV_MLP_FLUX_BLOCKS ? lc.per_sm[2] : FV_MLP_FLUX_BLOCKS),
+                 128, s, d, pd, G);
     else
-      k_phase1<K_FLUX, T, G14><<<g2, 128, 0, s>>>(d, pd, G);
+      launch_pdl(k_phase1<K_FLUX, T, G14>, g2, 128, s, d, pd, G);
   }
-  { ProfScope sc(ph, FV_PROF_UPDATE, s); k_phase1<K_UPD, T, G14><<<g3, 256, 0, s>>>(d, pd, G); }
+  { ProfScope sc(ph, FV_PROF_UPDATE, s); launch_pdl(k_phase1<K_UPD, T, G14>, g3, 256, s, d, pd, G); }
 }
 
 static GasT<double> gas64(const DevMesh &d) { return GasT<double>::make(d.gamma, d.tol, d.maxit); }
@@ -1669,15 +1700,15 @@ static void phaseN_all(const DevMesh *ms, const PhaseDesc *pds, int n, const Gas
                        cudaStream_t s) {
   const int g0 = grid_for(cells, 256, lc.per_sm[0]), g1 = grid_for(cells, 256, lc.per_sm[1]);
   const int g2 = grid_for(faces, 128, lc.per_sm[2]), g3 = grid_for(cells, 256, lc.per_sm[3]);
-  if (sizeof(T) == 8) k_phaseN<K_PRIM, T, G14><<<g0, 256, 0, s>>>(ms, pds, n, G);
-  k_phaseN<K_GRAD, T, G14><<<g1, 256, 0, s>>>(ms, pds, n, G);
+  if (sizeof(T) == 8) launch_pdl(k_phaseN<K_PRIM, T, G14>, g0, 256, s, ms, pds, n, G);
+  launch_pdl(k_phaseN<K_GRAD, T, G14>, g1, 256, s, ms, pds, n, G);
   if (mlp)
-    k_flux_mlpN<T, G14><<<grid_for(faces, 128, lc.per_sm[2] < FV_MLP_FLUX_BLOCKS ? lc.per_sm[2]
-                                                                                  : FV_MLP_FLUX_BLOCKS),
-                          128, 0, s>>>(ms, pds, n, G, mlp);
+    launch_pdl(k_flux_mlpN<T, G14>,
+               grid_for(faces, 128, lc.per_sm[2] < FV_MLP_FLUX_BLOCKS ? lc.per_sm[2] : FV_MLP_FLUX_BLOCKS),
+               128, s, ms, pds, n, G, mlp);
   else
-    k_phaseN<K_FLUX, T, G14><<<g2, 128, 0, s>>>(ms, pds, n, G);
-  k_phaseN<K_UPD, T, G14><<<g3, 256, 0, s>>>(ms, pds, n, G);
+    launch_pdl(k_phaseN<K_FLUX, T, G14>, g2, 128, s, ms, pds, n, G);
+  launch_pdl(k_phaseN<K_UPD, T, G14>, g3, 256, s, ms, pds, n, G);
 }
 
 int launch_phase_multi(const DevMesh *ms, const PhaseDesc *pds, int n, const DevMesh &d0,
