@@ -18,7 +18,7 @@
  *     levels taken at the right time by linear interpolation in time
  *     ("repositioning / interpolation"); a coarse cell takes the time
  *     integral of the fine-side fluxes across a level interface.
- * Scheme choices the paper leaves open (all stated in the design doc):
+ * Scheme choices the paper leaves open (the same on the CUDA path):
  *   least-squares gradients of primitives, MUSCL reconstruction with the
  *   minmod limiter, the exact Godunov Riemann solver (Toro, "Riemann Solvers
  *   and Numerical Methods for Fluid Dynamics", ch. 4: pressure functions,

@@ -5,8 +5,8 @@ TEST INFRASTRUCTURE: only ``tests/``, ``__graft_entry__.smoke()`` and the
 no code with the CUDA path; both only consume the seeded inputs of
 ``paper_1704_01144_gb300.inputs``.
 
-Parity status of each function (what pins it) is listed in the oracle
-header and in DESIGN.md.
+What pins each function is listed in the headers of fv_oracle.c and
+mlp_oracle.c.
 """
 from __future__ import annotations
 
