@@ -116,7 +116,7 @@ int fv_set_state(fv_mesh *m, const double *prim_soa, int on_device, void *stream
 int fv_get_state(fv_mesh *m, double *cons_soa, int on_device, void *stream);
 
 /*
- * Alg. 2 lines 1-2: computes every cell's local explicit time step
+ * Alg. 2 (time steps, then levels): computes every cell's local explicit time step
  * dt_i = 2 CFL V_i / sum_f A_f (|u_i . n_f| + c_i), dt_min = min_i dt_i, the
  * level k_i = max{k <= L-1 : 2^k dt_min <= dt_i}, then lowers levels until
  * neighbours differ by at most one (Sec. 2.2), and builds the level-sorted
@@ -128,7 +128,7 @@ int fv_get_state(fv_mesh *m, double *cons_soa, int on_device, void *stream);
 int fv_assign_levels(fv_mesh *m, double *dt_min_out, int32_t *level_counts_out, void *stream);
 
 /* Local explicit time step dt_i of every cell (caller's order) computed by
- * the last level assignment (Alg. 2 line 1): host dt_out[n_tets].  The
+ * the last level assignment (the time-step computation of Alg. 2): host dt_out[n_tets].  The
  * assignment evaluates dt_i in FP32 with a certified relative bound (at
  * most 2^-12, typically ~3e-6) and in FP64 wherever the minimum or a level
  * decision needs the exact value: those entries, dt_min and every level are
@@ -175,7 +175,7 @@ int fv_residual_level(fv_mesh *m, int level, int stage, double *R_soa_dev, void 
 
 /*
  * Runs the next n_phases phases of the current cycle.  The phases of one
- * cycle, for s = 1..2^(L-1): B(s) starts levels 0..tau(s) (Alg. 2 lines 5-9:
+ * cycle, for s = 1..2^(L-1): B(s) starts levels 0..tau(s) (the subiteration loop of Alg. 2:
  * predictor fluxes on faces of level <= tau, U* of those cells), then
  * E(s,k) for k = 0,1,.. while s mod 2^k == 0 (corrector fluxes on faces of
  * level k, flux time integrals, U^{n+1} of level-k cells).  3 * 2^(L-1) - 1

@@ -10,9 +10,9 @@
  * What it computes (paper Sec. 2.2, Eq. 1 and Algorithm 2):
  *   - Eq. 1 with S = 0 and inviscid Euler fluxes (gamma from the config):
  *       d/dt (V_i U_i) = - sum_f sigma_f F_f A_f
- *   - Alg. 2 line 1: a local explicit time step per cell; Delta t = min.
- *   - Alg. 2 line 2: level k_i with dt_k = 2^k Delta t, neighbours within 1.
- *   - Alg. 2 lines 4-9: 2^theta subiterations; level k begins every 2^k.
+ *   - Alg. 2, time steps: a local explicit time step per cell; Delta t = min.
+ *   - Alg. 2, levels: level k_i with dt_k = 2^k Delta t, neighbours within 1.
+ *   - Alg. 2, subiterations: 2^theta subiterations; level k begins every 2^k.
  *   - Predictor / corrector ("extensive prediction / correction"): one Heun
  *     (SSP-RK2) step per level step, fluxes in flux form; neighbours of other
  *     levels taken at the right time by linear interpolation in time
@@ -634,7 +634,7 @@ static double local_dt(const orc *o, int64_t i) {
   return (((2.0 * o->cfl) * o->vol[i]) * r) / S;
 }
 
-/* Alg. 2 lines 1-2: Delta t = min_i dt_i; level k_i = the largest k in
+/* Alg. 2, time steps and levels: Delta t = min_i dt_i; level k_i = the largest k in
  * [0, L-1] with 2^k Delta t <= dt_i; then lower levels until every pair of
  * neighbours differs by at most one (repeated until nothing changes). */
 int orc_assign_levels(orc *o, double *dtmin_out, int8_t *levels_out, int32_t *counts_out) {
@@ -828,7 +828,7 @@ static phase_t phase_at(int theta, int idx) {
   phase_t ph = {0, 0, 0};
   int nsub = 1 << theta;
   for (int s = 1; s <= nsub; ++s) {
-    /* Alg. 2 lines 5-9: tau = largest tmp <= theta with (s-1) mod 2^tmp == 0 */
+    /* Alg. 2, subiteration s: tau = largest tmp <= theta with (s-1) mod 2^tmp == 0 */
     int tau = 0;
     for (int tmp = 1; tmp <= theta; ++tmp)
       if (((s - 1) % (1 << tmp)) == 0) tau = tmp;

@@ -1,7 +1,7 @@
 // fv_api.cu -- the C ABI of include/fv.h: mesh lifecycle, state transfer,
 // level assignment and the phase driver of Algorithm 2.
 //
-// The schedule of a cycle with theta = L - 1 (Alg. 2 lines 4-9) is a fixed
+// The schedule of a cycle with theta = L - 1 (the subiteration loop of Alg. 2) is a fixed
 // list of 3 * 2^theta - 1 phases:  for s = 1..2^theta,  B(s) starts the levels
 // 0..tau(s) at T = s - 1, then E(s, k) ends the step of level k at T = s for
 // k = 0, 1, ... while s mod 2^k == 0 (finest first).  The host keeps, per

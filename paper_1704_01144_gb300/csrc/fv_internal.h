@@ -137,7 +137,7 @@ struct LaunchCfg {
 };
 inline LaunchCfg default_launch() { return LaunchCfg{{8, 8, 16, 8}}; }
 
-// ---- host schedule of one cycle (Alg. 2 lines 4-9) -------------------
+// ---- host schedule of one cycle (the subiteration loop of Alg. 2) ----
 // kind 0: begin levels 0..level at T; kind 1: end the step of `level` at T
 struct SchedPhase {
   int kind;
