@@ -78,12 +78,38 @@ KERNEL_SOURCES = ["paper_1704_01144_gb300/csrc/fv_kernels.cu",
                   "paper_1704_01144_gb300/csrc/fv_mlp.cuh"]
 
 
+def strip_comments(src: str) -> str:
+    """C/C++ source without its // and /* */ comments and trailing blanks:
+    what the compiler sees, so that editing a comment keeps the hash."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            out.append(" ")
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    return "\n".join(ln.rstrip() for ln in "".join(out).split("\n") if ln.strip())
+
+
 def kernel_source_hash() -> str:
+    """Hash of the kernel sources with comments stripped."""
     import hashlib
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, f), encoding="utf-8") as fh:
+            h.update(strip_comments(fh.read()).encode())
     return h.hexdigest()[:16]
 
 
