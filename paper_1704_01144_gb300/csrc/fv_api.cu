@@ -281,6 +281,7 @@ int fv_mesh_load(const double *xyz, int64_t n_nodes, const int64_t *tets, int64_
   AL(d.lev_tmp, N);
   AL(d.flev, F);
   AL(d.ckey, N);
+  AL(d.cmask, N);
   AL(d.fkey, F);
   AL(d.cl, N);
   AL(d.fl, F);

@@ -82,6 +82,8 @@ struct DevMesh {
   // levels and sorted lists
   int8_t *lev, *lev_tmp, *flev;
   uint8_t *ckey, *fkey;
+  uint8_t *cmask;         // per cell: bit j set when the neighbour across face j is
+                          // one level finer (that face's integral accumulates)
   int *cl, *fl, *coff, *foff;
   int *sort_cnt;          // bucket x block counts, scratch of the level sort
   double *dt;             // local time steps (see k_dt32: exact where a decision needs it)

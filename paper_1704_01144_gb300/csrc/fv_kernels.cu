@@ -354,25 +354,23 @@ __global__ void __launch_bounds__(256) k_smooth(DevMesh d, const int8_t *__restr
 
 // cell sort key: 2 level + (1 unless a neighbour is one level finer), so the
 // cells a phase touches are contiguous: levels <= tau followed by the
-// level-(tau+1) cells next to level tau
-__device__ __forceinline__ uint8_t cell_key_of(const DevMesh &d, int i) {
-  int k = d.lev[i];
-  int finer = 0;
+// level-(tau+1) cells next to level tau.  Also stored: the mask of the faces
+// whose neighbour is finer (the corrector update takes their accumulated
+// integrals) and, in the FP32-flux mode, the cycle's level in the cell's FP32
+// state record (read with the state, so the phase kernels need no separate
+// level lookup).
+__device__ __forceinline__ void cell_key_store(const DevMesh &d, int i) {
+  const int k = d.lev[i];
+  unsigned finer = 0;
   int4 nb4 = d.cnb4[i];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     int nb = nbr_of(nb4, j);
-    if (nb >= 0 && d.lev[nb] < k) finer = 1;
+    if (nb >= 0 && d.lev[nb] < k) finer |= 1u << j;
   }
-  return (uint8_t)(2 * k + (finer ? 0 : 1));
-}
-
-// the cell's sort key; in the FP32-flux mode the cycle's level is also
-// stamped into the cell's FP32 state record (read with the state, so the
-// phase kernels need no separate level lookup)
-__device__ __forceinline__ void cell_key_store(const DevMesh &d, int i) {
-  d.ckey[i] = cell_key_of(d, i);
-  if (d.Un32) d.Un32[(size_t)i * REC_U32 + 5] = (float)d.lev[i];
+  d.ckey[i] = (uint8_t)(2 * k + (finer ? 0 : 1));
+  d.cmask[i] = (uint8_t)finer;
+  if (d.Un32) d.Un32[(size_t)i * REC_U32 + 5] = (float)k;
 }
 
 __global__ void __launch_bounds__(256) k_cell_keys(DevMesh d) {
@@ -608,8 +606,18 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort_scatter_multi(MultiTiles 
 }
 
 // ------------------------------------------------------ state at a time --
-__device__ __forceinline__ void load_state(const DevMesh &d, const PhaseLevels &pl, int c,
-                                           double U[5]) {
+// whether some level of the phase reads its predicted (or interpolated)
+// state
+__device__ __forceinline__ bool reads_predicted(const PhaseLevels &pl) {
+  bool any = false;
+#pragma unroll
+  for (int j = 0; j < FV_MAXL; ++j) any |= pl.mode[j] != 0;
+  return any;
+}
+
+// the state of cell c at the phase time (FP64 mode); returns its level
+__device__ __forceinline__ int load_state(const DevMesh &d, const PhaseLevels &pl, int c,
+                                          double U[5], bool = false) {
   const size_t N = d.N;
   int k = d.lev[c];
   int mode = pl.mode[k];
@@ -627,22 +635,26 @@ __device__ __forceinline__ void load_state(const DevMesh &d, const PhaseLevels &
       U[q] = a + w * (b - a);
     }
   }
+  return k;
 }
 
 // FP32-flux mode: the state at the phase time from the FP32 records of U^n
-// and of the predicted state; the record of U^n carries the cell's level
-__device__ __forceinline__ void load_state(const DevMesh &d, const PhaseLevels &pl, int c,
-                                           float U[5]) {
-  float a[REC_U32];
+// and of the predicted state; the record of U^n carries the cell's level.
+// With `both` (the phase reads some level's predicted state) the predicted
+// record is loaded together with U^n rather than after its level is known.
+// Returns the level.
+__device__ __forceinline__ int load_state(const DevMesh &d, const PhaseLevels &pl, int c,
+                                          float U[5], bool both = false) {
+  float a[REC_U32], b[REC_U32];
   ldrec<REC_U32>(d.Un32 + (size_t)c * REC_U32, a);
+  if (both) ldrec<REC_U32>(d.Us32 + (size_t)c * REC_U32, b);
   const int k = (int)a[5];
   const int mode = pl.mode[k];
   if (mode == 0) {
 #pragma unroll
     for (int q = 0; q < 5; ++q) U[q] = a[q];
   } else {
-    float b[REC_U32];
-    ldrec<REC_U32>(d.Us32 + (size_t)c * REC_U32, b);
+    if (!both) ldrec<REC_U32>(d.Us32 + (size_t)c * REC_U32, b);
     if (mode == 1) {
 #pragma unroll
       for (int q = 0; q < 5; ++q) U[q] = b[q];
@@ -652,6 +664,7 @@ __device__ __forceinline__ void load_state(const DevMesh &d, const PhaseLevels &
       for (int q = 0; q < 5; ++q) U[q] = a[q] + w * (b[q] - a[q]);
     }
   }
+  return k;
 }
 
 __device__ __forceinline__ void to_prim(const double U[5], double gm1, double W[5]) {
@@ -689,8 +702,9 @@ __device__ __forceinline__ void prim_item(const DevMesh &d, const PhaseLevels &p
 // FP64 mode: from the W records the primitives kernel wrote.  FP32-flux
 // mode (INLINE_W): the primitives of the cell and of its neighbours are
 // computed here from their states at the phase time, and the cell's own
-// primitives are stored in its W record for the flux kernel; there is no
-// separate primitives kernel.
+// primitives are stored in its W record for the flux kernel, with its level
+// in slot 5; there is no separate primitives kernel.  Both records are
+// stored after every load.
 template <typename T>
 __device__ __forceinline__ void grad_cell(const DevMesh &d, const PhaseLevels &pl, int i) {
   constexpr bool INLINE_W = sizeof(T) == 4;
@@ -698,14 +712,15 @@ __device__ __forceinline__ void grad_cell(const DevMesh &d, const PhaseLevels &p
   const T *lsw = lswrec(d, T(0));
   const T *fgeo = georec(d, T(0));
   const double gm1 = d.gamma - 1.0;
+  const bool both = INLINE_W && reads_predicted(pl);
   T Wi[REC_W], g[REC_G], w[REC_LSW];
   if (INLINE_W) {
     T U[5];
-    load_state(d, pl, i, U);
+    const int k = load_state(d, pl, i, U, both);
     to_prim(U, gm1, Wi);
+    Wi[5] = T(k);
 #pragma unroll
-    for (int q = 5; q < REC_W; ++q) Wi[q] = T(0);
-    strec<REC_W>((T *)d.W + (size_t)i * REC_W, Wi);
+    for (int q = 6; q < REC_W; ++q) Wi[q] = T(0);
   } else {
     ldrec<REC_W>(W + (size_t)i * REC_W, Wi);
   }
@@ -720,7 +735,7 @@ __device__ __forceinline__ void grad_cell(const DevMesh &d, const PhaseLevels &p
     if (nb >= 0) {
       if (INLINE_W) {
         T U[5];
-        load_state(d, pl, nb, U);
+        load_state(d, pl, nb, U, both);
         to_prim(U, gm1, Wn);
       } else {
         ldrec<REC_W>(W + (size_t)nb * REC_W, Wn);
@@ -746,6 +761,7 @@ __device__ __forceinline__ void grad_cell(const DevMesh &d, const PhaseLevels &p
     }
   }
   strec<REC_G>(grec_w(d, T(0)) + (size_t)i * REC_G, g);
+  if (INLINE_W) strec<REC_W>((T *)d.W + (size_t)i * REC_W, Wi);
 }
 
 template <typename T>
@@ -916,7 +932,11 @@ __device__ __forceinline__ void flux_item(const DevMesh &d, const GasT<T> &G, in
   } else {
     double h = 0.5 * ldexp(__longlong_as_double((long long)*d.dtmin_bits), level);
     int2 fc = d.fcell[f];
-    bool iface = fc.y >= 0 && d.lev[fc.x] != d.lev[fc.y];
+    // the FP32-flux mode has the cells' levels in slot 5 of the W records
+    // the face states were just read from
+    const T *Wr = (const T *)d.W;
+    bool iface = fc.y >= 0 && (f32 ? Wr[(size_t)fc.x * REC_W + 5] != Wr[(size_t)fc.y * REC_W + 5]
+                                   : d.lev[fc.x] != d.lev[fc.y]);
     double phi[REC_FA];
     if (f32) {
       float a[REC_FA32];
@@ -976,41 +996,54 @@ __device__ __forceinline__ void update_item(const DevMesh &d, int stage, int lev
     strec<REC_U32>(d.Us32 + (size_t)i * REC_U32, a);
     return;
   }
+  // every load comes before the first store (the reset of the accumulated
+  // integrals is last), so the four face loads and the state loads overlap
+  // instead of waiting on one another behind possibly aliasing stores.  At
+  // the end of a step, faces to finer neighbours (cmask) contribute their
+  // accumulated integrals.
+  const unsigned finer = stage == 2 ? d.cmask[i] : 0u;
+  bool reset[4];
+  const double *src[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    reset[j] = (finer >> j) & 1u;
+    src[j] = (reset[j] ? d.ACC : d.FA) + (size_t)nbr_of(cf, j) * REC_FA;
+  }
   double S[5];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    int f = nbr_of(cf, j);
     bool neg = !((own >> j) & 1u);
     double v[REC_FA];
-    if (stage == 2 && d.flev[f] != level) {
-      double *a = d.ACC + (size_t)f * REC_FA;
-      ldrec<REC_FA>(a, v);
-      const double z[REC_FA] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-      strec<REC_FA>(a, z);
-    } else {
-      ldrec<REC_FA>(d.FA + (size_t)f * REC_FA, v);
-    }
+    ldrec<REC_FA>(src[j], v);
 #pragma unroll
     for (int c = 0; c < 5; ++c) S[c] = j == 0 ? flip(v[c], neg) : S[c] + flip(v[c], neg);
   }
-  double iV = d.ivol[i];
+  const double iV = d.ivol[i];
+  double u[5];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) u[c] = d.Un[c * N + i];
   if (stage == 1) {
     double cdt = -ldexp(dtmin, (int)d.lev[i]) * iV;
 #pragma unroll
-    for (int c = 0; c < 5; ++c) d.Us[c * N + i] = d.Un[c * N + i] + cdt * S[c];
+    for (int c = 0; c < 5; ++c) d.Us[c * N + i] = u[c] + cdt * S[c];
   } else {
     float r[REC_U32];
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
-      double u = d.Un[c * N + i] - iV * S[c];
-      d.Un[c * N + i] = u;
-      r[c] = (float)u;
+      u[c] = u[c] - iV * S[c];
+      r[c] = (float)u[c];
     }
+#pragma unroll
+    for (int c = 0; c < 5; ++c) d.Un[c * N + i] = u[c];
     if (F32) {
       r[5] = (float)level;  // the cell ends the step of its own level
       r[6] = r[7] = 0.0f;
       strec<REC_U32>(d.Un32 + (size_t)i * REC_U32, r);
     }
+    const double z[REC_FA] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (reset[j]) strec<REC_FA>(const_cast<double *>(src[j]), z);
   }
 }
 
@@ -1056,12 +1089,12 @@ __device__ __forceinline__ void run_item(const DevMesh &d, const PhaseDesc &p, c
 
 // flux: 128 threads, 8 blocks per SM in FP32 (64 registers), 4 in FP64;
 // FP64 gradients need ~96 registers (2 blocks of 256); the update (a gather
-// waiting on memory) fits in 40 registers for 6 resident blocks of 256; the
-// rest fit in 64
+// with all of its loads in flight at once) fits in 48 registers for 5
+// resident blocks of 256; the rest fit in 64
 #define KBOUNDS(KIND, T)                                                                      \
   __launch_bounds__((KIND) == K_FLUX ? 128 : 256,                                             \
                     (KIND) == K_FLUX ? (sizeof(T) == 4 ? 8 : 4)                               \
-                    : (KIND) == K_UPD ? 6                                                     \
+                    : (KIND) == K_UPD ? 5                                                     \
                                       : ((KIND) == K_GRAD && sizeof(T) == 8 ? 2 : 4))
 
 template <int KIND, typename T, bool G14>
