@@ -250,6 +250,27 @@ int fv_use_graph(fv_mesh *m, int enable);
 int fv_set_launch(fv_mesh *m, const int32_t per_sm[4]);
 int fv_get_launch(fv_mesh *m, int32_t per_sm[4]);
 
+/*
+ * Gradient-flux fusion for latency-bound phases (FP32-flux mode with the
+ * two-rarefaction guess; other modes ignore it): a phase whose face list
+ * has at most max_faces faces computes both cells' least-squares gradients
+ * inside its flux kernel (a cell's gradient once per face of the cell)
+ * rather than in a gradient kernel of its own -- one dependent launch and
+ * one chain of gathers less, for more arithmetic per face.  The choice is
+ * taken on the device for every phase from the face count of the current
+ * level assignment, so a captured cycle follows the level distribution.
+ * Both ways compute the same operations on the same values.  0 turns the
+ * fusion off and is the default (FV_FUSE_FACES_DEFAULT): on a GB300 a
+ * dependent launch in a CUDA graph costs about 2 us while the recomputed
+ * gradients cost more, so fusion has measured slower for every threshold.
+ * A nonzero threshold adds one launch per phase.  Setting it drops a
+ * captured graph.  Errors: FV_ERR_INVALID_ARG (NULL argument, negative
+ * count, inside a cycle or a batch).
+ */
+#define FV_FUSE_FACES_DEFAULT 0
+int fv_set_fusion(fv_mesh *m, int64_t max_faces);
+int fv_get_fusion(fv_mesh *m, int64_t *max_faces_out);
+
 /* kernel classes of the profiler */
 #define FV_PROF_LEVELS 0 /* level assignment: dt, levels, sorts */
 #define FV_PROF_PRIM 1   /* primitives at the phase time */

@@ -231,6 +231,7 @@ int fv_mesh_load(const double *xyz, int64_t n_nodes, const int64_t *tets, int64_
   d.tol = cfg->newton_tol;
   d.maxit = cfg->newton_max_iter;
   d.precision = cfg->precision;
+  d.fuse_faces = FV_FUSE_FACES_DEFAULT;
   const bool f32 = cfg->precision == FV_FP32_FLUX;
   const int nblk_c = (int)((N + 1023) / 1024), nblk_f = (int)((F + 1023) / 1024);
   size_t cnt_size = (size_t)16 * (nblk_c > nblk_f ? nblk_c : nblk_f) + 16;
@@ -288,6 +289,7 @@ int fv_mesh_load(const double *xyz, int64_t n_nodes, const int64_t *tets, int64_
   AL(d.coff, 2 * FV_MAXL + 1);
   AL(d.foff, FV_MAXL + 1);
   AL(d.dt, N);
+  AL(d.dt32, N);
   AL(d.dteps, N);
   AL(d.dthi_bits, 1);
   AL(d.dtmin_bits, 1);
@@ -453,10 +455,14 @@ int fv_get_local_dt(fv_mesh *m, double *dt_out) {
   CK(cudaDeviceSynchronize());
   const size_t N = m->d.N;
   std::vector<double> dt(N);
+  std::vector<float> est(N), eps(N);
   std::vector<int> n2o(N);
   CK(cudaMemcpy(dt.data(), m->d.dt, N * sizeof(double), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(est.data(), m->d.dt32, N * sizeof(float), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(eps.data(), m->d.dteps, N * sizeof(float), cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(n2o.data(), m->new2old_dev, N * sizeof(int), cudaMemcpyDeviceToHost));
-  for (size_t i = 0; i < N; ++i) dt_out[n2o[i]] = dt[i];
+  // the exact value where the assignment needed it, else the FP32 estimate
+  for (size_t i = 0; i < N; ++i) dt_out[n2o[i]] = eps[i] > 0.0f ? (double)est[i] : dt[i];
   return FV_OK;
 }
 
@@ -596,6 +602,24 @@ int fv_set_launch(fv_mesh *m, const int32_t per_sm[4]) {
 int fv_get_launch(fv_mesh *m, int32_t per_sm[4]) {
   if (!m || !per_sm) return fail(FV_ERR_INVALID_ARG, "fv_get_launch: NULL argument");
   for (int k = 0; k < 4; ++k) per_sm[k] = m->launch.per_sm[k];
+  return FV_OK;
+}
+
+int fv_set_fusion(fv_mesh *m, int64_t max_faces) {
+  if (!m || max_faces < 0) return fail(FV_ERR_INVALID_ARG, "fv_set_fusion: bad argument");
+  if (m->in_batch || (m->in_cycle && m->next_phase > 0))
+    return fail(FV_ERR_INVALID_ARG, "fv_set_fusion: mesh is inside a cycle or a batch");
+  m->d.fuse_faces = (int)(max_faces < FV_MAX_ITEMS ? max_faces : FV_MAX_ITEMS);
+  if (m->cycle_graph) {
+    cudaGraphExecDestroy(m->cycle_graph);
+    m->cycle_graph = nullptr;
+  }
+  return FV_OK;
+}
+
+int fv_get_fusion(fv_mesh *m, int64_t *max_faces_out) {
+  if (!m || !max_faces_out) return fail(FV_ERR_INVALID_ARG, "fv_get_fusion: NULL argument");
+  *max_faces_out = m->d.fuse_faces;
   return FV_OK;
 }
 

@@ -86,8 +86,9 @@ struct DevMesh {
                           // one level finer (that face's integral accumulates)
   int *cl, *fl, *coff, *foff;
   int *sort_cnt;          // bucket x block counts, scratch of the level sort
-  double *dt;             // local time steps (see k_dt32: exact where a decision needs it)
-  float *dteps;           // relative bound of dt's FP32 estimate (0: dt is exact)
+  double *dt;             // exact local time steps (where dteps = 0)
+  float *dt32;            // FP32 estimates of the local time steps (where dteps > 0)
+  float *dteps;           // relative bound of the estimate (0: dt holds the exact value)
   unsigned long long *dthi_bits;  // smallest upper bound of the estimates (bit pattern)
   unsigned long long *dtmin_bits;  // bit pattern of dt_min (positive double)
   double *tdev;           // physical time
@@ -102,6 +103,9 @@ struct DevMesh {
   // FV_GUESS_MLP with the packed network weights (device, PK_WORDS words)
   int guess;
   const uint32_t *mlp;
+  // FP32-flux mode: phases with at most this many faces fuse their gradients
+  // into the flux kernel (0: never)
+  int fuse_faces;
   // physics
   double gamma, cfl, tol;
   int maxit;

@@ -200,7 +200,10 @@ __global__ void k_init_min2(unsigned long long *a, unsigned long long *b) {
 // and every level decision an estimate cannot settle are then taken on exact
 // FP64 values, so levels and dt_min are bit for bit those of the all-FP64
 // evaluation.
-__device__ __forceinline__ void local_dt32(const DevMesh &d, int i, double &dt, float &eps) {
+// Returns true with the estimate val and its bound eps, or false after the
+// exact value was computed (local_dt_of: stored in d.dt[i], returned in
+// exact).
+__device__ __forceinline__ bool local_dt32(const DevMesh &d, int i, float &val, float &eps, double &exact) {
   const float u = 5.9604645e-8f;  // 2^-24
   float r, mx, my, mz, E, iv;
   if (d.Un32) {
@@ -220,9 +223,8 @@ __device__ __forceinline__ void local_dt32(const DevMesh &d, int i, double &dt, 
   const float P = E - ke;
   const float eP = u * (E + 8.0f * ke + P);              // |P~ - P| to first order
   if (!(r > 0.0f) || !(P > 4.0f * eP) || !isfinite(E + mm)) {
-    dt = local_dt_of(d, i);
-    eps = 0.0f;
-    return;
+    exact = local_dt_of(d, i);
+    return false;
   }
   const float relP = eP / (P - eP);
   const float p = gm1 * P;
@@ -249,88 +251,117 @@ __device__ __forceinline__ void local_dt32(const DevMesh &d, int i, double &dt, 
     S += A * t;
     eS += A * (6.0f * u * amn + relc * rc + 4.0f * u * t);
   }
-  const float val = 2.0f * (float)d.cfl * r / (iv * S);
+  val = 2.0f * (float)d.cfl * r / (iv * S);
   float e = eS / S + 3.0f * u + 10.0f * u;
   e = 1.25f * e + 16.0f * u + 1e-13f;
   if (!(e <= 2.44140625e-4f) || !isfinite(val) || !(val > 0.0f)) {  // 2^-12
-    dt = local_dt_of(d, i);
-    eps = 0.0f;
-    return;
+    exact = local_dt_of(d, i);
+    return false;
   }
-  dt = (double)val;
   eps = e;
-  d.dt[i] = dt;
+  return true;
 }
 
-// pass 1 of one cell: its estimate; returns its upper bound
-__device__ __forceinline__ double dt32_cell(const DevMesh &d, int i) {
-  double dt;
-  float e;
-  local_dt32(d, i, dt, e);
-  d.dteps[i] = e;
-  return dt * (1.0 + (double)e);
+// The passes below compare in FP32 with directed rounding, which is exact
+// for these questions: lo = val (1 - e) rounded down and hi = val (1 + e)
+// rounded up enclose the cell's exact step, and for a float x and a double t,
+// t <= x exactly when t rounded up to FP32 is <= x (x <= t when x <= t
+// rounded down).  FP64 arithmetic -- a small fraction of the SM's FP32 rate
+// on this GPU -- is left to the cells an interval cannot settle.
+
+// pass 1 of one cell: its estimate (dt32, dteps) or its exact value (dt,
+// dteps = 0); lowers the FP32 upper bound hi32 or the exact minimum hi64
+__device__ __forceinline__ void dt32_cell(const DevMesh &d, int i, float &hi32, double &hi64) {
+  float v, e;
+  double x;
+  if (local_dt32(d, i, v, e, x)) {
+    d.dt32[i] = v;
+    d.dteps[i] = e;
+    hi32 = fminf(hi32, __fmul_ru(v, __fadd_ru(1.0f, e)));
+  } else {
+    d.dteps[i] = 0.0f;
+    hi64 = fmin(hi64, x);
+  }
 }
 
 // pass 2 of one cell: exact if its lower bound reaches the smallest upper
-// bound hi (it can hold the minimum); returns its exact value then, else +inf
-__device__ __forceinline__ double dt_min_exact_cell(const DevMesh &d, int i, double hi) {
+// bound hi (hi_rd: hi rounded down to FP32), so that it can hold the
+// minimum; lowers m by its exact value then
+__device__ __forceinline__ void dt_min_exact_cell(const DevMesh &d, int i, double hi, float hi_rd, double &m) {
   const float e = d.dteps[i];
-  double dt = d.dt[i];
-  if (e > 0.0f && dt * (1.0 - (double)e) <= hi) {
-    dt = local_dt_of(d, i);
-    d.dteps[i] = 0.0f;
-    return dt;
+  if (e > 0.0f) {
+    if (__fmul_rd(d.dt32[i], __fsub_rd(1.0f, e)) <= hi_rd) {
+      m = fmin(m, local_dt_of(d, i));
+      d.dteps[i] = 0.0f;
+    }
+  } else {
+    const double dt = d.dt[i];
+    if (dt <= hi) m = fmin(m, dt);
   }
-  if (e == 0.0f && dt <= hi) return dt;
-  return __longlong_as_double(0x7ff0000000000000LL);
 }
 
 // pass 1: estimates and the smallest upper bound
 __global__ void __launch_bounds__(256) k_dt32(DevMesh d) {
-  double local_hi = __longlong_as_double(0x7ff0000000000000LL);
+  float hi32 = __int_as_float(0x7f800000);
+  double hi64 = __longlong_as_double(0x7ff0000000000000LL);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x)
-    local_hi = fmin(local_hi, dt32_cell(d, i));
-  block_min_to(local_hi, d.dthi_bits);
+    dt32_cell(d, i, hi32, hi64);
+  block_min_to(fmin((double)hi32, hi64), d.dthi_bits);
 }
 
 // pass 2: every cell that can hold the minimum (lower bound <= the smallest
 // upper bound) is made exact; dt_min = the exact minimum over them
 __global__ void __launch_bounds__(256) k_dt_min_exact(DevMesh d) {
   const double hi = __longlong_as_double((long long)*d.dthi_bits);
-  double local_min = __longlong_as_double(0x7ff0000000000000LL);
+  const float hi_rd = __double2float_rd(hi);
+  double m = __longlong_as_double(0x7ff0000000000000LL);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x)
-    local_min = fmin(local_min, dt_min_exact_cell(d, i, hi));
-  block_min_to(local_min, d.dtmin_bits);
+    dt_min_exact_cell(d, i, hi, hi_rd, m);
+  block_min_to(m, d.dtmin_bits);
 }
 
-// k_i = max{k <= L-1 : 2^k dt_min <= dt_i}
-__device__ __forceinline__ int8_t level0_of(const DevMesh &d, double dtmin, int i) {
-  double dt = d.dt[i];
-  int k = 0;
-  while (k + 1 < d.L && ldexp(dtmin, k + 1) <= dt) ++k;
-  return (int8_t)k;
+// the thresholds of the level rule, t[k] = 2^k dt_min for k < L, and t[k]
+// rounded up to FP32, filled once per block (every thread calls it)
+struct LevelRule {
+  double t[FV_MAXL];
+  float tu[FV_MAXL];
+};
+__device__ __forceinline__ void level_rule_fill(LevelRule &r, const DevMesh &d) {
+  if (threadIdx.x < d.L) {
+    const double t = ldexp(__longlong_as_double((long long)*d.dtmin_bits), (int)threadIdx.x);
+    r.t[threadIdx.x] = t;
+    r.tu[threadIdx.x] = __double2float_ru(t);
+  }
+  __syncthreads();
 }
 
-// the same decision from an estimate: certain when no threshold 2^k dt_min
-// falls inside (lo, hi]; otherwise taken on the exact value
-__device__ __forceinline__ int8_t level0_certified_of(const DevMesh &d, double dtmin, int i) {
+// k_i = max{k <= L-1 : 2^k dt_min <= dt_i}, taken on the exact value, or on
+// the estimate's interval when no threshold falls inside it
+__device__ __forceinline__ int8_t level0_certified_of(const DevMesh &d, const LevelRule &r, int i) {
   const float e = d.dteps[i];
   if (e > 0.0f) {
-    const double dt = d.dt[i], lo = dt * (1.0 - (double)e), hi = dt * (1.0 + (double)e);
+    const float v = d.dt32[i];
+    const float lo = __fmul_rd(v, __fsub_rd(1.0f, e)), hi = __fmul_ru(v, __fadd_ru(1.0f, e));
     int klo = 0, khi = 0;
-    while (klo + 1 < d.L && ldexp(dtmin, klo + 1) <= lo) ++klo;
-    while (khi + 1 < d.L && ldexp(dtmin, khi + 1) <= hi) ++khi;
+    for (int k = 1; k < d.L; ++k) {
+      klo += r.tu[k] <= lo;
+      khi += r.tu[k] <= hi;
+    }
     if (klo == khi) return (int8_t)klo;
     local_dt_of(d, i);
     d.dteps[i] = 0.0f;
   }
-  return level0_of(d, dtmin, i);
+  const double dt = d.dt[i];
+  int k = 0;
+  while (k + 1 < d.L && r.t[k + 1] <= dt) ++k;
+  return (int8_t)k;
 }
 
 __global__ void __launch_bounds__(256) k_levels0_certified(DevMesh d) {
-  const double dtmin = __longlong_as_double((long long)*d.dtmin_bits);
+  __shared__ LevelRule r;
+  level_rule_fill(r, d);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x)
-    d.lev_tmp[i] = level0_certified_of(d, dtmin, i);
+    d.lev_tmp[i] = level0_certified_of(d, r, i);
 }
 
 // one Jacobi sweep of k_i <- min(k_i, 1 + min_j k_j); L-1 sweeps reach the
@@ -543,12 +574,13 @@ __global__ void __launch_bounds__(256) k_dt_multi(MultiTiles a, int op) {
   double m = __longlong_as_double(0x7ff0000000000000LL);
   const int end = min(d.N, (tile + 1) * SORT_TILE);
   if (op == 0) {
-    for (int i = tile * SORT_TILE + threadIdx.x; i < end; i += blockDim.x) m = fmin(m, dt32_cell(d, i));
-    block_min_to(m, d.dthi_bits);
+    float hi32 = __int_as_float(0x7f800000);
+    for (int i = tile * SORT_TILE + threadIdx.x; i < end; i += blockDim.x) dt32_cell(d, i, hi32, m);
+    block_min_to(fmin((double)hi32, m), d.dthi_bits);
   } else {
     const double hi = __longlong_as_double((long long)*d.dthi_bits);
-    for (int i = tile * SORT_TILE + threadIdx.x; i < end; i += blockDim.x)
-      m = fmin(m, dt_min_exact_cell(d, i, hi));
+    const float hi_rd = __double2float_rd(hi);
+    for (int i = tile * SORT_TILE + threadIdx.x; i < end; i += blockDim.x) dt_min_exact_cell(d, i, hi, hi_rd, m);
     block_min_to(m, d.dtmin_bits);
   }
 }
@@ -559,9 +591,10 @@ __global__ void __launch_bounds__(256) k_cells_multi(MultiTiles a, int op) {
   int inst, tile;
   if (!tile_of(a, inst, tile)) return;
   const DevMesh &d = a.ms[inst];
-  double dtmin = __longlong_as_double((long long)*d.dtmin_bits);
+  __shared__ LevelRule r;
+  if (op == 0) level_rule_fill(r, d);
   for (int i = tile * SORT_TILE + threadIdx.x; i < min(d.N, (tile + 1) * SORT_TILE); i += blockDim.x) {
-    if (op == 0) d.lev_tmp[i] = level0_certified_of(d, dtmin, i);
+    if (op == 0) d.lev_tmp[i] = level0_certified_of(d, r, i);
     else if (op == 1) d.lev[i] = d.lev_tmp[i];
     else if (op == 2) d.lev[i] = smooth_of(d, d.lev_tmp, i);
     else if (op == 3) d.lev_tmp[i] = smooth_of(d, d.lev, i);
@@ -697,34 +730,20 @@ __device__ __forceinline__ void prim_item(const DevMesh &d, const PhaseLevels &p
   strec<REC_W>((WT *)d.W + (size_t)i * REC_W, Wt);
 }
 
-// least-squares gradients of the primitives of the cell at list position
-// idx: g = sum_j w_j (W_nb(j) - W_i), ghost states on boundary faces.
-// FP64 mode: from the W records the primitives kernel wrote.  FP32-flux
-// mode (INLINE_W): the primitives of the cell and of its neighbours are
-// computed here from their states at the phase time, and the cell's own
-// primitives are stored in its W record for the flux kernel, with its level
-// in slot 5; there is no separate primitives kernel.  Both records are
-// stored after every load.
+// least-squares gradient of the primitives of cell i, whose own primitives
+// are Wi: g = sum_j w_j (W_nb(j) - W_i), ghost states on boundary faces.
+// FP64 mode: neighbours from the W records the primitives kernel wrote;
+// FP32-flux mode: from their states at the phase time (`both`: load the
+// predicted record together with U^n).
 template <typename T>
-__device__ __forceinline__ void grad_cell(const DevMesh &d, const PhaseLevels &pl, int i) {
+__device__ __forceinline__ void lsq_grad(const DevMesh &d, const PhaseLevels &pl, bool both, int i,
+                                         const T Wi[5], T g[REC_G]) {
   constexpr bool INLINE_W = sizeof(T) == 4;
   const T *W = (const T *)d.W;
-  const T *lsw = lswrec(d, T(0));
   const T *fgeo = georec(d, T(0));
   const double gm1 = d.gamma - 1.0;
-  const bool both = INLINE_W && reads_predicted(pl);
-  T Wi[REC_W], g[REC_G], w[REC_LSW];
-  if (INLINE_W) {
-    T U[5];
-    const int k = load_state(d, pl, i, U, both);
-    to_prim(U, gm1, Wi);
-    Wi[5] = T(k);
-#pragma unroll
-    for (int q = 6; q < REC_W; ++q) Wi[q] = T(0);
-  } else {
-    ldrec<REC_W>(W + (size_t)i * REC_W, Wi);
-  }
-  ldrec<REC_LSW>(lsw + (size_t)i * REC_LSW, w);
+  T w[REC_LSW];
+  ldrec<REC_LSW>(lswrec(d, T(0)) + (size_t)i * REC_LSW, w);
   int4 nb4 = d.cnb4[i];
 #pragma unroll
   for (int q = 0; q < REC_G; ++q) g[q] = T(0);
@@ -760,6 +779,30 @@ __device__ __forceinline__ void grad_cell(const DevMesh &d, const PhaseLevels &p
       g[3 * c + 2] += w[3 * j + 2] * dd;
     }
   }
+}
+
+// gradient item of the cell at list position idx.  FP64 mode: from the W
+// records the primitives kernel wrote.  FP32-flux mode (INLINE_W): the
+// primitives of the cell and of its neighbours are computed here from their
+// states at the phase time, and the cell's own primitives are stored in its W
+// record for the flux kernel, with its level in slot 5; there is no separate
+// primitives kernel.  Both records are stored after every load.
+template <typename T>
+__device__ __forceinline__ void grad_cell(const DevMesh &d, const PhaseLevels &pl, int i) {
+  constexpr bool INLINE_W = sizeof(T) == 4;
+  const bool both = INLINE_W && reads_predicted(pl);
+  T Wi[REC_W], g[REC_G];
+  if (INLINE_W) {
+    T U[5];
+    const int k = load_state(d, pl, i, U, both);
+    to_prim(U, d.gamma - 1.0, Wi);
+    Wi[5] = T(k);
+#pragma unroll
+    for (int q = 6; q < REC_W; ++q) Wi[q] = T(0);
+  } else {
+    ldrec<REC_W>((const T *)d.W + (size_t)i * REC_W, Wi);
+  }
+  lsq_grad<T>(d, pl, both, i, Wi, g);
   strec<REC_G>(grec_w(d, T(0)) + (size_t)i * REC_G, g);
   if (INLINE_W) strec<REC_W>((T *)d.W + (size_t)i * REC_W, Wi);
 }
@@ -910,8 +953,49 @@ __device__ __forceinline__ float flip(float v, bool neg) {
 // where it only feeds the predictor).  stage 2 (corrector of `level`): the
 // step's flux time integral Phi = (dt_k/2) (F1 A + F2 A) is formed in FP64
 // (in the FP32-flux mode from the FP32 sum of the two fluxes) and stored; on
-// a level interface Phi is added to ACC[f] (the coarse side's integral), on a
-// boundary face to BND[f] (the conservation ledger).
+// a level interface (iface) Phi is added to ACC[f] (the coarse side's
+// integral), on a boundary face (bnd) to BND[f] (the conservation ledger).
+template <typename T>
+__device__ __forceinline__ void flux_store(const DevMesh &d, int stage, int level, int f, const T FAt[5],
+                                           bool iface, bool bnd) {
+  const bool f32 = sizeof(T) == 4;
+  if (stage == 1) {
+    if (f32) {
+      float v[REC_FA32] = {(float)FAt[0], (float)FAt[1], (float)FAt[2], (float)FAt[3], (float)FAt[4], 0.f, 0.f, 0.f};
+      strec<REC_FA32>(d.FA32 + (size_t)f * REC_FA32, v);
+    } else {
+      double v[REC_FA] = {(double)FAt[0], (double)FAt[1], (double)FAt[2], (double)FAt[3], (double)FAt[4], 0.0};
+      strec<REC_FA>(d.FA + (size_t)f * REC_FA, v);
+    }
+    return;
+  }
+  double h = 0.5 * ldexp(__longlong_as_double((long long)*d.dtmin_bits), level);
+  double phi[REC_FA];
+  if (f32) {
+    float a[REC_FA32];
+    ldrec<REC_FA32>(d.FA32 + (size_t)f * REC_FA32, a);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) phi[c] = h * (double)(a[c] + (float)FAt[c]);
+  } else {
+    double a[REC_FA];
+    ldrec<REC_FA>(d.FA + (size_t)f * REC_FA, a);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) phi[c] = h * (a[c] + (double)FAt[c]);
+  }
+  phi[5] = 0.0;
+  strec<REC_FA>(d.FA + (size_t)f * REC_FA, phi);
+  if (iface || bnd) {
+    double *dst = (iface ? d.ACC : d.BND) + (size_t)f * REC_FA;
+    double acc[REC_FA];
+    ldrec<REC_FA>(dst, acc);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) acc[c] += phi[c];
+    strec<REC_FA>(dst, acc);
+  }
+}
+
+// flux item of the face at list position idx, from the phase's primitive and
+// gradient records
 template <typename T, bool G14, bool MLP = false>
 __device__ __forceinline__ void flux_item(const DevMesh &d, const GasT<T> &G, int stage, int level,
                                           int idx, const uint32_t *sw = nullptr) {
@@ -921,45 +1005,97 @@ __device__ __forceinline__ void flux_item(const DevMesh &d, const GasT<T> &G, in
   int rc = face_flux<T, G14, MLP>(d, G, (const T *)d.W, grec(d, T(0)), georec(d, T(0)), f, FAt, sw);
   if (MLP && f < 0) return;
   if (rc) atomicOr(d.status, FV_STATUS_RIEMANN);
-  if (stage == 1) {
-    if (f32) {
-      float v[REC_FA32] = {(float)FAt[0], (float)FAt[1], (float)FAt[2], (float)FAt[3], (float)FAt[4], 0.f, 0.f, 0.f};
-      strec<REC_FA32>(d.FA32 + (size_t)f * REC_FA32, v);
-    } else {
-      double v[REC_FA] = {(double)FAt[0], (double)FAt[1], (double)FAt[2], (double)FAt[3], (double)FAt[4], 0.0};
-      strec<REC_FA>(d.FA + (size_t)f * REC_FA, v);
-    }
-  } else {
-    double h = 0.5 * ldexp(__longlong_as_double((long long)*d.dtmin_bits), level);
+  bool iface = false, bnd = false;
+  if (stage == 2) {
     int2 fc = d.fcell[f];
     // the FP32-flux mode has the cells' levels in slot 5 of the W records
     // the face states were just read from
     const T *Wr = (const T *)d.W;
-    bool iface = fc.y >= 0 && (f32 ? Wr[(size_t)fc.x * REC_W + 5] != Wr[(size_t)fc.y * REC_W + 5]
-                                   : d.lev[fc.x] != d.lev[fc.y]);
-    double phi[REC_FA];
-    if (f32) {
-      float a[REC_FA32];
-      ldrec<REC_FA32>(d.FA32 + (size_t)f * REC_FA32, a);
-#pragma unroll
-      for (int c = 0; c < 5; ++c) phi[c] = h * (double)(a[c] + (float)FAt[c]);
-    } else {
-      double a[REC_FA];
-      ldrec<REC_FA>(d.FA + (size_t)f * REC_FA, a);
-#pragma unroll
-      for (int c = 0; c < 5; ++c) phi[c] = h * (a[c] + (double)FAt[c]);
-    }
-    phi[5] = 0.0;
-    strec<REC_FA>(d.FA + (size_t)f * REC_FA, phi);
-    if (iface || fc.y < 0) {
-      double *dst = (iface ? d.ACC : d.BND) + (size_t)f * REC_FA;
-      double acc[REC_FA];
-      ldrec<REC_FA>(dst, acc);
-#pragma unroll
-      for (int c = 0; c < 5; ++c) acc[c] += phi[c];
-      strec<REC_FA>(dst, acc);
-    }
+    iface = fc.y >= 0 && (f32 ? Wr[(size_t)fc.x * REC_W + 5] != Wr[(size_t)fc.y * REC_W + 5]
+                              : d.lev[fc.x] != d.lev[fc.y]);
+    bnd = fc.y < 0;
   }
+  flux_store<T>(d, stage, level, f, FAt, iface, bnd);
+}
+
+// FP32-flux mode, phases with few faces (fused_phase): the Riemann inputs of
+// face f with both cells' primitives and gradients computed here from the
+// states at the phase time -- the arithmetic of the gradient kernel followed
+// by that of face_states -- so the phase needs no gradient records.  Returns
+// fcell.y; iface: the two cells are on different levels.
+__device__ __forceinline__ int face_states_fused(const DevMesh &d, const PhaseLevels &pl, bool both, int f,
+                                                 float WL[5], float WR[5], float n[3], float &A,
+                                                 bool &iface) {
+  int2 fc = d.fcell[f];
+  const int L = fc.x, R = fc.y;
+  float geo[REC_FG];
+  ldrec<REC_FG>(d.fgeo32 + (size_t)f * REC_FG, geo);
+  n[0] = geo[0];
+  n[1] = geo[1];
+  n[2] = geo[2];
+  A = geo[3];
+  const float r[3] = {geo[4], geo[5], geo[6]};
+  const double gm1 = d.gamma - 1.0;
+  float U[5], Wi[5], g[REC_G];
+  const int kL = load_state(d, pl, L, U, both);
+  to_prim(U, gm1, Wi);
+  lsq_grad<float>(d, pl, both, L, Wi, g);
+  iface = false;
+  if (R >= 0) {
+    float Wj[5];
+    const int kR = load_state(d, pl, R, U, both);
+    to_prim(U, gm1, Wj);
+    iface = kL != kR;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      float dW = Wj[c] - Wi[c];
+      float gir = (g[3 * c] * r[0] + g[3 * c + 1] * r[1]) + g[3 * c + 2] * r[2];
+      WL[c] = Wi[c] + 0.5f * minmod(2.0f * gir - dW, dW);
+    }
+    lsq_grad<float>(d, pl, both, R, Wj, g);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      float dW = Wj[c] - Wi[c];
+      float gjr = (g[3 * c] * r[0] + g[3 * c + 1] * r[1]) + g[3 * c + 2] * r[2];
+      WR[c] = Wj[c] - 0.5f * minmod(2.0f * gjr - dW, dW);
+    }
+  } else {
+    float Wg[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) Wg[c] = Wi[c];
+    if (R == -FV_BC_WALL) {
+      float un = (Wi[1] * n[0] + Wi[2] * n[1]) + Wi[3] * n[2];
+#pragma unroll
+      for (int e = 0; e < 3; ++e) Wg[1 + e] = Wi[1 + e] - (2.0f * un) * n[e];
+    }
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      float dW = Wg[c] - Wi[c];
+      float gir = (g[3 * c] * r[0] + g[3 * c + 1] * r[1]) + g[3 * c + 2] * r[2];
+      WL[c] = Wi[c] + 0.5f * minmod(2.0f * gir - dW, dW);
+    }
+#pragma unroll
+    for (int c = 0; c < 5; ++c) WR[c] = WL[c];
+  }
+  return R;
+}
+
+template <bool G14>
+__device__ __forceinline__ void flux_item_fused(const DevMesh &d, const GasT<float> &G, int stage, int level,
+                                                const PhaseLevels &pl, bool both, int idx) {
+  const int f = d.fl[idx];
+  float WL[5], WR[5], n[3], A, Fx[5], FAt[5];
+  bool iface;
+  const int R = face_states_fused(d, pl, both, f, WL, WR, n, A, iface);
+  int it, rc;
+  if (R >= 0)
+    rc = godunov_flux<float, G14, false>(G, WL, WR, n, Fx, it, 0.0f, 1.0f);
+  else
+    rc = boundary_flux<float, G14>(G, -R, WL, n, Fx, it);
+#pragma unroll
+  for (int c = 0; c < 5; ++c) FAt[c] = Fx[c] * A;
+  if (rc) atomicOr(d.status, FV_STATUS_RIEMANN);
+  flux_store<float>(d, stage, level, f, FAt, iface, R < 0);
 }
 
 // per-cell gather over its 4 faces in local order (deterministic, no
@@ -1097,13 +1233,48 @@ __device__ __forceinline__ void run_item(const DevMesh &d, const PhaseDesc &p, c
                     : (KIND) == K_UPD ? 5                                                     \
                                       : ((KIND) == K_GRAD && sizeof(T) == 8 ? 2 : 4))
 
+// FP32-flux mode with the two-rarefaction guess: a phase with at most
+// d.fuse_faces faces is latency-bound (about a wave of faces or less, each a
+// chain of dependent loads), so its flux kernel computes the gradients it
+// needs itself (a cell's gradient once per face of the cell) and its
+// gradient kernel does nothing.  Decided on the device from the phase's
+// face count, so a captured cycle follows every level assignment.
+__device__ __forceinline__ bool fused_phase(const DevMesh &d, const PhaseDesc &p) {
+  return d.fuse_faces > 0 && d.guess == FV_GUESS_TWO_RAREFACTION &&
+         d.foff[p.fb1] - d.foff[p.fb0] <= d.fuse_faces;
+}
+
 template <int KIND, typename T, bool G14>
 __global__ void KBOUNDS(KIND, T) k_phase1(DevMesh d, const __grid_constant__ PhaseDesc p, GasT<T> G) {
   pdl_wait();
   int beg, end;
   kind_range(d, p, KIND, beg, end);
-  for (int idx = beg + blockIdx.x * blockDim.x + threadIdx.x; idx < end; idx += gridDim.x * blockDim.x)
-    run_item<KIND, T, G14>(d, p, G, idx);
+  bool fused = false;
+  if constexpr (sizeof(T) == 4 && (KIND == K_GRAD || KIND == K_FLUX)) fused = fused_phase(d, p);
+  if (!fused)
+    for (int idx = beg + blockIdx.x * blockDim.x + threadIdx.x; idx < end; idx += gridDim.x * blockDim.x)
+      run_item<KIND, T, G14>(d, p, G, idx);
+  pdl_trigger();
+}
+
+// the flux of a fused phase (FP32-flux mode): with both cells' gradients to
+// compute per face it needs more registers than the plain flux kernel, and
+// runs where a wave of faces or less is in flight anyway.  Launched after the
+// plain flux kernel of every phase; exactly one of the two has work.
+#ifndef FV_FUSED_BLOCKS
+#define FV_FUSED_BLOCKS 4  // resident 128-thread blocks per SM (up to 128 registers)
+#endif
+template <bool G14>
+__global__ void __launch_bounds__(128, FV_FUSED_BLOCKS) k_flux_fused(DevMesh d, const __grid_constant__ PhaseDesc p,
+                                                                     GasT<float> G) {
+  pdl_wait();
+  if (fused_phase(d, p)) {
+    int beg, end;
+    kind_range(d, p, K_FLUX, beg, end);
+    const bool both = reads_predicted(p.pl);
+    for (int idx = beg + blockIdx.x * blockDim.x + threadIdx.x; idx < end; idx += gridDim.x * blockDim.x)
+      flux_item_fused<G14>(d, G, p.stage, p.level, p.pl, both, idx);
+  }
   pdl_trigger();
 }
 
@@ -1690,6 +1861,11 @@ static void phase1_all(const DevMesh &d, const PhaseDesc &pd, const GasT<T> &G, 
                  128, s, d, pd, G);
     else
       launch_pdl(k_phase1<K_FLUX, T, G14>, g2, 128, s, d, pd, G);
+    if constexpr (sizeof(T) == 4)
+      if (d.guess == FV_GUESS_TWO_RAREFACTION && d.fuse_faces > 0)
+        launch_pdl(k_flux_fused<G14>,
+                   grid_for(d.F, 128, lc.per_sm[2] < FV_FUSED_BLOCKS ? lc.per_sm[2] : FV_FUSED_BLOCKS), 128, s,
+                   d, pd, G);
   }
   { ProfScope sc(ph, FV_PROF_UPDATE, s); launch_pdl(k_phase1<K_UPD, T, G14>, g3, 256, s, d, pd, G); }
 }

@@ -69,7 +69,7 @@ EXPORTS = [
     "fv_mlp_label", "fv_mlp_loss_grad", "fv_mlp_adam", "fv_mlp_train", "fv_mlp_train_steps",
     "fv_mlp_load", "fv_set_guess", "fv_harvest_pairs", "fv_godunov_flux_batch_mlp",
     "fv_use_persistent", "fv_barrier_selftest", "fv_level_history", "fv_batch_mlp_load",
-    "fv_batch_set_guess",
+    "fv_batch_set_guess", "fv_set_fusion", "fv_get_fusion",
 ]
 
 FV_MLP_PARAMS = 4673
@@ -77,6 +77,7 @@ FV_MLP_PACKED_BYTES = 10240
 FV_MLP_TARGET_PBAR, FV_MLP_TARGET_TR = 0, 1
 
 FV_NOALLOC_MAX_CELLS = 1 << 22
+FV_FUSE_FACES_DEFAULT = 0
 
 FV_PROF_LEVELS, FV_PROF_PRIM, FV_PROF_GRAD, FV_PROF_FLUX, FV_PROF_UPDATE = range(5)
 FV_PROF_N = 5
@@ -142,6 +143,8 @@ def lib():
     L.fv_batch_free.restype = None
     for nm in ("fv_set_launch", "fv_get_launch", "fv_batch_set_launch", "fv_batch_get_launch"):
         getattr(L, nm).argtypes = [vp, i32p]
+    L.fv_set_fusion.argtypes = [vp, i64]
+    L.fv_get_fusion.argtypes = [vp, C.POINTER(C.c_int64)]
     L.fv_godunov_flux_batch.argtypes = [vp, vp, vp, i64, C.POINTER(fv_config), C.c_int, vp, vp, vp]
     L.fv_assign_levels_noalloc.argtypes = [vp, vp, i64, C.c_int, vp, vp, vp]
     L.fv_get_level_lists.argtypes = [vp, C.POINTER(C.c_int64), i32p, i8p, i32p]
@@ -608,6 +611,16 @@ def fv_get_launch(h):
     return list(a)
 
 
+def fv_set_fusion(h, max_faces):
+    _check(lib().fv_set_fusion(h, int(max_faces)), "fv_set_fusion")
+
+
+def fv_get_fusion(h):
+    a = C.c_int64()
+    _check(lib().fv_get_fusion(h, C.byref(a)), "fv_get_fusion")
+    return a.value
+
+
 def fv_batch_set_launch(b, per_sm):
     _check(lib().fv_batch_set_launch(b, _launch4(per_sm)), "fv_batch_set_launch")
 
@@ -676,6 +689,12 @@ class Mesh:
 
     def get_launch(self):
         return fv_get_launch(self.h)
+
+    def set_fusion(self, max_faces):
+        fv_set_fusion(self.h, max_faces)
+
+    def get_fusion(self):
+        return fv_get_fusion(self.h)
 
     def profile_enable(self, enable):
         fv_profile_enable(self.h, enable)
