@@ -234,7 +234,8 @@ int fv_mesh_load(const double *xyz, int64_t n_nodes, const int64_t *tets, int64_
   d.fuse_faces = FV_FUSE_FACES_DEFAULT;
   const bool f32 = cfg->precision == FV_FP32_FLUX;
   const int nblk_c = (int)((N + 1023) / 1024), nblk_f = (int)((F + 1023) / 1024);
-  size_t cnt_size = (size_t)16 * (nblk_c > nblk_f ? nblk_c : nblk_f) + 16;
+  // the cell counts (2L buckets per tile), then the face counts (L per tile)
+  size_t cnt_size = (size_t)16 * (nblk_c + nblk_f) + 32;
 #define AL(p, n)                       \
   do {                                 \
     int r_ = dalloc(m, &(p), (n));     \

@@ -57,6 +57,14 @@ static inline int grid_for(int64_t items, int block, int per_sm) {
   } while (0)
 
 // ------------------------------------------------------------- helpers ---
+// Programmatic dependent launch: a kernel of the cycle waits (in hardware) for the
+// kernel before it to finish and flush before it reads anything, and lets
+// the next one be launched once its own items are done, so launch and
+// ramp-up of the next kernel overlap the drain of this one.  Without a
+// programmatic predecessor the wait returns at once.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // N-element record loads/stores with 16-byte vector accesses (records are
 // 16-byte aligned: cudaMalloc bases and strides that are multiples of 16 B)
 template <int NE>
@@ -184,8 +192,10 @@ __device__ __forceinline__ void block_min_to(double local_min, unsigned long lon
 }
 
 __global__ void k_init_min2(unsigned long long *a, unsigned long long *b) {
+  pdl_wait();
   *a = 0x7ff0000000000000ULL;
   *b = 0x7ff0000000000000ULL;
+  pdl_trigger();
 }
 
 // ---- certified FP32 estimate of the local step.  The estimate dt~ comes
@@ -304,20 +314,24 @@ __device__ __forceinline__ void dt_min_exact_cell(const DevMesh &d, int i, doubl
 __global__ void __launch_bounds__(256) k_dt32(DevMesh d) {
   float hi32 = __int_as_float(0x7f800000);
   double hi64 = __longlong_as_double(0x7ff0000000000000LL);
+  pdl_wait();
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x)
     dt32_cell(d, i, hi32, hi64);
   block_min_to(fmin((double)hi32, hi64), d.dthi_bits);
+  pdl_trigger();
 }
 
 // pass 2: every cell that can hold the minimum (lower bound <= the smallest
 // upper bound) is made exact; dt_min = the exact minimum over them
 __global__ void __launch_bounds__(256) k_dt_min_exact(DevMesh d) {
+  pdl_wait();
   const double hi = __longlong_as_double((long long)*d.dthi_bits);
   const float hi_rd = __double2float_rd(hi);
   double m = __longlong_as_double(0x7ff0000000000000LL);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x)
     dt_min_exact_cell(d, i, hi, hi_rd, m);
   block_min_to(m, d.dtmin_bits);
+  pdl_trigger();
 }
 
 // the thresholds of the level rule, t[k] = 2^k dt_min for k < L, and t[k]
@@ -359,9 +373,11 @@ __device__ __forceinline__ int8_t level0_certified_of(const DevMesh &d, const Le
 
 __global__ void __launch_bounds__(256) k_levels0_certified(DevMesh d) {
   __shared__ LevelRule r;
+  pdl_wait();
   level_rule_fill(r, d);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x)
     d.lev_tmp[i] = level0_certified_of(d, r, i);
+  pdl_trigger();
 }
 
 // one Jacobi sweep of k_i <- min(k_i, 1 + min_j k_j); L-1 sweeps reach the
@@ -379,8 +395,10 @@ __device__ __forceinline__ int8_t smooth_of(const DevMesh &d, const int8_t *src,
 
 __global__ void __launch_bounds__(256) k_smooth(DevMesh d, const int8_t *__restrict__ src,
                                                 int8_t *__restrict__ dst) {
+  pdl_wait();
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x)
     dst[i] = smooth_of(d, src, i);
+  pdl_trigger();
 }
 
 // cell sort key: 2 level + (1 unless a neighbour is one level finer), so the
@@ -390,7 +408,7 @@ __global__ void __launch_bounds__(256) k_smooth(DevMesh d, const int8_t *__restr
 // integrals) and, in the FP32-flux mode, the cycle's level in the cell's FP32
 // state record (read with the state, so the phase kernels need no separate
 // level lookup).
-__device__ __forceinline__ void cell_key_store(const DevMesh &d, int i) {
+__device__ __forceinline__ int cell_key_store(const DevMesh &d, int i) {
   const int k = d.lev[i];
   unsigned finer = 0;
   int4 nb4 = d.cnb4[i];
@@ -399,28 +417,21 @@ __device__ __forceinline__ void cell_key_store(const DevMesh &d, int i) {
     int nb = nbr_of(nb4, j);
     if (nb >= 0 && d.lev[nb] < k) finer |= 1u << j;
   }
-  d.ckey[i] = (uint8_t)(2 * k + (finer ? 0 : 1));
+  const int key = 2 * k + (finer ? 0 : 1);
+  d.ckey[i] = (uint8_t)key;
   d.cmask[i] = (uint8_t)finer;
   if (d.Un32) d.Un32[(size_t)i * REC_U32 + 5] = (float)k;
-}
-
-__global__ void __launch_bounds__(256) k_cell_keys(DevMesh d) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x)
-    cell_key_store(d, i);
+  return key;
 }
 
 // face level = min of the two cell levels; faces sort by it
-__device__ __forceinline__ void face_key_of(const DevMesh &d, int f) {
+__device__ __forceinline__ int face_key_of(const DevMesh &d, int f) {
   int2 fc = d.fcell[f];
   int a = d.lev[fc.x];
   int k = fc.y >= 0 ? min(a, (int)d.lev[fc.y]) : a;
   d.flev[f] = (int8_t)k;
   d.fkey[f] = (uint8_t)k;
-}
-
-__global__ void __launch_bounds__(256) k_face_keys(DevMesh d) {
-  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < d.F; f += gridDim.x * blockDim.x)
-    face_key_of(d, f);
+  return k;
 }
 
 // ---- stable counting sort of small keys (< 16 buckets), 1024 items per tile
@@ -442,10 +453,6 @@ __device__ __forceinline__ void sort_hist_tile(const uint8_t *__restrict__ key, 
   if (threadIdx.x < nb) cnt[threadIdx.x * nblk + tile] = h[threadIdx.x];
 }
 
-__global__ void __launch_bounds__(SORT_THREADS) k_sort_hist(const uint8_t *__restrict__ key, int n,
-                                                            int nb, int *cnt) {
-  sort_hist_tile(key, n, nb, cnt, blockIdx.x, gridDim.x);
-}
 
 // exclusive scan over the bucket-major (bucket, tile) counts by one block of
 // 1024 threads; also writes the bucket offsets off[0..nb]
@@ -486,9 +493,6 @@ __device__ __forceinline__ void sort_scan_block(int *cnt, int total, int nblk, i
   if (threadIdx.x == 0) off[nb] = carry;
 }
 
-__global__ void __launch_bounds__(1024) k_sort_scan(int *cnt, int total, int nblk, int nb, int *off) {
-  sort_scan_block(cnt, total, nblk, nb, off);
-}
 
 // stable scatter of one tile: lanes with equal keys rank in lane (= item)
 // order, warps in order, earlier rounds first
@@ -524,10 +528,44 @@ __device__ __forceinline__ void sort_scatter_tile(const uint8_t *__restrict__ ke
   }
 }
 
-__global__ void __launch_bounds__(SORT_THREADS) k_sort_scatter(const uint8_t *__restrict__ key, int n,
-                                                               int nb, const int *__restrict__ cnt,
-                                                               int *__restrict__ out) {
-  sort_scatter_tile(key, n, nb, cnt, out, blockIdx.x, gridDim.x);
+
+// One mesh's cell and face sorts share each launch: the key computation and
+// the per-tile counts (tiles 0..nc-1 are cells, the rest faces), the two
+// scans (block 0 cells, block 1 faces), the two stable scatters.  The cell
+// counts sit at sort_cnt[0 .. 2L nc), the face counts after them.
+__global__ void __launch_bounds__(SORT_THREADS) k_keys_hist(DevMesh d, int nc, int nf) {
+  __shared__ int h[16];
+  pdl_wait();
+  if (threadIdx.x < 16) h[threadIdx.x] = 0;
+  __syncthreads();
+  const bool faces = (int)blockIdx.x >= nc;
+  const int tile = faces ? blockIdx.x - nc : blockIdx.x, n = faces ? d.F : d.N;
+  for (int r = 0; r < SORT_TILE / SORT_THREADS; ++r) {
+    const int i = tile * SORT_TILE + r * SORT_THREADS + threadIdx.x;
+    if (i < n) atomicAdd(&h[faces ? face_key_of(d, i) : cell_key_store(d, i)], 1);
+  }
+  __syncthreads();
+  if (!faces && threadIdx.x < 2 * d.L) d.sort_cnt[threadIdx.x * nc + tile] = h[threadIdx.x];
+  if (faces && threadIdx.x < d.L) d.sort_cnt[2 * d.L * nc + threadIdx.x * nf + tile] = h[threadIdx.x];
+  pdl_trigger();
+}
+
+__global__ void __launch_bounds__(1024) k_sort_scan2(DevMesh d, int nc, int nf) {
+  pdl_wait();
+  if (blockIdx.x == 0)
+    sort_scan_block(d.sort_cnt, 2 * d.L * nc, nc, 2 * d.L, d.coff);
+  else
+    sort_scan_block(d.sort_cnt + 2 * d.L * nc, d.L * nf, nf, d.L, d.foff);
+  pdl_trigger();
+}
+
+__global__ void __launch_bounds__(SORT_THREADS) k_sort_scatter2(DevMesh d, int nc, int nf) {
+  pdl_wait();
+  if ((int)blockIdx.x < nc)
+    sort_scatter_tile(d.ckey, d.N, 2 * d.L, d.sort_cnt, d.cl, blockIdx.x, nc);
+  else
+    sort_scatter_tile(d.fkey, d.F, d.L, d.sort_cnt + 2 * d.L * nc, d.fl, blockIdx.x - nc, nf);
+  pdl_trigger();
 }
 
 // ---- batched level assignment: block b of a grid covering every instance's
@@ -1189,13 +1227,6 @@ __device__ __forceinline__ void update_item(const DevMesh &d, int stage, int lev
 // instances' range lengths)
 enum { K_PRIM = 0, K_GRAD = 1, K_FLUX = 2, K_UPD = 3 };
 
-// Programmatic dependent launch: a phase kernel waits (in hardware) for the
-// kernel before it to finish and flush before it reads anything, and lets
-// the next one be launched once its own items are done, so launch and
-// ramp-up of the next kernel overlap the drain of this one.  Without a
-// programmatic predecessor the wait returns at once.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 __device__ __forceinline__ void kind_range(const DevMesh &d, const PhaseDesc &p, int kind, int &beg,
                                            int &end) {
@@ -1784,50 +1815,6 @@ int launch_flux_batch(const double *WL, const double *WR, const double *nrm, int
 // ================================================================ hosts ==
 void init_device_info() { num_sms(); }
 
-int launch_assign_levels(const DevMesh &d, int L, int *cnt_scratch, ProfHook *ph, cudaStream_t s) {
-  int g = grid_for(d.N, 256, 8);
-  ProfScope scope(ph, FV_PROF_LEVELS, s);
-  k_init_min2<<<1, 1, 0, s>>>(d.dtmin_bits, d.dthi_bits);
-  k_dt32<<<g, 256, 0, s>>>(d);
-  k_dt_min_exact<<<g, 256, 0, s>>>(d);
-  k_levels0_certified<<<g, 256, 0, s>>>(d);
-  // L-1 Jacobi sweeps between lev_tmp and lev; the result must land in lev
-  const int8_t *src = d.lev_tmp;
-  int8_t *dst = d.lev;
-  if (L == 1) {
-    cudaMemcpyAsync(d.lev, d.lev_tmp, d.N, cudaMemcpyDeviceToDevice, s);
-  } else {
-    // with an even number of sweeps, start with a copy so the last one writes lev
-    if ((L - 1) % 2 == 0) {
-      cudaMemcpyAsync(d.lev, d.lev_tmp, d.N, cudaMemcpyDeviceToDevice, s);
-      src = d.lev;
-      dst = d.lev_tmp;
-    }
-    for (int sw = 0; sw < L - 1; ++sw) {
-      k_smooth<<<g, 256, 0, s>>>(d, src, dst);
-      const int8_t *t = dst;
-      dst = (int8_t *)src;
-      src = t;
-    }
-  }
-  FV_LAUNCH_CHECK();
-  // cell keys and sort (2L buckets)
-  k_cell_keys<<<g, 256, 0, s>>>(d);
-  int nblk = (d.N + SORT_TILE - 1) / SORT_TILE;
-  k_sort_hist<<<nblk, SORT_THREADS, 0, s>>>(d.ckey, d.N, 2 * L, cnt_scratch);
-  k_sort_scan<<<1, 1024, 0, s>>>(cnt_scratch, 2 * L * nblk, nblk, 2 * L, d.coff);
-  k_sort_scatter<<<nblk, SORT_THREADS, 0, s>>>(d.ckey, d.N, 2 * L, cnt_scratch, d.cl);
-  // faces (L buckets)
-  int gf = grid_for(d.F, 256, 8);
-  k_face_keys<<<gf, 256, 0, s>>>(d);
-  int nblkf = (d.F + SORT_TILE - 1) / SORT_TILE;
-  k_sort_hist<<<nblkf, SORT_THREADS, 0, s>>>(d.fkey, d.F, L, cnt_scratch);
-  k_sort_scan<<<1, 1024, 0, s>>>(cnt_scratch, L * nblkf, nblkf, L, d.foff);
-  k_sort_scatter<<<nblkf, SORT_THREADS, 0, s>>>(d.fkey, d.F, L, cnt_scratch, d.fl);
-  FV_LAUNCH_CHECK();
-  return FV_OK;
-}
-
 // launch with a programmatic dependency on the previous kernel of the stream
 template <typename... KArgs, typename... Args>
 static void launch_pdl(void (*kernel)(KArgs...), int grid, int block, cudaStream_t s, Args... args) {
@@ -1841,6 +1828,43 @@ static void launch_pdl(void (*kernel)(KArgs...), int grid, int block, cudaStream
   cfg.attrs = &attr;
   cfg.numAttrs = 1;
   cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+int launch_assign_levels(const DevMesh &d, int L, int *cnt_scratch, ProfHook *ph, cudaStream_t s) {
+  (void)cnt_scratch;  // d.sort_cnt
+  int g = grid_for(d.N, 256, 8);
+  ProfScope scope(ph, FV_PROF_LEVELS, s);
+  launch_pdl(k_init_min2, 1, 1, s, d.dtmin_bits, d.dthi_bits);
+  launch_pdl(k_dt32, g, 256, s, d);
+  launch_pdl(k_dt_min_exact, g, 256, s, d);
+  launch_pdl(k_levels0_certified, g, 256, s, d);
+  // L-1 Jacobi sweeps between lev_tmp and lev; the result must land in lev
+  const int8_t *src = d.lev_tmp;
+  int8_t *dst = d.lev;
+  if (L == 1) {
+    cudaMemcpyAsync(d.lev, d.lev_tmp, d.N, cudaMemcpyDeviceToDevice, s);
+  } else {
+    // with an even number of sweeps, start with a copy so the last one writes lev
+    if ((L - 1) % 2 == 0) {
+      cudaMemcpyAsync(d.lev, d.lev_tmp, d.N, cudaMemcpyDeviceToDevice, s);
+      src = d.lev;
+      dst = d.lev_tmp;
+    }
+    for (int sw = 0; sw < L - 1; ++sw) {
+      launch_pdl(k_smooth, g, 256, s, d, src, dst);
+      const int8_t *t = dst;
+      dst = (int8_t *)src;
+      src = t;
+    }
+  }
+  FV_LAUNCH_CHECK();
+  // cell keys (2L buckets) and face keys (L buckets), sorted together
+  const int nc = (d.N + SORT_TILE - 1) / SORT_TILE, nf = (d.F + SORT_TILE - 1) / SORT_TILE;
+  launch_pdl(k_keys_hist, nc + nf, SORT_THREADS, s, d, nc, nf);
+  launch_pdl(k_sort_scan2, 2, 1024, s, d, nc, nf);
+  launch_pdl(k_sort_scatter2, nc + nf, SORT_THREADS, s, d, nc, nf);
+  FV_LAUNCH_CHECK();
+  return FV_OK;
 }
 
 template <typename T, bool G14>
