@@ -18,6 +18,13 @@
  *     levels taken at the right time by linear interpolation in time
  *     ("repositioning / interpolation"); a coarse cell takes the time
  *     integral of the fine-side fluxes across a level interface.
+ *   - Two orders of the level steps within a cycle: order 0 ends each level's
+ *     step when its time is reached, finest first, the coarse cell taking the
+ *     fine-side integrals across an interface at once; order 1 is the order
+ *     of Alg. 2's loops (every level that begins at subiteration s is
+ *     predicted and corrected in it, coarsest first, and its interface
+ *     integrals are corrected when its next step begins -- Alg. 2's
+ *     intensive correction; Alg. 3's extra subiteration applies the last).
  * Scheme choices the paper leaves open (the same on the CUDA path):
  *   least-squares gradients of primitives, MUSCL reconstruction with the
  *   minmod limiter, the exact Godunov Riemann solver (Toro, "Riemann Solvers
@@ -84,6 +91,8 @@ typedef struct orc {
   unsigned char *mark;
   double t, dtmin;
   int have_levels; /* 1 inside a cycle (levels assigned) */
+  int order;       /* 0: corrector of the finest level first, at the end of its
+                     step; 1: the paper's order (see phase_at_paper) */
   int next_phase;  /* index of the next phase inside the cycle */
   int64_t tn[ORC_MAXL]; /* step start of each level, in Delta t units */
   int pred[ORC_MAXL];   /* 1 while U* of that level is valid */
@@ -848,6 +857,55 @@ static phase_t phase_at(int theta, int idx) {
   return ph;
 }
 
+/* Order 1, the order of Alg. 2's subiteration loop (Sec. 2.2).  Subiteration
+ * s with tau = tau(s) and T0 = s - 1:
+ *   - if s > 1, commit(tau, T0): the levels <= tau, whose steps end at T0,
+ *     take their end states with the intensive correction of Alg. 2 -- the
+ *     provisional integral of each face to a finer neighbour is replaced by
+ *     the integral the finer cells accumulated over the step;
+ *   - begin(tau, T0), the predictor of the levels <= tau (as in order 0);
+ *   - for tau' = tau down to 0, correct(tau', T0 + 2^tau'): the corrector of
+ *     level tau' at the end of its step, computed before the finer levels
+ *     have advanced: finer neighbours enter its gradients extrapolated
+ *     linearly in time from U^n and U* (Alg. 2's repositioning), and each
+ *     face to a finer neighbour enters with the provisional integral
+ *     dt_k F1 A; the result is the level's provisional end state.
+ * After the last subiteration, commit(theta, 2^theta) -- the extra pass of
+ * Alg. 3's loop over 2^theta + 1 subiterations.  The paper does not say
+ * which provisional interface flux its coarse corrector uses; the predictor
+ * flux F1 is the reading taken here.  Kinds: 0 begin, 2 correct, 3 commit. */
+static int n_phases_paper(int theta) { return 4 * (1 << theta) - 1; }
+
+static phase_t phase_at_paper(int theta, int idx) {
+  phase_t ph = {3, theta, (int64_t)1 << theta};
+  int nsub = 1 << theta;
+  for (int s = 1; s <= nsub; ++s) {
+    int tau = 0;
+    for (int tmp = 1; tmp <= theta; ++tmp)
+      if (((s - 1) % (1 << tmp)) == 0) tau = tmp;
+    if (s > 1) {
+      if (idx == 0) {
+        ph.kind = 3; ph.level = tau; ph.T = s - 1;
+        return ph;
+      }
+      --idx;
+    }
+    if (idx == 0) {
+      ph.kind = 0; ph.level = tau; ph.T = s - 1;
+      return ph;
+    }
+    --idx;
+    for (int k = tau; k >= 0; --k) {
+      if (idx == 0) {
+        ph.kind = 2; ph.level = k; ph.T = (s - 1) + ((int64_t)1 << k);
+        return ph;
+      }
+      --idx;
+    }
+  }
+  return ph; /* the final commit */
+}
+
 /* Begin(s): every level <= tau starts a step at T: fluxes F1 on every face
  * of face-level <= tau, then the predictor U* = U^n + dt_k R(U^n). */
 static int phase_begin(orc *o, int tau, int64_t T) {
@@ -978,20 +1036,150 @@ static int phase_end(orc *o, int k, int64_t T) {
   return ORC_OK;
 }
 
+/* Order 1: the corrector of level k computed at the end T of its step
+ * (see phase_at_paper).  Fluxes F2 and Phi = dt_k (F1 + F2)/2 A on the
+ * face-level-k faces exactly as in phase_end; the cells of level k get the
+ * provisional end state U^n - sum sigma phi / V in Us, where phi is Phi on
+ * their own-level faces (and faces to coarser neighbours) and dt_k F1 A on
+ * faces to finer neighbours, whose accumulator starts at minus that value. */
+static int phase_correct(orc *o, int k, int64_t T) {
+  compute_W(o, T);
+  memset(o->mark, 0, o->nc);
+  for (int64_t f = 0; f < o->nf; ++f)
+    if (o->flev[f] == k) {
+      o->mark[o->fown[f]] = 1;
+      if (o->fnb[f] >= 0) o->mark[o->fnb[f]] = 1;
+    }
+  compute_gradients_marked(o);
+  double dtk = ldexp(o->dtmin, k);
+  int err = 0;
+  int64_t iters = 0, calls = 0, cnt = 0;
+#pragma omp parallel for schedule(static) reduction(| : err) reduction(+ : iters, calls, cnt)
+  for (int64_t f = 0; f < o->nf; ++f)
+    if (o->flev[f] == k) {
+      double F2A[5];
+      int it = 0;
+      if (face_flux_A(o, f, F2A, &it)) {
+        err |= 1;
+        continue;
+      }
+      iters += it;
+      calls += 1;
+      cnt += 1;
+      int interface = o->fnb[f] >= 0 && o->lev[o->fown[f]] != o->lev[o->fnb[f]];
+      for (int c = 0; c < 5; ++c) {
+        double phi = dtk * (0.5 * (o->F1A[5 * f + c] + F2A[c]));
+        o->F1A[5 * f + c] = phi;
+        if (interface) o->ACC[5 * f + c] += phi;
+        if (o->fnb[f] < 0) o->BND[5 * f + c] += phi;
+      }
+    }
+  o->newton_iters += iters;
+  o->riemann_calls += calls;
+  o->n_faceevals[k] += cnt;
+  if (err) {
+    set_msg("Riemann solver failed (vacuum or no convergence)");
+    return ORC_ERIEMANN;
+  }
+  int64_t upd = 0;
+#pragma omp parallel for schedule(static) reduction(| : err) reduction(+ : upd)
+  for (int64_t i = 0; i < o->nc; ++i) {
+    if (o->lev[i] != k) continue;
+    double S[5] = {0, 0, 0, 0, 0};
+    for (int j = 0; j < 4; ++j) {
+      int64_t f = o->cface[4 * i + j];
+      double s = o->csgn[4 * i + j];
+      if (o->flev[f] == k) {
+        for (int c = 0; c < 5; ++c) S[c] += s * o->F1A[5 * f + c];
+      } else { /* a finer neighbour: provisional integral from the predictor flux */
+        for (int c = 0; c < 5; ++c) {
+          double prov = dtk * o->F1A[5 * f + c];
+          S[c] += s * prov;
+          o->ACC[5 * f + c] -= prov;
+        }
+      }
+    }
+    for (int c = 0; c < 5; ++c) o->Us[5 * i + c] = o->U[5 * i + c] - S[c] / o->vol[i];
+    if (!check_state(o, o->Us, i)) err |= 1;
+    upd += 1;
+  }
+  o->n_updates[k] += upd;
+  if (err) {
+    set_msg("non-physical corrected state");
+    return ORC_ENONPHYS;
+  }
+  return ORC_OK;
+}
+
+/* Order 1: the levels <= tau end their steps at T (Alg. 2's intensive
+ * correction): U^{n+1} = Us - sum sigma ACC / V over the faces to finer
+ * neighbours (ACC = the finer side's integral minus the provisional one),
+ * which are then reset; a cell without finer neighbours takes Us as it is. */
+static int phase_commit(orc *o, int tau, int64_t T) {
+  int err = 0;
+#pragma omp parallel for schedule(static) reduction(| : err)
+  for (int64_t i = 0; i < o->nc; ++i) {
+    int k = o->lev[i];
+    if (k > tau) continue;
+    int any = 0;
+    double S[5] = {0, 0, 0, 0, 0};
+    for (int j = 0; j < 4; ++j) {
+      int64_t f = o->cface[4 * i + j];
+      if (o->flev[f] >= k) continue;
+      double s = o->csgn[4 * i + j];
+      for (int c = 0; c < 5; ++c) S[c] += s * o->ACC[5 * f + c];
+      any = 1;
+    }
+    for (int j = 0; j < 4; ++j) {
+      int64_t f = o->cface[4 * i + j];
+      if (o->flev[f] < k)
+        for (int c = 0; c < 5; ++c) o->ACC[5 * f + c] = 0.0;
+    }
+    for (int c = 0; c < 5; ++c)
+      o->U[5 * i + c] = any ? o->Us[5 * i + c] - S[c] / o->vol[i] : o->Us[5 * i + c];
+    if (!check_state(o, o->U, i)) err |= 1;
+  }
+  for (int k = 0; k <= tau; ++k) {
+    o->tn[k] = T;
+    o->pred[k] = 0;
+  }
+  if (err) {
+    set_msg("non-physical corrected state");
+    return ORC_ENONPHYS;
+  }
+  return ORC_OK;
+}
+
+static int phases_per_cycle(const orc *o) {
+  return o->order == 1 ? n_phases_paper(o->theta) : n_phases(o->theta);
+}
+
+int orc_set_order(orc *o, int order) {
+  if ((order != 0 && order != 1) || (o->have_levels && o->next_phase > 0)) {
+    set_msg("orc_set_order: order 0 or 1, between cycles");
+    return ORC_EINVAL;
+  }
+  o->order = order;
+  return ORC_OK;
+}
+
 /* run n phases of the current cycle (levels must be assigned) */
 int orc_run_phases(orc *o, int n) {
   if (!o->have_levels) {
     set_msg("orc_run_phases: levels not assigned");
     return ORC_EINVAL;
   }
-  int total = n_phases(o->theta);
+  int total = phases_per_cycle(o);
   for (int q = 0; q < n; ++q) {
     if (o->next_phase >= total) {
       set_msg("orc_run_phases: past the end of the cycle");
       return ORC_EINVAL;
     }
-    phase_t ph = phase_at(o->theta, o->next_phase);
-    int rc = ph.kind == 0 ? phase_begin(o, ph.level, ph.T) : phase_end(o, ph.level, ph.T);
+    phase_t ph = o->order == 1 ? phase_at_paper(o->theta, o->next_phase) : phase_at(o->theta, o->next_phase);
+    int rc = ph.kind == 0   ? phase_begin(o, ph.level, ph.T)
+             : ph.kind == 1 ? phase_end(o, ph.level, ph.T)
+             : ph.kind == 2 ? phase_correct(o, ph.level, ph.T)
+                            : phase_commit(o, ph.level, ph.T);
     if (rc) return rc;
     o->next_phase++;
     if (o->next_phase == total) { /* cycle complete */
@@ -1003,7 +1191,7 @@ int orc_run_phases(orc *o, int n) {
   return ORC_OK;
 }
 
-int orc_phases_per_cycle(const orc *o) { return n_phases(o->theta); }
+int orc_phases_per_cycle(const orc *o) { return phases_per_cycle(o); }
 
 int orc_advance(orc *o, int n_cycles, double *t_out) {
   for (int c = 0; c < n_cycles; ++c) {
@@ -1012,7 +1200,7 @@ int orc_advance(orc *o, int n_cycles, double *t_out) {
       rc = orc_assign_levels(o, NULL, NULL, NULL);
       if (rc) return rc;
     }
-    rc = orc_run_phases(o, n_phases(o->theta) - o->next_phase);
+    rc = orc_run_phases(o, phases_per_cycle(o) - o->next_phase);
     if (rc) return rc;
   }
   if (t_out) *t_out = o->t;
@@ -1237,10 +1425,13 @@ int orc_num_threads(void) {
 }
 
 /* the phase list of one cycle, for schedule checks: kind 0 = begin of the
- * levels 0..level, kind 1 = end of the step of `level`; T in Delta t units */
-int orc_phase_info(int theta, int idx, int *kind, int *level, int64_t *T) {
-  if (theta < 0 || theta >= ORC_MAXL || idx < 0 || idx >= n_phases(theta)) return ORC_EINVAL;
-  phase_t ph = phase_at(theta, idx);
+ * levels 0..level, 1 = end of the step of `level` (order 0), 2 = corrector
+ * of `level`, 3 = commit of the levels 0..level (order 1); T in Delta t
+ * units from the cycle start */
+int orc_phase_info(int theta, int order, int idx, int *kind, int *level, int64_t *T) {
+  const int n = order == 1 ? n_phases_paper(theta) : n_phases(theta);
+  if (theta < 0 || theta >= ORC_MAXL || (order != 0 && order != 1) || idx < 0 || idx >= n) return ORC_EINVAL;
+  phase_t ph = order == 1 ? phase_at_paper(theta, idx) : phase_at(theta, idx);
   *kind = ph.kind;
   *level = ph.level;
   *T = ph.T;

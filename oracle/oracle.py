@@ -50,6 +50,7 @@ def lib():
         L.orc_get_levels.argtypes = [vp, i8p]
         L.orc_run_phases.argtypes = [vp, C.c_int]
         L.orc_phases_per_cycle.argtypes = [vp]
+        L.orc_set_order.argtypes = [vp, C.c_int]
         L.orc_advance.argtypes = [vp, C.c_int, dp]
         L.orc_residual_level.argtypes = [vp, C.c_int, C.c_int, dp]
         L.orc_global_step.argtypes = [vp, C.c_double]
@@ -64,7 +65,7 @@ def lib():
         L.orc_muscl_pair.argtypes = [dp] * 7
         L.orc_boundary_flux.argtypes = [C.c_double, C.c_int, dp, dp, C.c_double, C.c_int, dp]
         L.orc_num_threads.restype = C.c_int
-        L.orc_phase_info.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+        L.orc_phase_info.argtypes = [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                      C.POINTER(C.c_int64)]
         L.orc_set_threads.argtypes = [C.c_int]
         fp = C.POINTER(C.c_float)
@@ -197,6 +198,13 @@ class Oracle:
     def phases_per_cycle(self):
         return int(lib().orc_phases_per_cycle(self.h))
 
+    def set_order(self, order):
+        """0: each level's corrector when its step ends, finest first (the
+        default); 1: the order of Alg. 2's loops, coarsest first within a
+        subiteration, with the intensive correction deferred to the level's
+        next step (fv_oracle.c, phase_at_paper).  Between cycles only."""
+        _check(lib().orc_set_order(self.h, int(order)), "orc_set_order")
+
     def run_phases(self, n):
         _check(lib().orc_run_phases(self.h, int(n)), "orc_run_phases")
 
@@ -296,14 +304,16 @@ def set_threads(n):
     lib().orc_set_threads(int(n))
 
 
-def phase_list(theta):
+def phase_list(theta, order=0):
     """The phases of one cycle: list of (kind, level, T); kind 'B' begins
-    levels 0..level at T, kind 'E' ends the step of `level` at T."""
+    levels 0..level at T, 'E' ends the step of `level` at T (order 0), 'C'
+    corrects `level` at the end T of its step and 'I' commits the levels
+    0..level at T (order 1, Oracle.set_order)."""
     out = []
     idx = 0
     kind, level, T = C.c_int(), C.c_int(), C.c_int64()
-    while lib().orc_phase_info(int(theta), idx, C.byref(kind), C.byref(level), C.byref(T)) == 0:
-        out.append(("B" if kind.value == 0 else "E", level.value, T.value))
+    while lib().orc_phase_info(int(theta), int(order), idx, C.byref(kind), C.byref(level), C.byref(T)) == 0:
+        out.append(("BECI"[kind.value], level.value, T.value))
         idx += 1
     return out
 

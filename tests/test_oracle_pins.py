@@ -432,3 +432,143 @@ def test_residual_stage1_matches_predictor(oracle_mod):
     o.run_phases(3)                        # E(1,0), B(2), E(2,0)
     R2 = o.residual_level(1, 2)            # level 1 ends at T = 2
     assert np.isfinite(R2).all() and np.abs(R2[:, lev == 1]).max() > 0
+
+
+# ------------------------------------------- the paper's order (Alg. 2 loops)
+def _alg2_paper_order(theta):
+    """Alg. 2's loops as the paper prints them, step by step: for every
+    subiteration, tau from the loop over tmp; the intensive correction of
+    {0..tau} when subiteration > 1; the predictor of {0..tau}; then the
+    corrector of tau' = tau down to 0.  Alg. 3 adds one subiteration, whose
+    only work left is the last intensive correction, of every level."""
+    out = []
+    for sub in range(1, 2 ** theta + 1):
+        tau = 0
+        for tmp in range(1, theta + 1):
+            if (sub - 1) % 2 ** tmp == 0:
+                tau = tmp
+        if sub > 1:
+            out.append(("I", tau, sub - 1))
+        out.append(("B", tau, sub - 1))
+        for tp in range(tau, -1, -1):
+            out.append(("C", tp, sub - 1 + 2 ** tp))
+    out.append(("I", theta, 2 ** theta))
+    return out
+
+
+def test_paper_order_schedule_follows_alg2_loops(oracle_mod):
+    want = [int(x) for x in read_golden("schedule_theta3.txt")[0].split()]
+    for theta in range(6):
+        ph = oracle_mod.phase_list(theta, order=1)
+        assert ph == _alg2_paper_order(theta)
+        assert len(ph) == 4 * 2 ** theta - 1
+        # C(tau) = 2^(theta - tau): level k is corrected 2^(theta-k) times,
+        # each time at the end of a step that began at a multiple of 2^k,
+        # and committed exactly when that step's end time is reached
+        for k in range(theta + 1):
+            ends = [T for kind, lvl, T in ph if kind == "C" and lvl == k]
+            assert ends == [2 ** k * (j + 1) for j in range(2 ** (theta - k))]
+            commits = [T for kind, lvl, T in ph if kind == "I" and lvl >= k]
+            assert commits == ends
+    assert [lvl for kind, lvl, _ in oracle_mod.phase_list(3, order=1) if kind == "B"] == want
+
+
+def test_paper_order_single_level_equals_global_stepping_bitwise(oracle_mod):
+    """With one level the two orders are the same Heun step."""
+    mesh, prim = I.blast_case(n=7, ratio=4.0)
+    a = oracle_mod.Oracle(mesh, max_levels=1)
+    a.set_prim(prim)
+    a.set_order(1)
+    g = oracle_mod.Oracle(mesh, max_levels=1)
+    g.set_prim(prim)
+    for _ in range(3):
+        dt, _, _ = a.assign_levels()
+        a.advance(1)
+        g.global_step(dt)
+    assert np.array_equal(a.get_cons(), g.get_cons())
+
+
+@pytest.mark.parametrize("L", [2, 4])
+def test_paper_order_conservation_ledger(oracle_mod, L):
+    """The deferred intensive correction replaces every provisional
+    interface integral by the finer side's: totals are conserved to
+    round-off."""
+    mesh, prim = I.blast_case(n=10, ratio=8.0)
+    o = oracle_mod.Oracle(mesh, max_levels=L)
+    o.set_prim(prim)
+    o.set_order(1)
+    vol, _ = o.cell_geometry()
+    M0 = (o.get_cons() * vol).sum(axis=1)
+    o.advance(3)
+    M1 = (o.get_cons() * vol).sum(axis=1)
+    led = o.boundary_ledger()
+    scale = np.abs(o.get_cons() * vol).sum(axis=1).max()
+    assert np.abs(M1 - M0 + led).max() <= 1e-14 * scale
+    assert led[0] == 0.0 and led[4] == 0.0
+
+
+def test_paper_order_free_stream_preserved(oracle_mod):
+    mesh, prim = I.uniform_flow_case(n=6)
+    o = oracle_mod.Oracle(mesh, max_levels=3)
+    o.set_prim(prim)
+    o.set_order(1)
+    U0 = o.get_cons()
+    o.advance(3)
+    rel = np.abs(o.get_cons() - U0).max(axis=1) / np.abs(U0).max(axis=1)
+    assert rel.max() <= 1e-13
+
+
+def test_paper_order_time_consistency(oracle_mod):
+    """As test_time_interpolation_is_consistent, for the paper's order: one
+    cycle and the same time in global steps of dt_min approach each other
+    faster than first order as the CFL number halves, although the coarse
+    corrector sees its finer neighbours only extrapolated in time and its
+    interface integrals only provisionally."""
+    rng = np.random.default_rng(5)
+    x = I.graded_coords(12, 6.0)
+    mesh = I.box_tet_mesh(x, x, x, jitter=0.1, rng=rng,
+                          bc_planes={k: 2 for k in ("x0", "x1", "y0", "y1", "z0", "z1")})
+    c = mesh.centroids()
+    s = 0.3 * c[:, 0] + 0.2 * c[:, 0] ** 2 + 0.1 * c[:, 1] + 0.05 * c[:, 2] ** 2
+    prim = np.empty((5, mesh.n_tets))
+    prim[0] = 1.0 + 0.5 * s
+    prim[1], prim[2], prim[3] = 0.4, 0.1, 0.05
+    prim[4] = 1.0 + s
+    rel = []
+    for cfl in (0.4, 0.2, 0.1, 0.05):
+        a = oracle_mod.Oracle(mesh, cfl=cfl, max_levels=3)
+        a.set_prim(prim)
+        a.set_order(1)
+        dt, _, counts = a.assign_levels()
+        assert (counts > 0).all()
+        U0 = a.get_cons()
+        a.advance(1)
+        g = oracle_mod.Oracle(mesh, cfl=cfl, max_levels=1)
+        g.set_prim(prim)
+        for _ in range(4):
+            g.global_step(dt)
+        rel.append(np.abs(a.get_cons() - g.get_cons()).max() / np.abs(g.get_cons() - U0).max())
+    ratios = [rel[i] / rel[i + 1] for i in range(3)]
+    assert math.prod(ratios) ** (1 / 3) > 2.3, ratios
+
+
+def test_paper_order_differs_from_finest_first_by_the_interface_treatment(oracle_mod):
+    """Same levels, a different scheme at level interfaces: the two orders
+    agree to well under the blast's own change per cycle, yet not to
+    round-off."""
+    mesh, prim = I.blast_case(n=10, ratio=8.0)
+    a = oracle_mod.Oracle(mesh, max_levels=4)
+    b = oracle_mod.Oracle(mesh, max_levels=4)
+    for o in (a, b):
+        o.set_prim(prim)
+    b.set_order(1)
+    U0 = a.get_cons()
+    for _ in range(2):
+        a.advance(1)
+        b.advance(1)
+        np.testing.assert_array_equal(a.levels(), b.levels())
+    Ua, Ub = a.get_cons(), b.get_cons()
+    diff = np.abs(Ua - Ub).max(axis=1)
+    change = np.abs(Ua - U0).max(axis=1)
+    assert (diff > 1e-9 * np.abs(Ua).max(axis=1)).any()
+    assert (diff <= 0.1 * change).all(), (diff, change)
