@@ -486,6 +486,35 @@ def main_ours(args):
         persistent = time_cycles(fv, torch, chosen["g"], prim, stream, flush)
         chosen["g"].use_persistent(False)
         persistent["vs_graph"] = round(persistent["value"] / chosen["value"], 4)
+    # the paper's order of the level steps (Alg. 2's loops, the coarse
+    # corrector first and the intensive correction of its interface
+    # integrals at its next step) on the same mesh and graph: cost per cycle,
+    # and how far its state is from the finest-first order's after the same
+    # cycles from the same initial state
+    paper_order = None
+    if chosen["g"] is not None:
+        g = chosen["g"]
+        small = g.n <= 4_000_000
+        if small:
+            g.set_state(prim)
+            for _ in range(8):
+                g.advance(1, stream=stream, want_time=False)
+            torch.cuda.synchronize()
+            U_ff = g.get_state()
+        g.set_order(fv.FV_ORDER_PAPER)
+        paper_order = time_cycles(fv, torch, g, prim, stream, flush, cycles=5, warmup=3)
+        paper_order["vs_finest_first"] = round(paper_order["value"] / chosen["value"], 4)
+        if small:
+            U_po = g.get_state()
+            mom = np.sqrt((U_ff[1:4] ** 2).sum(axis=0)).max()
+            sc = np.array([np.abs(U_ff[0]).max(), mom, mom, mom, np.abs(U_ff[4]).max()])
+            paper_order["state_rel_diff_after_8_cycles"] = float(
+                (np.abs(U_po - U_ff).max(axis=1) / sc).max())
+        g.set_order(fv.FV_ORDER_FINEST_FIRST)
+        paper_order["what"] = ("FV_ORDER_PAPER: Alg. 2's order (every level that begins at a "
+                               "subiteration predicted and corrected in it, coarsest first; "
+                               "interface integrals corrected when its next step begins), same "
+                               "mesh, precision, graph and timing as the line's value")
     e2e = None if args.no_e2e else run_e2e(fv, torch, chosen["g"], max(3, min(args.steps, 10)), 1,
                                            stream)
 
@@ -586,6 +615,7 @@ def main_ours(args):
             "autotuned_blocks_per_sm": {"prim_grad_flux_update": chosen["launch_per_sm"],
                                         "cached": chosen["autotune_cached"]},
             "persistent_cycle": persistent,
+            "paper_order": paper_order,
             "level_history": chosen["level_history"],
             "cell_updates_per_step": chosen["cell_updates"] / args.steps,
             "face_evals_per_step": chosen["face_evals"] / args.steps,

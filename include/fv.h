@@ -175,15 +175,43 @@ int fv_residual_level(fv_mesh *m, int level, int stage, double *R_soa_dev, void 
 
 /*
  * Runs the next n_phases phases of the current cycle.  The phases of one
- * cycle, for s = 1..2^(L-1): B(s) starts levels 0..tau(s) (the subiteration loop of Alg. 2:
- * predictor fluxes on faces of level <= tau, U* of those cells), then
- * E(s,k) for k = 0,1,.. while s mod 2^k == 0 (corrector fluxes on faces of
- * level k, flux time integrals, U^{n+1} of level-k cells).  3 * 2^(L-1) - 1
- * phases in all; completing the last one ends the cycle (time advances by
- * 2^(L-1) dt_min).  A pause/resume hook for phase-by-phase checks.
- * Errors: FV_ERR_INVALID_ARG (no active cycle, or past its end).
+ * cycle in FV_ORDER_FINEST_FIRST, for s = 1..2^(L-1): B(s) starts levels
+ * 0..tau(s) (the subiteration loop of Alg. 2: predictor fluxes on faces of
+ * level <= tau, U* of those cells), then E(s,k) for k = 0,1,.. while
+ * s mod 2^k == 0 (corrector fluxes on faces of level k, flux time integrals,
+ * U^{n+1} of level-k cells): 3 * 2^(L-1) - 1 phases.  In FV_ORDER_PAPER
+ * (fv_set_order): for s > 1 the commit of levels 0..tau(s), B(s), then the
+ * correctors of tau' = tau(s) down to 0, and a final commit of every level:
+ * 4 * 2^(L-1) - 1 phases.  Completing the last phase ends the cycle (time
+ * advances by 2^(L-1) dt_min).  A pause/resume hook for phase-by-phase
+ * checks.  Errors: FV_ERR_INVALID_ARG (no active cycle, or past its end).
  */
 int fv_advance_phases(fv_mesh *m, int n_phases, void *stream);
+
+/*
+ * The order of the level steps inside a cycle (Alg. 2, Sec. 2.2).
+ * FV_ORDER_FINEST_FIRST (the default): a level's corrector runs when its
+ * step's end time is reached, finest level first, and a coarse cell takes
+ * the finer side's accumulated integral on each face to a finer neighbour
+ * at once.  FV_ORDER_PAPER: the order of Alg. 2's loops -- every level that
+ * begins a step at subiteration s is predicted, then corrected coarsest
+ * first at the end time of its step, before the finer levels advance: finer
+ * neighbours enter its gradients extrapolated linearly in time, each face
+ * to a finer neighbour enters with the provisional integral dt_k F1 A, and
+ * when the level's next step begins (Alg. 2's "intensive correction"; Alg.
+ * 3's extra subiteration for the last one) the provisional integrals are
+ * replaced by the finer side's.  Both conserve mass, momentum and energy
+ * exactly and coincide with one level.  FV_ORDER_PAPER needs 5 doubles per
+ * cell more in the FP32-flux mode; batches, the persistent cycle and
+ * fv_residual_level take FV_ORDER_FINEST_FIRST only (the persistent cycle
+ * falls back to the graph path).  Between cycles only; drops a captured
+ * graph.  Errors: FV_ERR_INVALID_ARG (bad order, inside a cycle or a batch),
+ * FV_ERR_NOMEM.
+ */
+#define FV_ORDER_FINEST_FIRST 0
+#define FV_ORDER_PAPER 1
+int fv_set_order(fv_mesh *m, int order);
+int fv_get_order(fv_mesh *m, int *order_out);
 
 /*
  * Advances n_cycles complete cycles (Alg. 2), each starting with level

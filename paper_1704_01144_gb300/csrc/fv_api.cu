@@ -123,7 +123,8 @@ int persistent_tables(fv_mesh *m) {
 }
 
 bool persistent_on(const fv_mesh *m) {
-  return m->use_persistent && !m->prof.on && m->d.guess == FV_GUESS_TWO_RAREFACTION;
+  return m->use_persistent && !m->prof.on && m->d.guess == FV_GUESS_TWO_RAREFACTION &&
+         m->order == FV_ORDER_FINEST_FIRST;
 }
 
 // a whole cycle: level assignment, every phase in one cooperative launch,
@@ -497,6 +498,8 @@ int fv_get_level_lists(fv_mesh *m, int64_t *cells_out, int32_t *cell_off_out,
 int fv_residual_level(fv_mesh *m, int level, int stage, double *R_soa_dev, void *stream) {
   if (!m || !R_soa_dev) return fail(FV_ERR_INVALID_ARG, "fv_residual_level: NULL argument");
   if (!m->in_cycle) return fail(FV_ERR_INVALID_ARG, "fv_residual_level: no active cycle");
+  if (m->order != FV_ORDER_FINEST_FIRST)
+    return fail(FV_ERR_INVALID_ARG, "fv_residual_level: defined for FV_ORDER_FINEST_FIRST");
   if (level < 0 || level >= m->L || (stage != 1 && stage != 2))
     return fail(FV_ERR_INVALID_ARG, "fv_residual_level: bad level or stage");
   if (stage == 2 && !m->pred[level])
@@ -603,6 +606,34 @@ int fv_set_launch(fv_mesh *m, const int32_t per_sm[4]) {
 int fv_get_launch(fv_mesh *m, int32_t per_sm[4]) {
   if (!m || !per_sm) return fail(FV_ERR_INVALID_ARG, "fv_get_launch: NULL argument");
   for (int k = 0; k < 4; ++k) per_sm[k] = m->launch.per_sm[k];
+  return FV_OK;
+}
+
+int fv_set_order(fv_mesh *m, int order) {
+  if (!m || (order != FV_ORDER_FINEST_FIRST && order != FV_ORDER_PAPER))
+    return fail(FV_ERR_INVALID_ARG, "fv_set_order: bad argument");
+  if (m->in_batch || (m->in_cycle && m->next_phase > 0))
+    return fail(FV_ERR_INVALID_ARG, "fv_set_order: mesh is inside a cycle or a batch");
+  if (order == m->order) return FV_OK;
+  CK(cudaSetDevice(m->cfg.device));
+  if (order == FV_ORDER_PAPER && m->d.precision == FV_FP32_FLUX && !m->d.UsD) {
+    int rc = dalloc(m, &m->d.UsD, 5 * (size_t)m->d.N);
+    if (rc) return rc;
+  }
+  m->order = order;
+  m->phases = make_phases(m->theta, order);
+  m->in_cycle = false;
+  m->next_phase = 0;
+  if (m->cycle_graph) {
+    cudaGraphExecDestroy(m->cycle_graph);
+    m->cycle_graph = nullptr;
+  }
+  return FV_OK;
+}
+
+int fv_get_order(fv_mesh *m, int *order_out) {
+  if (!m || !order_out) return fail(FV_ERR_INVALID_ARG, "fv_get_order: NULL argument");
+  *order_out = m->order;
   return FV_OK;
 }
 

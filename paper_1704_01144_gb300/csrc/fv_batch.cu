@@ -119,6 +119,8 @@ int fv_batch_create(fv_mesh *const *meshes, int n, fv_batch **out) {
                    "fv_batch_create: meshes must share device, precision, gamma and Newton settings");
     if (m->d.guess != FV_GUESS_TWO_RAREFACTION)
       return bfail(FV_ERR_INVALID_ARG, "fv_batch_create: batches use the two-rarefaction guess");
+    if (m->order != FV_ORDER_FINEST_FIRST)
+      return bfail(FV_ERR_INVALID_ARG, "fv_batch_create: batches use FV_ORDER_FINEST_FIRST");
   }
   BCK(cudaSetDevice(m0->cfg.device));
   fv_batch *b = new fv_batch();

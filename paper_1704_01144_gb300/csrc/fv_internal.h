@@ -76,6 +76,7 @@ struct DevMesh {
   // state
   double *Un, *Us, *G;  // Us: predicted state (FP64 mode only)
   float *Un32, *Us32;    // FP32-flux mode: FP32 shadow of U^n, predicted state ([N][REC_U32])
+  double *UsD;           // FP32-flux mode, order 1: the provisional end state in FP64 (SoA [5][N])
   float *G32;
   double *FA, *ACC, *BND;
   float *FA32;         // FP32-flux mode: predictor flux x area
@@ -124,7 +125,7 @@ struct PhaseLevels {
 // kernel covers (cells: coff buckets [b0, b1); faces: foff buckets).
 struct PhaseDesc {
   PhaseLevels pl;
-  int stage, level;
+  int stage, level;  // stage 1 begin, 2 end, 3 correct, 4 commit (see phase_desc)
   int pb0, pb1;  // primitives
   int gb0, gb1;  // gradients
   int fb0, fb1;  // faces
@@ -144,29 +145,46 @@ struct LaunchCfg {
 inline LaunchCfg default_launch() { return LaunchCfg{{8, 8, 16, 8}}; }
 
 // ---- host schedule of one cycle (the subiteration loop of Alg. 2) ----
-// kind 0: begin levels 0..level at T; kind 1: end the step of `level` at T
+// kind 0: begin (predict) levels 0..level at T; kind 1: end the step of
+// `level` at T (order 0); kind 2: correct `level` at the end T of its step,
+// giving its provisional end state (order 1); kind 3: commit levels 0..level
+// at T with the deferred interface correction (order 1)
 struct SchedPhase {
   int kind;
   int level;
   int64_t T;  // time in dt_min units from the cycle start
 };
 
-inline std::vector<SchedPhase> make_phases(int theta) {
+// Order 0 (FV_ORDER_FINEST_FIRST): for s = 1..2^theta, B(s) then the ends of
+// the levels k with s mod 2^k == 0, finest first.  Order 1 (FV_ORDER_PAPER):
+// the loops of Alg. 2 -- for s > 1 the commit of levels 0..tau(s) at s - 1,
+// B(s), then the correctors of tau' = tau(s) down to 0 at s - 1 + 2^tau' --
+// and the final commit of every level (the extra subiteration of Alg. 3).
+inline std::vector<SchedPhase> make_phases(int theta, int order = 0) {
   std::vector<SchedPhase> out;
   int nsub = 1 << theta;
   for (int s = 1; s <= nsub; ++s) {
     int tau = 0;
     for (int tmp = 1; tmp <= theta; ++tmp)
       if ((s - 1) % (1 << tmp) == 0) tau = tmp;
-    out.push_back({0, tau, (int64_t)(s - 1)});
-    for (int k = 0; k <= theta && s % (1 << k) == 0; ++k) out.push_back({1, k, (int64_t)s});
+    if (order == 1) {
+      if (s > 1) out.push_back({3, tau, (int64_t)(s - 1)});
+      out.push_back({0, tau, (int64_t)(s - 1)});
+      for (int k = tau; k >= 0; --k) out.push_back({2, k, (int64_t)(s - 1) + ((int64_t)1 << k)});
+    } else {
+      out.push_back({0, tau, (int64_t)(s - 1)});
+      for (int k = 0; k <= theta && s % (1 << k) == 0; ++k) out.push_back({1, k, (int64_t)s});
+    }
   }
+  if (order == 1) out.push_back({3, theta, (int64_t)nsub});
   return out;
 }
 
 // the view of every level at time T from each level's step start tn and
-// whether its predicted state exists
-inline PhaseLevels levels_at(int L, const int64_t *tn, const bool *pred, int64_t T) {
+// whether its predicted (or, order 1, provisional end) state exists; with
+// `extrapolate` (order 1 correctors) a level may be taken up to one step past
+// its predicted state, linearly
+inline PhaseLevels levels_at(int L, const int64_t *tn, const bool *pred, int64_t T, bool extrapolate = false) {
   PhaseLevels pl;
   for (int j = 0; j < FV_MAXL; ++j) {
     pl.w[j] = 0.0;
@@ -174,7 +192,7 @@ inline PhaseLevels levels_at(int L, const int64_t *tn, const bool *pred, int64_t
     if (j >= L) continue;
     int64_t dd = T - tn[j];
     int64_t span = (int64_t)1 << j;
-    if (dd <= 0 || dd > span || !pred[j]) continue;  // U^n (or not needed)
+    if (dd <= 0 || dd > (extrapolate ? 2 * span : span) || !pred[j]) continue;  // U^n (or not needed)
     if (dd == span) {
       pl.mode[j] = 1;
     } else {
@@ -187,16 +205,18 @@ inline PhaseLevels levels_at(int L, const int64_t *tn, const bool *pred, int64_t
 
 // what a phase covers: begin(tau) -> primitives of levels <= tau+2,
 // gradients of levels <= tau plus the level-(tau+1) cells next to level tau,
-// faces of level <= tau, updates of levels <= tau; end(k) -> primitives of
-// levels k-1..k+2, gradients of level k plus the halo of k+1, faces of level
-// k, updates of level k (cell buckets: 2 level + no-finer-neighbour)
+// faces of level <= tau, updates of levels <= tau; end(k) and correct(k) ->
+// primitives of levels k-1..k+2, gradients of level k plus the halo of k+1,
+// faces of level k, updates of level k; commit(tau) -> updates of levels
+// <= tau only (cell buckets: 2 level + no-finer-neighbour).  Stages: 1
+// begin, 2 end, 3 correct, 4 commit.
 inline PhaseDesc phase_desc(int L, const int64_t *tn, const bool *pred, const SchedPhase &ph) {
   const int nb = 2 * L;
   auto cl = [nb](int b) { return b < 0 ? 0 : (b > nb ? nb : b); };
   auto fclip = [L](int b) { return b < 0 ? 0 : (b > L ? L : b); };
   PhaseDesc pd;
   memset(&pd, 0, sizeof pd);
-  pd.pl = levels_at(L, tn, pred, ph.T);
+  pd.pl = levels_at(L, tn, pred, ph.T, ph.kind == 2);
   pd.active = 1;
   pd.level = ph.level;
   if (ph.kind == 0) {
@@ -206,9 +226,12 @@ inline PhaseDesc phase_desc(int L, const int64_t *tn, const bool *pred, const Sc
     pd.gb0 = 0; pd.gb1 = cl(2 * tau + 3);
     pd.fb0 = 0; pd.fb1 = fclip(tau + 1);
     pd.ub0 = 0; pd.ub1 = cl(2 * tau + 2);
+  } else if (ph.kind == 3) {
+    pd.stage = 4;
+    pd.ub0 = 0; pd.ub1 = cl(2 * ph.level + 2);
   } else {
     int k = ph.level;
-    pd.stage = 2;
+    pd.stage = ph.kind == 1 ? 2 : 3;
     pd.pb0 = cl(2 * (k - 1)); pd.pb1 = cl(2 * (k + 3));
     pd.gb0 = cl(2 * k); pd.gb1 = cl(2 * k + 3);
     pd.fb0 = fclip(k); pd.fb1 = fclip(k + 1);
@@ -220,9 +243,14 @@ inline PhaseDesc phase_desc(int L, const int64_t *tn, const bool *pred, const Sc
 inline void phase_apply(int64_t *tn, bool *pred, const SchedPhase &ph) {
   if (ph.kind == 0) {
     for (int j = 0; j <= ph.level; ++j) pred[j] = true;
-  } else {
+  } else if (ph.kind == 1) {
     tn[ph.level] = ph.T;
     pred[ph.level] = false;
+  } else if (ph.kind == 3) {
+    for (int j = 0; j <= ph.level; ++j) {
+      tn[j] = ph.T;
+      pred[j] = false;
+    }
   }
 }
 
@@ -290,6 +318,7 @@ struct fv_mesh {
   double *FAt = nullptr;       // residual-hook scratch (REC_FA x F; also host staging)
   int *cnt_scratch = nullptr;  // level-sort counts
   std::vector<SchedPhase> phases;
+  int order = 0;               // FV_ORDER_FINEST_FIRST or FV_ORDER_PAPER
   bool in_cycle = false;
   int next_phase = 0;
   int64_t tn[FV_MAXL];

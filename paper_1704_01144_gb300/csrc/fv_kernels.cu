@@ -1044,7 +1044,7 @@ __device__ __forceinline__ void flux_item(const DevMesh &d, const GasT<T> &G, in
   if (MLP && f < 0) return;
   if (rc) atomicOr(d.status, FV_STATUS_RIEMANN);
   bool iface = false, bnd = false;
-  if (stage == 2) {
+  if (stage != 1) {
     int2 fc = d.fcell[f];
     // the FP32-flux mode has the cells' levels in slot 5 of the W records
     // the face states were just read from
@@ -1145,6 +1145,132 @@ __device__ __forceinline__ void flux_item_fused(const DevMesh &d, const GasT<flo
 //           accumulated integral; the FP32 shadow of U^n is refreshed.
 // Positivity is checked by the next level assignment and on demand
 // (fv_status), not here.
+// Order 1 (the paper's order), the corrector of cell i of `level`: the
+// provisional end state U^n - S/V, S = sum sigma phi over the cell's faces,
+// phi = Phi on its own-level faces (and faces to coarser neighbours) and the
+// provisional dt_k F1 A on faces to finer neighbours, whose accumulators
+// start from minus that value (the finer side adds its integrals to them).
+// The state goes to the FP64 predicted-state array (FP64 mode) or to UsD
+// and the FP32 predicted record (FP32-flux mode), where the finer levels
+// interpolate it.  Every load before the first store.
+template <bool F32>
+__device__ __forceinline__ void correct_cell(const DevMesh &d, int level, int i) {
+  const size_t N = d.N;
+  const double dtk = ldexp(__longlong_as_double((long long)*d.dtmin_bits), level);
+  const unsigned own = d.cown[i], finer = d.cmask[i];
+  const int4 cf = d.cf4[i];
+  double S[5];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int f = nbr_of(cf, j);
+    const bool neg = !((own >> j) & 1u);
+    double v[REC_FA];
+    if ((finer >> j) & 1u) {
+      if (F32) {
+        float a[REC_FA32];
+        ldrec<REC_FA32>(d.FA32 + (size_t)f * REC_FA32, a);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) v[c] = dtk * (double)a[c];
+      } else {
+        ldrec<REC_FA>(d.FA + (size_t)f * REC_FA, v);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) v[c] = dtk * v[c];
+      }
+    } else {
+      ldrec<REC_FA>(d.FA + (size_t)f * REC_FA, v);
+    }
+#pragma unroll
+    for (int c = 0; c < 5; ++c) S[c] = j == 0 ? flip(v[c], neg) : S[c] + flip(v[c], neg);
+  }
+  const double iV = d.ivol[i];
+  double u[5];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) u[c] = d.Un[c * N + i];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) u[c] = u[c] - iV * S[c];
+  double *Up = F32 ? d.UsD : d.Us;
+#pragma unroll
+  for (int c = 0; c < 5; ++c) Up[c * N + i] = u[c];
+  if (F32) {
+    float r[REC_U32];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) r[c] = (float)u[c];
+    r[5] = (float)level;
+    r[6] = r[7] = 0.0f;
+    strec<REC_U32>(d.Us32 + (size_t)i * REC_U32, r);
+  }
+  // the accumulators of the faces to finer neighbours start from minus the
+  // provisional integral (re-read: the loads above must not wait on these)
+  if (finer) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (!((finer >> j) & 1u)) continue;
+      const int f = nbr_of(cf, j);
+      double p[REC_FA], acc[REC_FA];
+      if (F32) {
+        float a[REC_FA32];
+        ldrec<REC_FA32>(d.FA32 + (size_t)f * REC_FA32, a);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) p[c] = dtk * (double)a[c];
+      } else {
+        ldrec<REC_FA>(d.FA + (size_t)f * REC_FA, p);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) p[c] = dtk * p[c];
+      }
+      ldrec<REC_FA>(d.ACC + (size_t)f * REC_FA, acc);
+#pragma unroll
+      for (int c = 0; c < 5; ++c) acc[c] -= p[c];
+      strec<REC_FA>(d.ACC + (size_t)f * REC_FA, acc);
+    }
+  }
+}
+
+// Order 1, the commit of cell i at the end of its step (Alg. 2's intensive
+// correction): U^{n+1} = Up - (1/V) sum sigma ACC over the faces to finer
+// neighbours (ACC = their integral minus the provisional one), which are
+// reset; a cell without finer neighbours takes its provisional state as it
+// is.
+template <bool F32>
+__device__ __forceinline__ void commit_cell(const DevMesh &d, int i) {
+  const size_t N = d.N;
+  const unsigned finer = d.cmask[i];
+  const double *Up = F32 ? d.UsD : d.Us;
+  double u[5];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) u[c] = Up[c * N + i];
+  if (finer) {
+    const unsigned own = d.cown[i];
+    const int4 cf = d.cf4[i];
+    double S[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (!((finer >> j) & 1u)) continue;
+      const bool neg = !((own >> j) & 1u);
+      double v[REC_FA];
+      ldrec<REC_FA>(d.ACC + (size_t)nbr_of(cf, j) * REC_FA, v);
+#pragma unroll
+      for (int c = 0; c < 5; ++c) S[c] += flip(v[c], neg);
+    }
+    const double iV = d.ivol[i];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) u[c] = u[c] - iV * S[c];
+    const double z[REC_FA] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if ((finer >> j) & 1u) strec<REC_FA>(d.ACC + (size_t)nbr_of(cf, j) * REC_FA, z);
+  }
+#pragma unroll
+  for (int c = 0; c < 5; ++c) d.Un[c * N + i] = u[c];
+  if (F32) {
+    float r[REC_U32];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) r[c] = (float)u[c];
+    r[5] = (float)d.lev[i];
+    r[6] = r[7] = 0.0f;
+    strec<REC_U32>(d.Un32 + (size_t)i * REC_U32, r);
+  }
+}
+
 template <bool F32>
 __device__ __forceinline__ void update_item(const DevMesh &d, int stage, int level, int idx) {
   const size_t N = d.N;
@@ -1225,7 +1351,8 @@ __device__ __forceinline__ void update_item(const DevMesh &d, int stage, int lev
 // mesh (k_phase1), or over the concatenated ranges of a batch of meshes
 // (k_phaseN: a flattened work index, split by a per-block prefix over the
 // instances' range lengths)
-enum { K_PRIM = 0, K_GRAD = 1, K_FLUX = 2, K_UPD = 3 };
+enum { K_PRIM = 0, K_GRAD = 1, K_FLUX = 2, K_UPD = 3, K_CORR = 4, K_COMMIT = 5 };  // K_CORR, K_COMMIT:
+// the cell updates of order 1's correct (stage 3) and commit (stage 4) phases
 
 
 __device__ __forceinline__ void kind_range(const DevMesh &d, const PhaseDesc &p, int kind, int &beg,
@@ -1250,8 +1377,12 @@ __device__ __forceinline__ void run_item(const DevMesh &d, const PhaseDesc &p, c
     grad_item<T>(d, p.pl, idx);
   else if (KIND == K_FLUX)
     flux_item<T, G14>(d, G, p.stage, p.level, idx);
-  else
+  else if (KIND == K_UPD)
     update_item<sizeof(T) == 4>(d, p.stage, p.level, idx);
+  else if (KIND == K_CORR)
+    correct_cell<sizeof(T) == 4>(d, p.level, d.cl[idx]);
+  else
+    commit_cell<sizeof(T) == 4>(d, d.cl[idx]);
 }
 
 // flux: 128 threads, 8 blocks per SM in FP32 (64 registers), 4 in FP64;
@@ -1872,6 +2003,11 @@ static void phase1_all(const DevMesh &d, const PhaseDesc &pd, const GasT<T> &G, 
                        ProfHook *ph, cudaStream_t s) {
   const int g0 = grid_for(d.N, 256, lc.per_sm[0]), g1 = grid_for(d.N, 256, lc.per_sm[1]);
   const int g2 = grid_for(d.F, 128, lc.per_sm[2]), g3 = grid_for(d.N, 256, lc.per_sm[3]);
+  if (pd.stage == 4) {  // a commit (order 1) updates cells only
+    ProfScope sc(ph, FV_PROF_UPDATE, s);
+    launch_pdl(k_phase1<K_COMMIT, T, G14>, g3, 256, s, d, pd, G);
+    return;
+  }
   if (sizeof(T) == 8) {  // FP32-flux mode: primitives computed inside the gradient kernel
     ProfScope sc(ph, FV_PROF_PRIM, s);
     launch_pdl(k_phase1<K_PRIM, T, G14>, g0, 256, s, d, pd, G);
@@ -1891,7 +2027,13 @@ static void phase1_all(const DevMesh &d, const PhaseDesc &pd, const GasT<T> &G, 
                    grid_for(d.F, 128, lc.per_sm[2] < FV_FUSED_BLOCKS ? lc.per_sm[2] : FV_FUSED_BLOCKS), 128, s,
                    d, pd, G);
   }
-  { ProfScope sc(ph, FV_PROF_UPDATE, s); launch_pdl(k_phase1<K_UPD, T, G14>, g3, 256, s, d, pd, G); }
+  {
+    ProfScope sc(ph, FV_PROF_UPDATE, s);
+    if (pd.stage == 3)
+      launch_pdl(k_phase1<K_CORR, T, G14>, g3, 256, s, d, pd, G);
+    else
+      launch_pdl(k_phase1<K_UPD, T, G14>, g3, 256, s, d, pd, G);
+  }
 }
 
 static GasT<double> gas64(const DevMesh &d) { return GasT<double>::make(d.gamma, d.tol, d.maxit); }

@@ -69,7 +69,7 @@ EXPORTS = [
     "fv_mlp_label", "fv_mlp_loss_grad", "fv_mlp_adam", "fv_mlp_train", "fv_mlp_train_steps",
     "fv_mlp_load", "fv_set_guess", "fv_harvest_pairs", "fv_godunov_flux_batch_mlp",
     "fv_use_persistent", "fv_barrier_selftest", "fv_level_history", "fv_batch_mlp_load",
-    "fv_batch_set_guess", "fv_set_fusion", "fv_get_fusion",
+    "fv_batch_set_guess", "fv_set_fusion", "fv_get_fusion", "fv_set_order", "fv_get_order",
 ]
 
 FV_MLP_PARAMS = 4673
@@ -78,6 +78,7 @@ FV_MLP_TARGET_PBAR, FV_MLP_TARGET_TR = 0, 1
 
 FV_NOALLOC_MAX_CELLS = 1 << 22
 FV_FUSE_FACES_DEFAULT = 0
+FV_ORDER_FINEST_FIRST, FV_ORDER_PAPER = 0, 1
 
 FV_PROF_LEVELS, FV_PROF_PRIM, FV_PROF_GRAD, FV_PROF_FLUX, FV_PROF_UPDATE = range(5)
 FV_PROF_N = 5
@@ -144,6 +145,8 @@ def lib():
     for nm in ("fv_set_launch", "fv_get_launch", "fv_batch_set_launch", "fv_batch_get_launch"):
         getattr(L, nm).argtypes = [vp, i32p]
     L.fv_set_fusion.argtypes = [vp, i64]
+    L.fv_set_order.argtypes = [vp, C.c_int]
+    L.fv_get_order.argtypes = [vp, C.POINTER(C.c_int)]
     L.fv_get_fusion.argtypes = [vp, C.POINTER(C.c_int64)]
     L.fv_godunov_flux_batch.argtypes = [vp, vp, vp, i64, C.POINTER(fv_config), C.c_int, vp, vp, vp]
     L.fv_assign_levels_noalloc.argtypes = [vp, vp, i64, C.c_int, vp, vp, vp]
@@ -621,6 +624,16 @@ def fv_get_fusion(h):
     return a.value
 
 
+def fv_set_order(h, order):
+    _check(lib().fv_set_order(h, int(order)), "fv_set_order")
+
+
+def fv_get_order(h):
+    a = C.c_int()
+    _check(lib().fv_get_order(h, C.byref(a)), "fv_get_order")
+    return a.value
+
+
 def fv_batch_set_launch(b, per_sm):
     _check(lib().fv_batch_set_launch(b, _launch4(per_sm)), "fv_batch_set_launch")
 
@@ -695,6 +708,12 @@ class Mesh:
 
     def get_fusion(self):
         return fv_get_fusion(self.h)
+
+    def set_order(self, order):
+        fv_set_order(self.h, order)
+
+    def get_order(self):
+        return fv_get_order(self.h)
 
     def profile_enable(self, enable):
         fv_profile_enable(self.h, enable)

@@ -38,16 +38,29 @@ def ending_levels(theta: int, s: int) -> list[int]:
     return out
 
 
-def phases(theta: int) -> list[tuple[str, int, int]]:
-    """The phase list of one cycle as (kind, level, T): 'B' starts the levels
-    0..level at time T (units of dt_min from the cycle start); 'E' ends the
-    step of `level` at T.  3 * 2^theta - 1 phases in all."""
+def phases(theta: int, order: int = 0) -> list[tuple[str, int, int]]:
+    """The phase list of one cycle as (kind, level, T), the host schedule of
+    the library (fv_internal.h, make_phases).  Order 0: 'B' starts the levels
+    0..level at time T (units of dt_min from the cycle start), 'E' ends the
+    step of `level` at T; 3 * 2^theta - 1 phases.  Order 1 (the paper's):
+    'I' commits the levels 0..level at T, 'B' as before, 'C' corrects `level`
+    at the end T of its step, coarsest first; 4 * 2^theta - 1 phases."""
     out = []
     taus = tau_sequence(theta)
     for s in range(1, (1 << theta) + 1):
-        out.append(("B", taus[s - 1], s - 1))
-        for k in ending_levels(theta, s):
-            out.append(("E", k, s))
+        tau = taus[s - 1]
+        if order == 1:
+            if s > 1:
+                out.append(("I", tau, s - 1))
+            out.append(("B", tau, s - 1))
+            for k in range(tau, -1, -1):
+                out.append(("C", k, s - 1 + (1 << k)))
+        else:
+            out.append(("B", tau, s - 1))
+            for k in ending_levels(theta, s):
+                out.append(("E", k, s))
+    if order == 1:
+        out.append(("I", theta, 1 << theta))
     return out
 
 

@@ -1,0 +1,152 @@
+"""The paper's order of the level steps (FV_ORDER_PAPER) on the GPU against
+the oracle's order 1 (Alg. 2's loops: every level that begins at a
+subiteration is predicted and corrected in it, coarsest first; the
+intensive correction of its interface integrals when its next step begins).
+
+Bar: FP64 within 1e-12 of the oracle after every phase and after whole
+cycles; the FP32-flux mode within 1e-5; one level bitwise equal to the
+finest-first order; the conservation ledger to round-off.
+"""
+import numpy as np
+import pytest
+
+from paper_1704_01144_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP64, TOL_FP32 = 1e-12, 1e-5
+
+
+@pytest.fixture(scope="module")
+def fv():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1704_01144_gb300 import build, fv as F
+    build.build()
+    F.lib()
+    return F
+
+
+def rel(U, Uo):
+    """Relative L-inf error per quantity (density, momentum vector, energy);
+    a field at rest has its momentum measured against the largest scale."""
+    m = np.sqrt((Uo[1:4] ** 2).sum(axis=0)).max()
+    scale = np.array([np.abs(Uo[0]).max(), m, m, m, np.abs(Uo[4]).max()])
+    scale = np.maximum(scale, scale.max() * 1e-3)
+    return float((np.abs(U - Uo).max(axis=1) / scale).max())
+
+
+def pair(fv, oracle_mod, mesh, prim, L, precision=0):
+    g = fv.Mesh(mesh, max_levels=L, precision=precision)
+    g.set_order(fv.FV_ORDER_PAPER)
+    assert g.get_order() == fv.FV_ORDER_PAPER
+    g.set_state(prim)
+    o = oracle_mod.Oracle(mesh, max_levels=L)
+    o.set_order(1)
+    o.set_prim(prim)
+    return g, o
+
+
+def test_host_schedule_matches_oracle(oracle_mod):
+    from paper_1704_01144_gb300 import schedule as S
+    for theta in range(6):
+        assert S.phases(theta, 1) == oracle_mod.phase_list(theta, order=1)
+
+
+def test_phase_by_phase_matches_oracle(fv, oracle_mod):
+    from paper_1704_01144_gb300 import schedule as S
+    mesh, prim = I.blast_case(n=9, ratio=8.0)
+    L = 4
+    g, o = pair(fv, oracle_mod, mesh, prim, L)
+    g.assign_levels()
+    _, _, counts = o.assign_levels()
+    assert (counts > 0).sum() >= 3
+    phases = S.phases(L - 1, 1)
+    for idx, (kind, level, T) in enumerate(phases):
+        g.advance_phases(1)
+        o.run_phases(1)
+        assert rel(g.get_state(), o.get_cons()) <= TOL_FP64, (idx, kind, level)
+    assert g.status() == 0
+
+
+@pytest.mark.parametrize("L", [2, 4])
+def test_cycles_match_oracle_fp64(fv, oracle_mod, L):
+    mesh, prim = I.blast_case(n=12, ratio=8.0)
+    g, o = pair(fv, oracle_mod, mesh, prim, L)
+    for c in range(3):
+        g.advance(1)
+        o.advance(1)
+        np.testing.assert_array_equal(g.levels(), o.levels())
+        assert rel(g.get_state(), o.get_cons()) <= TOL_FP64, c
+    assert g.status() == 0
+
+
+@pytest.mark.parametrize("fusion", [0, 1 << 30])
+def test_cycles_match_oracle_fp32_flux(fv, oracle_mod, fusion):
+    mesh, prim = I.blast_case(n=12, ratio=8.0)
+    g, o = pair(fv, oracle_mod, mesh, prim, 4, precision=fv.FV_FP32_FLUX)
+    g.set_fusion(fusion)
+    for c in range(3):
+        g.advance(1)
+        o.advance(1)
+        np.testing.assert_array_equal(g.levels(), o.levels())
+    assert rel(g.get_state(), o.get_cons()) <= TOL_FP32
+    assert g.status() == 0
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_single_level_equals_finest_first_bitwise(fv, precision):
+    mesh, prim = I.blast_case(n=9, ratio=4.0)
+    out = []
+    for order in (fv.FV_ORDER_FINEST_FIRST, fv.FV_ORDER_PAPER):
+        g = fv.Mesh(mesh, max_levels=1, precision=precision)
+        g.set_order(order)
+        g.set_state(prim)
+        g.advance(3)
+        out.append(g.get_state())
+        g.close()
+    np.testing.assert_array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_conservation_ledger(fv, precision):
+    mesh, prim = I.blast_case(n=12, ratio=8.0)
+    g = fv.Mesh(mesh, max_levels=4, precision=precision)
+    g.set_order(fv.FV_ORDER_PAPER)
+    g.set_state(prim)
+    vol = g.volumes()
+    M0 = (g.get_state() * vol).sum(axis=1)
+    g.advance(3)
+    U = g.get_state()
+    M1 = (U * vol).sum(axis=1)
+    led = g.boundary_ledger()
+    scale = np.abs(U * vol).sum(axis=1).max()
+    assert np.abs(M1 - M0 + led).max() <= 1e-13 * scale
+    assert led[0] == 0.0 and led[4] == 0.0
+
+
+def test_order_setter_and_guards(fv):
+    import torch
+    mesh, prim = I.blast_case(n=6)
+    g = fv.Mesh(mesh, max_levels=2)
+    assert g.get_order() == fv.FV_ORDER_FINEST_FIRST
+    with pytest.raises(fv.FvError):
+        g.set_order(2)
+    g.set_state(prim)
+    g.set_order(fv.FV_ORDER_PAPER)
+    g.assign_levels()
+    g.advance_phases(1)
+    with pytest.raises(fv.FvError):
+        g.set_order(fv.FV_ORDER_FINEST_FIRST)  # inside a cycle
+    R = torch.empty((5, g.n), dtype=torch.float64, device="cuda")
+    with pytest.raises(fv.FvError):
+        g.residual_level(0, 1, R)  # defined for the finest-first order
+    g.advance_phases(6)  # 4 * 2 - 1 = 7 phases per cycle at L = 2
+    assert g.status() == 0
+    with pytest.raises(fv.FvError):
+        fv.Batch([g])
+    g.set_order(fv.FV_ORDER_FINEST_FIRST)
+    b = fv.Batch([g])
+    b.close()
+    g.close()
