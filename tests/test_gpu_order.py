@@ -48,12 +48,6 @@ def pair(fv, oracle_mod, mesh, prim, L, precision=0):
     return g, o
 
 
-def test_host_schedule_matches_oracle(oracle_mod):
-    from paper_1704_01144_gb300 import schedule as S
-    for theta in range(6):
-        assert S.phases(theta, 1) == oracle_mod.phase_list(theta, order=1)
-
-
 def test_phase_by_phase_matches_oracle(fv, oracle_mod):
     from paper_1704_01144_gb300 import schedule as S
     mesh, prim = I.blast_case(n=9, ratio=8.0)

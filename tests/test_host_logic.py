@@ -57,3 +57,12 @@ def test_face_frame_marshalling():
     assert WL[:, 0].tolist() == [1.0, 0.5, 0.0, 0.0, 2.0]
     assert WR[:, 0].tolist() == [0.5, -0.25, 0.0, 0.0, 1.0]
     assert n[:, 0].tolist() == [1.0, 0.0, 0.0]
+
+
+def test_paper_order_host_schedule_matches_oracle(oracle_mod):
+    """The library's host schedule for FV_ORDER_PAPER (mirrored in
+    schedule.phases) is the oracle's order-1 phase list."""
+    from paper_1704_01144_gb300 import schedule as S
+    for theta in range(6):
+        assert S.phases(theta, 1) == oracle_mod.phase_list(theta, order=1)
+        assert S.phases(theta) == oracle_mod.phase_list(theta)
