@@ -50,23 +50,28 @@ __device__ __forceinline__ double fpow(double a, double b) { return pow(a, b); }
 __device__ __forceinline__ float fpow(float a, float b) { return powf(a, b); }
 __device__ __forceinline__ double fsqrt(double a) { return sqrt(a); }
 __device__ __forceinline__ float fsqrt(float a) { return sqrtf(a); }
+// quotient inside the solver: exact in FP64; in FP32 the fast division
+// intrinsic (a reciprocal and a product, about 2 ulps), well inside the
+// FP32-flux mode's stated tolerance and its Newton stopping tests
+__device__ __forceinline__ double qdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float qdiv(float a, float b) { return __fdividef(a, b); }
 
 // pressure function of side K and its derivative (Toro Eqs. 4.6-4.7, 4.37)
 template <typename T>
 __device__ __forceinline__ void pressure_fn(const GasT<T> &G, T p, T rK, T pK, T aK, T &f, T &df) {
   if (p > pK) {
-    T A = T(2) / (G.gp1 * rK);
+    T A = qdiv(T(2), G.gp1 * rK);
     T B = G.k_gm1_gp1 * pK;
-    T q = fsqrt(A / (p + B));
+    T q = fsqrt(qdiv(A, p + B));
     f = (p - pK) * q;
-    df = q * (T(1) - T(0.5) * (p - pK) / (B + p));
+    df = q * (T(1) - qdiv(T(0.5) * (p - pK), B + p));
   } else {
-    T pr = p / pK;
+    T pr = qdiv(p, pK);
     T pz = fpow(pr, G.z);
     f = (G.two_gm1 * aK) * (pz - T(1));
     // d/dp of the rarefaction branch: (p/pK)^(-(g+1)/(2g)) / (rK aK), and
     // -(g+1)/(2g) = z - 1
-    df = (pz / pr) / (rK * aK);
+    df = qdiv(qdiv(pz, pr), rK * aK);
   }
 }
 
@@ -89,7 +94,7 @@ template <typename T, bool GUESS = false>
 __device__ __forceinline__ int riemann_star(const GasT<T> &G, T rL, T uL, T pL, T rR, T uR, T pR,
                                             T &ps, T &us, int &iters, T gabs = T(0),
                                             T gmul = T(1)) {
-  T aL = fsqrt(G.g * pL / rL), aR = fsqrt(G.g * pR / rR);
+  T aL = fsqrt(qdiv(G.g * pL, rL)), aR = fsqrt(qdiv(G.g * pR, rR));
   T du = uR - uL;
   if (G.two_gm1 * (aL + aR) <= du) return 1;
   T p;
@@ -97,8 +102,8 @@ __device__ __forceinline__ int riemann_star(const GasT<T> &G, T rL, T uL, T pL, 
     p = gabs;
   } else {
     T num = aL + aR - T(0.5) * G.gm1 * du;
-    T den = aL / fpow(pL, G.z) + aR / fpow(pR, G.z);
-    p = fpow(num / den, G.inv_z);
+    T den = qdiv(aL, fpow(pL, G.z)) + qdiv(aR, fpow(pR, G.z));
+    p = fpow(qdiv(num, den), G.inv_z);
     if (GUESS) p *= gmul;
   }
   T pfloor = T(1e-6) * (pL < pR ? pL : pR);
@@ -114,9 +119,9 @@ __device__ __forceinline__ int riemann_star(const GasT<T> &G, T rL, T uL, T pL, 
       conv = true;
       break;
     }
-    T pn = p - fsum / (dfL + dfR);
+    T pn = p - qdiv(fsum, dfL + dfR);
     if (pn < pfloor) pn = pfloor;
-    T change = fabs(pn - p) / (T(0.5) * (pn + p));
+    T change = qdiv(fabs(pn - p), T(0.5) * (pn + p));
     p = pn;
     if (change <= G.tol) {
       conv = true;
@@ -140,14 +145,14 @@ __device__ __forceinline__ void sample_face(const GasT<T> &G, T rL, T uL, T pL, 
                                             T ps, T us, T &r, T &u, T &p, int &side) {
   if (T(0) <= us) {
     side = 0;
-    T aL = fsqrt(G.g * pL / rL);
+    T aL = fsqrt(qdiv(G.g * pL, rL));
     if (ps > pL) {
-      T SL = uL - aL * fsqrt(G.shock_a * (ps / pL) + G.shock_b);
+      T SL = uL - aL * fsqrt(G.shock_a * qdiv(ps, pL) + G.shock_b);
       if (T(0) <= SL) {
         r = rL; u = uL; p = pL;
       } else {
-        T q = ps / pL;
-        r = rL * ((q + G.k_gm1_gp1) / (G.k_gm1_gp1 * q + T(1)));
+        T q = qdiv(ps, pL);
+        r = rL * qdiv(q + G.k_gm1_gp1, G.k_gm1_gp1 * q + T(1));
         u = us; p = ps;
       }
     } else {
@@ -155,29 +160,29 @@ __device__ __forceinline__ void sample_face(const GasT<T> &G, T rL, T uL, T pL, 
       if (T(0) <= SHL) {
         r = rL; u = uL; p = pL;
       } else {
-        T pr = ps / pL;
+        T pr = qdiv(ps, pL);
         T STL = us - aL * fpow(pr, G.z);
         if (T(0) >= STL) {
           r = rL * fpow(pr, G.inv_g);
           u = us; p = ps;
         } else {
-          T c = T(2) / G.gp1 + (G.gm1 / (G.gp1 * aL)) * uL;
+          T c = qdiv(T(2), G.gp1) + qdiv(G.gm1, G.gp1 * aL) * uL;
           r = rL * fpow(c, G.two_gm1);
-          u = (T(2) / G.gp1) * (aL + T(0.5) * G.gm1 * uL);
+          u = qdiv(T(2), G.gp1) * (aL + T(0.5) * G.gm1 * uL);
           p = pL * fpow(c, G.inv_z);
         }
       }
     }
   } else {
     side = 1;
-    T aR = fsqrt(G.g * pR / rR);
+    T aR = fsqrt(qdiv(G.g * pR, rR));
     if (ps > pR) {
-      T SR = uR + aR * fsqrt(G.shock_a * (ps / pR) + G.shock_b);
+      T SR = uR + aR * fsqrt(G.shock_a * qdiv(ps, pR) + G.shock_b);
       if (T(0) >= SR) {
         r = rR; u = uR; p = pR;
       } else {
-        T q = ps / pR;
-        r = rR * ((q + G.k_gm1_gp1) / (G.k_gm1_gp1 * q + T(1)));
+        T q = qdiv(ps, pR);
+        r = rR * qdiv(q + G.k_gm1_gp1, G.k_gm1_gp1 * q + T(1));
         u = us; p = ps;
       }
     } else {
@@ -185,15 +190,15 @@ __device__ __forceinline__ void sample_face(const GasT<T> &G, T rL, T uL, T pL, 
       if (T(0) >= SHR) {
         r = rR; u = uR; p = pR;
       } else {
-        T pr = ps / pR;
+        T pr = qdiv(ps, pR);
         T STR = us + aR * fpow(pr, G.z);
         if (T(0) <= STR) {
           r = rR * fpow(pr, G.inv_g);
           u = us; p = ps;
         } else {
-          T c = T(2) / G.gp1 - (G.gm1 / (G.gp1 * aR)) * uR;
+          T c = qdiv(T(2), G.gp1) - qdiv(G.gm1, G.gp1 * aR) * uR;
           r = rR * fpow(c, G.two_gm1);
-          u = (T(2) / G.gp1) * (-aR + T(0.5) * G.gm1 * uR);
+          u = qdiv(T(2), G.gp1) * (-aR + T(0.5) * G.gm1 * uR);
           p = pR * fpow(c, G.inv_z);
         }
       }
@@ -249,11 +254,11 @@ __device__ __forceinline__ Side14<T> make_side14(const GasT<T> &G, T rK, T pK) {
   Side14<T> s;
   s.r = rK;
   s.p = pK;
-  s.a = fsqrt(G.g * pK / rK);
+  s.a = fsqrt(qdiv(G.g * pK, rK));
   s.iq = rroot7(pK);
-  s.c = pK * s.iq / (rK * s.a);
+  s.c = qdiv(pK * s.iq, rK * s.a);
   s.e = T(5) * s.a;
-  s.A = T(2) / (G.gp1 * rK);
+  s.A = qdiv(T(2), G.gp1 * rK);
   s.B = G.k_gm1_gp1 * pK;
   return s;
 }
@@ -277,16 +282,16 @@ __device__ __forceinline__ void pressure_fn14(const Side14<double> &K, double p,
 __device__ __forceinline__ void pressure_fn14(const Side14<float> &K, float p, float, float,
                                               float &f, float &df) {
   if (p > K.p) {
-    float q = sqrtf(K.A / (p + K.B));
+    float q = sqrtf(qdiv(K.A, p + K.B));
     f = (p - K.p) * q;
-    df = q * (1.0f - 0.5f * (p - K.p) / (K.B + p));
+    df = q * (1.0f - qdiv(0.5f * (p - K.p), K.B + p));
   } else {
-    float pr = p / K.p;
+    float pr = qdiv(p, K.p);
     float ir = rroot7(pr);             // pr^(-1/7), about one ulp
     float ir2 = ir * ir;
     float ir6 = ir2 * ir2 * ir2;       // pr^(-6/7), only the slope uses it
-    f = K.e * (1.0f / ir - 1.0f);      // pr^(1/7) - 1 from the reciprocal
-    df = ir6 / (K.r * K.a);
+    f = K.e * (qdiv(1.0f, ir) - 1.0f);  // pr^(1/7) - 1 from the reciprocal
+    df = qdiv(ir6, K.r * K.a);
   }
 }
 
@@ -295,7 +300,7 @@ __device__ __forceinline__ double ratio17(const Side14<double> &K, double ps, do
   return p17 * K.iq;
 }
 __device__ __forceinline__ float ratio17(const Side14<float> &K, float ps, float) {
-  return 1.0f / rroot7(ps / K.p);
+  return qdiv(1.0f, rroot7(qdiv(ps, K.p)));
 }
 
 template <typename T>
@@ -317,7 +322,7 @@ __device__ __forceinline__ int riemann_star14(const GasT<T> &G, const Side14<T> 
     p = gabs;
   } else {
     T num = L.a + R.a - T(0.5) * G.gm1 * du;
-    p = ipow7(num / (L.a * L.iq + R.a * R.iq));
+    p = ipow7(qdiv(num, L.a * L.iq + R.a * R.iq));
     if (GUESS) p *= gmul;
   }
   T pfloor = T(1e-6) * (L.p < R.p ? L.p : R.p);
@@ -335,9 +340,9 @@ __device__ __forceinline__ int riemann_star14(const GasT<T> &G, const Side14<T> 
       conv = true;
       break;
     }
-    T pn = p - fsum / (dfL + dfR);
+    T pn = p - qdiv(fsum, dfL + dfR);
     if (pn < pfloor) pn = pfloor;
-    T change = fabs(pn - p) / (T(0.5) * (pn + p));
+    T change = qdiv(fabs(pn - p), T(0.5) * (pn + p));
     p = pn;
     if (change <= G.tol) {
       conv = true;
@@ -364,12 +369,12 @@ __device__ __forceinline__ void sample_face14(const GasT<T> &G, const Side14<T> 
   if (T(0) <= us) {
     side = 0;
     if (ps > L.p) {
-      T SL = uL - L.a * fsqrt(G.shock_a * (ps / L.p) + G.shock_b);
+      T SL = uL - L.a * fsqrt(G.shock_a * qdiv(ps, L.p) + G.shock_b);
       if (T(0) <= SL) {
         r = L.r; u = uL; p = L.p;
       } else {
-        T q = ps / L.p;
-        r = L.r * ((q + G.k_gm1_gp1) / (G.k_gm1_gp1 * q + T(1)));
+        T q = qdiv(ps, L.p);
+        r = L.r * qdiv(q + G.k_gm1_gp1, G.k_gm1_gp1 * q + T(1));
         u = us; p = ps;
       }
     } else {
@@ -383,9 +388,9 @@ __device__ __forceinline__ void sample_face14(const GasT<T> &G, const Side14<T> 
           r = L.r * ipow5(pr17);
           u = us; p = ps;
         } else {
-          T c = T(2) / G.gp1 + (G.gm1 / (G.gp1 * L.a)) * uL;
+          T c = qdiv(T(2), G.gp1) + qdiv(G.gm1, G.gp1 * L.a) * uL;
           r = L.r * ipow5(c);
-          u = (T(2) / G.gp1) * (L.a + T(0.5) * G.gm1 * uL);
+          u = qdiv(T(2), G.gp1) * (L.a + T(0.5) * G.gm1 * uL);
           p = L.p * ipow7(c);
         }
       }
@@ -393,12 +398,12 @@ __device__ __forceinline__ void sample_face14(const GasT<T> &G, const Side14<T> 
   } else {
     side = 1;
     if (ps > R.p) {
-      T SR = uR + R.a * fsqrt(G.shock_a * (ps / R.p) + G.shock_b);
+      T SR = uR + R.a * fsqrt(G.shock_a * qdiv(ps, R.p) + G.shock_b);
       if (T(0) >= SR) {
         r = R.r; u = uR; p = R.p;
       } else {
-        T q = ps / R.p;
-        r = R.r * ((q + G.k_gm1_gp1) / (G.k_gm1_gp1 * q + T(1)));
+        T q = qdiv(ps, R.p);
+        r = R.r * qdiv(q + G.k_gm1_gp1, G.k_gm1_gp1 * q + T(1));
         u = us; p = ps;
       }
     } else {
@@ -412,9 +417,9 @@ __device__ __forceinline__ void sample_face14(const GasT<T> &G, const Side14<T> 
           r = R.r * ipow5(pr17);
           u = us; p = ps;
         } else {
-          T c = T(2) / G.gp1 - (G.gm1 / (G.gp1 * R.a)) * uR;
+          T c = qdiv(T(2), G.gp1) - qdiv(G.gm1, G.gp1 * R.a) * uR;
           r = R.r * ipow5(c);
-          u = (T(2) / G.gp1) * (-R.a + T(0.5) * G.gm1 * uR);
+          u = qdiv(T(2), G.gp1) * (-R.a + T(0.5) * G.gm1 * uR);
           p = R.p * ipow7(c);
         }
       }
@@ -452,7 +457,7 @@ __device__ __forceinline__ int godunov_flux(const GasT<T> &G, const T WL[5], con
 #pragma unroll
   for (int d = 0; d < 3; ++d) V0[d] = un0 * n[d] + ((left ? WL[1 + d] : WR[1 + d]) - uns * n[d]);
   T mass = r0 * un0;
-  T E0 = p0 / G.gm1 + T(0.5) * r0 * ((V0[0] * V0[0] + V0[1] * V0[1]) + V0[2] * V0[2]);
+  T E0 = qdiv(p0, G.gm1) + T(0.5) * r0 * ((V0[0] * V0[0] + V0[1] * V0[1]) + V0[2] * V0[2]);
   F[0] = mass;
 #pragma unroll
   for (int d = 0; d < 3; ++d) F[1 + d] = mass * V0[d] + p0 * n[d];
@@ -488,7 +493,7 @@ __device__ __forceinline__ int boundary_flux(const GasT<T> &G, int bc, const T W
   }
   iters = 0;
   T r = WL[0], p = WL[4];
-  T E = p / G.gm1 + T(0.5) * r * ((WL[1] * WL[1] + WL[2] * WL[2]) + WL[3] * WL[3]);
+  T E = qdiv(p, G.gm1) + T(0.5) * r * ((WL[1] * WL[1] + WL[2] * WL[2]) + WL[3] * WL[3]);
   T mass = r * un;
   F[0] = mass;
 #pragma unroll
