@@ -144,3 +144,33 @@ def test_order_setter_and_guards(fv):
     b = fv.Batch([g])
     b.close()
     g.close()
+
+
+def test_learned_guess_in_the_paper_order(fv, oracle_mod):
+    """The learned guess only changes where Newton starts: with the paper's
+    order it still converges to the oracle's solution."""
+    import torch
+    mesh, prim = I.blast_case(n=8, ratio=8.0)
+    g, o = pair(fv, oracle_mod, mesh, prim, 3, precision=fv.FV_FP32_FLUX)
+    th = torch.from_numpy(fv.fv_mlp_init(3).astype(np.float32)).cuda()
+    g.mlp_load(th, fv.FV_MLP_TARGET_TR, -1.0)
+    g.set_state(prim)
+    for _ in range(2):
+        g.advance(1)
+        o.advance(1)
+    assert g.status() == 0
+    assert rel(g.get_state(), o.get_cons()) <= TOL_FP32
+
+
+@pytest.mark.parametrize("n,L", [(2, 8), (3, 5), (1, 2)])
+def test_tiny_meshes_many_levels(fv, oracle_mod, n, L):
+    """Meshes of 6 to 162 tets, up to the largest number of levels: empty
+    levels, a cycle of 4 * 2^(L-1) - 1 phases."""
+    mesh, prim = I.blast_case(n=n, ratio=8.0)
+    g, o = pair(fv, oracle_mod, mesh, prim, L)
+    for _ in range(2):
+        g.advance(1)
+        o.advance(1)
+    assert g.status() == 0
+    np.testing.assert_array_equal(g.levels(), o.levels())
+    assert rel(g.get_state(), o.get_cons()) <= TOL_FP64
