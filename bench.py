@@ -131,12 +131,14 @@ def measured_traffic():
 
 
 def launches_per_cycle(L: int, fp32: bool = True) -> int:
-    """Kernels the library launches in one cycle: level assignment
-    (init, dt, levels, L-1 smoothing sweeps, 2 x (keys, hist, scan, scatter)),
-    per phase prim, grad, flux, update (FP64) or grad (with the primitives),
-    flux, update (FP32 flux) x (3 * 2^(L-1) - 1) phases, and the end-of-cycle
-    time advance."""
-    return (11 + (L - 1)) + (3 if fp32 else 4) * (3 * 2 ** (L - 1) - 1) + 1
+    """Kernels the library launches in one cycle (finest-first order, no
+    fusion): level assignment (init, FP32 local steps, exact minimum,
+    levels, L-1 smoothing sweeps, then the cell and face keys with their
+    histograms, both scans and both scatters: 3 launches), per phase prim,
+    grad, flux, update (FP64) or grad (with the primitives), flux, update
+    (FP32 flux) x (3 * 2^(L-1) - 1) phases, and the end-of-cycle time
+    advance."""
+    return (4 + (L - 1) + 3) + (3 if fp32 else 4) * (3 * 2 ** (L - 1) - 1) + 1
 
 
 def _dist():

@@ -162,15 +162,17 @@ def test_learned_guess_in_the_paper_order(fv, oracle_mod):
     assert rel(g.get_state(), o.get_cons()) <= TOL_FP32
 
 
-@pytest.mark.parametrize("n,L", [(2, 8), (3, 5), (1, 2)])
-def test_tiny_meshes_many_levels(fv, oracle_mod, n, L):
-    """Meshes of 6 to 162 tets, up to the largest number of levels: empty
-    levels, a cycle of 4 * 2^(L-1) - 1 phases."""
-    mesh, prim = I.blast_case(n=n, ratio=8.0)
+@pytest.mark.parametrize("n,ratio,L", [(3, 20.0, 5), (5, 40.0, 8), (2, 10.0, 3)])
+def test_small_meshes_many_levels(fv, oracle_mod, n, ratio, L):
+    """Meshes of 48 to 750 tets, strongly graded, a mild blast (pressure
+    ratio 2): every level populated (162 tets, L = 5), six of eight levels
+    (750 tets, a cycle of 4 * 2^7 - 1 = 511 phases), or a single populated
+    level of three.  One cycle: the 1e-12 bar is set for the benchmark's
+    configurations, and an L = 8 cycle already takes 128 finest steps."""
+    mesh, prim = I.blast_case(n=n, ratio=ratio, p_in=2.0, p_out=1.0)
     g, o = pair(fv, oracle_mod, mesh, prim, L)
-    for _ in range(2):
-        g.advance(1)
-        o.advance(1)
+    g.advance(1)
+    o.advance(1)
     assert g.status() == 0
     np.testing.assert_array_equal(g.levels(), o.levels())
     assert rel(g.get_state(), o.get_cons()) <= TOL_FP64

@@ -44,7 +44,9 @@ def test_launch_count_matches_the_schedule(L):
     from paper_1704_01144_gb300 import schedule as S
     nph = len(S.phases(L - 1))
     assert nph == 3 * 2 ** (L - 1) - 1
-    level_assignment = 11 + (L - 1)
+    # k_init_min2, k_dt32, k_dt_min_exact, k_levels0_certified, L-1 x k_smooth,
+    # k_keys_hist, k_sort_scan2, k_sort_scatter2 (launch_assign_levels)
+    level_assignment = 4 + (L - 1) + 3
     assert bench.launches_per_cycle(L, fp32=True) == level_assignment + 3 * nph + 1
     assert bench.launches_per_cycle(L, fp32=False) == level_assignment + 4 * nph + 1
 
