@@ -85,6 +85,7 @@ int run_phase(fv_mesh *m, const SchedPhase &ph, cudaStream_t s) {
 int start_cycle(fv_mesh *m, cudaStream_t s) {
   int rc = fvk::launch_assign_levels(m->d, m->L, m->cnt_scratch, &m->prof, s);
   if (rc) return fail(rc, "level assignment launch failed");
+  m->acc_dirty = true;
   for (int j = 0; j < FV_MAXL; ++j) {
     m->tn[j] = 0;
     m->pred[j] = false;
@@ -140,6 +141,7 @@ int run_cycle_persistent(fv_mesh *m, cudaStream_t s) {
   if (rc) return fail(rc, "time advance launch failed");
   m->in_cycle = false;
   m->next_phase = 0;
+  m->acc_dirty = false;  // a whole cycle consumes every accumulated integral
   return FV_OK;
 }
 
@@ -155,6 +157,7 @@ int run_phases(fv_mesh *m, int n, cudaStream_t s) {
       if (rc) return fail(rc, "time advance launch failed");
       m->in_cycle = false;
       m->next_phase = 0;
+      m->acc_dirty = false;  // a whole cycle consumes every accumulated integral
     }
   }
   return FV_OK;
@@ -343,6 +346,15 @@ int fv_mesh_load(const double *xyz, int64_t n_nodes, const int64_t *tets, int64_
     urc |= upload(d.lsw, lsw);
     urc |= upload(d.fcell, fcell);
     urc |= upload(d.fgeo, geo);
+    std::vector<int> bf;
+    for (size_t f = 0; f < F; ++f)
+      if (H.fnb[f] < 0) bf.push_back((int)f);
+    m->n_bfaces = (int)bf.size();
+    if (dalloc(m, &m->bfaces_dev, bf.size())) {
+      fv_mesh_free(m);
+      return FV_ERR_NOMEM;
+    }
+    if (!bf.empty()) urc |= upload(m->bfaces_dev, bf);
     if (f32) {
       std::vector<float> iv32(N);
       for (size_t i = 0; i < N; ++i) iv32[i] = (float)(1.0 / H.vol[i]);
@@ -395,8 +407,11 @@ static int set_state_impl(fv_mesh *m, const double *src_host_or_dev, int on_devi
     CKL(fvk::launch_set_cons(m->d, src, m->new2old_dev, s));
   else
     CKL(fvk::launch_set_state(m->d, src, m->new2old_dev, s));
-  CK(cudaMemsetAsync(m->d.ACC, 0, REC_FA * (size_t)m->d.F * sizeof(double), s));
-  CK(cudaMemsetAsync(m->d.BND, 0, REC_FA * (size_t)m->d.F * sizeof(double), s));
+  // the accumulators are all zero after a completed cycle; the ledger is
+  // only ever written on boundary faces
+  if (m->acc_dirty) CK(cudaMemsetAsync(m->d.ACC, 0, REC_FA * (size_t)m->d.F * sizeof(double), s));
+  m->acc_dirty = false;
+  CKL(fvk::launch_zero_faces(m->d.BND, m->bfaces_dev, m->n_bfaces, s));
   CK(cudaMemsetAsync(m->d.counters, 0, 3 * sizeof(long long), s));
   if (!on_device) CK(cudaStreamSynchronize(s));
   m->in_cycle = false;

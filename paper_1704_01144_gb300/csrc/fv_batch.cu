@@ -269,6 +269,9 @@ int fv_batch_advance(fv_batch *b, int n_cycles, void *stream) {
     if (m->in_cycle)
       return bfail(FV_ERR_INVALID_ARG, "fv_batch_advance: a mesh is inside a cycle of its own");
   BCK(cudaSetDevice(b->device));
+  // the batch schedule runs whole cycles, but a failed launch could leave a
+  // mesh mid-cycle: the next fv_set_state clears its accumulators
+  for (fv_mesh *m : b->meshes) m->acc_dirty = true;
   cudaStream_t s = (cudaStream_t)stream;
   const bool graphable = b->use_graph && s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread;
   if (graphable && !b->graph && n_cycles > 0) {

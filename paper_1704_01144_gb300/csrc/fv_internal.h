@@ -319,6 +319,12 @@ struct fv_mesh {
   int *cnt_scratch = nullptr;  // level-sort counts
   std::vector<SchedPhase> phases;
   int order = 0;               // FV_ORDER_FINEST_FIRST or FV_ORDER_PAPER
+  // the boundary faces (the only faces whose ledger entries are ever
+  // written) and whether the interface accumulators may hold values: they
+  // are all zero after every completed cycle
+  int *bfaces_dev = nullptr;
+  int n_bfaces = 0;
+  bool acc_dirty = false;
   bool in_cycle = false;
   int next_phase = 0;
   int64_t tn[FV_MAXL];
@@ -354,6 +360,7 @@ int launch_residual(const DevMesh &d, int precision, const PhaseLevels &pl, int 
 int launch_time_advance(const DevMesh &d, int theta, cudaStream_t s);
 int launch_set_state(const DevMesh &d, const double *prim, const int *new2old, cudaStream_t s);
 int launch_set_cons(const DevMesh &d, const double *cons, const int *new2old, cudaStream_t s);
+int launch_zero_faces(double *rec, const int *faces, int n, cudaStream_t s);
 int launch_get_state(const DevMesh &d, double *cons, const int *new2old, cudaStream_t s);
 int launch_get_levels(const DevMesh &d, int8_t *lev, const int *new2old, cudaStream_t s);
 int launch_check_state(const DevMesh &d, cudaStream_t s);

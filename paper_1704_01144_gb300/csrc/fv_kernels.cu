@@ -2229,6 +2229,20 @@ int launch_set_state(const DevMesh &d, const double *prim, const int *new2old, c
   return FV_OK;
 }
 
+// zero the [REC_FA] double records of the listed faces
+__global__ void __launch_bounds__(256) k_zero_faces(double *__restrict__ rec, const int *__restrict__ faces, int n) {
+  const double z[REC_FA] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    strec<REC_FA>(rec + (size_t)faces[i] * REC_FA, z);
+}
+
+int launch_zero_faces(double *rec, const int *faces, int n, cudaStream_t s) {
+  if (n <= 0) return FV_OK;
+  k_zero_faces<<<grid_for(n, 256, 8), 256, 0, s>>>(rec, faces, n);
+  FV_LAUNCH_CHECK();
+  return FV_OK;
+}
+
 int launch_set_cons(const DevMesh &d, const double *cons, const int *new2old, cudaStream_t s) {
   k_set_cons<<<grid_for(d.N, 256, 8), 256, 0, s>>>(d, cons, new2old);
   FV_LAUNCH_CHECK();
