@@ -176,3 +176,21 @@ def test_small_meshes_many_levels(fv, oracle_mod, n, ratio, L):
     assert g.status() == 0
     np.testing.assert_array_equal(g.levels(), o.levels())
     assert rel(g.get_state(), o.get_cons()) <= TOL_FP64
+
+
+def test_persistent_switch_falls_back_to_the_graph_path(fv):
+    """The persistent cycle runs the finest-first order only: with the
+    paper's order selected it falls back to the graph path, results
+    unchanged."""
+    mesh, prim = I.blast_case(n=9, ratio=8.0)
+    out = []
+    for persistent in (False, True):
+        g = fv.Mesh(mesh, max_levels=3, precision=fv.FV_FP32_FLUX)
+        g.set_order(fv.FV_ORDER_PAPER)
+        g.use_persistent(persistent)
+        g.set_state(prim)
+        g.advance(2)
+        assert g.status() == 0
+        out.append(g.get_state())
+        g.close()
+    np.testing.assert_array_equal(out[0], out[1])
