@@ -100,6 +100,12 @@ __device__ __forceinline__ void strec(double *p, const double *o) {
 #pragma unroll
   for (int k = 0; k < NE / 2; ++k) reinterpret_cast<double2 *>(p)[k] = make_double2(o[2 * k], o[2 * k + 1]);
 }
+// x 2^k for a positive normal x whose scaled value stays normal (dt_min and
+// the level steps 2^k dt_min): the exponent field plus k -- exact, the value
+// ldexp gives, in integer instructions only
+__device__ __forceinline__ double scale2(double x, int k) {
+  return __longlong_as_double(__double_as_longlong(x) + ((long long)k << 52));
+}
 __device__ __forceinline__ int nbr_of(const int4 &v, int j) {
   return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w;
 }
@@ -1007,7 +1013,7 @@ __device__ __forceinline__ void flux_store(const DevMesh &d, int stage, int leve
     }
     return;
   }
-  double h = 0.5 * ldexp(__longlong_as_double((long long)*d.dtmin_bits), level);
+  double h = scale2(__longlong_as_double((long long)*d.dtmin_bits), level - 1);  // dt_k / 2
   double phi[REC_FA];
   if (f32) {
     float a[REC_FA32];
@@ -1156,7 +1162,7 @@ __device__ __forceinline__ void flux_item_fused(const DevMesh &d, const GasT<flo
 template <bool F32>
 __device__ __forceinline__ void correct_cell(const DevMesh &d, int level, int i) {
   const size_t N = d.N;
-  const double dtk = ldexp(__longlong_as_double((long long)*d.dtmin_bits), level);
+  const double dtk = scale2(__longlong_as_double((long long)*d.dtmin_bits), level);
   const unsigned own = d.cown[i], finer = d.cmask[i];
   const int4 cf = d.cf4[i];
   double S[5];
@@ -1290,7 +1296,7 @@ __device__ __forceinline__ void update_item(const DevMesh &d, int stage, int lev
     }
     float a[REC_U32];
     ldrec<REC_U32>(d.Un32 + (size_t)i * REC_U32, a);
-    float cdt = -ldexpf((float)dtmin, (int)a[5]) * d.ivol32[i];
+    float cdt = -(float)scale2(dtmin, (int)a[5]) * d.ivol32[i];
 #pragma unroll
     for (int c = 0; c < 5; ++c) a[c] = a[c] + cdt * S[c];
     strec<REC_U32>(d.Us32 + (size_t)i * REC_U32, a);
@@ -1323,7 +1329,7 @@ __device__ __forceinline__ void update_item(const DevMesh &d, int stage, int lev
 #pragma unroll
   for (int c = 0; c < 5; ++c) u[c] = d.Un[c * N + i];
   if (stage == 1) {
-    double cdt = -ldexp(dtmin, (int)d.lev[i]) * iV;
+    double cdt = -scale2(dtmin, (int)d.lev[i]) * iV;
 #pragma unroll
     for (int c = 0; c < 5; ++c) d.Us[c * N + i] = u[c] + cdt * S[c];
   } else {
