@@ -63,3 +63,19 @@ def test_null_handle_is_rejected_without_gpu(libfv):
     out = C.c_void_p(1)
     assert libfv.fv_mesh_load(None, 0, None, 0, None, None, C.byref(out)) == fv.FV_ERR_INVALID_ARG
     assert out.value is None
+
+
+@pytest.mark.parametrize("std,compiler,flags", [("c99", "gcc", ["-x", "c"]), ("c++17", "g++", ["-x", "c++"])])
+def test_header_is_plain_c_and_cxx(tmp_path, std, compiler, flags):
+    """include/fv.h is a C ABI: it compiles on its own as pedantic C99 (no
+    C++ constructs outside its extern "C" guard) and as C++, warning-free."""
+    import shutil
+    import subprocess
+    if shutil.which(compiler) is None:
+        pytest.skip(f"{compiler} not found")
+    src = tmp_path / "use_header.c"
+    src.write_text('#include "fv.h"\nint main(void) { fv_config c; (void)c; return FV_OK; }\n')
+    r = subprocess.run([compiler, *flags, f"-std={std}", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                        "-I", os.path.join(ROOT, "include"), "-c", str(src), "-o", str(tmp_path / "o.o")],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
