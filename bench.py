@@ -72,6 +72,33 @@ def update_bytes_per_cell_update(fp32: bool) -> float:
     return predictor + corrector
 
 
+def roofline_entry(prof, face_evals, cell_updates, fp32, kernel, peak_gbs, peak_src, traffic):
+    """The roofline object of one kernel class from the profiled cycles:
+    achieved = algorithmic bytes per unit x units / the class's event time,
+    against the measured HBM copy bandwidth; traffic = the committed ncu DRAM
+    bytes per unit x units per launch (None without a current capture).
+    prof[kernel] = (total ms, launches)."""
+    ms, n = prof[kernel]
+    if n == 0 or ms <= 0:
+        return None
+    if kernel == "flux":
+        units, bpu, tkey = face_evals, flux_bytes_per_eval(fp32), "flux"
+    else:
+        units, bpu, tkey = cell_updates, update_bytes_per_cell_update(fp32), "update"
+    achieved = units * bpu / (ms * 1e-3) / 1e9
+    tr = None
+    if traffic is not None:
+        key = f"{tkey}_{'fp32' if fp32 else 'fp64'}_dram_bytes_per_unit"
+        if key in traffic:
+            tr = round(float(traffic[key]) * units / n)
+    return {"bound": "hbm", "kernel": f"k_{kernel}", "achieved": round(achieved, 1),
+            "peak": peak_gbs, "unit": "GB/s", "frac": round(achieved / peak_gbs, 4),
+            "traffic": tr, "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)",
+            "algorithmic_bytes_per_unit": bpu,
+            "unit_counted": "face evaluation" if kernel == "flux" else "cell update",
+            "units_per_launch": round(units / n, 1), "avg_launch_ms": ms / n, "launches": n}
+
+
 KERNEL_SOURCES = ["paper_1704_01144_gb300/csrc/fv_kernels.cu",
                   "paper_1704_01144_gb300/csrc/fv_riemann.cuh",
                   "paper_1704_01144_gb300/csrc/fv_internal.h",
@@ -539,26 +566,8 @@ def main_ours(args):
     traffic = measured_traffic()
 
     def roofline(r, fp32, kernel):
-        ms, n = r["prof"][kernel]
-        if n == 0 or ms <= 0:
-            return None
-        if kernel == "flux":
-            units, bpu, tkey = r["prof_face_evals"], flux_bytes_per_eval(fp32), "flux"
-        else:
-            units, bpu, tkey = r["prof_cell_updates"], update_bytes_per_cell_update(fp32), "update"
-        achieved = units * bpu / (ms * 1e-3) / 1e9
-        peak = float(peaks["hbm_gbs"])
-        tr = None
-        if traffic is not None:
-            key = f"{tkey}_{'fp32' if fp32 else 'fp64'}_dram_bytes_per_unit"
-            if key in traffic:
-                tr = round(float(traffic[key]) * units / n)
-        return {"bound": "hbm", "kernel": f"k_{kernel}", "achieved": round(achieved, 1),
-                "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": tr, "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)",
-                "algorithmic_bytes_per_unit": bpu,
-                "unit_counted": "face evaluation" if kernel == "flux" else "cell update",
-                "units_per_launch": round(units / n, 1), "avg_launch_ms": ms / n, "launches": n}
+        return roofline_entry(r["prof"], r["prof_face_evals"], r["prof_cell_updates"], fp32, kernel,
+                              float(peaks["hbm_gbs"]), peak_src, traffic)
 
     def dominant(r, fp32):
         k = max(("flux", "update"), key=lambda q: r["prof"][q][0])

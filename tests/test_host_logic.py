@@ -68,3 +68,33 @@ def test_paper_order_host_schedule_matches_oracle(oracle_mod):
     for theta in range(6):
         assert S.phases(theta, 1) == oracle_mod.phase_list(theta, order=1)
         assert S.phases(theta) == oracle_mod.phase_list(theta)
+
+
+def test_roofline_entry_arithmetic():
+    """achieved = algorithmic bytes per unit x units / time; frac against the
+    peak; traffic = committed per-unit DRAM bytes x units per launch."""
+    import bench
+    prof = {"flux": (2.0, 46), "update": (0.0, 0)}
+    fe, cu = 11_187_220, 2_728_706  # two cycles of the 1M-tet blast
+    r = bench.roofline_entry(prof, fe, cu, True, "flux", 6690.8, "measured",
+                             {"flux_fp32_dram_bytes_per_unit": "139.0"})
+    assert r["algorithmic_bytes_per_unit"] == 121.0
+    assert r["achieved"] == round(fe * 121.0 / 2e-3 / 1e9, 1)
+    assert r["frac"] == round(r["achieved"] / 6690.8, 4)
+    assert r["traffic"] == round(139.0 * fe / 46)
+    assert r["units_per_launch"] == round(fe / 46, 1) and r["launches"] == 46
+    assert bench.roofline_entry(prof, fe, cu, True, "update", 6690.8, "measured", None) is None
+    r64 = bench.roofline_entry({"update": (1.0, 46)}, fe, cu, False, "update", 6690.8, "measured", None)
+    assert r64["algorithmic_bytes_per_unit"] == 383 and r64["traffic"] is None
+
+
+def test_algorithmic_bytes_match_the_documented_breakdown():
+    """Per face evaluation: index 4, two cells 8, geometry 28/56, predictor
+    flux record 20/40, corrector also reads it (20/40) and writes the FP64
+    integral (40), half of each cell's primitives and gradients 40/80; mean
+    of predictor and corrector (121 / 209).  Per cell update: 319 / 383."""
+    import bench
+    assert bench.flux_bytes_per_eval(True) == 121.0
+    assert bench.flux_bytes_per_eval(False) == 209.0
+    assert bench.update_bytes_per_cell_update(True) == 319
+    assert bench.update_bytes_per_cell_update(False) == 383
