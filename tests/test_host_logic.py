@@ -89,10 +89,11 @@ def test_roofline_entry_arithmetic():
 
 
 def test_algorithmic_bytes_match_the_documented_breakdown():
-    """Per face evaluation: index 4, two cells 8, geometry 28/56, predictor
-    flux record 20/40, corrector also reads it (20/40) and writes the FP64
-    integral (40), half of each cell's primitives and gradients 40/80; mean
-    of predictor and corrector (121 / 209).  Per cell update: 319 / 383."""
+    """Per face evaluation: index 4, two cells 8, geometry 28/56, half of
+    each cell's primitives and gradients 40/80; the predictor writes its
+    flux record (20/40), the corrector reads it back, writes the FP64
+    integral (40) and reads 2 level bytes; mean of the two stages 121 / 209.
+    Per cell update, both stages: 319 / 383."""
     import bench
     assert bench.flux_bytes_per_eval(True) == 121.0
     assert bench.flux_bytes_per_eval(False) == 209.0
