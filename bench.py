@@ -184,19 +184,99 @@ def _load_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+NVML_CLOCK_SM = 1
+# clock-event reason bits of the NVIDIA management library that reject a run
+# (sw_power_cap is kept and noted)
+NVML_REASONS = (("sw_power_cap", 0x4), ("hw_slowdown", 0x8),
+                ("sw_thermal_slowdown", 0x20), ("hw_thermal_slowdown", 0x40))
+
+
+class NvmlClocks:
+    """Read-only queries of the NVIDIA management library through ctypes:
+    one device's SM clock, its maximum and the active clock-event reasons.
+    ``lib`` replaces the shared library (tests pass a fake)."""
+
+    def __init__(self, gpu_index: int, lib=None):
+        import ctypes
+        self.ct = ctypes
+        self.lib = lib if lib is not None else ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        n = ctypes.c_uint(0)
+        if self.lib.nvmlDeviceGetCount_v2(ctypes.byref(n)) != 0 or n.value == 0:
+            raise OSError("no NVML device")
+        # a container that shows one GPU numbers it 0 whatever CUDA_VISIBLE_DEVICES says
+        idx = 0 if n.value == 1 else gpu_index
+        if idx >= n.value:
+            raise OSError(f"NVML device {idx} of {n.value}")
+        self.h = ctypes.c_void_p()
+        if self.lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(idx), ctypes.byref(self.h)) != 0:
+            raise OSError("no NVML handle")
+        m = ctypes.c_uint(0)
+        ok = self.lib.nvmlDeviceGetMaxClockInfo(self.h, NVML_CLOCK_SM, ctypes.byref(m)) == 0
+        self.max_mhz = float(m.value) if ok else None
+        try:
+            self.reasons_fn = self.lib.nvmlDeviceGetCurrentClocksEventReasons
+        except AttributeError:
+            self.reasons_fn = self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def sample(self):
+        """(SM MHz, max SM MHz, set of reason names), or None on an NVML error."""
+        c, r = self.ct.c_uint(0), self.ct.c_ulonglong(0)
+        if self.lib.nvmlDeviceGetClockInfo(self.h, NVML_CLOCK_SM, self.ct.byref(c)) != 0:
+            return None
+        if self.reasons_fn(self.h, self.ct.byref(r)) != 0:
+            return None
+        return (float(c.value), self.max_mhz,
+                {nm for nm, bit in NVML_REASONS if r.value & bit})
+
+    def close(self):
+        self.lib.nvmlShutdown()
+
+
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """Clocks and throttle reasons sampled during the timed region: NVML
+    every 5 ms from a thread (so that even a short timed region has
+    samples), else nvidia-smi every 200 ms.  Entering returns once the first
+    sample is in."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    SMI_NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, nvml_lib=None, interval_s: float = 0.005):
         self.gpu = gpu_index
+        self.nvml_lib = nvml_lib
+        self.interval = interval_s
         self.proc = None
         self.path = None
+        self.nv = None
+        self.rows = []
+        self.source = None
+
+    def _poll(self):
+        while not self.stop.is_set():
+            row = self.nv.sample()
+            if row is not None:
+                self.rows.append(row)
+            self.stop.wait(self.interval)
 
     def __enter__(self):
+        import threading
+        try:
+            self.nv = NvmlClocks(self.gpu, self.nvml_lib)
+        except (OSError, AttributeError):
+            self.nv = None
+        if self.nv is not None:
+            self.source = f"NVML every {self.interval * 1e3:g} ms"
+            self.stop = threading.Event()
+            self.thread = threading.Thread(target=self._poll, daemon=True)
+            self.thread.start()
+            t0 = time.perf_counter()
+            while not self.rows and time.perf_counter() - t0 < 1.0:
+                time.sleep(0.001)
+            return self
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
@@ -205,11 +285,20 @@ class ClockSampler:
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
                  "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
                 stderr=subprocess.DEVNULL)
+            self.source = "nvidia-smi every 200 ms"
+            t0 = time.perf_counter()
+            while os.path.getsize(self.path) == 0 and time.perf_counter() - t0 < 3.0 \
+                    and self.proc.poll() is None:
+                time.sleep(0.01)
         except (OSError, FileNotFoundError):
             self.proc = None
         return self
 
     def __exit__(self, *exc):
+        if self.nv is not None:
+            self.stop.set()
+            self.thread.join(timeout=5)
+            self.nv.close()
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -218,29 +307,45 @@ class ClockSampler:
                 self.proc.kill()
             self.fh.close()
 
-    def summary(self):
-        if self.proc is None or not self.path:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    def _smi_rows(self):
+        rows = []
         with open(self.path) as fh:
             for ln in fh:
                 parts = [p.strip() for p in ln.split(",")]
                 if len(parts) < 9:
                     continue
                 try:
-                    sm.append(float(parts[1]))
-                    smax.append(float(parts[2]))
+                    sm, smax = float(parts[1]), float(parts[2])
                 except ValueError:
                     continue
-                for nm, v in zip(names, parts[5:9]):
-                    if v.lower() == "active":
-                        reasons.add(nm)
+                rows.append((sm, smax, {nm for nm, v in zip(self.SMI_NAMES, parts[5:9])
+                                        if v.lower() == "active"}))
         os.unlink(self.path)
-        if not sm:
+        return rows
+
+    def summary(self):
+        if self.nv is None and (self.proc is None or not self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = self.rows if self.nv is not None else self._smi_rows()
+        if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
-                "reasons": sorted(reasons), "samples": len(sm)}
+        smax = [r[1] for r in rows if r[1] is not None]
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(set().union(*(r[2] for r in rows))),
+                "samples": len(rows), "sampler": self.source}
+
+
+def clocks_rejected(c) -> bool:
+    """A timed region is taken again once when its clock record shows a
+    thermal or hardware slowdown, or SM clocks well below their maximum with
+    no reason (a leftover clock lock); a power cap is kept and noted."""
+    if any(r in ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown")
+           for r in c.get("reasons", [])):
+        return True
+    sm, smax = c.get("sm_mhz"), c.get("sm_max_mhz")
+    return (sm is not None and smax and sm < 0.9 * smax
+            and "sw_power_cap" not in c.get("reasons", []))
 
 
 def build_workload(name):
@@ -282,26 +387,39 @@ def run_mode(fv, torch, mesh, prim, L, precision, steps, warmup, stream, flush, 
         for _ in range(warmup):
             g.advance(1, stream=stream, want_time=False)
     torch.cuda.synchronize()
-    c0 = g.work_counters()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(steps)]
-    if torch.distributed.is_initialized():
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    t_wall0 = time.perf_counter()
-    with ClockSampler(gpu_index) as clk:
-        with torch.cuda.stream(stream):
-            for k in range(steps):
-                flush.add_(1.0)                      # L2 flush between timed steps
-                ev[k][0].record(stream)
-                g.advance(1, stream=stream, want_time=False)
-                ev[k][1].record(stream)
+    for attempt in range(2):
+        c0 = g.work_counters()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        if torch.distributed.is_initialized():
+            torch.distributed.barrier()
         torch.cuda.synchronize()
-    t_wall = time.perf_counter() - t_wall0
-    if torch.distributed.is_initialized():
-        torch.distributed.barrier()
-    ms = sum(a.elapsed_time(b) for a, b in ev)
-    c1 = g.work_counters()
+        t_wall0 = time.perf_counter()
+        with ClockSampler(gpu_index) as clk:
+            with torch.cuda.stream(stream):
+                for k in range(steps):
+                    flush.add_(1.0)                      # L2 flush between timed steps
+                    ev[k][0].record(stream)
+                    g.advance(1, stream=stream, want_time=False)
+                    ev[k][1].record(stream)
+            torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall0
+        if torch.distributed.is_initialized():
+            torch.distributed.barrier()
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        c1 = g.work_counters()
+        clocks = clk.summary()
+        bad = clocks_rejected(clocks)
+        if torch.distributed.is_initialized():  # every rank takes the same decision
+            flag = torch.tensor([int(bad)], device="cuda")
+            torch.distributed.all_reduce(flag, op=torch.distributed.ReduceOp.MAX)
+            bad = bool(flag.item())
+        if attempt == 0 and bad:
+            clocks_first = clocks
+            continue  # taken again once
+        if attempt == 1:
+            clocks["first_attempt_rejected"] = clocks_first
+        break
     st = g.status()
     if st != 0:
         raise RuntimeError(f"device status {st}: {fv.fv_last_error()}")
@@ -318,7 +436,7 @@ def run_mode(fv, torch, mesh, prim, L, precision, steps, warmup, stream, flush, 
     out = {
         "ms_total": ms, "ms_per_step": ms / steps, "wall_s": t_wall,
         "cell_updates": cell_updates, "face_evals": face_evals,
-        "value": cell_updates / (ms * 1e-3), "clocks": clk.summary(),
+        "value": cell_updates / (ms * 1e-3), "clocks": clocks,
         "prof": prof, "prof_face_evals": p1[2] - p0[2], "prof_cell_updates": p1[1] - p0[1],
         "launch_per_sm": per_sm, "autotune_cached": tune["cached"],
         "level_history": history,

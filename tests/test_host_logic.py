@@ -99,3 +99,88 @@ def test_algorithmic_bytes_match_the_documented_breakdown():
     assert bench.flux_bytes_per_eval(False) == 209.0
     assert bench.update_bytes_per_cell_update(True) == 319
     assert bench.update_bytes_per_cell_update(False) == 383
+
+
+class FakeNvml:
+    """Stands in for the NVIDIA management library: a device count, an SM
+    clock that follows a script, and clock-event reason bits."""
+
+    def __init__(self, count=1, clocks=(2070, 2070, 1980), reasons=(0, 0x4, 0x4), fail_at=None):
+        self.count, self.clocks, self.reasons = count, list(clocks), list(reasons)
+        self.i, self.fail_at, self.index, self.shut = 0, fail_at, None, False
+
+    def nvmlInit_v2(self):
+        return 0
+
+    def nvmlShutdown(self):
+        self.shut = True
+        return 0
+
+    def nvmlDeviceGetCount_v2(self, p):
+        p._obj.value = self.count
+        return 0
+
+    def nvmlDeviceGetHandleByIndex_v2(self, idx, p):
+        self.index = idx.value
+        p._obj.value = 1234
+        return 0
+
+    def nvmlDeviceGetMaxClockInfo(self, h, kind, p):
+        assert kind == 1  # the SM clock
+        p._obj.value = 2070
+        return 0
+
+    def nvmlDeviceGetClockInfo(self, h, kind, p):
+        assert kind == 1
+        if self.i == self.fail_at:
+            self.i += 1
+            return 999
+        p._obj.value = self.clocks[min(self.i, len(self.clocks) - 1)]
+        return 0
+
+    def nvmlDeviceGetCurrentClocksEventReasons(self, h, p):
+        p._obj.value = self.reasons[min(self.i, len(self.reasons) - 1)]
+        self.i += 1
+        return 0
+
+
+def test_nvml_clock_samples_decode_reasons():
+    import bench
+    lib = FakeNvml(reasons=(0, 0x4 | 0x1, 0x8 | 0x40 | 0x20))
+    nv = bench.NvmlClocks(3, lib)
+    assert lib.index == 0  # one visible device is index 0 whatever the CUDA index
+    assert nv.sample() == (2070.0, 2070.0, set())
+    assert nv.sample() == (2070.0, 2070.0, {"sw_power_cap"})  # the idle bit is not a reason
+    assert nv.sample() == (1980.0, 2070.0,
+                           {"hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"})
+    lib8 = FakeNvml(count=8)
+    bench.NvmlClocks(3, lib8)
+    assert lib8.index == 3
+    with pytest.raises(OSError):
+        bench.NvmlClocks(8, FakeNvml(count=8))
+
+
+def test_clock_sampler_summary_over_the_timed_region():
+    import time
+    import bench
+    lib = FakeNvml(clocks=(2070, 1, 1500, 2070, 2070), reasons=(0, 0x8, 0, 0x4, 0), fail_at=1)
+    with bench.ClockSampler(0, nvml_lib=lib, interval_s=0.001) as clk:
+        assert clk.rows  # entering waits for the first sample
+        while lib.i < 8:
+            time.sleep(0.001)
+    s = clk.summary()
+    assert lib.shut and s["sm_max_mhz"] == 2070.0 and s["sm_mhz"] == 2070.0
+    # the failed query (index 1) is skipped with its reasons
+    assert s["reasons"] == ["sw_power_cap"] and s["samples"] >= 6
+    assert s["sampler"].startswith("NVML")
+
+
+def test_clock_rejection_rule():
+    import bench
+    ok = {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": []}
+    assert not bench.clocks_rejected(ok)
+    assert not bench.clocks_rejected({**ok, "sm_mhz": 1700.0, "reasons": ["sw_power_cap"]})
+    for r in ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"):
+        assert bench.clocks_rejected({**ok, "reasons": [r]})
+    assert bench.clocks_rejected({**ok, "sm_mhz": 1200.0})  # stuck low, no reason
+    assert not bench.clocks_rejected({"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]})
