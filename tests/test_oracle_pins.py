@@ -16,13 +16,19 @@ from paper_1704_01144_gb300 import schedule as S
 
 # ----------------------------------------------------------- Riemann solver
 def test_riemann_star_matches_toro_table(oracle_mod):
-    """Exact star states of Toro's five standard tests (Table 4.3)."""
+    """Exact star states of Toro's five standard tests (Table 4.3): pressure
+    and velocity from the solver, the densities either side of the contact
+    from the sampled solution just left and right of it (shock and
+    rarefaction branches of both sides)."""
     for ln in read_golden("toro_table_4_3.txt"):
         vals = ln.split()
         WL = tuple(map(float, vals[0:3]))
         WR = tuple(map(float, vals[3:6]))
         ps, us, _ = oracle_mod.riemann(WL, WR, tol=1e-12, maxit=100)
-        for got, txt in ((ps, vals[6]), (us, vals[7])):
+        e = 1e-9 * (1.0 + abs(us))
+        rsl = oracle_mod.riemann_sample(WL, WR, us - e, tol=1e-12)[0]
+        rsr = oracle_mod.riemann_sample(WL, WR, us + e, tol=1e-12)[0]
+        for got, txt in ((ps, vals[6]), (us, vals[7]), (rsl, vals[8]), (rsr, vals[9])):
             decimals = len(txt.split(".")[1]) if "." in txt else 0
             # one unit of the last printed digit, or 1e-5 relative (test 4's
             # data are themselves test 3's star states rounded to 6 digits)
