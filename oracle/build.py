@@ -16,22 +16,28 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liboracle.so")
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(OUT_DIR, exist_ok=True)
-    if (not force and os.path.exists(LIB)
-            and os.path.getmtime(LIB) >= max(os.path.getmtime(s) for s in SRCS)):
-        return LIB
+def compile_lib(srcs, out: str, verbose: bool = False) -> str:
+    """Compile C sources into the shared library ``out`` with the oracle's
+    flags (OpenMP when the compiler has it)."""
     base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-            *SRCS, "-o", LIB + ".tmp", "-lm"]
+            *srcs, "-o", out + ".tmp", "-lm"]
     for extra in (["-fopenmp"], []):
         cmd = base[:1] + extra + base[1:]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if verbose:
             sys.stderr.write(" ".join(cmd) + "\n" + r.stdout + r.stderr)
         if r.returncode == 0:
-            os.replace(LIB + ".tmp", LIB)
-            return LIB
+            os.replace(out + ".tmp", out)
+            return out
     raise RuntimeError("oracle build failed:\n" + r.stderr)
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    os.makedirs(OUT_DIR, exist_ok=True)
+    if (not force and os.path.exists(LIB)
+            and os.path.getmtime(LIB) >= max(os.path.getmtime(s) for s in SRCS)):
+        return LIB
+    return compile_lib(SRCS, LIB, verbose)
 
 
 if __name__ == "__main__":

@@ -1360,18 +1360,25 @@ int orc_stats(const orc *o, int64_t *updates, int64_t *faceevals, int64_t *newto
 
 /* least-squares gradient of one scalar field q (nc) -> g (3 x nc SoA); ghost
  * values on boundary faces copy the cell's own value */
-int orc_scalar_gradient(const orc *o, const double *q, double *g_soa) {
+/* Least-squares gradient of a cell scalar q, through the scheme's own
+ * gradient routine: q is put in every primitive slot of the scratch W and
+ * gradient_cell runs on each cell; a boundary face contributes nothing
+ * (its ghost copies q).  W and G are scratch that every phase recomputes. */
+int orc_scalar_gradient(orc *o, const double *q, double *g_soa) {
+  for (int64_t i = 0; i < o->nc; ++i)
+    for (int c = 0; c < 5; ++c) o->W[5 * i + c] = q[i];
   for (int64_t i = 0; i < o->nc; ++i) {
-    double g[3] = {0, 0, 0};
-    for (int j = 0; j < 4; ++j) {
-      int64_t f = o->cface[4 * i + j];
-      int64_t nb = o->csgn[4 * i + j] > 0 ? o->fnb[f] : o->fown[f];
-      double d = nb >= 0 ? q[nb] - q[i] : 0.0;
-      const double *w = o->lsw + 12 * i + 3 * j;
-      for (int a = 0; a < 3; ++a) g[a] += w[a] * d;
-    }
-    for (int a = 0; a < 3; ++a) g_soa[a * o->nc + i] = g[a];
+    gradient_cell(o, i);
+    for (int a = 0; a < 3; ++a) g_soa[a * o->nc + i] = o->G[15 * i + a];
   }
+  return ORC_OK;
+}
+
+/* r = x_j - x_i per face (3 x nf, SoA): to the neighbour's centroid, or on a
+ * boundary face to the ghost centroid (the mirror image of the cell's) */
+int orc_face_offsets(const orc *o, double *r_soa) {
+  for (int64_t f = 0; f < o->nf; ++f)
+    for (int d = 0; d < 3; ++d) r_soa[d * o->nf + f] = o->fr[3 * f + d];
   return ORC_OK;
 }
 
@@ -1408,6 +1415,11 @@ int orc_boundary_flux(double gamma, int bc, const double *WL, const double *n, d
   int it;
   if (bc != 1 && bc != 2) return ORC_EINVAL;
   return boundary_flux(&G, bc, WL, n, F, &it);
+}
+
+int orc_ghost_state(int bc, const double *n, const double *W, double *Wg) {
+  ghost_state(bc, n, W, Wg);
+  return ORC_OK;
 }
 
 int orc_muscl_pair(const double *Wi, const double *Wj, const double *gi, const double *gj,

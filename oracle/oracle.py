@@ -11,6 +11,7 @@ mlp_oracle.c.
 from __future__ import annotations
 
 import ctypes as C
+import os
 
 import numpy as np
 
@@ -22,7 +23,9 @@ _lib = None
 def lib():
     global _lib
     if _lib is None:
-        path = _build.build()
+        # FV_ORACLE_LIB: a library built from modified sources, for the test
+        # that plants mistakes in the oracle and checks that its pins fail
+        path = os.environ.get("FV_ORACLE_LIB") or _build.build()
         L = C.CDLL(path)
         dp = C.POINTER(C.c_double)
         i64p = C.POINTER(C.c_int64)
@@ -57,6 +60,8 @@ def lib():
         L.orc_boundary_ledger.argtypes = [vp, dp]
         L.orc_stats.argtypes = [vp, i64p, i64p, i64p, i64p]
         L.orc_scalar_gradient.argtypes = [vp, dp, dp]
+        L.orc_face_offsets.argtypes = [vp, dp]
+        L.orc_ghost_state.argtypes = [C.c_int, dp, dp, dp]
         L.orc_riemann.argtypes = [C.c_double] * 7 + [C.c_double, C.c_int, dp, dp,
                                                      C.POINTER(C.c_int)]
         L.orc_riemann_sample.argtypes = [C.c_double] * 7 + [C.c_double, C.c_int, C.c_double,
@@ -179,6 +184,12 @@ class Oracle:
                             bc.ctypes.data_as(C.POINTER(C.c_int8)), _dp(area), _dp(nrm))
         return own, nb, bc, area, nrm
 
+    def face_offsets(self):
+        """r = x_j - x_i per face, (3, nf); the ghost centroid on boundary faces."""
+        r = np.empty((3, self.nf))
+        lib().orc_face_offsets(self.h, _dp(r))
+        return r
+
     # method ----------------------------------------------------------------
     def assign_levels(self):
         dtmin = C.c_double()
@@ -286,6 +297,16 @@ def boundary_flux(bc, WL, n, gamma=1.4, tol=1e-10, maxit=50):
     if rc != 0:
         raise OracleError(f"orc_boundary_flux failed ({rc})")
     return F
+
+
+def ghost_state(bc, n, W):
+    """The boundary ghost state of the primitives W across a face of unit
+    normal n (bc 1 slip wall, 2 transmissive)."""
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    n = np.ascontiguousarray(n, dtype=np.float64)
+    Wg = np.empty(5)
+    lib().orc_ghost_state(int(bc), _dp(n), _dp(W), _dp(Wg))
+    return Wg
 
 
 def muscl_pair(Wi, Wj, gi, gj, r):

@@ -81,6 +81,72 @@ def _physical_flux(W, n, gamma=1.4):
     return np.array([r * un, *(r * un * vel + p * n), un * (E + p)])
 
 
+def test_two_rarefaction_guess_is_exact(oracle_mod):
+    """The two-rarefaction estimate (Toro Eq. 4.46) is the exact star
+    pressure when both waves are rarefactions, so Newton stops after one
+    iteration there (Toro's test 2 and random two-rarefaction problems)."""
+    assert oracle_mod.riemann((1.0, -2.0, 0.4), (1.0, 2.0, 0.4), tol=1e-12, maxit=100)[2] == 1
+    rng = np.random.default_rng(11)
+    seen = 0
+    for _ in range(300):
+        r, p, u = rng.uniform(0.2, 2, 2), rng.uniform(0.2, 2, 2), rng.uniform(-1, 1, 2)
+        ps, _, it = oracle_mod.riemann((r[0], u[0], p[0]), (r[1], u[1], p[1]), tol=1e-12,
+                                       maxit=100)
+        if ps < min(p):
+            seen += 1
+            assert it == 1, (r, u, p)
+    assert seen > 20
+
+
+def test_sampled_solution_is_mirror_symmetric_and_continuous(oracle_mod):
+    """Mirroring x -> -x swaps the sides and negates velocities: the state at
+    xi of (WL | WR) equals the mirrored state at -xi of (mirror WR | mirror
+    WL), for shock and rarefaction branches of both sides, fans included;
+    and the fan joins its head state and the star state continuously."""
+    rng = np.random.default_rng(12)
+    for _ in range(200):
+        r, p, u = rng.uniform(0.2, 2, 2), rng.uniform(0.2, 2, 2), rng.uniform(-1.5, 1.5, 2)
+        WL, WR = (r[0], u[0], p[0]), (r[1], u[1], p[1])
+        try:
+            ps, us, _ = oracle_mod.riemann(WL, WR, tol=1e-13, maxit=100)
+        except oracle_mod.OracleError:
+            continue  # vacuum
+        mL, mR = (r[1], -u[1], p[1]), (r[0], -u[0], p[0])
+        for xi in rng.uniform(-4, 4, 8):
+            a = oracle_mod.riemann_sample(WL, WR, xi, tol=1e-13)
+            b = oracle_mod.riemann_sample(mL, mR, -xi, tol=1e-13)
+            np.testing.assert_allclose(a, (b[0], -b[1], b[2]), rtol=1e-9, atol=1e-12)
+        # the right fan, when there is one: head u_R + a_R, tail u* + a*_R
+        aR = math.sqrt(1.4 * p[1] / r[1])
+        if ps < p[1]:
+            head = u[1] + aR
+            tail = us + aR * (ps / p[1]) ** (0.4 / 2.8)
+            e = 1e-9
+            np.testing.assert_allclose(oracle_mod.riemann_sample(WL, WR, head - e, tol=1e-13),
+                                       WR, rtol=1e-6)
+            np.testing.assert_allclose(oracle_mod.riemann_sample(WL, WR, tail + e, tol=1e-13),
+                                       oracle_mod.riemann_sample(WL, WR, tail - e, tol=1e-13),
+                                       rtol=1e-6)
+
+
+def test_ghost_state_is_a_reflection(oracle_mod):
+    """A slip wall's ghost keeps density and pressure, reverses the normal
+    velocity and keeps the tangential one (so reflecting twice gives the
+    state back); a transmissive ghost is the state itself."""
+    rng = np.random.default_rng(13)
+    for _ in range(50):
+        W = np.array([rng.uniform(0.2, 2), *rng.normal(size=3), rng.uniform(0.2, 2)])
+        n = rng.normal(size=3)
+        n /= np.linalg.norm(n)
+        G = oracle_mod.ghost_state(1, n, W)
+        assert G[0] == W[0] and G[4] == W[4]
+        un, gn = W[1:4] @ n, G[1:4] @ n
+        assert gn == pytest.approx(-un, abs=1e-14)
+        np.testing.assert_allclose(G[1:4] - gn * n, W[1:4] - un * n, rtol=0, atol=1e-14)
+        np.testing.assert_allclose(oracle_mod.ghost_state(1, n, G), W, rtol=0, atol=1e-14)
+        np.testing.assert_array_equal(oracle_mod.ghost_state(2, n, W), W)
+
+
 def test_riemann_identical_states_give_physical_flux(oracle_mod):
     rng = np.random.default_rng(4)
     for _ in range(50):
@@ -186,6 +252,22 @@ def test_mesh_closure_and_volume(oracle_mod):
     # Euler's relation for the face count: 4 T = 2 F_int + F_bnd
     assert 4 * o.n == 2 * (nb >= 0).sum() + (nb < 0).sum()
     assert (nb < 0).sum() == 6 * 2 * 7 * 7
+    b = nb < 0
+    assert area[b].sum() == pytest.approx(6.0, rel=1e-13)  # the unit cube's surface
+    # centroid offsets: to the neighbour's centroid; on a boundary face to the
+    # ghost centroid, the mirror image of the cell's in the face plane (the
+    # box's faces are the planes x_d = 0 and x_d = 1, with normals -e_d, +e_d)
+    r = o.face_offsets()
+    np.testing.assert_allclose(r[:, ~b], xc[:, nb[~b]] - xc[:, own[~b]], rtol=0, atol=1e-15)
+    d = np.abs(nrm[:, b]).argmax(axis=0)
+    cols = np.arange(b.sum())
+    assert np.allclose(np.abs(nrm[:, b][d, cols]), 1.0, atol=1e-14)
+    plane = (nrm[:, b][d, cols] > 0).astype(float)
+    mid = xc[:, own[b]] + 0.5 * r[:, b]
+    np.testing.assert_allclose(mid[d, cols], plane, rtol=0, atol=1e-14)
+    tang = r[:, b] - (r[:, b] * nrm[:, b]).sum(0) * nrm[:, b]
+    assert np.abs(tang).max() < 1e-15
+    assert ((r[:, b] * nrm[:, b]).sum(0) > 0).all()  # outward, past the face
 
 
 def test_mesh_rejects_inverted_tet(oracle_mod):
@@ -295,7 +377,14 @@ def _levels_brute_force(o, cons, L, cfl=0.5, gamma=1.4):
 
 
 def test_level_assignment_matches_brute_force(oracle_mod):
+    """Local steps, dt_min and levels against numpy and a graph distance
+    transform, on a state with varying density and velocity (so that every
+    term of the local step matters: with rho = 1 and u = 0, rho c = c)."""
     mesh, prim = I.blast_case(n=9, ratio=8.0)
+    rng = np.random.default_rng(14)
+    prim = prim.copy()
+    prim[0] *= rng.uniform(0.5, 2.0, prim.shape[1])
+    prim[1:4] += 0.5 * rng.normal(size=(3, prim.shape[1]))
     o = oracle_mod.Oracle(mesh, max_levels=5)
     o.set_prim(prim)
     dtmin, lev, counts = o.assign_levels()
@@ -322,21 +411,51 @@ def test_free_stream_preserved_multilevel(oracle_mod):
     assert rel.max() <= 1e-13
 
 
+def _tilted_blast(n):
+    """The blast with the pressure tilted by 0.05 (x + 2y + 3z): opposite
+    walls feel different pressures, so the walls' momentum impulse is far
+    from zero (a centred blast in a box would cancel it by symmetry)."""
+    mesh, prim = I.blast_case(n=n, ratio=8.0)
+    xc = mesh.xyz[mesh.tets].mean(axis=1).T
+    prim = prim.copy()
+    prim[4] += 0.05 * (xc[0] + 2.0 * xc[1] + 3.0 * xc[2])
+    return mesh, prim
+
+
+def _ledger_balance(o, cycles):
+    vol, _ = o.cell_geometry()
+    M0 = (o.get_cons() * vol).sum(axis=1)
+    o.advance(cycles)
+    M1 = (o.get_cons() * vol).sum(axis=1)
+    led = o.boundary_ledger()
+    scale = np.abs(o.get_cons() * vol).sum(axis=1).max()
+    return M1 - M0 + led, led, scale
+
+
 @pytest.mark.parametrize("L", [1, 4])
 def test_conservation_ledger(oracle_mod, L):
     """sum_i V_i U_i(t) + boundary flux integral = sum_i V_i U_i(0), to
     round-off, across level interfaces too."""
-    mesh, prim = I.blast_case(n=10, ratio=8.0)
+    mesh, prim = _tilted_blast(10)
     o = oracle_mod.Oracle(mesh, max_levels=L)
     o.set_prim(prim)
-    vol, _ = o.cell_geometry()
-    M0 = (o.get_cons() * vol).sum(axis=1)
-    o.advance(3)
-    M1 = (o.get_cons() * vol).sum(axis=1)
-    led = o.boundary_ledger()
-    scale = np.abs(o.get_cons() * vol).sum(axis=1).max()
-    assert np.abs(M1 - M0 + led).max() <= 1e-14 * scale
+    bal, led, scale = _ledger_balance(o, 3)
+    assert np.abs(bal).max() <= 1e-14 * scale
     assert led[0] == 0.0 and led[4] == 0.0        # walls pass no mass or energy
+    assert np.abs(led[1:4]).min() > 1e-5 * scale  # but a momentum impulse
+
+
+def test_conservation_ledger_through_open_ends(oracle_mod):
+    """Flow through the transmissive ends of the Sod tube: mass, momentum
+    and energy cross the boundary, and the ledger balances them."""
+    mesh, prim = I.sod_case()
+    prim = prim.copy()
+    prim[1] = 0.3
+    o = oracle_mod.Oracle(mesh, max_levels=1)
+    o.set_prim(prim)
+    bal, led, scale = _ledger_balance(o, 20)
+    assert np.abs(bal).max() <= 1e-14 * scale
+    assert abs(led[0]) > 1e-4 * scale and abs(led[4]) > 1e-4 * scale
 
 
 def test_single_level_adaptive_equals_global_stepping_bitwise(oracle_mod):
@@ -499,18 +618,14 @@ def test_paper_order_conservation_ledger(oracle_mod, L):
     """The deferred intensive correction replaces every provisional
     interface integral by the finer side's: totals are conserved to
     round-off."""
-    mesh, prim = I.blast_case(n=10, ratio=8.0)
+    mesh, prim = _tilted_blast(10)
     o = oracle_mod.Oracle(mesh, max_levels=L)
     o.set_prim(prim)
     o.set_order(1)
-    vol, _ = o.cell_geometry()
-    M0 = (o.get_cons() * vol).sum(axis=1)
-    o.advance(3)
-    M1 = (o.get_cons() * vol).sum(axis=1)
-    led = o.boundary_ledger()
-    scale = np.abs(o.get_cons() * vol).sum(axis=1).max()
-    assert np.abs(M1 - M0 + led).max() <= 1e-14 * scale
+    bal, led, scale = _ledger_balance(o, 3)
+    assert np.abs(bal).max() <= 1e-14 * scale
     assert led[0] == 0.0 and led[4] == 0.0
+    assert np.abs(led[1:4]).min() > 1e-5 * scale
 
 
 def test_paper_order_free_stream_preserved(oracle_mod):
