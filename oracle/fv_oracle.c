@@ -34,6 +34,30 @@
  * Loops are in natural order; OpenMP is used only over independent items
  * (each iteration writes its own slot), so results do not depend on the
  * thread count.  Build with -ffp-contract=off.
+ *
+ * Pins (tests/test_oracle_pins.py; no function is unpinned):
+ *   riemann_star, riemann_sample  Toro's Table 4.3 (p*, u* and the star
+ *       densities of five tests); exact guess and one Newton iteration on
+ *       two rarefactions; mirror symmetry of the sampled solution and its
+ *       continuity at fan edges; Sod's self-similar profile;
+ *   godunov_flux, boundary_flux, ghost_state  identical states give the
+ *       physical flux; supersonic flow is upwind; F(WL,WR,n) = -F(WR,WL,-n);
+ *       a wall passes only the star pressure, equal to the Godunov flux
+ *       against the reflected state; the ghost is a reflection (wall) or a
+ *       copy (transmissive);
+ *   muscl_pair, minmod  textbook 1D MUSCL-minmod on a uniform chain;
+ *   gradient_cell and the weights  exact on linear fields;
+ *   orc_create geometry  closed cells, total volume and surface, face
+ *       count, centroid offsets and mirrored ghost centroids;
+ *   local_dt, orc_assign_levels  numpy and a graph distance transform;
+ *   phase_at, phase_at_paper  the tau(s) example of Sec. 2.2 and Alg. 2's
+ *       loops; per-cycle update counts = C(tau) and the paper's Tables 1-3;
+ *   the phases  free stream kept; conservation ledger to round-off (walls
+ *       with a net impulse, open ends with through-flow; both orders); one
+ *       level = global Heun stepping bitwise; Sod converges to the exact
+ *       solution; better than first-order time consistency across levels.
+ * tests/test_oracle_mutants.py plants one plausible mistake at a time in a
+ * copy of this file and checks that some pin fails.
  */
 #include <math.h>
 #include <stdint.h>

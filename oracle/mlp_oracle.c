@@ -33,7 +33,9 @@
  * differences; the first two Adam steps against their closed forms;
  * features of mirrored states; the Sod star pressure of Toro's table; the
  * target of two rarefactions is 0 and the weak-shock scaling keeps the
- * target bounded as the shock vanishes.
+ * target bounded as the shock vanishes.  tests/test_oracle_mutants.py plants
+ * one plausible mistake at a time in a copy of this file and checks that
+ * some pin fails.
  */
 #include <math.h>
 #include <stdint.h>
