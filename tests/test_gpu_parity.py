@@ -227,22 +227,66 @@ def test_fp32_flux_sod(fvmod, orc):
     assert err <= TOL_FP32
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_conservation_ledger_gpu(fvmod, precision):
-    """Exact conservation in both precision modes (the FP32 mode keeps the
-    flux time integrals and residual sums in FP64)."""
-    mesh, prim = I.blast_case(n=12, ratio=8.0)
-    g = fvmod.Mesh(mesh, max_levels=4, precision=precision)
-    g.set_state(prim)
+def _tilted_blast(n):
+    """The blast with the pressure tilted by 0.05 (x + 2y + 3z): opposite
+    walls feel different pressures, so their net momentum impulse is far
+    from zero (a centred blast in a box cancels it by symmetry)."""
+    mesh, prim = I.blast_case(n=n, ratio=8.0)
+    xc = mesh.xyz[mesh.tets].mean(axis=1).T
+    prim = prim.copy()
+    prim[4] += 0.05 * (xc[0] + 2.0 * xc[1] + 3.0 * xc[2])
+    return mesh, prim
+
+
+def _ledger_run(g, o, mesh, prim, cycles):
+    """Balance, GPU ledger, oracle ledger, the field's scale and the gross
+    boundary impulse (twice the largest pressure next to the boundary x the
+    boundary's area x the time), the scale of the ledger's rounding."""
     vol = g.volumes()
     M0 = (g.get_state() * vol).sum(axis=1)
-    g.advance(4)
+    g.advance(cycles)
+    o.advance(cycles)
     U = g.get_state()
     M1 = (U * vol).sum(axis=1)
     led = g.boundary_ledger()
     scale = np.abs(U * vol).sum(axis=1).max()
-    assert np.abs(M1 - M0 + led).max() <= 1e-14 * scale
+    _, nb, _, area, _ = o.face_data()
+    p_bnd = prim[4][(mesh.face_bc != 0).any(axis=1)].max()
+    gross = 2.0 * p_bnd * area[nb < 0].sum() * o.t
+    return M1 - M0 + led, led, o.boundary_ledger(), scale, gross
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_conservation_ledger_gpu(fvmod, orc, precision):
+    """Exact conservation in both precision modes (the FP32 mode keeps the
+    flux time integrals and residual sums in FP64), with a net wall impulse;
+    the ledger itself matches the oracle's (1e-12 in FP64, 1e-5 with FP32
+    fluxes, of the gross boundary impulse)."""
+    mesh, prim = _tilted_blast(12)
+    g, o = pair(fvmod, orc, mesh, prim, 4, precision=precision)
+    bal, led, lo, scale, gross = _ledger_run(g, o, mesh, prim, 4)
+    assert np.abs(bal).max() <= 1e-14 * scale
     assert led[0] == 0.0 and led[4] == 0.0
+    assert np.abs(led[1:4]).min() > 1e-5 * scale
+    assert np.abs(lo[1:4]).min() > 100 * 1e-5 * gross  # the comparison has teeth
+    tol = (1e-12 if precision == 0 else 1e-5) * gross
+    assert np.abs(led - lo).max() <= tol, (led, lo, gross)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_ledger_through_open_ends_gpu(fvmod, orc, precision):
+    """Flow through the Sod tube's transmissive ends: mass, momentum and
+    energy cross the boundary, the totals balance to round-off, and the
+    ledger matches the oracle's."""
+    mesh, prim = I.sod_case()
+    prim = prim.copy()
+    prim[1] = 0.3
+    g, o = pair(fvmod, orc, mesh, prim, 1, precision=precision)
+    bal, led, lo, scale, gross = _ledger_run(g, o, mesh, prim, 20)
+    assert np.abs(bal).max() <= 1e-14 * scale
+    assert abs(led[0]) > 1e-4 * scale and abs(led[4]) > 1e-4 * scale
+    tol = (1e-12 if precision == 0 else 1e-5) * gross
+    assert np.abs(led - lo).max() <= tol, (led, lo, gross)
 
 
 def test_free_stream_gpu(fvmod):
