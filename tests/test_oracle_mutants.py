@@ -119,6 +119,21 @@ MUTANTS = [
      "double phi = dt * (o->F1A[5 * f + c] + F2A[c]);", 0),
     ("boundary ledger misses the paper-order corrector integral", FV,
      "if (o->fnb[f] < 0) o->BND[5 * f + c] += phi;", "(void)0;", 1),
+    ("residual: sign", FV,
+     "for (int c = 0; c < 5; ++c) R_soa[c * o->nc + i] = -S[c] / o->vol[i];",
+     "for (int c = 0; c < 5; ++c) R_soa[c * o->nc + i] = S[c] / o->vol[i];", 0),
+    ("residual at stage 2 one subiteration after the step start", FV,
+     "int64_t T = o->tn[k] + (stage == 2 ? ((int64_t)1 << k) : 0);",
+     "int64_t T = o->tn[k] + (stage == 2 ? 1 : 0);", 0),
+    ("global Heun step: second stage on U^n", FV,
+     "  o->U = o->Us;\n  compute_W(o, 0);", "  compute_W(o, 0);", 0),
+    ("face sign of the neighbour cell", FV,
+     "o->csgn[4 * nb->tet + nb->j] = -1;", "o->csgn[4 * nb->tet + nb->j] = 1;", 0),
+    ("LS weights: offsets of the neighbour's faces not reversed", FV,
+     "double s = o->csgn[4 * i + j] > 0 ? 1.0 : -1.0;", "double s = 1.0;", 0),
+    ("state check accepts a negative pressure", FV,
+     "return (W[0] > 0.0 && W[4] > 0.0 && isfinite(W[0])",
+     "return (W[0] > 0.0 && isfinite(W[0])", 0),
     # the paper's order
     ("paper order: provisional integral with the corrector's sign", FV,
      "o->ACC[5 * f + c] -= prov;", "o->ACC[5 * f + c] += prov;", 0),

@@ -397,6 +397,29 @@ def test_level_assignment_matches_brute_force(oracle_mod):
     assert np.abs(lev[own[m]].astype(int) - lev[nb[m]]).max() <= 1   # Sec. 2.2
 
 
+def test_nonphysical_states_are_reported(oracle_mod):
+    """A state with non-positive pressure or density stops the scheme with
+    an error instead of running on (the level assignment checks every cell
+    first); positive states pass."""
+    mesh, prim = I.blast_case(n=5)
+    o = oracle_mod.Oracle(mesh, max_levels=2)
+    o.set_prim(prim)
+    cons = o.get_cons()
+    for comp, value in ((4, 0.5 * (cons[1, 7] ** 2 + cons[2, 7] ** 2 + cons[3, 7] ** 2) / cons[0, 7]
+                         - 1e-3), (0, -1.0)):
+        bad = cons.copy()
+        bad[comp, 7] = value          # E below the kinetic energy, or rho < 0
+        o.set_cons(bad)
+        with pytest.raises(RuntimeError, match="non-physical"):
+            o.assign_levels()
+    o.set_cons(cons)
+    o.assign_levels()
+    with pytest.raises(RuntimeError):
+        bad = prim.copy()
+        bad[4, 3] = -0.1
+        o.set_prim(bad)
+
+
 # ------------------------------------------------------- whole-scheme pins
 def test_free_stream_preserved_multilevel(oracle_mod):
     mesh, prim = I.uniform_flow_case(n=6)
