@@ -82,10 +82,10 @@ def autotune(target, signature: str, stream=None, reps: int = 3, cache_path: str
     tried = [(list(best), best_ms)]
     for k in ORDER:
         for v in CANDIDATES[KINDS[k]]:
-            if v == best[k]:
-                continue
             cand = list(best)
             cand[k] = v
+            if any(cand == t for t, _ in tried):  # timed already
+                continue
             target.set_launch(cand)
             ms = _time_cycles(torch, target, stream, reps, reset)
             tried.append((cand, ms))

@@ -1,6 +1,7 @@
 """Host-side logic of the benchmark and the learned-guess pipeline that runs
 without a GPU: the level-history summary (the paper's Sec. 5 shares), the
 launch count against the schedule, and the face-frame marshalling."""
+import json
 import os
 import sys
 
@@ -184,3 +185,73 @@ def test_clock_rejection_rule():
         assert bench.clocks_rejected({**ok, "reasons": [r]})
     assert bench.clocks_rejected({**ok, "sm_mhz": 1200.0})  # stuck low, no reason
     assert not bench.clocks_rejected({"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]})
+
+
+class _FakeClock:
+    t = 0.0
+
+
+class _FakeEvent:
+    def __init__(self, enable_timing=False):
+        self.t = None
+
+    def record(self, stream=None):
+        self.t = _FakeClock.t
+
+    def synchronize(self):
+        pass
+
+    def elapsed_time(self, other):
+        return other.t - self.t
+
+
+class _FakeTarget:
+    """A mesh whose cycle costs more the farther its blocks per SM are from
+    an optimum; advance() moves the fake clock on."""
+
+    def __init__(self, opt):
+        self.opt, self.launch, self.advances, self.resets = opt, [8, 8, 16, 8], 0, 0
+
+    def get_launch(self):
+        return list(self.launch)
+
+    def set_launch(self, per_sm):
+        self.launch = list(per_sm)
+
+    def advance(self, n, stream=None, want_time=True):
+        self.advances += 1
+        _FakeClock.t += 1.0 + sum((a - b) ** 2 for a, b in zip(self.launch, self.opt)) * 1e-3
+
+
+def test_autotuner_descends_and_caches(tmp_path, monkeypatch):
+    """Coordinate descent over the kernel kinds finds the optimum a separable
+    cost puts among the candidates, times every candidate from the reset
+    state, stores the choice under the GPU and workload key, and a second
+    call applies the cached choice without timing anything."""
+    import torch
+    from paper_1704_01144_gb300 import autotune as AT
+    monkeypatch.setattr(torch.cuda, "get_device_name", lambda *a: "FakeGPU")
+    monkeypatch.setattr(torch.cuda, "current_device", lambda: 0)
+    monkeypatch.setattr(torch.cuda, "Event", _FakeEvent)
+    cache = str(tmp_path / "tune.json")
+    opt = [16, 4, 32, 16]
+    tgt = _FakeTarget(opt)
+
+    def reset():
+        tgt.resets += 1
+
+    best, info = AT.autotune(tgt, "sig", stream=object(), reps=2, cache_path=cache, reset=reset)
+    assert best == opt and tgt.launch == opt and not info["cached"]
+    n_timed = len(info["tried"])
+    assert n_timed == 1 + sum(len(AT.CANDIDATES[k]) - 1 for k in AT.KINDS)
+    assert tgt.resets == n_timed and tgt.advances == n_timed * 3  # capture + 2 reps each
+    assert info["ms"] == pytest.approx(1.0)
+    stored = json.load(open(cache))
+    assert stored["FakeGPU|sig"]["per_sm"] == opt
+    other = _FakeTarget([4, 4, 8, 4])
+    best2, info2 = AT.autotune(other, "sig", stream=object(), cache_path=cache)
+    assert info2["cached"] and best2 == opt and other.launch == opt and other.advances == 0
+    best3, info3 = AT.autotune(_FakeTarget(opt), "other-workload", stream=object(), reps=1,
+                               cache_path=cache)
+    assert not info3["cached"] and set(json.load(open(cache))) == {"FakeGPU|sig",
+                                                                   "FakeGPU|other-workload"}
