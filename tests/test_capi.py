@@ -79,3 +79,20 @@ def test_header_is_plain_c_and_cxx(tmp_path, std, compiler, flags):
                         "-I", os.path.join(ROOT, "include"), "-c", str(src), "-o", str(tmp_path / "o.o")],
                        capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_product_path_fails_loudly_without_a_gpu_or_library(libfv, monkeypatch):
+    """There is no CPU fallback: without a CUDA device the first call that
+    needs one raises FvError with FV_ERR_CUDA, and without the built library
+    the binding raises ImportError."""
+    import torch
+    from paper_1704_01144_gb300 import fv, inputs as I
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    mesh, _ = I.blast_case(n=3)
+    with pytest.raises(fv.FvError, match="FV_ERR_CUDA"):
+        fv.Mesh(mesh, max_levels=2)
+    monkeypatch.setattr(fv, "_lib", None)
+    monkeypatch.setattr(fv, "library_path", lambda: os.path.join(ROOT, "no_such_libfv.so"))
+    with pytest.raises(ImportError, match="no CPU fallback"):
+        fv.lib()
