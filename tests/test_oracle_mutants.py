@@ -134,7 +134,15 @@ MUTANTS = [
     ("state check accepts a negative pressure", FV,
      "return (W[0] > 0.0 && W[4] > 0.0 && isfinite(W[0])",
      "return (W[0] > 0.0 && isfinite(W[0])", 0),
+    ("predictor gradients only for the faces' owner cells", FV,
+     "if (o->fnb[f] >= 0) o->mark[o->fnb[f]] = 1;", "(void)0;", 0),
+    ("faces of the highest active level skipped at the step start", FV,
+     "    if (o->flev[f] <= tau) {\n      o->mark", "    if (o->flev[f] < tau) {\n      o->mark", 0),
     # the paper's order
+    ("paper order: no extrapolation past the predicted state", FV,
+     "} else if (num == ((int64_t)1 << k)) {", "} else if (num >= ((int64_t)1 << k)) {", 0),
+    ("paper order: commit also corrects own-level faces", FV,
+     "if (o->flev[f] >= k) continue;", "if (o->flev[f] > k) continue;", 0),
     ("paper order: provisional integral with the corrector's sign", FV,
      "o->ACC[5 * f + c] -= prov;", "o->ACC[5 * f + c] += prov;", 0),
     ("paper order: commit ignores the interface correction", FV,
@@ -157,6 +165,10 @@ MUTANTS = [
      "double num = aL + aR - 0.5 * (gamma - 1.0) * (uR - uL);",
      "double num = aL + aR + 0.5 * (gamma - 1.0) * (uR - uL);", 0),
     ("shock scale squared, not cubed", MLP, "return r * r * r;", "return r * r;", 0),
+    ("feature: left velocity not taken relative to the mean", MLP,
+     "x[1] = (pair[1] - ub) / ab;", "x[1] = pair[1] / ab;", 0),
+    ("target 0 relative to the two-rarefaction guess", MLP,
+     "if (target == 0) return log(ps / pb);", "if (target == 0) return log(ps / ptr);", 0),
     ("target 1: log of the inverse ratio", MLP,
      "return sc > 0.0 ? log(ps / ptr) / sc : 0.0;", "return sc > 0.0 ? log(ptr / ps) / sc : 0.0;", 0),
     ("forward pass: first layer transposed", MLP,
