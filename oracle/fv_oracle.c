@@ -55,7 +55,9 @@
  *   the phases  free stream kept; conservation ledger to round-off (walls
  *       with a net impulse, open ends with through-flow; both orders); one
  *       level = global Heun stepping bitwise; Sod converges to the exact
- *       solution; better than first-order time consistency across levels.
+ *       solution; better than first-order time consistency across levels;
+ *       the two orders agree to O(dt^2); a begin phase's predictor equals
+ *       the level residual at its time (first and later subiterations).
  * tests/test_oracle_mutants.py plants one plausible mistake at a time in a
  * copy of this file and checks that some pin fails.
  */
