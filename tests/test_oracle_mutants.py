@@ -73,7 +73,13 @@ MUTANTS = [
     ("MUSCL right state from the left cell's gradient", FV,
      "double gjr = (gj[3 * c] * r[0] + gj[3 * c + 1] * r[1]) + gj[3 * c + 2] * r[2];",
      "double gjr = (gi[3 * c] * r[0] + gi[3 * c + 1] * r[1]) + gi[3 * c + 2] * r[2];", 0),
+    ("left shock speed: sign of the sound-speed term", FV,
+     "double SL = uL - aL * sqrt(", "double SL = uL + aL * sqrt(", 0),
     # geometry and the least-squares gradient
+    ("cell centroid: 1/5 for 1/4", FV,
+     "+ x[3][d]) * 0.25;", "+ x[3][d]) * 0.2;", 0),
+    ("face normals toward the owner", FV,
+     "if (vdot(av, to) > 0.0)", "if (vdot(av, to) < 0.0)", 0),
     ("LS matrix inverse: sign of a cofactor", FV,
      "double c01 = M[1][2] * M[2][0] - M[1][0] * M[2][2];",
      "double c01 = M[1][0] * M[2][2] - M[1][2] * M[2][0];", 0),
@@ -89,6 +95,8 @@ MUTANTS = [
      "return (((2.0 * o->cfl) * o->vol[i]) * r) / S;", "return ((o->cfl * o->vol[i]) * r) / S;", 0),
     ("local step: c in place of rho c", FV,
      "double rc = sqrt((o->gas.g * p) * r);", "double rc = sqrt((o->gas.g * p) / r);", 0),
+    ("local step: signed normal velocity", FV,
+     "S = S + o->farea[f] * (fabs(mn) + rc);", "S = S + o->farea[f] * (mn + rc);", 0),
     ("neighbour rule allows a jump of two levels", FV,
      "if (o->lev[i] > o->lev[nb] + 1) {", "if (o->lev[i] > o->lev[nb] + 2) {", 0),
     ("face level = the coarser side", FV,
@@ -148,6 +156,8 @@ MUTANTS = [
     ("paper order: commit ignores the interface correction", FV,
      "o->U[5 * i + c] = any ? o->Us[5 * i + c] - S[c] / o->vol[i] : o->Us[5 * i + c];",
      "o->U[5 * i + c] = o->Us[5 * i + c];", 0),
+    ("paper order: commit keeps the interface accumulators", FV,
+     "for (int c = 0; c < 5; ++c) o->ACC[5 * f + c] = 0.0;", "for (int c = 0; c < 5; ++c) (void)0;", 1),
     ("paper order: correctors finest first", FV,
      "for (int k = tau; k >= 0; --k) {\n      if (idx == 0) {\n        ph.kind = 2;",
      "for (int k = 0; k <= tau; ++k) {\n      if (idx == 0) {\n        ph.kind = 2;", 0),
