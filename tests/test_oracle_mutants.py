@@ -200,6 +200,16 @@ MUTANTS = [
      "theta[k] -= lr * m[k] / (sqrt(v[k]) + eps);", 0),
     ("bfloat16 rounding: ties away from zero", MLP,
      "u += 0x7fffu + ((u >> 16) & 1u);", "u += 0x8000u;", 0),
+    ("mean sound speed from p rho instead of p / rho", MLP,
+     "double ab = sqrt(gamma * pb / rb);", "double ab = sqrt(gamma * pb * rb);", 0),
+    ("quantised pass: inputs not rounded", MLP,
+     "xq[i] = (double)to_bf16(x[NIN * s + i]);", "xq[i] = (double)x[NIN * s + i];", 0),
+    ("quantised pass: output weights rounded too", MLP,
+     "out += (double)theta[OFF_W3 + o] * orc_gelu(a);",
+     "out += (double)to_bf16(theta[OFF_W3 + o]) * orc_gelu(a);", 0),
+    ("loss not averaged over the samples", MLP, "*loss = L / (double)n;", "*loss = L;", 0),
+    ("Adam first moment with beta2", MLP,
+     "m[k] = b1 * m[k] + (1.0 - b1) * grad[k];", "m[k] = b1 * m[k] + (1.0 - b2) * grad[k];", 0),
     ("quantised pass: first hidden layer not rounded", MLP,
      "h1[o] = (double)to_bf16((float)orc_gelu(a));", "h1[o] = orc_gelu(a);", 0),
 ]
