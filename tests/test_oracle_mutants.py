@@ -1,12 +1,13 @@
 """Planted mistakes: the oracle's pins must catch each of them.
 
 Every case plants one plausible mistake -- a dropped term, a wrong sign, a
-wrong index or operand, an off-by-one in the schedule -- in a copy of the
-oracle's C source, compiles the copy with the oracle's own flags, and runs
-the pins (`test_oracle_pins.py`, `test_oracle_mlp.py`) against it in a child
-process that loads the copy through FV_ORACLE_LIB.  A case passes when at
-least one pin fails.  The unmodified oracle passes every pin (the pin files
-themselves).  CPU only: the copies live in pytest's temporary directory.
+wrong index or operand, an off-by-one in the schedule -- in a copy of one of
+the oracle's C sources, compiles the copy with the oracle's own flags, and
+runs that source's pins (`test_oracle_pins.py` for fv_oracle.c,
+`test_oracle_mlp.py` for mlp_oracle.c) in a child process that loads the
+copy through FV_ORACLE_LIB.  A case passes when at least one pin fails.  The
+unmodified oracle passes every pin (the pin files themselves).  CPU only:
+the copies live in pytest's temporary directory.
 
 Mistakes that leave every result unchanged (the sign of a Newton slope, say,
 which changes only how the iteration converges) are not planted: no pin on
@@ -228,10 +229,13 @@ def _plant(src, text, repl, occ):
     return src[:pos] + repl + src[pos + len(text):]
 
 
-def _run_pins(lib):
+# the pins of each source file
+PINS = {FV: "tests/test_oracle_pins.py", MLP: "tests/test_oracle_mlp.py"}
+
+
+def _run_pins(lib, pins):
     env = dict(os.environ, FV_ORACLE_LIB=lib, OMP_NUM_THREADS="2")
-    cmd = [sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-           "tests/test_oracle_pins.py", "tests/test_oracle_mlp.py"]
+    cmd = [sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", pins]
     try:
         r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
     except subprocess.TimeoutExpired:
@@ -262,7 +266,7 @@ def test_every_planted_mistake_fails_a_pin(tmp_path):
             out.write_text(_plant(srcs[p], text, repl, occ) if p == path else srcs[p])
             files.append(str(out))
         lib = B.compile_lib(files, str(d / "liboracle.so"))
-        rc, tail = _run_pins(lib)
+        rc, tail = _run_pins(lib, PINS[path])
         return name, rc, tail
 
     with cf.ThreadPoolExecutor(max_workers=max(2, min(8, os.cpu_count() or 2))) as ex:
