@@ -255,3 +255,37 @@ def test_autotuner_descends_and_caches(tmp_path, monkeypatch):
                                cache_path=cache)
     assert not info3["cached"] and set(json.load(open(cache))) == {"FakeGPU|sig",
                                                                    "FakeGPU|other-workload"}
+
+
+def test_kernel_hash_ignores_comments_only():
+    """The hash that gates the committed DRAM counters changes with code,
+    not with comments or trailing blanks; string literals keep their
+    comment-like text."""
+    import bench
+    a = 'int f(int x) { // twice\n  return 2 * x; /* plain */ }\nconst char *s = "a // b";\n'
+    b = 'int f(int x) { // two times x\n  return 2 * x; /* doubled */ }   \n\nconst char *s = "a // b";\n'
+    c = 'int f(int x) {\n  return 3 * x; }\nconst char *s = "a // b";\n'
+    assert bench.strip_comments(a) == bench.strip_comments(b)
+    assert bench.strip_comments(a) != bench.strip_comments(c)
+    assert '"a // b"' in bench.strip_comments(a)
+
+
+def test_committed_traffic_counters_parse(monkeypatch):
+    """The committed ncu summary yields the per-unit DRAM bytes of both
+    kernel classes in both modes when the sources hash to its recorded
+    value, and nothing otherwise."""
+    import bench
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "not-the-recorded-hash")
+    assert bench.measured_traffic() is None
+    monkeypatch.undo()
+    recorded = None
+    with open(os.path.join(ROOT, "profiles", "dram_traffic_blast1m.md")) as fh:
+        for ln in fh:
+            if "kernel_source_sha256_16:" in ln:
+                recorded = ln.split(":", 1)[1].strip()
+    assert recorded and len(recorded) == 16
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: recorded)
+    t = bench.measured_traffic()
+    for key in ("flux_fp32", "update_fp32", "flux_fp64", "update_fp64"):
+        v = float(t[f"{key}_dram_bytes_per_unit"])
+        assert 50.0 < v < 1000.0
