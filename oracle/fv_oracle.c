@@ -39,7 +39,9 @@
  *   riemann_star, riemann_sample  Toro's Table 4.3 (p*, u* and the star
  *       densities of five tests); exact guess and one Newton iteration on
  *       two rarefactions; mirror symmetry of the sampled solution and its
- *       continuity at fan edges; Sod's self-similar profile;
+ *       continuity at fan edges; Sod's self-similar profile; for several
+ *       gamma the jump conditions of every wave (Rankine-Hugoniot across
+ *       shocks, isentropic fans with their characteristic structure);
  *   godunov_flux, boundary_flux, ghost_state  identical states give the
  *       physical flux; supersonic flow is upwind; F(WL,WR,n) = -F(WR,WL,-n);
  *       a wall passes only the star pressure, equal to the Godunov flux

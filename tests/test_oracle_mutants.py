@@ -46,6 +46,12 @@ MUTANTS = [
     ("right rarefaction fan: sign of the characteristic term", FV,
      "double c = 2.0 / gp1 - (gm1 / (gp1 * aR)) * (uR - xi);",
      "double c = 2.0 / gp1 + (gm1 / (gp1 * aR)) * (uR - xi);", 0),
+    ("shock pressure function: gamma 1.4 hard-coded", FV,
+     "double A = 2.0 / (G->gp1 * rK);", "double A = 2.0 / (2.4 * rK);", 0),
+    ("left fan tail: gamma 1.4 hard-coded in the sound speed ratio", FV,
+     "double asL = aL * pow(ps / pL, gm1 / (2.0 * g));", "double asL = aL * pow(ps / pL, 1.0 / 7.0);", 0),
+    ("left star density behind a rarefaction: exponent gamma", FV,
+     "*r = rL * pow(ps / pL, 1.0 / g);", "*r = rL * pow(ps / pL, g);", 0),
     # flux assembly
     ("tangential velocity from the downwind side", FV,
      "const double *Ws = side == 0 ? WL : WR;", "const double *Ws = side == 0 ? WR : WL;", 0),

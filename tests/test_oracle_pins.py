@@ -129,6 +129,63 @@ def test_sampled_solution_is_mirror_symmetric_and_continuous(oracle_mod):
                                        rtol=1e-6)
 
 
+@pytest.mark.parametrize("gamma", [1.2, 1.4, 5.0 / 3.0, 3.0])
+def test_riemann_jump_conditions_any_gamma(oracle_mod, gamma):
+    """For any gamma the sampled star states obey the laws of each wave:
+    across a shock the Rankine-Hugoniot conditions (mass, momentum and
+    energy fluxes equal in the shock's frame, its speed taken from the mass
+    condition); across a rarefaction constant entropy p / rho^gamma and the
+    Riemann invariant u -+ 2a/(gamma-1); across the contact, equal pressure
+    and velocity."""
+    rng = np.random.default_rng(15)
+    seen = {"shock": 0, "fan": 0}
+    for _ in range(200):
+        r, p, u = rng.uniform(0.2, 3, 2), rng.uniform(0.1, 5, 2), rng.uniform(-1, 1, 2)
+        WL, WR = (r[0], u[0], p[0]), (r[1], u[1], p[1])
+        try:
+            ps, us, _ = oracle_mod.riemann(WL, WR, gamma=gamma, tol=1e-13, maxit=100)
+        except oracle_mod.OracleError:
+            continue
+        e = 1e-9 * (1.0 + abs(us))
+        sl = oracle_mod.riemann_sample(WL, WR, us - e, gamma=gamma, tol=1e-13)
+        sr = oracle_mod.riemann_sample(WL, WR, us + e, gamma=gamma, tol=1e-13)
+        assert sl[2] == pytest.approx(ps, rel=1e-9) and sr[2] == pytest.approx(ps, rel=1e-9)
+        assert sl[1] == pytest.approx(us, abs=1e-9) and sr[1] == pytest.approx(us, abs=1e-9)
+        for K, star, sgn in ((WL, sl, -1.0), (WR, sr, 1.0)):
+            r1, u1, p1 = K
+            r2, u2, p2 = star
+            if p2 > p1 * (1 + 1e-9):  # shock
+                seen["shock"] += 1
+                S = (r2 * u2 - r1 * u1) / (r2 - r1)
+                m1, m2 = r1 * (u1 - S), r2 * (u2 - S)
+                assert m2 == pytest.approx(m1, rel=1e-8, abs=1e-10)
+                assert m1 * u1 + p1 == pytest.approx(m2 * u2 + p2, rel=1e-8)
+                E1 = p1 / (gamma - 1) + 0.5 * r1 * u1 * u1
+                E2 = p2 / (gamma - 1) + 0.5 * r2 * u2 * u2
+                assert (E1 + p1) * u1 - S * E1 == pytest.approx((E2 + p2) * u2 - S * E2,
+                                                                rel=1e-8, abs=1e-10)
+            elif p2 < p1 * (1 - 1e-9):  # rarefaction
+                seen["fan"] += 1
+                assert p2 / r2 ** gamma == pytest.approx(p1 / r1 ** gamma, rel=1e-9)
+                a1, a2 = math.sqrt(gamma * p1 / r1), math.sqrt(gamma * p2 / r2)
+                assert u2 - sgn * 2 * a2 / (gamma - 1) == pytest.approx(
+                    u1 - sgn * 2 * a1 / (gamma - 1), abs=1e-9 * (1 + a1))
+                # inside the fan the characteristic through the origin carries
+                # the state (u + sgn a = xi, p between p* and p_K); the star
+                # state holds only beyond the tail u* + sgn a*, with a* from
+                # the star state itself
+                head, tail = u1 + sgn * a1, u2 + sgn * a2
+                for xi in np.linspace(head, us, 13)[1:-1]:
+                    rf, uf, pf = oracle_mod.riemann_sample(WL, WR, xi, gamma=gamma, tol=1e-13)
+                    if sgn * (xi - tail) > 1e-9 * (1 + abs(tail)):          # in the fan
+                        af = math.sqrt(gamma * pf / rf)
+                        assert uf + sgn * af == pytest.approx(xi, abs=1e-9 * (1 + a1))
+                        assert p2 * (1 - 1e-12) <= pf <= p1 * (1 + 1e-12)
+                    elif sgn * (xi - tail) < -1e-9 * (1 + abs(tail)):       # star region
+                        assert (rf, uf, pf) == pytest.approx((r2, u2, p2), rel=1e-9, abs=1e-12)
+    assert seen["shock"] > 30 and seen["fan"] > 30
+
+
 def test_ghost_state_is_a_reflection(oracle_mod):
     """A slip wall's ghost keeps density and pressure, reverses the normal
     velocity and keeps the tangential one (so reflecting twice gives the
