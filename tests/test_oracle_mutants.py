@@ -55,6 +55,10 @@ MUTANTS = [
     # flux assembly
     ("tangential velocity from the downwind side", FV,
      "const double *Ws = side == 0 ? WL : WR;", "const double *Ws = side == 0 ? WR : WL;", 0),
+    ("Godunov energy: gamma 1.4 hard-coded", FV,
+     "double E0 = p0 / G->gm1 +", "double E0 = p0 / 0.4 +", 0),
+    ("transmissive energy: gamma 1.4 hard-coded", FV,
+     "double E = p / G->gm1 +", "double E = p / 0.4 +", 0),
     ("energy flux: dropped p", FV,
      "F[4] = un0 * (E0 + p0);", "F[4] = un0 * E0;", 0),
     ("momentum flux: dropped pressure", FV,

@@ -204,14 +204,17 @@ def test_ghost_state_is_a_reflection(oracle_mod):
         np.testing.assert_array_equal(oracle_mod.ghost_state(2, n, W), W)
 
 
-def test_riemann_identical_states_give_physical_flux(oracle_mod):
+@pytest.mark.parametrize("gamma", [1.4, 5.0 / 3.0])
+def test_riemann_identical_states_give_physical_flux(oracle_mod, gamma):
     rng = np.random.default_rng(4)
     for _ in range(50):
         W = np.array([rng.uniform(0.2, 2), *rng.uniform(-1, 1, 3), rng.uniform(0.2, 2)])
         n = rng.normal(size=3)
         n /= np.linalg.norm(n)
-        F = oracle_mod.godunov_flux(W, W, n)
-        np.testing.assert_allclose(F, _physical_flux(W, n), rtol=1e-12, atol=1e-13)
+        F = oracle_mod.godunov_flux(W, W, n, gamma=gamma)
+        np.testing.assert_allclose(F, _physical_flux(W, n, gamma), rtol=1e-12, atol=1e-13)
+        np.testing.assert_allclose(oracle_mod.boundary_flux(2, W, n, gamma=gamma),
+                                   _physical_flux(W, n, gamma), rtol=1e-14, atol=1e-15)
 
 
 def test_riemann_supersonic_flow_is_upwind(oracle_mod):
