@@ -78,6 +78,10 @@ MUTANTS = [
      "for (int d = 0; d < 3; ++d) Wg[1 + d] = W[1 + d] - un * n[d];", 0),
     ("minmod picks the larger slope", FV,
      "if (a > 0.0 && b > 0.0) return a < b ? a : b;", "if (a > 0.0 && b > 0.0) return a > b ? a : b;", 0),
+    ("minmod picks the larger slope when both are negative", FV,
+     "if (a < 0.0 && b < 0.0) return a > b ? a : b;", "if (a < 0.0 && b < 0.0) return a < b ? a : b;", 0),
+    ("MUSCL without the 1/2", FV,
+     "WR[c] = Wj[c] - 0.5 * minmod(2.0 * gjr - dW, dW);", "WR[c] = Wj[c] - minmod(2.0 * gjr - dW, dW);", 0),
     ("MUSCL left state: sign of dW inside the limiter", FV,
      "WL[c] = Wi[c] + 0.5 * minmod(2.0 * gir - dW, dW);",
      "WL[c] = Wi[c] + 0.5 * minmod(2.0 * gir + dW, dW);", 0),

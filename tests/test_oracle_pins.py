@@ -282,6 +282,30 @@ def test_muscl_reduces_to_textbook_1d_minmod(oracle_mod):
                                    atol=1e-14)
 
 
+def test_reconstruction_is_bounded_by_the_two_cells(oracle_mod):
+    """For any gradients and offset, each reconstructed face value lies
+    between the two cells' values (the minmod limiter never creates a new
+    extremum at the face), and a gradient that matches the jump exactly
+    (g.r = dW) is kept whole: W_L = W_R = the mean of the two cells."""
+    rng = np.random.default_rng(16)
+    for _ in range(300):
+        Wi, Wj = rng.normal(size=5), rng.normal(size=5)
+        Gi, Gj = 5 * rng.normal(size=15), 5 * rng.normal(size=15)
+        r = rng.normal(size=3)
+        WL, WR = oracle_mod.muscl_pair(Wi, Wj, Gi, Gj, r)
+        lo, hi = np.minimum(Wi, Wj), np.maximum(Wi, Wj)
+        assert (WL >= lo - 1e-15).all() and (WL <= hi + 1e-15).all()
+        assert (WR >= lo - 1e-15).all() and (WR <= hi + 1e-15).all()
+    r = np.array([0.3, -0.2, 0.5])
+    Wi, Wj = rng.normal(size=5), rng.normal(size=5)
+    G = np.zeros(15)
+    for c in range(5):
+        G[3 * c:3 * c + 3] = (Wj[c] - Wi[c]) * r / (r @ r)   # g.r = dW
+    WL, WR = oracle_mod.muscl_pair(Wi, Wj, G, G, r)
+    np.testing.assert_allclose(WL, 0.5 * (Wi + Wj), rtol=0, atol=1e-14)
+    np.testing.assert_allclose(WR, 0.5 * (Wi + Wj), rtol=0, atol=1e-14)
+
+
 def test_least_squares_gradient_exact_on_linear_fields(oracle_mod):
     mesh, _ = I.blast_case(n=6, ratio=3.0)
     o = oracle_mod.Oracle(mesh)
