@@ -168,6 +168,8 @@ MUTANTS = [
      "if (o->flev[f] >= k) continue;", "if (o->flev[f] > k) continue;", 0),
     ("paper order: provisional integral with the corrector's sign", FV,
      "o->ACC[5 * f + c] -= prov;", "o->ACC[5 * f + c] += prov;", 0),
+    ("paper order: provisional interface integral over half the step", FV,
+     "double prov = dtk * o->F1A[5 * f + c];", "double prov = 0.5 * dtk * o->F1A[5 * f + c];", 0),
     ("paper order: commit ignores the interface correction", FV,
      "o->U[5 * i + c] = any ? o->Us[5 * i + c] - S[c] / o->vol[i] : o->Us[5 * i + c];",
      "o->U[5 * i + c] = o->Us[5 * i + c];", 0),
