@@ -85,8 +85,10 @@ void fv_config_default(fv_config *cfg);
  * face of tet t opposite its local node j (FV_BC_*; interior faces 0).
  * Extracts faces, computes FP64 geometry (Sec. 2.1: the solver works on cells
  * and faces), renumbers cells along a Morton curve and uploads everything to
- * the device.  Synchronous.  Errors: FV_ERR_INVALID_ARG, FV_ERR_BAD_MESH,
- * FV_ERR_NOMEM, FV_ERR_CUDA.  *out is NULL on failure.
+ * the device.  Synchronous.  Errors: FV_ERR_INVALID_ARG (NULL argument,
+ * invalid configuration, or an empty mesh: n_tets or n_nodes <= 0, refused
+ * before any device call), FV_ERR_BAD_MESH, FV_ERR_NOMEM, FV_ERR_CUDA.
+ * *out is NULL on failure.
  */
 int fv_mesh_load(const double *xyz, int64_t n_nodes, const int64_t *tets, int64_t n_tets,
                  const int8_t *face_bc, const fv_config *cfg, fv_mesh **out);

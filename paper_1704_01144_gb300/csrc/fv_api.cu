@@ -207,6 +207,7 @@ int fv_mesh_load(const double *xyz, int64_t n_nodes, const int64_t *tets, int64_
       (cfg->precision != FV_FP64 && cfg->precision != FV_FP32_FLUX) ||
       (cfg->guess != FV_GUESS_TWO_RAREFACTION))
     return fail(FV_ERR_INVALID_ARG, "fv_mesh_load: invalid configuration");
+  if (n_tets <= 0 || n_nodes <= 0) return fail(FV_ERR_INVALID_ARG, "fv_mesh_load: bad sizes");
   CK(cudaSetDevice(cfg->device));
   fvk::init_device_info();
   HostMesh H;

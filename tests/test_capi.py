@@ -96,3 +96,25 @@ def test_product_path_fails_loudly_without_a_gpu_or_library(libfv, monkeypatch):
     monkeypatch.setattr(fv, "library_path", lambda: os.path.join(ROOT, "no_such_libfv.so"))
     with pytest.raises(ImportError, match="no CPU fallback"):
         fv.lib()
+
+
+def test_empty_inputs_are_refused_or_no_ops_without_gpu(libfv):
+    """Empty inputs are decided before any device call: an empty mesh and an
+    empty batch are refused with FV_ERR_INVALID_ARG, an empty flux batch is
+    a no-op (FV_OK, nothing read or written)."""
+    import ctypes as C
+    from paper_1704_01144_gb300 import fv
+    cfg = fv.fv_config_default()
+    xyz = (C.c_double * 3)()
+    tets = (C.c_int64 * 4)()
+    bc = (C.c_int8 * 4)()
+    out = C.c_void_p(1)
+    rc = libfv.fv_mesh_load(xyz, 1, tets, 0, bc, C.byref(cfg), C.byref(out))
+    assert rc == fv.FV_ERR_INVALID_ARG and out.value is None and "bad sizes" in fv.fv_last_error()
+    rc = libfv.fv_mesh_load(xyz, 0, tets, 1, bc, C.byref(cfg), C.byref(out))
+    assert rc == fv.FV_ERR_INVALID_ARG
+    meshes = (C.c_void_p * 1)()
+    assert libfv.fv_batch_create(meshes, 0, C.byref(out)) == fv.FV_ERR_INVALID_ARG
+    dummy = C.c_void_p(256)  # never dereferenced: nothing to do for count 0
+    assert libfv.fv_godunov_flux_batch(dummy, dummy, dummy, 0, C.byref(cfg), 0, dummy, dummy,
+                                       None) == fv.FV_OK
