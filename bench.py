@@ -360,6 +360,14 @@ def build_workload(name):
     return mesh, prim, L
 
 
+def data_desc(name):
+    if name == "sod":
+        return "synthetic (Sod tube on a Kuhn-split box)"
+    if name.startswith("ground"):
+        return "synthetic (seeded graded tet mesh, ground-plane blast wave)"
+    return "synthetic (seeded graded tet mesh, blast wave)"
+
+
 def describe(name, mesh, L):
     if name == "sod":
         return {"workload": f"Sod tube, {mesh.n_tets} tets (64x4x4 cubes, Kuhn split), L=1"}
@@ -723,7 +731,7 @@ def main_ours(args):
             "value": round(value, 1), "unit": "cell-updates/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 flux / f64 state", "data": "synthetic (seeded graded tet mesh, blast wave)",
+            "dtype": "f32 flux / f64 state", "data": data_desc(args.workload),
             "config": desc,
             "clocks": chosen["clocks"],
             "roofline": dominant(chosen, "fp32flux" in res),
@@ -896,7 +904,7 @@ def main_reference(args):
         "value": round(value, 1), "unit": "cell-updates/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic (seeded graded tet mesh, blast wave)", "config": desc,
+        "data": data_desc(args.workload), "config": desc,
         "cpu_baseline": {"value": round(value, 1), "unit": "cell-updates/s",
                          "cores": O.num_threads(), "kind": "oracle",
                          "sample": f"cycles {args.warmup + 1}..{args.warmup + args.steps} of the "

@@ -289,3 +289,24 @@ def test_committed_traffic_counters_parse(monkeypatch):
     for key in ("flux_fp32", "update_fp32", "flux_fp64", "update_fp64"):
         v = float(t[f"{key}_dram_bytes_per_unit"])
         assert 50.0 < v < 1000.0
+
+
+def test_reference_arm_prints_its_contract_line():
+    """`bench.py --impl reference` times the FP64 oracle on the host cores and
+    prints one JSON line with the reference keys (a small workload here)."""
+    import subprocess
+    import sys
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--workload", "sod", "--steps", "2", "--warmup", "3"],
+                         capture_output=True, text=True, timeout=300, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    r = json.loads(lines[0])
+    assert r["impl"] == "reference" and r["unit"] == "cell-updates/s" and r["value"] > 0
+    assert r["steps"] == 2 and r["warmup"] >= 3 and r["higher_is_better"] is True
+    assert r["data"].startswith("synthetic (Sod")
+    cb = r["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == r["value"] and cb["sample"]
+    e = r["e2e"]
+    assert e["value"] == r["value"] and e["h2d_bytes_per_step"] == 0 == e["d2h_bytes_per_step"]
