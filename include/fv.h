@@ -353,7 +353,10 @@ void fv_batch_free(fv_batch *b);
  * bc = FV_BC_INTERIOR: exact Riemann problem between WL and WR;
  * FV_BC_WALL / FV_BC_TRANSMISSIVE: boundary flux of WL (WR unused).
  * Arithmetic follows cfg->precision; gamma, newton_tol and newton_max_iter
- * come from cfg.  Device pointers; asynchronous on `stream`.
+ * come from cfg.  Device pointers; asynchronous on `stream`.  count = 0 is a
+ * no-op (FV_OK; no pointer is read).  Errors: FV_ERR_INVALID_ARG (NULL
+ * pointer, count < 0 or > 2^31 - 1, unknown bc or precision, bad gas or
+ * Newton settings), FV_ERR_CUDA.
  */
 int fv_godunov_flux_batch(const double *WL_dev, const double *WR_dev, const double *n_dev,
                           int64_t count, const fv_config *cfg, int bc, double *F_dev,
