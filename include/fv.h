@@ -301,6 +301,27 @@ int fv_get_launch(fv_mesh *m, int32_t per_sm[4]);
 int fv_set_fusion(fv_mesh *m, int64_t max_faces);
 int fv_get_fusion(fv_mesh *m, int64_t *max_faces_out);
 
+/*
+ * FP32-flux mode: the arithmetic of the predictor's residual sum
+ * (Alg. 2, "Extensive prediction": U* = U^n - (dt_k/V) sum sigma F1 A).
+ * FV_SUM_FP64 widens each FP32 flux and forms the sum and U* in FP64 from the
+ * FP64 U^n; FV_SUM_FP32 forms both in FP32 from the FP32 shadow of U^n.
+ * Either way U* is then rounded to its FP32 record, which only ever feeds the
+ * FP32 reconstruction of later fluxes; the corrector's sums, U^n and the flux
+ * time integrals are FP64 in both.  The FP64 mode ignores the setting.
+ * The default is FV_SUM_FP32: on a GB300 the FP64 sum costs 11 % of the
+ * cycle on the 1M-tet blast and on the 80M-tet ground blast, and moves the
+ * error against the FP64 reference by less than its own spread (9.1e-7
+ * against 9.3e-7 after 3 cycles of the 1M-tet blast).
+ * Setting it drops a captured graph.  Errors: FV_ERR_INVALID_ARG (NULL mesh,
+ * unknown value, inside a cycle or a batch).
+ */
+#define FV_SUM_FP32 0
+#define FV_SUM_FP64 1
+#define FV_PREDICTOR_SUM_DEFAULT FV_SUM_FP32
+int fv_set_predictor_sum(fv_mesh *m, int sum);
+int fv_get_predictor_sum(fv_mesh *m, int *sum_out);
+
 /* kernel classes of the profiler */
 #define FV_PROF_LEVELS 0 /* level assignment: dt, levels, sorts */
 #define FV_PROF_PRIM 1   /* primitives at the phase time */
@@ -376,15 +397,17 @@ int fv_probe_fma_peak(int device, int precision, double *tflops_out);
 /*
  * Level assignment that allocates nothing, for callers that cannot call
  * cudaMalloc when they need it: a host application that gives the library
- * only memory from its own fixed-budget pool, or a time loop being recorded
- * into a CUDA graph, where an allocation would synchronise the device or
- * break the capture.  The paper has no counterpart of this entry point.
+ * only memory from its own fixed-budget pool and accounts for every byte of
+ * it, or one running under an allocator that must see every device
+ * allocation.  The paper has no counterpart of this entry point.
  *
  * Same result as the level part of fv_assign_levels, on caller-owned device
  * arrays: dt_min = min_i dt_dev[i]; k_i = max{k <= max_levels-1 :
  * 2^k dt_min <= dt_i}; then max_levels-1 sweeps of
  * k_i <- min(k_i, 1 + min_j k_nbr(i,j)).  Inputs: dt_dev[n_cells] positive
- * finite local time steps; nbr_dev[4*n_cells] with nbr_dev[j*n_cells + i]
+ * finite local time steps (nothing checks this on the device: a zero,
+ * negative, infinite or NaN entry gives undefined levels and dt_min);
+ * nbr_dev[4*n_cells] with nbr_dev[j*n_cells + i]
  * the neighbour of cell i across its face j (any negative value: boundary).
  * Outputs: levels_dev[n_cells] and *dt_min_dev.  All four pointers are
  * device memory owned by the caller.  Asynchronous on `stream`.
@@ -392,11 +415,14 @@ int fv_probe_fma_peak(int device, int precision, double *tflops_out);
  * Scratch: one static device array of 256 + FV_NOALLOC_MAX_CELLS bytes that
  * every GPU which loads this library holds until the process exits.  The
  * first call on a device looks up that array's device address (with the
- * device current), so make it before any stream capture.  All calls share
- * the array and each re-initialises what it uses; calls that overlap on the
- * GPU (other streams or threads on the same device) race on it.
+ * device current) and caches it for the life of the process, so make that
+ * first call before any stream capture, and do not call it after a
+ * cudaDeviceReset.  All calls share the array and each re-initialises what
+ * it uses; calls that overlap on the GPU (other streams or threads on the
+ * same device) race on it.
  * Errors: FV_ERR_INVALID_ARG for a NULL pointer, n_cells outside
- * [1, FV_NOALLOC_MAX_CELLS] or max_levels outside [1, 8]; FV_ERR_CUDA.
+ * [1, FV_NOALLOC_MAX_CELLS], max_levels outside [1, 8] or a current device
+ * numbered 64 or above; FV_ERR_CUDA.
  */
 int fv_assign_levels_noalloc(const double *dt_dev, const int32_t *nbr_dev, int64_t n_cells,
                              int max_levels, int8_t *levels_dev, double *dt_min_dev,

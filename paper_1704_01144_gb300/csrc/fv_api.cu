@@ -237,6 +237,7 @@ int fv_mesh_load(const double *xyz, int64_t n_nodes, const int64_t *tets, int64_
   d.maxit = cfg->newton_max_iter;
   d.precision = cfg->precision;
   d.fuse_faces = FV_FUSE_FACES_DEFAULT;
+  d.pred_sum64 = FV_PREDICTOR_SUM_DEFAULT == FV_SUM_FP64;
   const bool f32 = cfg->precision == FV_FP32_FLUX;
   const int nblk_c = (int)((N + 1023) / 1024), nblk_f = (int)((F + 1023) / 1024);
   // the cell counts (2L buckets per tile), then the face counts (L per tile)
@@ -668,6 +669,25 @@ int fv_set_fusion(fv_mesh *m, int64_t max_faces) {
 int fv_get_fusion(fv_mesh *m, int64_t *max_faces_out) {
   if (!m || !max_faces_out) return fail(FV_ERR_INVALID_ARG, "fv_get_fusion: NULL argument");
   *max_faces_out = m->d.fuse_faces;
+  return FV_OK;
+}
+
+int fv_set_predictor_sum(fv_mesh *m, int sum) {
+  if (!m || (sum != FV_SUM_FP32 && sum != FV_SUM_FP64))
+    return fail(FV_ERR_INVALID_ARG, "fv_set_predictor_sum: bad argument");
+  if (m->in_batch || (m->in_cycle && m->next_phase > 0))
+    return fail(FV_ERR_INVALID_ARG, "fv_set_predictor_sum: mesh is inside a cycle or a batch");
+  m->d.pred_sum64 = sum == FV_SUM_FP64;
+  if (m->cycle_graph) {
+    cudaGraphExecDestroy(m->cycle_graph);
+    m->cycle_graph = nullptr;
+  }
+  return FV_OK;
+}
+
+int fv_get_predictor_sum(fv_mesh *m, int *sum_out) {
+  if (!m || !sum_out) return fail(FV_ERR_INVALID_ARG, "fv_get_predictor_sum: NULL argument");
+  *sum_out = m->d.pred_sum64 ? FV_SUM_FP64 : FV_SUM_FP32;
   return FV_OK;
 }
 

@@ -107,6 +107,9 @@ struct DevMesh {
   // FP32-flux mode: phases with at most this many faces fuse their gradients
   // into the flux kernel (0: never)
   int fuse_faces;
+  // FP32-flux mode: the predictor's residual sum in FP64 (FV_SUM_FP64) or
+  // FP32 (FV_SUM_FP32)
+  int pred_sum64;
   // physics
   double gamma, cfl, tol;
   int maxit;

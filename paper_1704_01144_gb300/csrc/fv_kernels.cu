@@ -994,9 +994,10 @@ __device__ __forceinline__ float flip(float v, bool neg) {
 }
 
 // stage 1 (predictor): the flux F1 A is stashed (FP32 in the FP32-flux mode,
-// where it only feeds the predictor).  stage 2 (corrector of `level`): the
-// step's flux time integral Phi = (dt_k/2) (F1 A + F2 A) is formed in FP64
-// (in the FP32-flux mode from the FP32 sum of the two fluxes) and stored; on
+// where it is an FP32 result of the FP32 flux).  stage 2 (corrector of
+// `level`): the step's flux time integral Phi = (dt_k/2) (F1 A + F2 A) is
+// formed in FP64 (in the FP32-flux mode each FP32 flux is widened first, so
+// the sum and the product are FP64 operations) and stored; on
 // a level interface (iface) Phi is added to ACC[f] (the coarse side's
 // integral), on a boundary face (bnd) to BND[f] (the conservation ledger).
 template <typename T>
@@ -1019,7 +1020,7 @@ __device__ __forceinline__ void flux_store(const DevMesh &d, int stage, int leve
     float a[REC_FA32];
     ldrec<REC_FA32>(d.FA32 + (size_t)f * REC_FA32, a);
 #pragma unroll
-    for (int c = 0; c < 5; ++c) phi[c] = h * (double)(a[c] + (float)FAt[c]);
+    for (int c = 0; c < 5; ++c) phi[c] = h * ((double)a[c] + (double)FAt[c]);
   } else {
     double a[REC_FA];
     ldrec<REC_FA>(d.FA + (size_t)f * REC_FA, a);
@@ -1284,6 +1285,32 @@ __device__ __forceinline__ void update_item(const DevMesh &d, int stage, int lev
   int i = d.cl[idx];
   unsigned own = d.cown[i];
   int4 cf = d.cf4[i];
+  if (stage == 1 && F32 && d.pred_sum64) {
+    // the predictor's residual sum in FP64 (each FP32 flux widened) and U*
+    // from the FP64 U^n; U* is rounded to its FP32 record, which only feeds
+    // fluxes
+    double S[5];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      bool neg = !((own >> j) & 1u);
+      float v[REC_FA32];
+      ldrec<REC_FA32>(d.FA32 + (size_t)nbr_of(cf, j) * REC_FA32, v);
+#pragma unroll
+      for (int c = 0; c < 5; ++c) S[c] = j == 0 ? flip((double)v[c], neg) : S[c] + flip((double)v[c], neg);
+    }
+    const int k = d.lev[i];
+    double u[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) u[c] = d.Un[c * N + i];
+    const double cdt = -scale2(dtmin, k) * d.ivol[i];
+    float r[REC_U32];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) r[c] = (float)(u[c] + cdt * S[c]);
+    r[5] = (float)k;
+    r[6] = r[7] = 0.0f;
+    strec<REC_U32>(d.Us32 + (size_t)i * REC_U32, r);
+    return;
+  }
   if (stage == 1 && F32) {
     float S[5];
 #pragma unroll

@@ -3,11 +3,11 @@
 //
 // Who needs it: code that cannot call cudaMalloc at the point where it wants
 // the temporal levels -- for example a host application that hands the
-// solver only memory from its own fixed-budget pool, or a time loop that is
-// being recorded into a CUDA graph, where an allocation would synchronise
-// the device or break the capture.  Such a caller keeps its own dt[] and
-// neighbour arrays on the device and gets the levels and dt_min written
-// into buffers it owns.
+// solver only memory from its own fixed-budget pool and accounts for every
+// byte of it, or one that runs under an allocator which must see every
+// device allocation, so that a library allocating behind its back breaks
+// the budget.  Such a caller keeps its own dt[] and neighbour arrays on the
+// device and gets the levels and dt_min written into buffers it owns.
 //
 // Scratch (the dt_min reduction word and the ping-pong level buffer of the
 // smoothing sweeps) lives in one file-scope __device__ array of fixed size,
@@ -104,11 +104,17 @@ extern "C" int fv_assign_levels_noalloc(const double *dt_dev, const int32_t *nbr
     return na_fail(FV_ERR_INVALID_ARG, "fv_assign_levels_noalloc: max_levels must be in [1, 8]");
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= FV_NOALLOC_MAX_DEVICES)
+  if (e != cudaSuccess)
     return na_fail(FV_ERR_CUDA, std::string("fv_assign_levels_noalloc: cudaGetDevice: ") +
                                     cudaGetErrorString(e));
+  if (dev < 0 || dev >= FV_NOALLOC_MAX_DEVICES)
+    return na_fail(FV_ERR_INVALID_ARG, "fv_assign_levels_noalloc: current device " + std::to_string(dev) +
+                                           " is beyond the " + std::to_string(FV_NOALLOC_MAX_DEVICES) +
+                                           " devices whose scratch address it caches");
   // once per device, with that device current: the device address of the
-  // static scratch (the host-side symbol is only a stand-in)
+  // static scratch (the host-side symbol is only a stand-in).  The address
+  // is cached for the life of the process; a cudaDeviceReset destroys the
+  // context it belongs to, and the library does not support use after one.
   void *base = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_setup_mutex);

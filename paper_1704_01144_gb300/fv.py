@@ -70,6 +70,7 @@ EXPORTS = [
     "fv_mlp_load", "fv_set_guess", "fv_harvest_pairs", "fv_godunov_flux_batch_mlp",
     "fv_use_persistent", "fv_barrier_selftest", "fv_level_history", "fv_batch_mlp_load",
     "fv_batch_set_guess", "fv_set_fusion", "fv_get_fusion", "fv_set_order", "fv_get_order",
+    "fv_set_predictor_sum", "fv_get_predictor_sum",
 ]
 
 FV_MLP_PARAMS = 4673
@@ -79,6 +80,7 @@ FV_MLP_TARGET_PBAR, FV_MLP_TARGET_TR = 0, 1
 FV_NOALLOC_MAX_CELLS = 1 << 22
 FV_FUSE_FACES_DEFAULT = 0
 FV_ORDER_FINEST_FIRST, FV_ORDER_PAPER = 0, 1
+FV_SUM_FP32, FV_SUM_FP64 = 0, 1
 
 FV_PROF_LEVELS, FV_PROF_PRIM, FV_PROF_GRAD, FV_PROF_FLUX, FV_PROF_UPDATE = range(5)
 FV_PROF_N = 5
@@ -148,6 +150,8 @@ def lib():
     L.fv_set_order.argtypes = [vp, C.c_int]
     L.fv_get_order.argtypes = [vp, C.POINTER(C.c_int)]
     L.fv_get_fusion.argtypes = [vp, C.POINTER(C.c_int64)]
+    L.fv_set_predictor_sum.argtypes = [vp, C.c_int]
+    L.fv_get_predictor_sum.argtypes = [vp, C.POINTER(C.c_int)]
     L.fv_godunov_flux_batch.argtypes = [vp, vp, vp, i64, C.POINTER(fv_config), C.c_int, vp, vp, vp]
     L.fv_assign_levels_noalloc.argtypes = [vp, vp, i64, C.c_int, vp, vp, vp]
     L.fv_get_level_lists.argtypes = [vp, C.POINTER(C.c_int64), i32p, i8p, i32p]
@@ -634,6 +638,16 @@ def fv_get_order(h):
     return a.value
 
 
+def fv_set_predictor_sum(h, sum_mode):
+    _check(lib().fv_set_predictor_sum(h, int(sum_mode)), "fv_set_predictor_sum")
+
+
+def fv_get_predictor_sum(h):
+    a = C.c_int()
+    _check(lib().fv_get_predictor_sum(h, C.byref(a)), "fv_get_predictor_sum")
+    return a.value
+
+
 def fv_batch_set_launch(b, per_sm):
     _check(lib().fv_batch_set_launch(b, _launch4(per_sm)), "fv_batch_set_launch")
 
@@ -714,6 +728,12 @@ class Mesh:
 
     def get_order(self):
         return fv_get_order(self.h)
+
+    def set_predictor_sum(self, sum_mode):
+        fv_set_predictor_sum(self.h, sum_mode)
+
+    def get_predictor_sum(self):
+        return fv_get_predictor_sum(self.h)
 
     def profile_enable(self, enable):
         fv_profile_enable(self.h, enable)

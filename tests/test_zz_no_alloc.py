@@ -1,8 +1,8 @@
 """The allocation-free level assignment (fv_assign_levels_noalloc).
 
 Some callers cannot allocate device memory when they need the levels (a
-host code that only lends the library memory from its own fixed pool, or a
-time loop recorded into a CUDA graph).  The entry point takes their device
+host code that only lends the library memory from its own fixed pool and
+accounts for every byte of it).  The entry point takes their device
 arrays and keeps its scratch in a static device array, so this test checks,
 through the C ABI, that two calls in a row (a larger mesh, then a smaller
 one, sharing that scratch) give exactly the levels and dt_min that
