@@ -1,17 +1,19 @@
 #!/usr/bin/env python
 """Benchmark of the temporally adaptive finite-volume hot path on GB300.
 
-Workload (default): spherical blast wave in the unit box on a 998,250-tet
-mesh (55^3 cubes, Kuhn split) graded 8:1 toward the centre with +-10 %
-seeded jitter, p = 10 inside r < 0.1 and 0.1 outside, rho = 1, L = 4
-temporal levels.  One step = one cycle of Algorithm 2 (level assignment +
-2^3 subiterations).  Metric: cell-updates per second weighted by the cost
-model of Sec. 2.2 (sum_k 2^(L-1-k) |Omega_k| per cycle), for the chosen form
-(FP32 reconstruction/flux, FP64 state and flux integrals) with plain FP64
-reported beside it.
+Workload (default): ground-plane half-sphere blast wave (p = 20 inside
+r < 0.1 over 0.1, rho = 1, u = 0) on a 79.87M-tet mesh of the unit box
+(237^3 cubes, Kuhn split) graded 8:1 toward (0.5, 0.5, 0) with +-10 % seeded
+jitter, the ground z = 0 a wall, L = 6 temporal levels.  One step = one
+cycle of Algorithm 2 (level assignment + 2^5 subiterations).  Metric:
+cell-updates per second weighted by the cost model of Sec. 2.2
+(sum_k 2^(L-1-k) |Omega_k| per cycle), for the chosen form (FP32
+reconstruction/flux, FP64 state, corrector sums and flux integrals) with
+plain FP64 reported beside it.  The 998,250-tet spherical blast (L = 4) is
+measured in the same run and reported as the sub-object ``blast1m``.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
-oracle on the same workload instead.
+oracle instead, on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
@@ -36,6 +38,17 @@ WORKLOADS = {
     "blast128k": (dict(n=28, ratio=8.0), 4),
     "sod": (None, 1),
     "ground80m": (dict(n=237, ratio=8.0), 6),
+}
+DEFAULT_WORKLOAD = "ground80m"
+
+# The CPU oracle's bounded sample of each workload: the same recipe on a
+# mesh it sets up and runs within seconds (the 79.87M-tet mesh alone takes
+# the oracle minutes and ~80 GB of host memory to set up), and the number of
+# cycles after which the sample restarts from its initial state (the strong
+# ground blast empties its core at the wall after a fixed physical time,
+# about 30 cycles at 100^3 cubes).
+ORACLE_SAMPLE = {
+    "ground80m": (dict(n=100, ratio=8.0), 8),
 }
 
 # Algorithmic bytes per unit of the two dominant kernels (unique bytes the
@@ -140,10 +153,11 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def measured_traffic():
-    """DRAM bytes per unit from the committed ncu summary, when it was taken
-    on the current kernel sources (else None: the counters are stale)."""
-    path = os.path.join(ROOT, "profiles", "dram_traffic_blast1m.md")
+def measured_traffic(workload: str = "blast1m"):
+    """DRAM bytes per unit from the committed ncu summary of a workload, when
+    it was taken on the current kernel sources (else None: the counters are
+    stale or there is no summary)."""
+    path = os.path.join(ROOT, "profiles", f"dram_traffic_{workload}.md")
     if not os.path.exists(path):
         return None
     vals = {}
@@ -348,9 +362,13 @@ def clocks_rejected(c) -> bool:
             and "sw_power_cap" not in c.get("reasons", []))
 
 
-def build_workload(name):
+def build_workload(name, sample=False):
+    """(mesh, initial primitives, L) of a workload; with ``sample`` the
+    oracle's bounded sample of it (the same recipe on a smaller mesh)."""
     from paper_1704_01144_gb300 import inputs as I
     kw, L = WORKLOADS[name]
+    if sample and name in ORACLE_SAMPLE:
+        kw = ORACLE_SAMPLE[name][0]
     if name == "sod":
         mesh, prim = I.sod_case()
     elif name.startswith("ground"):
@@ -358,6 +376,22 @@ def build_workload(name):
     else:
         mesh, prim = I.blast_case(**kw)
     return mesh, prim, L
+
+
+class _Shape:
+    """The sizes describe() prints, without building the mesh."""
+
+    def __init__(self, n_tets, shape):
+        self.n_tets, self.shape = n_tets, shape
+
+
+def build_workload_shape(name):
+    """(shape stand-in, L) of the full workload for its description."""
+    kw, L = WORKLOADS[name]
+    if name == "sod":
+        return _Shape(64 * 4 * 4 * 6, (64, 4, 4)), L
+    n = kw["n"]
+    return _Shape(6 * n ** 3, (n, n, n)), L
 
 
 def data_desc(name):
@@ -374,7 +408,7 @@ def describe(name, mesh, L):
     if name.startswith("ground"):
         return {"workload": f"ground-plane half-sphere blast (p 20 over 0.1), {mesh.n_tets} tets "
                             f"({mesh.shape[0]}^3 cubes, Kuhn split, 8:1 graded toward (0.5, 0.5, 0), "
-                            f"10% jitter), L={L} temporal levels"}
+                            f"10% jitter, ground z=0 a wall), L={L} temporal levels"}
     return {"workload": f"spherical blast wave, {mesh.n_tets} tets ({mesh.shape[0]}^3 cubes, "
                         f"Kuhn split, 8:1 graded, 10% jitter), L={L} temporal levels"}
 
@@ -390,12 +424,14 @@ def run_mode(fv, torch, mesh, prim, L, precision, steps, warmup, stream, flush, 
     # grid sizes picked by the project's autotuner (cached per GPU and workload)
     per_sm, tune = AT.autotune(g, f"mesh|N{g.n}|F{g.nf}|L{L}|prec{precision}{tag}", stream=stream,
                                reset=lambda: g.set_state(prim))
-    g.set_state(prim)
-    with torch.cuda.stream(stream):
-        for _ in range(warmup):
-            g.advance(1, stream=stream, want_time=False)
-    torch.cuda.synchronize()
     for attempt in range(2):
+        # every attempt starts from the initial state (the strong ground
+        # blast must stay within its first ~35 cycles)
+        g.set_state(prim)
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                g.advance(1, stream=stream, want_time=False)
+        torch.cuda.synchronize()
         c0 = g.work_counters()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(steps)]
@@ -435,6 +471,12 @@ def run_mode(fv, torch, mesh, prim, L, precision, steps, warmup, stream, flush, 
     face_evals = c1[2] - c0[2]
     history = level_history_summary(g, L)
     # per-kernel-class timing (CUDA events on the launching stream), 2 cycles
+    # after the same warm-up from the initial state
+    g.set_state(prim)
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            g.advance(1, stream=stream, want_time=False)
+    torch.cuda.synchronize()
     g.profile_enable(True)
     p0 = g.work_counters()
     g.advance(2, stream=stream, want_time=False)
@@ -476,8 +518,19 @@ def run_e2e(fv, torch, g, steps, warmup, stream):
             "h2d_bytes_per_step": 5 * n * 8, "d2h_bytes_per_step": 5 * n * 8}
 
 
-def cpu_baseline(mesh, prim, L, budget_s=15.0, max_cycles=4):
+def sample_desc(name, mesh, L):
+    """What the oracle's bounded sample of a workload is."""
+    if name in ORACLE_SAMPLE:
+        return (f"the same recipe on {mesh.n_tets} tets ({mesh.shape[0]}^3 cubes), L={L}, "
+                f"restarted from its initial state every {ORACLE_SAMPLE[name][1]} cycles")
+    return "the same workload"
+
+
+def cpu_baseline(name, budget_s=15.0, max_cycles=8):
+    """The FP64 CPU oracle, as it stands, on the host cores over the first
+    cycles of the workload's bounded sample (about budget_s seconds)."""
     from oracle import oracle as O
+    mesh, prim, L = build_workload(name, sample=True)
     o = O.Oracle(mesh, max_levels=L)
     o.set_prim(prim)
     t0 = time.perf_counter()
@@ -489,7 +542,7 @@ def cpu_baseline(mesh, prim, L, budget_s=15.0, max_cycles=4):
     cu = int(o.stats()["updates"].sum())
     return {"value": cu / dt, "unit": "cell-updates/s", "cores": O.num_threads(),
             "kind": "oracle",
-            "sample": f"first {cycles} cycle(s) of the same workload, FP64 CPU oracle "
+            "sample": f"first {cycles} cycle(s) of {sample_desc(name, mesh, L)}; FP64 CPU oracle "
                       f"({O.num_threads()} OpenMP threads), {dt:.1f} s"}
 
 
@@ -589,54 +642,40 @@ def gate_sweep(fv, torch, g, prim, guess, stream, flush, gates=(0.1, 0.3, 1.0, 1
     return out
 
 
-def main_ours(args):
-    import torch
-    ws, rank, local = _dist()
-    if ws > 1:
-        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
-    torch.cuda.set_device(local)
-    from paper_1704_01144_gb300 import build as fvbuild
-    from paper_1704_01144_gb300 import fv
-    fvbuild.build()
-    mesh, prim, L = build_workload(args.workload)
-    stream = torch.cuda.Stream()
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
-    gpu_index = local
-    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
-    if vis:
-        try:
-            gpu_index = int(vis.split(",")[local])
-        except ValueError:
-            pass
-
+def measure_workload(fv, torch, name, modes, args, stream, flush, gpu_index, local, ws,
+                     peaks, peak_src, alu_peaks, traffic, extras=True):
+    """Every measurement of one workload: the chosen form (value), plain
+    FP64, the learned guess, and (extras) the persistent cycle, the paper's
+    order and e2e.  Returns (fields of the JSON line, chosen run)."""
+    mesh, prim, L = build_workload(name)
     res = {}
-    modes = [m for m in args.modes.split(",") if m]
     guess = None
     if "fp32mlp" in modes:
         # ~10M pairs; the 80M ground blast is harvested early in its run (its
         # core nears vacuum, where the scheme has no positivity limiter)
-        hc, hp = (8, 1_250_000) if args.workload.startswith("ground") else (40, 250_000)
+        hc, hp = (8, 1_250_000) if name.startswith("ground") else (40, 250_000)
         guess = train_learned_guess(fv, torch, mesh, prim, L, cycles=hc, per_cycle=hp)
-    for name, prec in (("fp64", fv.FV_FP64), ("fp32flux", fv.FV_FP32_FLUX),
-                       ("fp32mlp", fv.FV_FP32_FLUX)):
-        if name not in modes:
+    for mname, prec in (("fp64", fv.FV_FP64), ("fp32flux", fv.FV_FP32_FLUX),
+                        ("fp32mlp", fv.FV_FP32_FLUX)):
+        if mname not in modes:
             continue
         setup, tag = None, ""
-        if name == "fp32mlp":
+        if mname == "fp32mlp":
             setup = lambda g: g.mlp_load(guess["params"], fv.FV_MLP_TARGET_TR, guess["gate"])
             tag = f"|mlp{guess['gate']}"
         g, r = run_mode(fv, torch, mesh, prim, L, prec, args.steps, args.warmup, stream, flush,
                         gpu_index, setup=setup, tag=tag)
-        if name == "fp64" and len(modes) > 1:
+        if mname == "fp64" and len(modes) > 1:
             g.close()      # not used again; frees its HBM before the next mode loads
             g = None
         r["g"] = g
-        res[name] = r
+        res[mname] = r
     chosen = next(res[k] for k in ("fp32flux", "fp64", "fp32mlp") if k in res)
+    fp32 = "fp32flux" in res
     # the same cycles as one persistent cooperative launch (grid barriers
     # between kernel kinds) instead of the graph of per-kind launches
     persistent = None
-    if chosen["g"] is not None:
+    if extras and chosen["g"] is not None:
         chosen["g"].use_persistent(True)
         persistent = time_cycles(fv, torch, chosen["g"], prim, stream, flush)
         chosen["g"].use_persistent(False)
@@ -647,7 +686,7 @@ def main_ours(args):
     # and how far its state is from the finest-first order's after the same
     # cycles from the same initial state
     paper_order = None
-    if chosen["g"] is not None:
+    if extras and chosen["g"] is not None:
         g = chosen["g"]
         small = g.n <= 4_000_000
         if small:
@@ -670,42 +709,27 @@ def main_ours(args):
                                "subiteration predicted and corrected in it, coarsest first; "
                                "interface integrals corrected when its next step begins), same "
                                "mesh, precision, graph and timing as the line's value")
-    e2e = None if args.no_e2e else run_e2e(fv, torch, chosen["g"], max(3, min(args.steps, 10)), 1,
-                                           stream)
+    e2e = None
+    if extras and not args.no_e2e:
+        chosen["g"].set_state(prim)      # the e2e steps also start from the initial state
+        e2e = run_e2e(fv, torch, chosen["g"], max(3, min(args.steps, 10)), 1, stream)
 
-    # whole-job aggregate over ranks (independent replicas, no data-path
-    # collective): the work of all ranks over the slowest rank's time
-    value = chosen["value"]
-    ms_step = chosen["ms_per_step"]
-    if ws > 1:
-        vals = replica_stats([chosen["cell_updates"], ms_step, e2e["value"] if e2e else 0.0], "cuda")
-        value, ms_step, e2e_total = aggregate_replicas(vals, args.steps)
-        if e2e:
-            e2e["value"] = e2e_total
+    def roofline(r, fp32_, kernel):
+        return roofline_entry(r["prof"], r["prof_face_evals"], r["prof_cell_updates"], fp32_, kernel,
+                              float(peaks["hbm_gbs"]), peak_src, traffic.get(name))
 
-    peaks, peak_src = _load_peaks()
-    alu_peaks = {"fp64_tflops": fv.fv_probe_fma_peak(fv.FV_FP64, local),
-                 "fp32_tflops": fv.fv_probe_fma_peak(fv.FV_FP32_FLUX, local),
-                 "derived_fp64_tflops": 152 * 2 * 2 * 2.07e9 / 1e12,
-                 "derived_fp32_tflops": 152 * 128 * 2 * 2.07e9 / 1e12}
-
-    traffic = measured_traffic()
-
-    def roofline(r, fp32, kernel):
-        return roofline_entry(r["prof"], r["prof_face_evals"], r["prof_cell_updates"], fp32, kernel,
-                              float(peaks["hbm_gbs"]), peak_src, traffic)
-
-    def dominant(r, fp32):
+    def dominant(r, fp32_):
         k = max(("flux", "update"), key=lambda q: r["prof"][q][0])
-        return roofline(r, fp32, k)
+        return roofline(r, fp32_, k)
 
     def fp64_alu(r):
         """FP64 flux kernel against the FP64 pipe: executed FP64 flops per face
         evaluation from the committed ncu op counts (DFMA = 2, DADD/DMUL = 1)."""
-        if traffic is None or "flux_fp64_fp64_flops_per_unit" not in traffic:
+        tr = traffic.get(name)
+        if tr is None or "flux_fp64_fp64_flops_per_unit" not in tr:
             return None
         ms, n = r["prof"]["flux"]
-        fl = float(traffic["flux_fp64_fp64_flops_per_unit"]) * r["prof_face_evals"]
+        fl = float(tr["flux_fp64_fp64_flops_per_unit"]) * r["prof_face_evals"]
         achieved = fl / (ms * 1e-3) / 1e12
         return {"bound": "alu", "kernel": "k_flux (FP64)", "achieved": round(achieved, 4),
                 "peak": round(alu_peaks["fp64_tflops"], 4), "unit": "TFLOP/s",
@@ -717,63 +741,139 @@ def main_ours(args):
         return {k: {"ms": round(v[0], 3), "launches": v[1], "share": round(v[0] / tot, 4)}
                 for k, v in r["prof"].items()}
 
-    line = None
+    desc = describe(name, mesh, L)
+    desc.update({"l2": "flushed between timed steps (256 MB write)",
+                 "step": "one cycle of Algorithm 2 (level assignment + 2^(L-1) subiterations)",
+                 "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
+                 "mode": "FP32 reconstruction/Riemann flux, FP64 state, corrector sums and "
+                         "flux time integrals (chosen form); CUDA graph per cycle"})
+    out = {
+        "value": chosen["value"], "ms_per_step": chosen["ms_per_step"],
+        "config": desc, "data": data_desc(name),
+        "clocks": chosen["clocks"],
+        "roofline": dominant(chosen, fp32),
+        "roofline_kernels": {k: roofline(chosen, fp32, k) for k in ("flux", "update")},
+        "e2e": e2e,
+        "gpu_launches": launches_per_cycle(L, fp32) * args.steps,
+        "plain_fp64": None if "fp64" not in res else {
+            "value": round(res["fp64"]["value"], 1), "unit": "cell-updates/s",
+            "ms_per_step": round(res["fp64"]["ms_per_step"], 4),
+            "roofline": dominant(res["fp64"], False),
+            "roofline_alu": fp64_alu(res["fp64"]),
+            "kernels": kernel_shares(res["fp64"]),
+            "clocks": res["fp64"]["clocks"]},
+        "kernels": kernel_shares(chosen),
+        "autotuned_blocks_per_sm": {"prim_grad_flux_update": chosen["launch_per_sm"],
+                                    "cached": chosen["autotune_cached"]},
+        "persistent_cycle": persistent,
+        "paper_order": paper_order,
+        "level_history": chosen["level_history"],
+        "cell_updates_per_step": chosen["cell_updates"] / args.steps,
+        "face_evals_per_step": chosen["face_evals"] / args.steps,
+    }
+    if "fp32mlp" in res:
+        r = res["fp32mlp"]
+        fl = lambda rr: rr["prof"]["flux"][0] / max(1, rr["prof_face_evals"]) * 1e6
+        sweep = gate_sweep(fv, torch, r["g"], prim, guess, stream, flush)
+        out["learned_guess"] = {
+            "what": "FP32-flux mode with the learned p* guess (bf16 tensor-core MLP fused "
+                    "into the flux kernel, gated by the two-rarefaction shock strength), "
+                    "same workload, graph and timing as the line's value",
+            "value": round(r["value"], 1), "unit": "cell-updates/s",
+            "ms_per_step": round(r["ms_per_step"], 4),
+            "vs_two_rarefaction_guess": round(r["value"] / chosen["value"], 4),
+            "flux_ns_per_face_eval": {"learned": round(fl(r), 4),
+                                      "two_rarefaction": round(fl(chosen), 4)},
+            "kernels": kernel_shares(r), "clocks": r["clocks"],
+            "training": guess["info"], "heldout": guess["eval"],
+            "train_s": round(guess["seconds"], 2),
+            "gate_sweep": sweep}
+    for r in res.values():
+        if r.get("g") is not None:
+            r["g"].close()
+    del guess
+    torch.cuda.empty_cache()
+    return out, chosen
+
+
+def main_ours(args):
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    from paper_1704_01144_gb300 import build as fvbuild
+    from paper_1704_01144_gb300 import fv
+    fvbuild.build()
+    stream = torch.cuda.Stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    gpu_index = local
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        try:
+            gpu_index = int(vis.split(",")[local])
+        except ValueError:
+            pass
+    modes = [m for m in args.modes.split(",") if m]
+    peaks, peak_src = _load_peaks()
+    alu_peaks = {"fp64_tflops": fv.fv_probe_fma_peak(fv.FV_FP64, local),
+                 "fp32_tflops": fv.fv_probe_fma_peak(fv.FV_FP32_FLUX, local),
+                 "derived_fp64_tflops": 152 * 2 * 2 * 2.07e9 / 1e12,
+                 "derived_fp32_tflops": 152 * 128 * 2 * 2.07e9 / 1e12}
+    traffic = {w: measured_traffic(w) for w in WORKLOADS}
+
+    out, chosen = measure_workload(fv, torch, args.workload, modes, args, stream, flush, gpu_index,
+                                   local, ws, peaks, peak_src, alu_peaks, traffic)
+    # the 998,250-tet spherical blast (L = 4) beside the headline: the chosen
+    # form and plain FP64, same timing
+    sub = None
+    if args.workload == DEFAULT_WORKLOAD and not args.no_sub:
+        s_out, _ = measure_workload(fv, torch, "blast1m", [m for m in modes if m != "fp32mlp"], args,
+                                    stream, flush, gpu_index, local, ws, peaks, peak_src, alu_peaks,
+                                    traffic, extras=False)
+        sub = {"value": round(s_out["value"], 1), "unit": "cell-updates/s",
+               "ms_per_step": round(s_out["ms_per_step"], 4), "config": s_out["config"],
+               "roofline": s_out["roofline"], "roofline_kernels": s_out["roofline_kernels"],
+               "plain_fp64": s_out["plain_fp64"], "kernels": s_out["kernels"],
+               "clocks": s_out["clocks"], "level_history": s_out["level_history"],
+               "cell_updates_per_step": s_out["cell_updates_per_step"]}
+
+    # whole-job aggregate over ranks (independent replicas, no data-path
+    # collective): the work of all ranks over the slowest rank's time
+    value = out["value"]
+    ms_step = out["ms_per_step"]
+    e2e = out["e2e"]
+    if ws > 1:
+        vals = replica_stats([chosen["cell_updates"], ms_step, e2e["value"] if e2e else 0.0], "cuda")
+        value, ms_step, e2e_total = aggregate_replicas(vals, args.steps)
+        if e2e:
+            e2e["value"] = e2e_total
+
     if rank == 0:
-        cpu = None if args.no_cpu_baseline else cpu_baseline(mesh, prim, L)
-        desc = describe(args.workload, mesh, L)
-        desc.update({"l2": "flushed between timed steps (256 MB write)",
-                     "step": "one cycle of Algorithm 2 (level assignment + 2^(L-1) subiterations)",
-                     "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
-                     "mode": "FP32 reconstruction/Riemann flux, FP64 state, residual sums and "
-                             "flux time integrals (chosen form); CUDA graph per cycle"})
+        cpu = None if (args.no_cpu_baseline or ws > 1) else cpu_baseline(args.workload)
         line = {
             "metric": "cell-updates/sec (adaptive-dt weighted) & HBM GB/s, chosen vs plain FP64",
             "value": round(value, 1), "unit": "cell-updates/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 flux / f64 state", "data": data_desc(args.workload),
-            "config": desc,
-            "clocks": chosen["clocks"],
-            "roofline": dominant(chosen, "fp32flux" in res),
-            "roofline_kernels": {k: roofline(chosen, "fp32flux" in res, k) for k in ("flux", "update")},
+            "dtype": "f32 flux / f64 state", "data": out["data"],
+            "config": out["config"],
+            "clocks": out["clocks"],
+            "roofline": out["roofline"],
+            "roofline_kernels": out["roofline_kernels"],
             "alu_peaks_measured": alu_peaks,
             "kernel_source_sha256_16": kernel_source_hash(),
             "e2e": e2e,
-            "gpu_launches": launches_per_cycle(L, "fp32flux" in res) * args.steps,
+            "gpu_launches": out["gpu_launches"],
             "cpu_baseline": cpu,
-            "plain_fp64": None if "fp64" not in res else {
-                "value": round(res["fp64"]["value"], 1), "unit": "cell-updates/s",
-                "ms_per_step": round(res["fp64"]["ms_per_step"], 4),
-                "roofline": dominant(res["fp64"], False),
-                "roofline_alu": fp64_alu(res["fp64"]),
-                "kernels": kernel_shares(res["fp64"]),
-                "clocks": res["fp64"]["clocks"]},
-            "kernels": kernel_shares(chosen),
-            "autotuned_blocks_per_sm": {"prim_grad_flux_update": chosen["launch_per_sm"],
-                                        "cached": chosen["autotune_cached"]},
-            "persistent_cycle": persistent,
-            "paper_order": paper_order,
-            "level_history": chosen["level_history"],
-            "cell_updates_per_step": chosen["cell_updates"] / args.steps,
-            "face_evals_per_step": chosen["face_evals"] / args.steps,
         }
-        if "fp32mlp" in res:
-            r = res["fp32mlp"]
-            fl = lambda rr: rr["prof"]["flux"][0] / max(1, rr["prof_face_evals"]) * 1e6
-            sweep = gate_sweep(fv, torch, r["g"], prim, guess, stream, flush)
-            line["learned_guess"] = {
-                "what": "FP32-flux mode with the learned p* guess (bf16 tensor-core MLP fused "
-                        "into the flux kernel, gated by the two-rarefaction shock strength), "
-                        "same workload, graph and timing as the line's value",
-                "value": round(r["value"], 1), "unit": "cell-updates/s",
-                "ms_per_step": round(r["ms_per_step"], 4),
-                "vs_two_rarefaction_guess": round(r["value"] / chosen["value"], 4),
-                "flux_ns_per_face_eval": {"learned": round(fl(r), 4),
-                                          "two_rarefaction": round(fl(chosen), 4)},
-                "kernels": kernel_shares(r), "clocks": r["clocks"],
-                "training": guess["info"], "heldout": guess["eval"],
-                "train_s": round(guess["seconds"], 2),
-                "gate_sweep": sweep}
+        for k in ("plain_fp64", "kernels", "autotuned_blocks_per_sm", "persistent_cycle",
+                  "paper_order", "level_history", "cell_updates_per_step", "face_evals_per_step",
+                  "learned_guess"):
+            if k in out:
+                line[k] = out[k]
+        if sub is not None:
+            line["blast1m"] = sub
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.barrier()
@@ -880,35 +980,55 @@ def main_batch(args):
 
 # ------------------------------------------------------------- reference ---
 def main_reference(args):
+    """The reference arm: the FP64 CPU oracle, as it stands, on the host
+    cores.  One step = one cycle of the workload's bounded sample (the same
+    recipe on a mesh the oracle runs within seconds, restarted from its
+    initial state, outside the timed region, every few cycles); rank 0
+    alone runs it."""
     ws, rank, _ = _dist()
     if rank != 0:
         return
     from oracle import oracle as O
-    mesh, prim, L = build_workload(args.workload)
+    mesh, prim, L = build_workload(args.workload, sample=True)
+    restart = ORACLE_SAMPLE.get(args.workload, (None, 1 << 30))[1]
     o = O.Oracle(mesh, max_levels=L)
     o.set_prim(prim)
+    done = 0
+
+    def one_cycle():
+        nonlocal done
+        if done and done % restart == 0:
+            o.set_prim(prim)
+            o.t = 0.0
+        u0 = o.stats()["updates"].sum()
+        t0 = time.perf_counter()
+        o.advance(1)
+        dt = time.perf_counter() - t0
+        done += 1
+        return dt, int(o.stats()["updates"].sum() - u0)
+
     for _ in range(args.warmup):
-        o.advance(1)
-    st0 = o.stats()["updates"].sum()
-    t0 = time.perf_counter()
+        one_cycle()
+    secs, cu = 0.0, 0
     for _ in range(args.steps):
-        o.advance(1)
-    dt = time.perf_counter() - t0
-    cu = int(o.stats()["updates"].sum() - st0)
-    value = cu / dt
-    desc = describe(args.workload, mesh, L)
+        dt, n = one_cycle()
+        secs += dt
+        cu += n
+    value = cu / secs
+    desc = describe(args.workload, *build_workload_shape(args.workload))
     desc["l2"] = "n/a (CPU)"
+    desc["oracle_sample"] = sample_desc(args.workload, mesh, L)
     line = {
         "impl": "reference",
         "metric": "cell-updates/sec (adaptive-dt weighted) & HBM GB/s, chosen vs plain FP64",
         "value": round(value, 1), "unit": "cell-updates/s", "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 3),
+        "warmup": args.warmup, "ms_per_step": round(secs * 1e3 / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": data_desc(args.workload), "config": desc,
         "cpu_baseline": {"value": round(value, 1), "unit": "cell-updates/s",
                          "cores": O.num_threads(), "kind": "oracle",
-                         "sample": f"cycles {args.warmup + 1}..{args.warmup + args.steps} of the "
-                                   f"workload on the FP64 CPU oracle"},
+                         "sample": f"cycles {args.warmup + 1}..{args.warmup + args.steps} of "
+                                   f"{sample_desc(args.workload, mesh, L)}, FP64 CPU oracle"},
         "e2e": {"value": round(value, 1), "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -921,8 +1041,10 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch64"], default="blast1m")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch64"], default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="skip the 998,250-tet blast sub-object of the default workload")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--modes", default="fp64,fp32flux,fp32mlp",
                     help="comma list of fp64, fp32flux (the line's value) and fp32mlp (FP32 flux with the learned guess)")
