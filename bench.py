@@ -823,7 +823,8 @@ def main_ours(args):
     traffic = {w: measured_traffic(w) for w in WORKLOADS}
 
     out, chosen = measure_workload(fv, torch, args.workload, modes, args, stream, flush, gpu_index,
-                                   local, ws, peaks, peak_src, alu_peaks, traffic)
+                                   local, ws, peaks, peak_src, alu_peaks, traffic,
+                                   extras=not args.no_extras)
     # the 998,250-tet spherical blast (L = 4) beside the headline: the chosen
     # form and plain FP64, same timing
     sub = None
@@ -1043,6 +1044,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch64"], default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the persistent-cycle, paper-order and e2e measurements")
     ap.add_argument("--no-sub", action="store_true",
                     help="skip the 998,250-tet blast sub-object of the default workload")
     ap.add_argument("--no-e2e", action="store_true")

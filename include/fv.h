@@ -322,6 +322,21 @@ int fv_get_fusion(fv_mesh *m, int64_t *max_faces_out);
 int fv_set_predictor_sum(fv_mesh *m, int sum);
 int fv_get_predictor_sum(fv_mesh *m, int *sum_out);
 
+/*
+ * FP32-flux mode with the two-rarefaction guess and no fusion: whether the
+ * flux kernel stages the records it gathers (face geometry, both cells'
+ * primitives and gradients) through shared memory with asynchronous copies,
+ * those of the next face in flight while the current face's Riemann problem
+ * is solved (1), or loads them into registers when it reaches each face
+ * (0).  Both compute the same operations on the same values (bitwise equal
+ * results).  Other modes ignore the setting.  Setting it drops a captured
+ * graph.  Errors: FV_ERR_INVALID_ARG (NULL argument, inside a cycle or a
+ * batch).
+ */
+#define FV_FLUX_STAGING_DEFAULT 0
+int fv_set_flux_staging(fv_mesh *m, int enable);
+int fv_get_flux_staging(fv_mesh *m, int *enabled_out);
+
 /* kernel classes of the profiler */
 #define FV_PROF_LEVELS 0 /* level assignment: dt, levels, sorts */
 #define FV_PROF_PRIM 1   /* primitives at the phase time */

@@ -238,6 +238,7 @@ int fv_mesh_load(const double *xyz, int64_t n_nodes, const int64_t *tets, int64_
   d.precision = cfg->precision;
   d.fuse_faces = FV_FUSE_FACES_DEFAULT;
   d.pred_sum64 = FV_PREDICTOR_SUM_DEFAULT == FV_SUM_FP64;
+  d.flux_staged = FV_FLUX_STAGING_DEFAULT;
   const bool f32 = cfg->precision == FV_FP32_FLUX;
   const int nblk_c = (int)((N + 1023) / 1024), nblk_f = (int)((F + 1023) / 1024);
   // the cell counts (2L buckets per tile), then the face counts (L per tile)
@@ -293,6 +294,10 @@ int fv_mesh_load(const double *xyz, int64_t n_nodes, const int64_t *tets, int64_
   AL(d.fkey, F);
   AL(d.cl, N);
   AL(d.fl, F);
+  AL(d.clf, N);
+  AL(d.cln, N);
+  AL(d.clb, N);
+  AL(d.flc, F);
   AL(d.coff, 2 * FV_MAXL + 1);
   AL(d.foff, FV_MAXL + 1);
   AL(d.dt, N);
@@ -688,6 +693,24 @@ int fv_set_predictor_sum(fv_mesh *m, int sum) {
 int fv_get_predictor_sum(fv_mesh *m, int *sum_out) {
   if (!m || !sum_out) return fail(FV_ERR_INVALID_ARG, "fv_get_predictor_sum: NULL argument");
   *sum_out = m->d.pred_sum64 ? FV_SUM_FP64 : FV_SUM_FP32;
+  return FV_OK;
+}
+
+int fv_set_flux_staging(fv_mesh *m, int enable) {
+  if (!m) return fail(FV_ERR_INVALID_ARG, "fv_set_flux_staging: NULL mesh");
+  if (m->in_batch || (m->in_cycle && m->next_phase > 0))
+    return fail(FV_ERR_INVALID_ARG, "fv_set_flux_staging: mesh is inside a cycle or a batch");
+  m->d.flux_staged = enable != 0;
+  if (m->cycle_graph) {
+    cudaGraphExecDestroy(m->cycle_graph);
+    m->cycle_graph = nullptr;
+  }
+  return FV_OK;
+}
+
+int fv_get_flux_staging(fv_mesh *m, int *enabled_out) {
+  if (!m || !enabled_out) return fail(FV_ERR_INVALID_ARG, "fv_get_flux_staging: NULL argument");
+  *enabled_out = m->d.flux_staged;
   return FV_OK;
 }
 

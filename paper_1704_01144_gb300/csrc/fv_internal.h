@@ -23,8 +23,10 @@
 //          [F][8] in FP32 mode), then the step's flux time integral;
 //          ACC[F][6] fine-side integral on level interfaces; BND[F][6]
 //          boundary ledger
-//   lists  cl[N] cells sorted by (level, has-finer-neighbour), coff[2L+1];
-//          fl[F] faces sorted by face level, foff[L+1]
+//   lists  cl[N] cells sorted by (level, has-finer-neighbour), coff[2L+1],
+//          with clf/cln/clb the sorted faces, neighbours and bits of each
+//          entry; fl[F] faces sorted by face level, foff[L+1], with flc the
+//          sorted cell pairs
 #pragma once
 
 #include <cuda_runtime.h>
@@ -86,6 +88,15 @@ struct DevMesh {
   uint8_t *cmask;         // per cell: bit j set when the neighbour across face j is
                           // one level finer (that face's integral accumulates)
   int *cl, *fl, *coff, *foff;
+  // the sorted lists also carry, per list position, what every phase kernel
+  // reads first about its item, so that a kernel reaches the item's
+  // neighbours and faces one dependent load earlier: cells their faces
+  // (clf = cf4[cl]), neighbours (cln = cnb4[cl]) and the bits own | finer << 4
+  // (clb); faces their two cells (flc = fcell[fl]).  Written by the level
+  // sort with the lists.
+  int4 *clf, *cln;
+  uint8_t *clb;
+  int2 *flc;
   int *sort_cnt;          // bucket x block counts, scratch of the level sort
   double *dt;             // exact local time steps (where dteps = 0)
   float *dt32;            // FP32 estimates of the local time steps (where dteps > 0)
@@ -110,6 +121,9 @@ struct DevMesh {
   // FP32-flux mode: the predictor's residual sum in FP64 (FV_SUM_FP64) or
   // FP32 (FV_SUM_FP32)
   int pred_sum64;
+  // FP32-flux mode, two-rarefaction guess, no fusion: the flux kernel stages
+  // its gathered inputs through shared memory (k_flux_staged)
+  int flux_staged;
   // physics
   double gamma, cfl, tol;
   int maxit;

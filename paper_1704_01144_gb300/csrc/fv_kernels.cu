@@ -500,11 +500,26 @@ __device__ __forceinline__ void sort_scan_block(int *cnt, int total, int nblk, i
 }
 
 
+// what a list entry carries: the item and, for cells, its faces, neighbours
+// and own | finer bits; for faces, its two cells
+template <bool FACES>
+__device__ __forceinline__ void emit_entry(const DevMesh &d, int i, int pos) {
+  if (FACES) {
+    d.fl[pos] = i;
+    d.flc[pos] = d.fcell[i];
+  } else {
+    d.cl[pos] = i;
+    d.clf[pos] = d.cf4[i];
+    d.cln[pos] = d.cnb4[i];
+    d.clb[pos] = (uint8_t)(d.cown[i] | (d.cmask[i] << 4));
+  }
+}
+
 // stable scatter of one tile: lanes with equal keys rank in lane (= item)
 // order, warps in order, earlier rounds first
-__device__ __forceinline__ void sort_scatter_tile(const uint8_t *__restrict__ key, int n, int nb,
-                                                  const int *__restrict__ cnt, int *__restrict__ out,
-                                                  int tile, int nblk) {
+template <bool FACES>
+__device__ __forceinline__ void sort_scatter_tile(const DevMesh &d, const uint8_t *__restrict__ key, int n,
+                                                  int nb, const int *__restrict__ cnt, int tile, int nblk) {
   __shared__ int wcount[SORT_THREADS / 32][16];
   __shared__ int run[16];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -522,7 +537,7 @@ __device__ __forceinline__ void sort_scatter_tile(const uint8_t *__restrict__ ke
     if (k >= 0) {
       int pre = run[k];
       for (int w = 0; w < warp; ++w) pre += wcount[w][k];
-      out[pre + rank] = i;
+      emit_entry<FACES>(d, i, pre + rank);
     }
     __syncthreads();
     if (threadIdx.x < 16) {
@@ -568,9 +583,9 @@ __global__ void __launch_bounds__(1024) k_sort_scan2(DevMesh d, int nc, int nf) 
 __global__ void __launch_bounds__(SORT_THREADS) k_sort_scatter2(DevMesh d, int nc, int nf) {
   pdl_wait();
   if ((int)blockIdx.x < nc)
-    sort_scatter_tile(d.ckey, d.N, 2 * d.L, d.sort_cnt, d.cl, blockIdx.x, nc);
+    sort_scatter_tile<false>(d, d.ckey, d.N, 2 * d.L, d.sort_cnt, blockIdx.x, nc);
   else
-    sort_scatter_tile(d.fkey, d.F, d.L, d.sort_cnt + 2 * d.L * nc, d.fl, blockIdx.x - nc, nf);
+    sort_scatter_tile<true>(d, d.fkey, d.F, d.L, d.sort_cnt + 2 * d.L * nc, blockIdx.x - nc, nf);
   pdl_trigger();
 }
 
@@ -678,8 +693,10 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort_scatter_multi(MultiTiles 
   if (!tile_of(a, inst, tile)) return;
   const DevMesh &d = a.ms[inst];
   int n = faces ? d.F : d.N;
-  sort_scatter_tile(faces ? d.fkey : d.ckey, n, faces ? d.L : 2 * d.L, d.sort_cnt, faces ? d.fl : d.cl,
-                    tile, (n + SORT_TILE - 1) / SORT_TILE);
+  if (faces)
+    sort_scatter_tile<true>(d, d.fkey, n, d.L, d.sort_cnt, tile, (n + SORT_TILE - 1) / SORT_TILE);
+  else
+    sort_scatter_tile<false>(d, d.ckey, n, 2 * d.L, d.sort_cnt, tile, (n + SORT_TILE - 1) / SORT_TILE);
 }
 
 // ------------------------------------------------------ state at a time --
@@ -779,16 +796,17 @@ __device__ __forceinline__ void prim_item(const DevMesh &d, const PhaseLevels &p
 // FP64 mode: neighbours from the W records the primitives kernel wrote;
 // FP32-flux mode: from their states at the phase time (`both`: load the
 // predicted record together with U^n).
+// nb4: the cell's neighbours; cfp: where its faces are (read only for a
+// wall face's normal)
 template <typename T>
 __device__ __forceinline__ void lsq_grad(const DevMesh &d, const PhaseLevels &pl, bool both, int i,
-                                         const T Wi[5], T g[REC_G]) {
+                                         const T Wi[5], T g[REC_G], const int4 nb4, const int4 *cfp) {
   constexpr bool INLINE_W = sizeof(T) == 4;
   const T *W = (const T *)d.W;
   const T *fgeo = georec(d, T(0));
   const double gm1 = d.gamma - 1.0;
   T w[REC_LSW];
   ldrec<REC_LSW>(lswrec(d, T(0)) + (size_t)i * REC_LSW, w);
-  int4 nb4 = d.cnb4[i];
 #pragma unroll
   for (int q = 0; q < REC_G; ++q) g[q] = T(0);
 #pragma unroll
@@ -807,7 +825,7 @@ __device__ __forceinline__ void lsq_grad(const DevMesh &d, const PhaseLevels &pl
 #pragma unroll
       for (int q = 0; q < 5; ++q) Wn[q] = Wi[q];
       if (nb == -FV_BC_WALL) {
-        const T *gf = fgeo + (size_t)nbr_of(d.cf4[i], j) * REC_FG;
+        const T *gf = fgeo + (size_t)nbr_of(*cfp, j) * REC_FG;
         T n0 = gf[0], n1 = gf[1], n2 = gf[2];
         T un = (Wi[1] * n0 + Wi[2] * n1) + Wi[3] * n2;
         Wn[1] = Wi[1] - (T(2) * un) * n0;
@@ -832,7 +850,8 @@ __device__ __forceinline__ void lsq_grad(const DevMesh &d, const PhaseLevels &pl
 // record for the flux kernel, with its level in slot 5; there is no separate
 // primitives kernel.  Both records are stored after every load.
 template <typename T>
-__device__ __forceinline__ void grad_cell(const DevMesh &d, const PhaseLevels &pl, int i) {
+__device__ __forceinline__ void grad_cell(const DevMesh &d, const PhaseLevels &pl, int i, const int4 nb4,
+                                          const int4 *cfp) {
   constexpr bool INLINE_W = sizeof(T) == 4;
   const bool both = INLINE_W && reads_predicted(pl);
   T Wi[REC_W], g[REC_G];
@@ -846,14 +865,15 @@ __device__ __forceinline__ void grad_cell(const DevMesh &d, const PhaseLevels &p
   } else {
     ldrec<REC_W>((const T *)d.W + (size_t)i * REC_W, Wi);
   }
-  lsq_grad<T>(d, pl, both, i, Wi, g);
+  lsq_grad<T>(d, pl, both, i, Wi, g, nb4, cfp);
   strec<REC_G>(grec_w(d, T(0)) + (size_t)i * REC_G, g);
   if (INLINE_W) strec<REC_W>((T *)d.W + (size_t)i * REC_W, Wi);
 }
 
+// the cell at list position idx, its neighbours from the list entry
 template <typename T>
 __device__ __forceinline__ void grad_item(const DevMesh &d, const PhaseLevels &pl, int idx) {
-  grad_cell<T>(d, pl, d.cl[idx]);
+  grad_cell<T>(d, pl, d.cl[idx], d.cln[idx], d.clf + idx);
 }
 
 // gradients (and, FP32-flux mode, primitives) of every cell by plain index:
@@ -861,7 +881,7 @@ __device__ __forceinline__ void grad_item(const DevMesh &d, const PhaseLevels &p
 template <typename T>
 __global__ void __launch_bounds__(256, 2) k_grad_all(DevMesh d, const __grid_constant__ PhaseLevels pl) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x)
-    grad_cell<T>(d, pl, i);
+    grad_cell<T>(d, pl, i, d.cnb4[i], d.cf4 + i);
 }
 
 // the learned starting guess of one face (warp-collective): where the
@@ -898,13 +918,12 @@ __device__ __forceinline__ void mlp_guess(const uint32_t *__restrict__ sw, float
 
 // the reconstructed inputs of face f's Riemann problem from the phase-time
 // primitive and gradient records: WL, WR (a boundary face copies WL into WR),
-// unit normal n and area A.  Returns fcell.y: the right cell, or minus the
-// boundary tag.
+// unit normal n and area A; fc = fcell[f], the face's cells.  Returns fc.y:
+// the right cell, or minus the boundary tag.
 template <typename T>
 __device__ __forceinline__ int face_states(const DevMesh &d, const T *__restrict__ W,
                                            const T *__restrict__ Gr, const T *__restrict__ fgeo, int f,
-                                           T WL[5], T WR[5], T n[3], T &A) {
-  int2 fc = d.fcell[f];
+                                           const int2 fc, T WL[5], T WR[5], T n[3], T &A) {
   const int L = fc.x, R = fc.y;
   T geo[REC_FG];
   ldrec<REC_FG>(fgeo + (size_t)f * REC_FG, geo);
@@ -956,11 +975,11 @@ __device__ __forceinline__ int face_states(const DevMesh &d, const T *__restrict
 template <typename T, bool G14, bool MLP = false>
 __device__ __forceinline__ int face_flux(const DevMesh &d, const GasT<T> &G, const T *__restrict__ W,
                                          const T *__restrict__ Gr, const T *__restrict__ fgeo, int f,
-                                         T FA[5], const uint32_t *sw = nullptr) {
+                                         const int2 fc, T FA[5], const uint32_t *sw = nullptr) {
   T WL[5], WR[5], n[3], A;
   int R = 0;
   if (!MLP || f >= 0) {
-    R = face_states<T>(d, W, Gr, fgeo, f, WL, WR, n, A);
+    R = face_states<T>(d, W, Gr, fgeo, f, fc, WL, WR, n, A);
   } else {
 #pragma unroll
     for (int c = 0; c < 5; ++c) WL[c] = WR[c] = c == 0 || c == 4 ? T(1) : T(0);
@@ -1046,13 +1065,13 @@ __device__ __forceinline__ void flux_item(const DevMesh &d, const GasT<T> &G, in
                                           int idx, const uint32_t *sw = nullptr) {
   const bool f32 = sizeof(T) == 4;
   int f = (!MLP || idx >= 0) ? d.fl[idx] : -1;
+  const int2 fc = (!MLP || idx >= 0) ? d.flc[idx] : make_int2(0, 0);  // the entry's cells
   T FAt[5];
-  int rc = face_flux<T, G14, MLP>(d, G, (const T *)d.W, grec(d, T(0)), georec(d, T(0)), f, FAt, sw);
+  int rc = face_flux<T, G14, MLP>(d, G, (const T *)d.W, grec(d, T(0)), georec(d, T(0)), f, fc, FAt, sw);
   if (MLP && f < 0) return;
   if (rc) atomicOr(d.status, FV_STATUS_RIEMANN);
   bool iface = false, bnd = false;
   if (stage != 1) {
-    int2 fc = d.fcell[f];
     // the FP32-flux mode has the cells' levels in slot 5 of the W records
     // the face states were just read from
     const T *Wr = (const T *)d.W;
@@ -1084,7 +1103,7 @@ __device__ __forceinline__ int face_states_fused(const DevMesh &d, const PhaseLe
   float U[5], Wi[5], g[REC_G];
   const int kL = load_state(d, pl, L, U, both);
   to_prim(U, gm1, Wi);
-  lsq_grad<float>(d, pl, both, L, Wi, g);
+  lsq_grad<float>(d, pl, both, L, Wi, g, d.cnb4[L], d.cf4 + L);
   iface = false;
   if (R >= 0) {
     float Wj[5];
@@ -1097,7 +1116,7 @@ __device__ __forceinline__ int face_states_fused(const DevMesh &d, const PhaseLe
       float gir = (g[3 * c] * r[0] + g[3 * c + 1] * r[1]) + g[3 * c + 2] * r[2];
       WL[c] = Wi[c] + 0.5f * minmod(2.0f * gir - dW, dW);
     }
-    lsq_grad<float>(d, pl, both, R, Wj, g);
+    lsq_grad<float>(d, pl, both, R, Wj, g, d.cnb4[R], d.cf4 + R);
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
       float dW = Wj[c] - Wi[c];
@@ -1152,7 +1171,8 @@ __device__ __forceinline__ void flux_item_fused(const DevMesh &d, const GasT<flo
 //           accumulated integral; the FP32 shadow of U^n is refreshed.
 // Positivity is checked by the next level assignment and on demand
 // (fv_status), not here.
-// Order 1 (the paper's order), the corrector of cell i of `level`: the
+// Order 1 (the paper's order), the corrector of the cell at list position
+// idx, of `level`: the
 // provisional end state U^n - S/V, S = sum sigma phi over the cell's faces,
 // phi = Phi on its own-level faces (and faces to coarser neighbours) and the
 // provisional dt_k F1 A on faces to finer neighbours, whose accumulators
@@ -1161,11 +1181,13 @@ __device__ __forceinline__ void flux_item_fused(const DevMesh &d, const GasT<flo
 // and the FP32 predicted record (FP32-flux mode), where the finer levels
 // interpolate it.  Every load before the first store.
 template <bool F32>
-__device__ __forceinline__ void correct_cell(const DevMesh &d, int level, int i) {
+__device__ __forceinline__ void correct_cell(const DevMesh &d, int level, int idx) {
   const size_t N = d.N;
   const double dtk = scale2(__longlong_as_double((long long)*d.dtmin_bits), level);
-  const unsigned own = d.cown[i], finer = d.cmask[i];
-  const int4 cf = d.cf4[i];
+  const int i = d.cl[idx];
+  const unsigned bits = d.clb[idx];
+  const unsigned own = bits & 15u, finer = bits >> 4;
+  const int4 cf = d.clf[idx];
   double S[5];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
@@ -1232,22 +1254,24 @@ __device__ __forceinline__ void correct_cell(const DevMesh &d, int level, int i)
   }
 }
 
-// Order 1, the commit of cell i at the end of its step (Alg. 2's intensive
+// Order 1, the commit of the cell at list position idx at the end of its step (Alg. 2's intensive
 // correction): U^{n+1} = Up - (1/V) sum sigma ACC over the faces to finer
 // neighbours (ACC = their integral minus the provisional one), which are
 // reset; a cell without finer neighbours takes its provisional state as it
 // is.
 template <bool F32>
-__device__ __forceinline__ void commit_cell(const DevMesh &d, int i) {
+__device__ __forceinline__ void commit_cell(const DevMesh &d, int idx) {
   const size_t N = d.N;
-  const unsigned finer = d.cmask[i];
+  const int i = d.cl[idx];
+  const unsigned bits = d.clb[idx];
+  const unsigned finer = bits >> 4;
   const double *Up = F32 ? d.UsD : d.Us;
   double u[5];
 #pragma unroll
   for (int c = 0; c < 5; ++c) u[c] = Up[c * N + i];
   if (finer) {
-    const unsigned own = d.cown[i];
-    const int4 cf = d.cf4[i];
+    const unsigned own = bits & 15u;
+    const int4 cf = d.clf[idx];
     double S[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -1282,9 +1306,11 @@ template <bool F32>
 __device__ __forceinline__ void update_item(const DevMesh &d, int stage, int level, int idx) {
   const size_t N = d.N;
   double dtmin = __longlong_as_double((long long)*d.dtmin_bits);
-  int i = d.cl[idx];
-  unsigned own = d.cown[i];
-  int4 cf = d.cf4[i];
+  // the cell, its faces and its bits from the list entry
+  const int i = d.cl[idx];
+  const unsigned bits = d.clb[idx];
+  const unsigned own = bits & 15u;
+  const int4 cf = d.clf[idx];
   if (stage == 1 && F32 && d.pred_sum64) {
     // the predictor's residual sum in FP64 (each FP32 flux widened) and U*
     // from the FP64 U^n; U* is rounded to its FP32 record, which only feeds
@@ -1334,7 +1360,7 @@ __device__ __forceinline__ void update_item(const DevMesh &d, int stage, int lev
   // instead of waiting on one another behind possibly aliasing stores.  At
   // the end of a step, faces to finer neighbours (cmask) contribute their
   // accumulated integrals.
-  const unsigned finer = stage == 2 ? d.cmask[i] : 0u;
+  const unsigned finer = stage == 2 ? bits >> 4 : 0u;
   bool reset[4];
   const double *src[4];
 #pragma unroll
@@ -1413,18 +1439,21 @@ __device__ __forceinline__ void run_item(const DevMesh &d, const PhaseDesc &p, c
   else if (KIND == K_UPD)
     update_item<sizeof(T) == 4>(d, p.stage, p.level, idx);
   else if (KIND == K_CORR)
-    correct_cell<sizeof(T) == 4>(d, p.level, d.cl[idx]);
+    correct_cell<sizeof(T) == 4>(d, p.level, idx);
   else
-    commit_cell<sizeof(T) == 4>(d, d.cl[idx]);
+    commit_cell<sizeof(T) == 4>(d, idx);
 }
 
 // flux: 128 threads, 8 blocks per SM in FP32 (64 registers), 4 in FP64;
 // FP64 gradients need ~96 registers (2 blocks of 256); the update (a gather
 // with all of its loads in flight at once) fits in 48 registers for 5
 // resident blocks of 256; the rest fit in 64
+#ifndef FV_FLUX32_BLOCKS
+#define FV_FLUX32_BLOCKS 8
+#endif
 #define KBOUNDS(KIND, T)                                                                      \
   __launch_bounds__((KIND) == K_FLUX ? 128 : 256,                                             \
-                    (KIND) == K_FLUX ? (sizeof(T) == 4 ? 8 : 4)                               \
+                    (KIND) == K_FLUX ? (sizeof(T) == 4 ? FV_FLUX32_BLOCKS : 4)                \
                     : (KIND) == K_UPD ? 5                                                     \
                                       : ((KIND) == K_GRAD && sizeof(T) == 8 ? 2 : 4))
 
@@ -1470,6 +1499,169 @@ __global__ void __launch_bounds__(128, FV_FUSED_BLOCKS) k_flux_fused(DevMesh d, 
     for (int idx = beg + blockIdx.x * blockDim.x + threadIdx.x; idx < end; idx += gridDim.x * blockDim.x)
       flux_item_fused<G14>(d, G, p.stage, p.level, p.pl, both, idx);
   }
+  pdl_trigger();
+}
+
+// ---- the FP32 flux with its inputs staged through shared memory.  Each
+// thread copies the records of its next face (geometry, both cells'
+// primitives and gradients: 14 chunks of 16 bytes) into its own slots of
+// shared memory with asynchronous copies (cp.async) while it solves the
+// Riemann problem of the current face, and loads the list entry of the face
+// after that into registers; the gathers of a face are in flight during the
+// previous face's arithmetic instead of stalling its warp.  Slots are
+// chunk-major ([chunk][thread]), so a warp's 16-byte reads of one chunk hit
+// consecutive banks.  The same operations as flux_item on the same values.
+#define FLUX_STAGE_CHUNKS 14
+#define FLUX_STAGE_THREADS 128
+#ifndef FV_STAGED_BLOCKS
+#define FV_STAGED_BLOCKS 7  // 28 KB of shared memory per block: 7 resident blocks per SM
+#endif
+
+__device__ __forceinline__ void cp_async16(float4 *dst_smem, const void *src) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(dst_smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(a), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// copies of face f's records (fc its cells) into slot t of st
+__device__ __forceinline__ void stage_face(const DevMesh &d, float4 (*st)[FLUX_STAGE_THREADS], int t, int f,
+                                           int2 fc) {
+  const float4 *geo = reinterpret_cast<const float4 *>(d.fgeo32 + (size_t)f * REC_FG);
+  const float4 *W = reinterpret_cast<const float4 *>(d.W);
+  const float4 *G = reinterpret_cast<const float4 *>(d.G32);
+  cp_async16(&st[0][t], geo);
+  cp_async16(&st[1][t], geo + 1);
+  cp_async16(&st[2][t], W + (size_t)fc.x * (REC_W / 4));
+  cp_async16(&st[3][t], W + (size_t)fc.x * (REC_W / 4) + 1);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) cp_async16(&st[4 + k][t], G + (size_t)fc.x * (REC_G / 4) + k);
+  if (fc.y >= 0) {
+    cp_async16(&st[8][t], W + (size_t)fc.y * (REC_W / 4));
+    cp_async16(&st[9][t], W + (size_t)fc.y * (REC_W / 4) + 1);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) cp_async16(&st[10 + k][t], G + (size_t)fc.y * (REC_G / 4) + k);
+  }
+}
+
+// face_states from the staged records (R = fc.y); iface: the two cells'
+// levels (slot 5 of their primitive records) differ
+__device__ __forceinline__ void face_states_staged(const float4 (*st)[FLUX_STAGE_THREADS], int t, int R,
+                                                   float WL[5], float WR[5], float n[3], float &A,
+                                                   bool &iface) {
+  const float4 g0 = st[0][t], g1 = st[1][t];
+  n[0] = g0.x;
+  n[1] = g0.y;
+  n[2] = g0.z;
+  A = g0.w;
+  const float r[3] = {g1.x, g1.y, g1.z};
+  const float4 a0 = st[2][t], a1 = st[3][t];
+  const float Wi[6] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y};
+  float gi[16];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float4 v = st[4 + k][t];
+    gi[4 * k] = v.x;
+    gi[4 * k + 1] = v.y;
+    gi[4 * k + 2] = v.z;
+    gi[4 * k + 3] = v.w;
+  }
+  if (R >= 0) {
+    const float4 b0 = st[8][t], b1 = st[9][t];
+    const float Wj[6] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y};
+    float gj[16];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float4 v = st[10 + k][t];
+      gj[4 * k] = v.x;
+      gj[4 * k + 1] = v.y;
+      gj[4 * k + 2] = v.z;
+      gj[4 * k + 3] = v.w;
+    }
+    iface = Wi[5] != Wj[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      float dW = Wj[c] - Wi[c];
+      float gir = (gi[3 * c] * r[0] + gi[3 * c + 1] * r[1]) + gi[3 * c + 2] * r[2];
+      float gjr = (gj[3 * c] * r[0] + gj[3 * c + 1] * r[1]) + gj[3 * c + 2] * r[2];
+      WL[c] = Wi[c] + 0.5f * minmod(2.0f * gir - dW, dW);
+      WR[c] = Wj[c] - 0.5f * minmod(2.0f * gjr - dW, dW);
+    }
+  } else {
+    iface = false;
+    float Wg[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) Wg[c] = Wi[c];
+    if (R == -FV_BC_WALL) {
+      float un = (Wi[1] * n[0] + Wi[2] * n[1]) + Wi[3] * n[2];
+#pragma unroll
+      for (int e = 0; e < 3; ++e) Wg[1 + e] = Wi[1 + e] - (2.0f * un) * n[e];
+    }
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      float dW = Wg[c] - Wi[c];
+      float gir = (gi[3 * c] * r[0] + gi[3 * c + 1] * r[1]) + gi[3 * c + 2] * r[2];
+      WL[c] = Wi[c] + 0.5f * minmod(2.0f * gir - dW, dW);
+    }
+#pragma unroll
+    for (int c = 0; c < 5; ++c) WR[c] = WL[c];
+  }
+}
+
+template <bool G14>
+__global__ void __launch_bounds__(FLUX_STAGE_THREADS, FV_STAGED_BLOCKS)
+    k_flux_staged(DevMesh d, const __grid_constant__ PhaseDesc p, GasT<float> G) {
+  __shared__ float4 st[FLUX_STAGE_CHUNKS][FLUX_STAGE_THREADS];
+  pdl_wait();
+  int beg, end;
+  kind_range(d, p, K_FLUX, beg, end);
+  const int t = threadIdx.x;
+  const int stride = gridDim.x * blockDim.x;
+  int idx = beg + blockIdx.x * blockDim.x + t;
+  // entries of the current face (its records staged) and of the next one
+  int f0 = -1, f1 = -1;
+  int2 c0 = make_int2(0, 0), c1 = make_int2(0, 0);
+  if (idx < end) {
+    f0 = d.fl[idx];
+    c0 = d.flc[idx];
+    stage_face(d, st, t, f0, c0);
+  }
+  cp_async_commit();
+  if (idx + stride < end) {
+    f1 = d.fl[idx + stride];
+    c1 = d.flc[idx + stride];
+  }
+  for (; idx < end; idx += stride) {
+    cp_async_wait_all();
+    float WL[5], WR[5], n[3], A;
+    bool iface;
+    face_states_staged(st, t, c0.y, WL, WR, n, A, iface);
+    // the slots are free: the next face's records go in flight, and the
+    // entry of the face after it
+    if (f1 >= 0) stage_face(d, st, t, f1, c1);
+    cp_async_commit();
+    int f2 = -1;
+    int2 c2 = make_int2(0, 0);
+    if (idx + 2 * stride < end) {
+      f2 = d.fl[idx + 2 * stride];
+      c2 = d.flc[idx + 2 * stride];
+    }
+    int it, rc;
+    float Fx[5], FAt[5];
+    if (c0.y >= 0)
+      rc = godunov_flux<float, G14, false>(G, WL, WR, n, Fx, it, 0.0f, 1.0f);
+    else
+      rc = boundary_flux<float, G14>(G, -c0.y, WL, n, Fx, it);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) FAt[c] = Fx[c] * A;
+    if (rc) atomicOr(d.status, FV_STATUS_RIEMANN);
+    flux_store<float>(d, p.stage, p.level, f0, FAt, p.stage != 1 && iface, p.stage != 1 && c0.y < 0);
+    f0 = f1;
+    c0 = c1;
+    f1 = f2;
+    c1 = c2;
+  }
+  cp_async_wait_all();
   pdl_trigger();
 }
 
@@ -1764,7 +1956,7 @@ __global__ void __launch_bounds__(128) k_flux_all(DevMesh d, GasT<T> G, int leve
     bool touch = d.lev[fc.x] == level || (fc.y >= 0 && d.lev[fc.y] == level);
     if (!touch) continue;
     T FAx[5];
-    if (face_flux<T, G14>(d, G, W, Gr, fgeo, f, FAx)) atomicOr(d.status, FV_STATUS_RIEMANN);
+    if (face_flux<T, G14>(d, G, W, Gr, fgeo, f, fc, FAx)) atomicOr(d.status, FV_STATUS_RIEMANN);
     double v[REC_FA] = {(double)FAx[0], (double)FAx[1], (double)FAx[2], (double)FAx[3], (double)FAx[4], 0.0};
     strec<REC_FA>(FAt + (size_t)f * REC_FA, v);
   }
@@ -2052,8 +2244,19 @@ static void phase1_all(const DevMesh &d, const PhaseDesc &pd, const GasT<T> &G, 
       launch_pdl(k_flux_mlp1<T, G14>,
                  grid_for(d.F, 128, lc.per_sm[2] < FV_MLP_FLUX_BLOCKS ? lc.per_sm[2] : FV_MLP_FLUX_BLOCKS),
                  128, s, d, pd, G);
-    else
-      launch_pdl(k_phase1<K_FLUX, T, G14>, g2, 128, s, d, pd, G);
+    else {
+      bool staged = false;
+      if constexpr (sizeof(T) == 4) {
+        if (d.fuse_faces == 0 && d.flux_staged) {
+          launch_pdl(k_flux_staged<G14>,
+                     grid_for(d.F, FLUX_STAGE_THREADS,
+                              lc.per_sm[2] < FV_STAGED_BLOCKS ? lc.per_sm[2] : FV_STAGED_BLOCKS),
+                     FLUX_STAGE_THREADS, s, d, pd, G);
+          staged = true;
+        }
+      }
+      if (!staged) launch_pdl(k_phase1<K_FLUX, T, G14>, g2, 128, s, d, pd, G);
+    }
     if constexpr (sizeof(T) == 4)
       if (d.guess == FV_GUESS_TWO_RAREFACTION && d.fuse_faces > 0)
         launch_pdl(k_flux_fused<G14>,
@@ -2175,7 +2378,7 @@ __global__ void __launch_bounds__(128) k_harvest(DevMesh d, const T *__restrict_
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) {
     int f = (int)((a * (long long)j + b) % (long long)d.F);
     T WL[5], WR[5], n[3], A;
-    int R = face_states<T>(d, W, Gr, fgeo, f, WL, WR, n, A);
+    int R = face_states<T>(d, W, Gr, fgeo, f, d.fcell[f], WL, WR, n, A);
     T unL = (WL[1] * n[0] + WL[2] * n[1]) + WL[3] * n[2];
     T unR = (WR[1] * n[0] + WR[2] * n[1]) + WR[3] * n[2];
     if (R == -FV_BC_WALL) unR = -unL;

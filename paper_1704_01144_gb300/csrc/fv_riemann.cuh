@@ -110,18 +110,23 @@ __device__ __forceinline__ int riemann_star(const GasT<T> &G, T rL, T uL, T pL, 
   if (p < pfloor) p = pfloor;
   int it;
   bool conv = false;
+  // as in riemann_star14: FP32 exits leave p where fL, fR were evaluated
+  T fL = T(0), fR = T(0);
+  bool at_p = false;
   for (it = 1; it <= G.maxit; ++it) {
-    T fL, dfL, fR, dfR;
+    T dfL, dfR;
     pressure_fn(G, p, rL, pL, aL, fL, dfL);
     pressure_fn(G, p, rR, pR, aR, fR, dfR);
     T fsum = fL + fR + du;
     if (at_rounding_floor(fsum, fL, fR, du)) {
       conv = true;
+      at_p = true;
       break;
     }
     T pn = p - qdiv(fsum, dfL + dfR);
     if (pn < pfloor) pn = pfloor;
     T change = qdiv(fabs(pn - p), T(0.5) * (pn + p));
+    at_p = pn == p;
     p = pn;
     if (change <= G.tol) {
       conv = true;
@@ -130,9 +135,11 @@ __device__ __forceinline__ int riemann_star(const GasT<T> &G, T rL, T uL, T pL, 
   }
   iters = it;
   if (!conv || !(p > T(0)) || !isfinite(p)) return 2;
-  T fL, dfL, fR, dfR;
-  pressure_fn(G, p, rL, pL, aL, fL, dfL);
-  pressure_fn(G, p, rR, pR, aR, fR, dfR);
+  if (sizeof(T) == 8 || !at_p) {
+    T dfL, dfR;
+    pressure_fn(G, p, rL, pL, aL, fL, dfL);
+    pressure_fn(G, p, rR, pR, aR, fR, dfR);
+  }
   ps = p;
   us = T(0.5) * (uL + uR) + T(0.5) * (fR - fL);
   return 0;
@@ -329,20 +336,29 @@ __device__ __forceinline__ int riemann_star14(const GasT<T> &G, const Side14<T> 
   if (p < pfloor) p = pfloor;
   int it;
   bool conv = false;
+  // fL, fR of the last evaluation, and whether p still is where they were
+  // evaluated (FP32: the rounding-floor exit, or an update that rounded to
+  // nothing -- the only way a relative change of 1e-10 passes in single
+  // precision).  Then u* takes them as they are, which is what evaluating
+  // them again at the same p would give.
+  T fL = T(0), fR = T(0);
+  bool at_p = false;
   for (it = 1; it <= G.maxit; ++it) {
     T p17 = T(0), rp6 = T(0);
     if (sizeof(T) == 8 && (p <= L.p || p <= R.p)) roots_of(p, p17, rp6);
-    T fL, dfL, fR, dfR;
+    T dfL, dfR;
     pressure_fn14(L, p, p17, rp6, fL, dfL);
     pressure_fn14(R, p, p17, rp6, fR, dfR);
     T fsum = fL + fR + du;
     if (at_rounding_floor(fsum, fL, fR, du)) {
       conv = true;
+      at_p = true;
       break;
     }
     T pn = p - qdiv(fsum, dfL + dfR);
     if (pn < pfloor) pn = pfloor;
     T change = qdiv(fabs(pn - p), T(0.5) * (pn + p));
+    at_p = pn == p;
     p = pn;
     if (change <= G.tol) {
       conv = true;
@@ -351,10 +367,13 @@ __device__ __forceinline__ int riemann_star14(const GasT<T> &G, const Side14<T> 
   }
   iters = it;
   if (!conv || !(p > T(0)) || !isfinite(p)) return 2;
-  T p17 = T(0), rp6 = T(0), fL, dfL, fR, dfR;
+  T p17 = T(0), rp6 = T(0);
   if (sizeof(T) == 8) roots_of(p, p17, rp6);
-  pressure_fn14(L, p, p17, rp6, fL, dfL);
-  pressure_fn14(R, p, p17, rp6, fR, dfR);
+  if (sizeof(T) == 8 || !at_p) {
+    T dfL, dfR;
+    pressure_fn14(L, p, p17, rp6, fL, dfL);
+    pressure_fn14(R, p, p17, rp6, fR, dfR);
+  }
   ps = p;
   ps17 = p17;
   us = T(0.5) * (uL + uR) + T(0.5) * (fR - fL);

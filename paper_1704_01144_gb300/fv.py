@@ -70,7 +70,7 @@ EXPORTS = [
     "fv_mlp_load", "fv_set_guess", "fv_harvest_pairs", "fv_godunov_flux_batch_mlp",
     "fv_use_persistent", "fv_barrier_selftest", "fv_level_history", "fv_batch_mlp_load",
     "fv_batch_set_guess", "fv_set_fusion", "fv_get_fusion", "fv_set_order", "fv_get_order",
-    "fv_set_predictor_sum", "fv_get_predictor_sum",
+    "fv_set_predictor_sum", "fv_get_predictor_sum", "fv_set_flux_staging", "fv_get_flux_staging",
 ]
 
 FV_MLP_PARAMS = 4673
@@ -150,6 +150,8 @@ def lib():
     L.fv_set_order.argtypes = [vp, C.c_int]
     L.fv_get_order.argtypes = [vp, C.POINTER(C.c_int)]
     L.fv_get_fusion.argtypes = [vp, C.POINTER(C.c_int64)]
+    L.fv_set_flux_staging.argtypes = [vp, C.c_int]
+    L.fv_get_flux_staging.argtypes = [vp, C.POINTER(C.c_int)]
     L.fv_set_predictor_sum.argtypes = [vp, C.c_int]
     L.fv_get_predictor_sum.argtypes = [vp, C.POINTER(C.c_int)]
     L.fv_godunov_flux_batch.argtypes = [vp, vp, vp, i64, C.POINTER(fv_config), C.c_int, vp, vp, vp]
@@ -648,6 +650,16 @@ def fv_get_predictor_sum(h):
     return a.value
 
 
+def fv_set_flux_staging(h, enable):
+    _check(lib().fv_set_flux_staging(h, int(bool(enable))), "fv_set_flux_staging")
+
+
+def fv_get_flux_staging(h):
+    a = C.c_int()
+    _check(lib().fv_get_flux_staging(h, C.byref(a)), "fv_get_flux_staging")
+    return bool(a.value)
+
+
 def fv_batch_set_launch(b, per_sm):
     _check(lib().fv_batch_set_launch(b, _launch4(per_sm)), "fv_batch_set_launch")
 
@@ -728,6 +740,12 @@ class Mesh:
 
     def get_order(self):
         return fv_get_order(self.h)
+
+    def set_flux_staging(self, enable):
+        fv_set_flux_staging(self.h, enable)
+
+    def get_flux_staging(self):
+        return fv_get_flux_staging(self.h)
 
     def set_predictor_sum(self, sum_mode):
         fv_set_predictor_sum(self.h, sum_mode)
