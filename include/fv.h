@@ -406,6 +406,57 @@ int fv_godunov_flux_batch(const double *WL_dev, const double *WR_dev, const doub
  */
 int fv_probe_fma_peak(int device, int precision, double *tflops_out);
 
+/* ---------------------------------------------------------------------
+ * Sharded runs (Sec. 3.3 and Sec. 4.3: a spatial domain decomposition in
+ * which every cell belongs to one subdomain, ghost cells copy the
+ * neighbouring subdomains' border cells, border faces are computed on both
+ * sides, and cells are weighted by their temporal level for the
+ * partition).  A subdomain is an fv_mesh of its own cells plus ghost layers;
+ * the caller drives its cycles phase by phase and moves the packed ghost
+ * records between subdomains (a device copy, NCCL or host staging).  The
+ * partition, the ghost layers and the driver are in the Python package
+ * (shard.py).
+ *
+ * The level assignment of Alg. 2 in three calls, so that a sharded run can
+ * take the minimum local step over all subdomains and give its ghost cells
+ * their owners' levels before the lists are sorted:
+ *  fv_levels_local_dt: the local steps and this mesh's minimum (synchronous,
+ *    written to *dt_min_out);
+ *  fv_levels_classify: the levels from dt_min (the global minimum): the
+ *    classification and the L-1 smoothing sweeps;
+ *  fv_levels_sort: the level-sorted lists; starts a cycle, as
+ *    fv_assign_levels does (fv_advance_phases runs its phases).
+ * fv_levels_local_dt, fv_levels_classify(its result), fv_levels_sort is
+ * fv_assign_levels.  Errors: FV_ERR_INVALID_ARG (NULL argument, out of
+ * order, dt_min not positive and finite, inside a cycle), FV_ERR_CUDA.
+ * ------------------------------------------------------------------- */
+int fv_levels_local_dt(fv_mesh *m, double *dt_min_out, void *stream);
+int fv_levels_classify(fv_mesh *m, double dt_min, void *stream);
+int fv_levels_sort(fv_mesh *m, void *stream);
+
+/*
+ * A halo plan: n cells of mesh m, given in the caller's order of its tets
+ * (the order fv_set_state uses), whose records fv_halo_pack writes into a
+ * device buffer and fv_halo_unpack reads back from one, record k for
+ * cells[k].  what = FV_HALO_LEVELS: one int8 level per cell (n bytes);
+ * FV_HALO_STATE: FV_HALO_STATE_DOUBLES doubles per cell (U^n and the
+ * predicted state of the mode, bit copies).  Buffers are device memory
+ * owned by the caller; asynchronous on `stream`.  The plan copies `cells`
+ * (host memory) and keeps a device copy; fv_halo_free releases it (before
+ * its mesh).  Errors: FV_ERR_INVALID_ARG (NULL argument, a cell outside the
+ * mesh, unknown `what`, unpacking into a mesh inside a batch), FV_ERR_NOMEM,
+ * FV_ERR_CUDA.
+ */
+typedef struct fv_halo fv_halo;
+#define FV_HALO_LEVELS 1
+#define FV_HALO_STATE 2
+#define FV_HALO_STATE_DOUBLES 20
+int fv_halo_create(fv_mesh *m, const int64_t *cells, int64_t n, fv_halo **out);
+int fv_halo_pack(fv_halo *h, int what, void *buf_dev, void *stream);
+int fv_halo_unpack(fv_halo *h, int what, const void *buf_dev, void *stream);
+int64_t fv_halo_size(fv_halo *h); /* n, or -1 for a NULL plan */
+void fv_halo_free(fv_halo *h);
+
 /* Largest n_cells fv_assign_levels_noalloc accepts (its static scratch). */
 #define FV_NOALLOC_MAX_CELLS (1 << 22)
 

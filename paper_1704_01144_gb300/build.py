@@ -20,7 +20,7 @@ LIB = os.path.join(OUT_DIR, "libfv.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["fv_kernels.cu", "fv_api.cu", "fv_batch.cu", "fv_noalloc.cu", "fv_probe.cu", "fv_mlp.cu"]
+CU_SOURCES = ["fv_kernels.cu", "fv_api.cu", "fv_batch.cu", "fv_noalloc.cu", "fv_probe.cu", "fv_mlp.cu", "fv_shard.cu"]
 CPP_SOURCES = ["fv_host.cpp"]
 
 

@@ -12,6 +12,8 @@
 // therefore fixed; ranges come from the level-sorted lists on the device.
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -82,9 +84,8 @@ int run_phase(fv_mesh *m, const SchedPhase &ph, cudaStream_t s) {
   return FV_OK;
 }
 
-int start_cycle(fv_mesh *m, cudaStream_t s) {
-  int rc = fvk::launch_assign_levels(m->d, m->L, m->cnt_scratch, &m->prof, s);
-  if (rc) return fail(rc, "level assignment launch failed");
+// host bookkeeping of a cycle whose levels were just assigned
+void begin_cycle_state(fv_mesh *m) {
   m->acc_dirty = true;
   for (int j = 0; j < FV_MAXL; ++j) {
     m->tn[j] = 0;
@@ -93,6 +94,13 @@ int start_cycle(fv_mesh *m, cudaStream_t s) {
   m->in_cycle = true;
   m->next_phase = 0;
   m->have_dt = true;
+}
+
+int start_cycle(fv_mesh *m, cudaStream_t s) {
+  int rc = fvk::launch_assign_levels(m->d, m->L, m->cnt_scratch, &m->prof, s);
+  if (rc) return fail(rc, "level assignment launch failed");
+  m->levels_step = 0;
+  begin_cycle_state(m);
   return FV_OK;
 }
 
@@ -469,6 +477,49 @@ int fv_assign_levels(fv_mesh *m, double *dt_min_out, int32_t *level_counts_out, 
     if (level_counts_out)
       for (int k = 0; k < m->L; ++k) level_counts_out[k] = coff[2 * k + 2] - coff[2 * k];
   }
+  return FV_OK;
+}
+
+// the level assignment in three calls, for sharded runs (fv.h)
+int fv_levels_local_dt(fv_mesh *m, double *dt_min_out, void *stream) {
+  if (!m || !dt_min_out) return fail(FV_ERR_INVALID_ARG, "fv_levels_local_dt: NULL argument");
+  if (m->in_cycle && m->next_phase > 0)
+    return fail(FV_ERR_INVALID_ARG, "fv_levels_local_dt: a cycle is in progress");
+  CK(cudaSetDevice(m->cfg.device));
+  cudaStream_t s = (cudaStream_t)stream;
+  m->in_cycle = false;
+  m->next_phase = 0;
+  m->levels_step = 0;
+  if (fvk::launch_levels_local_dt(m->d, s)) return fail(FV_ERR_CUDA, "fv_levels_local_dt: launch failed");
+  unsigned long long bits = 0;
+  CK(cudaMemcpyAsync(&bits, m->d.dtmin_bits, sizeof bits, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  memcpy(dt_min_out, &bits, sizeof(double));
+  m->levels_step = 1;
+  return FV_OK;
+}
+
+int fv_levels_classify(fv_mesh *m, double dt_min, void *stream) {
+  if (!m) return fail(FV_ERR_INVALID_ARG, "fv_levels_classify: NULL mesh");
+  if (m->levels_step != 1) return fail(FV_ERR_INVALID_ARG, "fv_levels_classify: call fv_levels_local_dt first");
+  if (!(dt_min > 0.0) || !std::isfinite(dt_min))
+    return fail(FV_ERR_INVALID_ARG, "fv_levels_classify: dt_min must be positive and finite");
+  CK(cudaSetDevice(m->cfg.device));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (fvk::launch_set_dt_min(m->d, dt_min, s) || fvk::launch_levels_classify(m->d, m->L, s))
+    return fail(FV_ERR_CUDA, "fv_levels_classify: launch failed");
+  m->levels_step = 2;
+  return FV_OK;
+}
+
+int fv_levels_sort(fv_mesh *m, void *stream) {
+  if (!m) return fail(FV_ERR_INVALID_ARG, "fv_levels_sort: NULL mesh");
+  if (m->levels_step != 2) return fail(FV_ERR_INVALID_ARG, "fv_levels_sort: call fv_levels_classify first");
+  CK(cudaSetDevice(m->cfg.device));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (fvk::launch_levels_sort(m->d, s)) return fail(FV_ERR_CUDA, "fv_levels_sort: launch failed");
+  m->levels_step = 0;
+  begin_cycle_state(m);
   return FV_OK;
 }
 

@@ -356,12 +356,20 @@ struct fv_mesh {
   bool use_persistent = false;    // whole cycles as one cooperative launch
   PhaseDesc *pds_dev = nullptr;   // the cycle's phase descriptors (persistent mode)
   GridBar *bar = nullptr;
+  int levels_step = 0;            // split level assignment: 1 after the local steps, 2 after classifying
 };
 
 // kernels (fv_kernels.cu)
 namespace fvk {
 void init_device_info();
 int launch_assign_levels(const DevMesh &d, int L, int *cnt_scratch, ProfHook *ph, cudaStream_t s);
+// its three parts (a sharded run inserts its exchanges between them)
+int launch_levels_local_dt(const DevMesh &d, cudaStream_t s);
+int launch_set_dt_min(const DevMesh &d, double dt_min, cudaStream_t s);
+int launch_levels_classify(const DevMesh &d, int L, cudaStream_t s);
+int launch_levels_sort(const DevMesh &d, cudaStream_t s);
+// ghost-cell records of a sharded run (fv_shard.cu)
+int launch_halo(const DevMesh &d, const int *cells, int n, int what, void *buf, bool pack, cudaStream_t s);
 int launch_phase(const DevMesh &d, const PhaseDesc &pd, const LaunchCfg &lc, ProfHook *ph,
                  cudaStream_t s);
 // batches: ms/pds are device arrays of n meshes / descriptors of one phase

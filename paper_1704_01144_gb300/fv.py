@@ -71,6 +71,8 @@ EXPORTS = [
     "fv_use_persistent", "fv_barrier_selftest", "fv_level_history", "fv_batch_mlp_load",
     "fv_batch_set_guess", "fv_set_fusion", "fv_get_fusion", "fv_set_order", "fv_get_order",
     "fv_set_predictor_sum", "fv_get_predictor_sum", "fv_set_flux_staging", "fv_get_flux_staging",
+    "fv_levels_local_dt", "fv_levels_classify", "fv_levels_sort", "fv_halo_create", "fv_halo_pack",
+    "fv_halo_unpack", "fv_halo_size", "fv_halo_free",
 ]
 
 FV_MLP_PARAMS = 4673
@@ -81,6 +83,8 @@ FV_NOALLOC_MAX_CELLS = 1 << 22
 FV_FUSE_FACES_DEFAULT = 0
 FV_ORDER_FINEST_FIRST, FV_ORDER_PAPER = 0, 1
 FV_SUM_FP32, FV_SUM_FP64 = 0, 1
+FV_HALO_LEVELS, FV_HALO_STATE = 1, 2
+FV_HALO_STATE_DOUBLES = 20
 
 FV_PROF_LEVELS, FV_PROF_PRIM, FV_PROF_GRAD, FV_PROF_FLUX, FV_PROF_UPDATE = range(5)
 FV_PROF_N = 5
@@ -150,6 +154,16 @@ def lib():
     L.fv_set_order.argtypes = [vp, C.c_int]
     L.fv_get_order.argtypes = [vp, C.POINTER(C.c_int)]
     L.fv_get_fusion.argtypes = [vp, C.POINTER(C.c_int64)]
+    L.fv_levels_local_dt.argtypes = [vp, dp, vp]
+    L.fv_levels_classify.argtypes = [vp, C.c_double, vp]
+    L.fv_levels_sort.argtypes = [vp, vp]
+    L.fv_halo_create.argtypes = [vp, C.POINTER(C.c_int64), i64, C.POINTER(vp)]
+    L.fv_halo_pack.argtypes = [vp, C.c_int, vp, vp]
+    L.fv_halo_unpack.argtypes = [vp, C.c_int, vp, vp]
+    L.fv_halo_size.argtypes = [vp]
+    L.fv_halo_size.restype = i64
+    L.fv_halo_free.argtypes = [vp]
+    L.fv_halo_free.restype = None
     L.fv_set_flux_staging.argtypes = [vp, C.c_int]
     L.fv_get_flux_staging.argtypes = [vp, C.POINTER(C.c_int)]
     L.fv_set_predictor_sum.argtypes = [vp, C.c_int]
@@ -660,6 +674,56 @@ def fv_get_flux_staging(h):
     return bool(a.value)
 
 
+def fv_levels_local_dt(h, stream=None) -> float:
+    v = C.c_double()
+    _check(lib().fv_levels_local_dt(h, C.byref(v), _stream(stream)), "fv_levels_local_dt")
+    return v.value
+
+
+def fv_levels_classify(h, dt_min, stream=None):
+    _check(lib().fv_levels_classify(h, float(dt_min), _stream(stream)), "fv_levels_classify")
+
+
+def fv_levels_sort(h, stream=None):
+    _check(lib().fv_levels_sort(h, _stream(stream)), "fv_levels_sort")
+
+
+class Halo:
+    """A halo plan of one mesh: cells (caller's order) whose records are
+    packed into / unpacked from a flat device buffer."""
+
+    def __init__(self, mesh, cells):
+        import numpy as _np
+        c = _np.ascontiguousarray(cells, dtype=_np.int64)
+        self.h = C.c_void_p()
+        _check(lib().fv_halo_create(mesh.h, c.ctypes.data_as(C.POINTER(C.c_int64)), c.size,
+                                    C.byref(self.h)), "fv_halo_create")
+        self.n = int(c.size)
+        self.mesh = mesh
+
+    def nbytes(self, what):
+        return self.n * (1 if what == FV_HALO_LEVELS else 8 * FV_HALO_STATE_DOUBLES)
+
+    def pack(self, what, buf, stream=None):
+        _check(lib().fv_halo_pack(self.h, int(what), C.c_void_p(buf.data_ptr()), _stream(stream)),
+               "fv_halo_pack")
+
+    def unpack(self, what, buf, stream=None):
+        _check(lib().fv_halo_unpack(self.h, int(what), C.c_void_p(buf.data_ptr()), _stream(stream)),
+               "fv_halo_unpack")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().fv_halo_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def fv_batch_set_launch(b, per_sm):
     _check(lib().fv_batch_set_launch(b, _launch4(per_sm)), "fv_batch_set_launch")
 
@@ -740,6 +804,15 @@ class Mesh:
 
     def get_order(self):
         return fv_get_order(self.h)
+
+    def levels_local_dt(self, stream=None):
+        return fv_levels_local_dt(self.h, stream)
+
+    def levels_classify(self, dt_min, stream=None):
+        fv_levels_classify(self.h, dt_min, stream)
+
+    def levels_sort(self, stream=None):
+        fv_levels_sort(self.h, stream)
 
     def set_flux_staging(self, enable):
         fv_set_flux_staging(self.h, enable)

@@ -1,5 +1,5 @@
 """The FP32 flux kernel that stages its gathered inputs through shared memory
-(k_flux_staged, the default) against the one that loads them into
+(k_flux_staged, off by default) against the one that loads them into
 registers: the same operations on the same values, so the states after
 several multi-level cycles are bitwise equal, in both orders of the level
 steps and with ragged face counts (a tiny mesh, fewer faces than threads)."""
@@ -23,7 +23,7 @@ def fv():
 
 def _run(fv, mesh, prim, L, staged, order, cycles):
     g = fv.Mesh(mesh, max_levels=L, precision=fv.FV_FP32_FLUX)
-    assert g.get_flux_staging() is True  # the default
+    assert g.get_flux_staging() is False  # the default
     g.set_flux_staging(staged)
     assert g.get_flux_staging() is staged
     g.set_order(order)
