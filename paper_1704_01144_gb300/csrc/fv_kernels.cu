@@ -440,9 +440,16 @@ __device__ __forceinline__ int face_key_of(const DevMesh &d, int f) {
   return k;
 }
 
-// ---- stable counting sort of small keys (< 16 buckets), 1024 items per tile
+// ---- stable counting sort of small keys (< 16 buckets), in tiles of
+// SORT_TILE (batches) or SORT_TILE1 (one mesh) items
 #define SORT_TILE 1024
 #define SORT_THREADS 256
+// items per tile of one large mesh's sort (from SORT_LARGE_CELLS cells):
+// larger tiles, fewer (bucket, tile) counts for the single-block scan (at
+// 80M cells, 1024-item tiles made the scan a millisecond per cycle); a
+// smaller mesh keeps SORT_TILE, which fills the GPU with more blocks
+#define SORT_TILE1 8192
+#define SORT_LARGE_CELLS (1 << 23)
 
 // per-tile bucket counts -> cnt[bucket * nblk + tile]
 __device__ __forceinline__ void sort_hist_tile(const uint8_t *__restrict__ key, int n, int nb, int *cnt,
@@ -517,15 +524,15 @@ __device__ __forceinline__ void emit_entry(const DevMesh &d, int i, int pos) {
 
 // stable scatter of one tile: lanes with equal keys rank in lane (= item)
 // order, warps in order, earlier rounds first
-template <bool FACES>
+template <bool FACES, int TILE = SORT_TILE>
 __device__ __forceinline__ void sort_scatter_tile(const DevMesh &d, const uint8_t *__restrict__ key, int n,
                                                   int nb, const int *__restrict__ cnt, int tile, int nblk) {
   __shared__ int wcount[SORT_THREADS / 32][16];
   __shared__ int run[16];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x < 16) run[threadIdx.x] = threadIdx.x < nb ? cnt[threadIdx.x * nblk + tile] : 0;
-  int base = tile * SORT_TILE;
-  for (int r = 0; r < SORT_TILE / SORT_THREADS; ++r) {
+  int base = tile * TILE;
+  for (int r = 0; r < TILE / SORT_THREADS; ++r) {
     int i = base + r * SORT_THREADS + threadIdx.x;
     int k = i < n ? (int)key[i] : -1;
     if (lane < 16) wcount[warp][lane] = 0;
@@ -554,6 +561,7 @@ __device__ __forceinline__ void sort_scatter_tile(const DevMesh &d, const uint8_
 // the per-tile counts (tiles 0..nc-1 are cells, the rest faces), the two
 // scans (block 0 cells, block 1 faces), the two stable scatters.  The cell
 // counts sit at sort_cnt[0 .. 2L nc), the face counts after them.
+template <int TILE>
 __global__ void __launch_bounds__(SORT_THREADS) k_keys_hist(DevMesh d, int nc, int nf) {
   __shared__ int h[16];
   pdl_wait();
@@ -561,8 +569,8 @@ __global__ void __launch_bounds__(SORT_THREADS) k_keys_hist(DevMesh d, int nc, i
   __syncthreads();
   const bool faces = (int)blockIdx.x >= nc;
   const int tile = faces ? blockIdx.x - nc : blockIdx.x, n = faces ? d.F : d.N;
-  for (int r = 0; r < SORT_TILE / SORT_THREADS; ++r) {
-    const int i = tile * SORT_TILE + r * SORT_THREADS + threadIdx.x;
+  for (int r = 0; r < TILE / SORT_THREADS; ++r) {
+    const int i = tile * TILE + r * SORT_THREADS + threadIdx.x;
     if (i < n) atomicAdd(&h[faces ? face_key_of(d, i) : cell_key_store(d, i)], 1);
   }
   __syncthreads();
@@ -580,12 +588,13 @@ __global__ void __launch_bounds__(1024) k_sort_scan2(DevMesh d, int nc, int nf) 
   pdl_trigger();
 }
 
+template <int TILE>
 __global__ void __launch_bounds__(SORT_THREADS) k_sort_scatter2(DevMesh d, int nc, int nf) {
   pdl_wait();
   if ((int)blockIdx.x < nc)
-    sort_scatter_tile<false>(d, d.ckey, d.N, 2 * d.L, d.sort_cnt, blockIdx.x, nc);
+    sort_scatter_tile<false, TILE>(d, d.ckey, d.N, 2 * d.L, d.sort_cnt, blockIdx.x, nc);
   else
-    sort_scatter_tile<true>(d, d.fkey, d.F, d.L, d.sort_cnt + 2 * d.L * nc, blockIdx.x - nc, nf);
+    sort_scatter_tile<true, TILE>(d, d.fkey, d.F, d.L, d.sort_cnt + 2 * d.L * nc, blockIdx.x - nc, nf);
   pdl_trigger();
 }
 
@@ -2186,13 +2195,31 @@ static void launch_pdl(void (*kernel)(KArgs...), int grid, int block, cudaStream
   cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
-int launch_assign_levels(const DevMesh &d, int L, int *cnt_scratch, ProfHook *ph, cudaStream_t s) {
-  (void)cnt_scratch;  // d.sort_cnt
+// the three parts of the level assignment: local steps and their minimum;
+// levels from dt_min (classification and smoothing); keys and sorted lists.
+// A sharded run puts the global minimum in between the first two and the
+// owners' levels of its ghost cells in between the last two.
+int launch_levels_local_dt(const DevMesh &d, cudaStream_t s) {
   int g = grid_for(d.N, 256, 8);
-  ProfScope scope(ph, FV_PROF_LEVELS, s);
   launch_pdl(k_init_min2, 1, 1, s, d.dtmin_bits, d.dthi_bits);
   launch_pdl(k_dt32, g, 256, s, d);
   launch_pdl(k_dt_min_exact, g, 256, s, d);
+  FV_LAUNCH_CHECK();
+  return FV_OK;
+}
+
+__global__ void k_set_bits(unsigned long long *bits, unsigned long long v) { *bits = v; }
+
+int launch_set_dt_min(const DevMesh &d, double dt_min, cudaStream_t s) {
+  unsigned long long v;
+  memcpy(&v, &dt_min, sizeof v);
+  launch_pdl(k_set_bits, 1, 1, s, d.dtmin_bits, v);
+  FV_LAUNCH_CHECK();
+  return FV_OK;
+}
+
+int launch_levels_classify(const DevMesh &d, int L, cudaStream_t s) {
+  int g = grid_for(d.N, 256, 8);
   launch_pdl(k_levels0_certified, g, 256, s, d);
   // L-1 Jacobi sweeps between lev_tmp and lev; the result must land in lev
   const int8_t *src = d.lev_tmp;
@@ -2214,13 +2241,34 @@ int launch_assign_levels(const DevMesh &d, int L, int *cnt_scratch, ProfHook *ph
     }
   }
   FV_LAUNCH_CHECK();
+  return FV_OK;
+}
+
+template <int TILE>
+static void launch_sort_tiles(const DevMesh &d, cudaStream_t s) {
   // cell keys (2L buckets) and face keys (L buckets), sorted together
-  const int nc = (d.N + SORT_TILE - 1) / SORT_TILE, nf = (d.F + SORT_TILE - 1) / SORT_TILE;
-  launch_pdl(k_keys_hist, nc + nf, SORT_THREADS, s, d, nc, nf);
+  const int nc = (d.N + TILE - 1) / TILE, nf = (d.F + TILE - 1) / TILE;
+  launch_pdl(k_keys_hist<TILE>, nc + nf, SORT_THREADS, s, d, nc, nf);
   launch_pdl(k_sort_scan2, 2, 1024, s, d, nc, nf);
-  launch_pdl(k_sort_scatter2, nc + nf, SORT_THREADS, s, d, nc, nf);
+  launch_pdl(k_sort_scatter2<TILE>, nc + nf, SORT_THREADS, s, d, nc, nf);
+}
+
+int launch_levels_sort(const DevMesh &d, cudaStream_t s) {
+  if (d.N >= SORT_LARGE_CELLS)
+    launch_sort_tiles<SORT_TILE1>(d, s);
+  else
+    launch_sort_tiles<SORT_TILE>(d, s);
   FV_LAUNCH_CHECK();
   return FV_OK;
+}
+
+int launch_assign_levels(const DevMesh &d, int L, int *cnt_scratch, ProfHook *ph, cudaStream_t s) {
+  (void)cnt_scratch;  // d.sort_cnt
+  ProfScope scope(ph, FV_PROF_LEVELS, s);
+  int rc = launch_levels_local_dt(d, s);
+  if (rc == FV_OK) rc = launch_levels_classify(d, L, s);
+  if (rc == FV_OK) rc = launch_levels_sort(d, s);
+  return rc;
 }
 
 template <typename T, bool G14>
