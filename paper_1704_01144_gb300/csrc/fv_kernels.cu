@@ -925,6 +925,32 @@ __device__ __forceinline__ void mlp_guess(const uint32_t *__restrict__ sw, float
   }
 }
 
+// FP32: the MUSCL-minmod reconstruction of both sides of an interior face
+// with Blackwell's paired FP32 instructions (two independent multiplies or
+// fused multiply-adds per instruction): each component's left and right
+// gradient projections g_i.r and g_j.r, the limiter arguments 2 g.r - dW
+// and the reconstructed values W_i + m/2, W_j - m/2 go pairwise; the
+// limiter itself stays per side.  The same operations as the plain form
+// (the projections accumulate x, then y, then z).
+__device__ __forceinline__ void reconstruct_pair(const float Wi[], const float gi[], const float Wj[],
+                                                 const float gj[], const float r[3], float WL[5],
+                                                 float WR[5]) {
+  const float2 r0 = make_float2(r[0], r[0]), r1 = make_float2(r[1], r[1]), r2 = make_float2(r[2], r[2]);
+  const float2 two = make_float2(2.0f, 2.0f), half = make_float2(0.5f, -0.5f);
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    float2 g = __fmul2_rn(make_float2(gi[3 * c], gj[3 * c]), r0);
+    g = __ffma2_rn(make_float2(gi[3 * c + 1], gj[3 * c + 1]), r1, g);
+    g = __ffma2_rn(make_float2(gi[3 * c + 2], gj[3 * c + 2]), r2, g);
+    const float dW = Wj[c] - Wi[c];
+    const float2 a = __ffma2_rn(two, g, make_float2(-dW, -dW));
+    const float2 m = make_float2(minmod(a.x, dW), minmod(a.y, dW));
+    const float2 w = __ffma2_rn(half, m, make_float2(Wi[c], Wj[c]));
+    WL[c] = w.x;
+    WR[c] = w.y;
+  }
+}
+
 // the reconstructed inputs of face f's Riemann problem from the phase-time
 // primitive and gradient records: WL, WR (a boundary face copies WL into WR),
 // unit normal n and area A; fc = fcell[f], the face's cells.  Returns fc.y:
@@ -948,13 +974,17 @@ __device__ __forceinline__ int face_states(const DevMesh &d, const T *__restrict
     T Wj[REC_W], gj[REC_G];
     ldrec<REC_W>(W + (size_t)R * REC_W, Wj);
     ldrec<REC_G>(Gr + (size_t)R * REC_G, gj);
+    if constexpr (sizeof(T) == 4) {
+      reconstruct_pair(Wi, gi, Wj, gj, r, WL, WR);
+    } else {
 #pragma unroll
-    for (int c = 0; c < 5; ++c) {
-      T dW = Wj[c] - Wi[c];
-      T gir = (gi[3 * c] * r[0] + gi[3 * c + 1] * r[1]) + gi[3 * c + 2] * r[2];
-      T gjr = (gj[3 * c] * r[0] + gj[3 * c + 1] * r[1]) + gj[3 * c + 2] * r[2];
-      WL[c] = Wi[c] + T(0.5) * minmod(T(2) * gir - dW, dW);
-      WR[c] = Wj[c] - T(0.5) * minmod(T(2) * gjr - dW, dW);
+      for (int c = 0; c < 5; ++c) {
+        T dW = Wj[c] - Wi[c];
+        T gir = (gi[3 * c] * r[0] + gi[3 * c + 1] * r[1]) + gi[3 * c + 2] * r[2];
+        T gjr = (gj[3 * c] * r[0] + gj[3 * c + 1] * r[1]) + gj[3 * c + 2] * r[2];
+        WL[c] = Wi[c] + T(0.5) * minmod(T(2) * gir - dW, dW);
+        WR[c] = Wj[c] - T(0.5) * minmod(T(2) * gjr - dW, dW);
+      }
     }
   } else {
     // reconstruct toward the ghost (mirror image of the cell in the face)

@@ -114,23 +114,22 @@ __device__ __forceinline__ int riemann_star(const GasT<T> &G, T rL, T uL, T pL, 
   if (p < pfloor) p = pfloor;
   int it;
   bool conv = false;
-  // as in riemann_star14: FP32 exits leave p where fL, fR were evaluated
-  T fL = T(0), fR = T(0);
-  bool at_p = false;
+  // as in riemann_star14: FP64 evaluates again at the final p, FP32 extends
+  // the last values along their slopes
+  T fL = T(0), fR = T(0), dfL = T(0), dfR = T(0), dp = T(0);
   for (it = 1; it <= G.maxit; ++it) {
-    T dfL, dfR;
     pressure_fn(G, p, rL, pL, aL, fL, dfL);
     pressure_fn(G, p, rR, pR, aR, fR, dfR);
     T fsum = fL + fR + du;
     if (at_rounding_floor(fsum, fL, fR, du)) {
       conv = true;
-      at_p = true;
+      dp = T(0);
       break;
     }
     T pn = p - qdiv(fsum, dfL + dfR);
     if (pn < pfloor) pn = pfloor;
     T change = qdiv(fabs(pn - p), T(0.5) * (pn + p));
-    at_p = pn == p;
+    dp = pn - p;
     p = pn;
     if (change <= G.tol) {
       conv = true;
@@ -139,10 +138,12 @@ __device__ __forceinline__ int riemann_star(const GasT<T> &G, T rL, T uL, T pL, 
   }
   iters = it;
   if (!conv || !(p > T(0)) || !isfinite(p)) return 2;
-  if (sizeof(T) == 8 || !at_p) {
-    T dfL, dfR;
+  if (sizeof(T) == 8) {
     pressure_fn(G, p, rL, pL, aL, fL, dfL);
     pressure_fn(G, p, rR, pR, aR, fR, dfR);
+  } else {
+    fL += dfL * dp;
+    fR += dfR * dp;
   }
   ps = p;
   us = T(0.5) * (uL + uR) + T(0.5) * (fR - fL);
@@ -242,6 +243,18 @@ __device__ __forceinline__ float rroot7(float x) {
   float r2 = r * r, r4 = r2 * r2;
   return r * (8.0f - x * (r4 * r2 * r)) * (1.0f / 7.0f);
 }
+// FP32: the inverse seventh roots of two values at once, the Newton step
+// with paired instructions (the seed's logarithm and power stay per value)
+__device__ __forceinline__ float2 rroot7_pair(float2 x) {
+  const float2 lg = __fmul2_rn(make_float2(__log2f(x.x), __log2f(x.y)),
+                               make_float2(-0.14285714285714285f, -0.14285714285714285f));
+  const float2 r = make_float2(exp2f(lg.x), exp2f(lg.y));
+  const float2 r2 = __fmul2_rn(r, r), r4 = __fmul2_rn(r2, r2);
+  const float2 r7 = __fmul2_rn(__fmul2_rn(r4, r2), r);
+  const float2 t = __ffma2_rn(make_float2(-x.x, -x.y), r7, make_float2(8.0f, 8.0f));
+  return __fmul2_rn(__fmul2_rn(r, t), make_float2(1.0f / 7.0f, 1.0f / 7.0f));
+}
+
 template <typename T>
 __device__ __forceinline__ T ipow5(T c) {
   T c2 = c * c;
@@ -272,6 +285,41 @@ __device__ __forceinline__ Side14<T> make_side14(const GasT<T> &G, T rK, T pK) {
   s.A = qdiv(T(2), G.gp1 * rK);
   s.B = G.k_gm1_gp1 * pK;
   return s;
+}
+
+// FP32: both sides' constants at once with paired instructions (the
+// reciprocals, square roots and the seventh roots' seeds stay per side):
+// a = sqrt(g p / r), iq = p^(-1/7), c = p iq / (r a), e = 5 a,
+// A = 2 / ((g+1) r), B = (g-1)/(g+1) p
+__device__ __forceinline__ void make_sides14_pair(const GasT<float> &G, float rL, float pL, float rR, float pR,
+                                                  Side14<float> &L, Side14<float> &R) {
+  const float2 p = make_float2(pL, pR), r = make_float2(rL, rR);
+  const float2 ir = make_float2(qdiv(1.0f, rL), qdiv(1.0f, rR));
+  const float2 q = __fmul2_rn(__fmul2_rn(make_float2(G.g, G.g), p), ir);
+  const float2 a = __fmul2_rn(q, make_float2(rsqrtf(q.x), rsqrtf(q.y)));
+  const float2 iq = rroot7_pair(p);
+  const float2 ra = __fmul2_rn(r, a);
+  const float2 c = __fmul2_rn(__fmul2_rn(p, iq), make_float2(qdiv(1.0f, ra.x), qdiv(1.0f, ra.y)));
+  const float2 e = __fmul2_rn(make_float2(5.0f, 5.0f), a);
+  const float two_gp1 = (float)(2.0 / (1.4 + 1.0));  // the gamma = 1.4 path only
+  const float2 A = __fmul2_rn(make_float2(two_gp1, two_gp1), ir);
+  const float2 B = __fmul2_rn(make_float2(G.k_gm1_gp1, G.k_gm1_gp1), p);
+  L.r = rL;
+  L.p = pL;
+  L.a = a.x;
+  L.iq = iq.x;
+  L.c = c.x;
+  L.e = e.x;
+  L.A = A.x;
+  L.B = B.x;
+  R.r = rR;
+  R.p = pR;
+  R.a = a.y;
+  R.iq = iq.y;
+  R.c = c.y;
+  R.e = e.y;
+  R.A = A.y;
+  R.B = B.y;
 }
 
 // f_K(p) and f_K'(p).  FP64: from p17 = p^(1/7) and rp6 = p^(-6/7), shared
@@ -340,29 +388,29 @@ __device__ __forceinline__ int riemann_star14(const GasT<T> &G, const Side14<T> 
   if (p < pfloor) p = pfloor;
   int it;
   bool conv = false;
-  // fL, fR of the last evaluation, and whether p still is where they were
-  // evaluated (FP32: the rounding-floor exit, or an update that rounded to
-  // nothing -- the only way a relative change of 1e-10 passes in single
-  // precision).  Then u* takes them as they are, which is what evaluating
-  // them again at the same p would give.
-  T fL = T(0), fR = T(0);
-  bool at_p = false;
+  // fL, fR and their slopes at the last evaluated iterate, and the step from
+  // it to the final p (0 on the rounding-floor exit).  FP64 evaluates both
+  // pressure functions again at the final p, as the oracle does.  FP32
+  // extends the last values to it along their slopes: the FP32 tolerance
+  // (2e-6) bounds the step, so the neglected second-order term is ~1e-12
+  // relative, far below single-precision rounding, and the two evaluations
+  // are saved.
+  T fL = T(0), fR = T(0), dfL = T(0), dfR = T(0), dp = T(0);
   for (it = 1; it <= G.maxit; ++it) {
     T p17 = T(0), rp6 = T(0);
     if (sizeof(T) == 8 && (p <= L.p || p <= R.p)) roots_of(p, p17, rp6);
-    T dfL, dfR;
     pressure_fn14(L, p, p17, rp6, fL, dfL);
     pressure_fn14(R, p, p17, rp6, fR, dfR);
     T fsum = fL + fR + du;
     if (at_rounding_floor(fsum, fL, fR, du)) {
       conv = true;
-      at_p = true;
+      dp = T(0);
       break;
     }
     T pn = p - qdiv(fsum, dfL + dfR);
     if (pn < pfloor) pn = pfloor;
     T change = qdiv(fabs(pn - p), T(0.5) * (pn + p));
-    at_p = pn == p;
+    dp = pn - p;
     p = pn;
     if (change <= G.tol) {
       conv = true;
@@ -372,11 +420,13 @@ __device__ __forceinline__ int riemann_star14(const GasT<T> &G, const Side14<T> 
   iters = it;
   if (!conv || !(p > T(0)) || !isfinite(p)) return 2;
   T p17 = T(0), rp6 = T(0);
-  if (sizeof(T) == 8) roots_of(p, p17, rp6);
-  if (sizeof(T) == 8 || !at_p) {
-    T dfL, dfR;
+  if (sizeof(T) == 8) {
+    roots_of(p, p17, rp6);
     pressure_fn14(L, p, p17, rp6, fL, dfL);
     pressure_fn14(R, p, p17, rp6, fR, dfR);
+  } else {
+    fL += dfL * dp;
+    fR += dfR * dp;
   }
   ps = p;
   ps17 = p17;
@@ -463,7 +513,13 @@ __device__ __forceinline__ int godunov_flux(const GasT<T> &G, const T WL[5], con
   T r0, un0, p0;
   int side;
   if (G14) {
-    Side14<T> L = make_side14(G, WL[0], WL[4]), R = make_side14(G, WR[0], WR[4]);
+    Side14<T> L, R;
+    if constexpr (sizeof(T) == 4) {
+      make_sides14_pair(G, WL[0], WL[4], WR[0], WR[4], L, R);
+    } else {
+      L = make_side14(G, WL[0], WL[4]);
+      R = make_side14(G, WR[0], WR[4]);
+    }
     T p17;
     int rc = riemann_star14<T, GUESS>(G, L, unL, R, unR, ps, us, p17, iters, gabs, gmul);
     if (rc) return rc;
