@@ -549,6 +549,13 @@ int fv_mlp_pack(const float *params_dev, int n_params, int target, double gate, 
  * asynchronous. */
 int fv_mlp_infer(const void *packed_dev, const float *x_dev, int64_t count, float *y_dev, void *stream);
 
+/* The same inference with CUDA's tanhf in the activations instead of the
+ * hardware tanh approximation the flux kernel uses: a check that separates
+ * the approximation's error from the bfloat16 quantisation (the flux kernels
+ * never call it).  Arguments and errors as fv_mlp_infer. */
+int fv_mlp_infer_exact_tanh(const void *packed_dev, const float *x_dev, int64_t count, float *y_dev,
+                            void *stream);
+
 /* Training data from harvested pairs pairs_dev[6*count] = (rL, uL, pL, rR,
  * uR, pR) in the face frame: the exact star pressure pstar_dev[count] (FP64
  * Newton to a relative change of 1e-14), the features x_dev[6*count], the

@@ -236,6 +236,7 @@ __global__ void k_mlp_pack(const float *__restrict__ th, int target, float gate,
 }
 
 // standalone bfloat16 inference (the flux kernel's device function)
+template <bool EXACT>
 __global__ void __launch_bounds__(128, 4) k_mlp_infer(const uint32_t *__restrict__ pk,
                                                       const float *__restrict__ X, int n,
                                                       float *__restrict__ Y) {
@@ -250,7 +251,7 @@ __global__ void __launch_bounds__(128, 4) k_mlp_infer(const uint32_t *__restrict
 #pragma unroll
     for (int c = 0; c < 6; ++c) x[c] = ok ? X[6 * (size_t)i + c] : (c == 1 || c == 4 ? 0.0f : 1.0f);
     __syncwarp();
-    float y = mlp_eval_warp(sw, x);
+    float y = mlp_eval_warp<EXACT>(sw, x);
     if (ok) Y[i] = y;
   }
 }
@@ -396,16 +397,31 @@ int fv_mlp_pack(const float *params_dev, int n_params, int target, double gate, 
   return FV_OK;
 }
 
-int fv_mlp_infer(const void *packed_dev, const float *x_dev, int64_t count, float *y_dev, void *stream) {
+static int mlp_infer(const void *packed_dev, const float *x_dev, int64_t count, float *y_dev, void *stream,
+                     bool exact) {
   if (!packed_dev || (count > 0 && (!x_dev || !y_dev)) || count < 0 || count > 0x7fffffff)
     return mfail(FV_ERR_INVALID_ARG, "fv_mlp_infer: bad argument");
   if ((uintptr_t)packed_dev % 16) return mfail(FV_ERR_INVALID_ARG, "fv_mlp_infer: packed buffer not 16-byte aligned");
   if (count == 0) return FV_OK;
   int n = (int)count;
   int grid = (n + 127) / 128, cap = 4 * sm_count();
-  k_mlp_infer<<<grid < cap ? grid : cap, 128, 0, (cudaStream_t)stream>>>((const uint32_t *)packed_dev, x_dev, n, y_dev);
+  if (exact)
+    k_mlp_infer<true><<<grid < cap ? grid : cap, 128, 0, (cudaStream_t)stream>>>((const uint32_t *)packed_dev, x_dev,
+                                                                                 n, y_dev);
+  else
+    k_mlp_infer<false><<<grid < cap ? grid : cap, 128, 0, (cudaStream_t)stream>>>((const uint32_t *)packed_dev, x_dev,
+                                                                                  n, y_dev);
   MCK(cudaGetLastError());
   return FV_OK;
+}
+
+int fv_mlp_infer(const void *packed_dev, const float *x_dev, int64_t count, float *y_dev, void *stream) {
+  return mlp_infer(packed_dev, x_dev, count, y_dev, stream, false);
+}
+
+int fv_mlp_infer_exact_tanh(const void *packed_dev, const float *x_dev, int64_t count, float *y_dev,
+                            void *stream) {
+  return mlp_infer(packed_dev, x_dev, count, y_dev, stream, true);
 }
 
 int fv_mlp_label(const double *pairs_dev, int64_t count, double gamma, int target, float *x_dev,

@@ -62,9 +62,10 @@ __device__ __forceinline__ float tanh_fast(float x) {
 
 // inference activation: the tanh form with the hardware tanh approximation
 // (relative error near 2^-11, below bfloat16's 2^-8 resolution)
+template <bool EXACT = false>
 __device__ __forceinline__ float gelu_infer(float x) {
   float u = 0.7978845608028654f * (x + 0.044715f * (x * x * x));
-  return 0.5f * x * (1.0f + tanh_fast(u));
+  return 0.5f * x * (1.0f + (EXACT ? tanhf(u) : tanh_fast(u)));
 }
 
 __device__ __forceinline__ void mma_k8(float c[4], uint32_t a0, uint32_t a1, uint32_t b0) {
@@ -127,6 +128,11 @@ __device__ __forceinline__ float shock_strength(float gamma, float rL, float uL,
 // call it together (mma.sync and full-mask shuffles).  sw: packed weights.
 // The two 16-face tiles go one after the other, which halves the live
 // fragments (the weights are read from shared memory once per tile).
+// EXACT: the library's correctly rounded-ish tanhf in the activations
+// instead of the hardware approximation (the check that separates the
+// approximation's error from the bfloat16 quantisation; not used in flux
+// kernels)
+template <bool EXACT = false>
 __device__ __forceinline__ float mlp_eval_warp(const uint32_t *__restrict__ sw, const float x[6]) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
@@ -158,8 +164,8 @@ __device__ __forceinline__ float mlp_eval_warp(const uint32_t *__restrict__ sw, 
       const float c0 = b1[8 * j + 2 * t], c1 = b1[8 * j + 2 * t + 1];
       float c[4] = {c0, c1, c0, c1};
       mma_k8(c, a1f[0], a1f[1], sw[PK_W1 + j * 32 + lane]);
-      a2f[j >> 1][(j & 1) * 2 + 0] = pack_bf16x2(gelu_infer(c[0]), gelu_infer(c[1]));
-      a2f[j >> 1][(j & 1) * 2 + 1] = pack_bf16x2(gelu_infer(c[2]), gelu_infer(c[3]));
+      a2f[j >> 1][(j & 1) * 2 + 0] = pack_bf16x2(gelu_infer<EXACT>(c[0]), gelu_infer<EXACT>(c[1]));
+      a2f[j >> 1][(j & 1) * 2 + 1] = pack_bf16x2(gelu_infer<EXACT>(c[2]), gelu_infer<EXACT>(c[3]));
     }
     // layer 2 + GELU + the output layer's partial dot products
     float y0 = 0.f, y1 = 0.f;
@@ -173,8 +179,8 @@ __device__ __forceinline__ float mlp_eval_warp(const uint32_t *__restrict__ sw, 
         mma_k16(c, a2f[kk], bw.x, bw.y);
       }
       const float v0 = w3[8 * j + 2 * t], v1 = w3[8 * j + 2 * t + 1];
-      y0 += gelu_infer(c[0]) * v0 + gelu_infer(c[1]) * v1;
-      y1 += gelu_infer(c[2]) * v0 + gelu_infer(c[3]) * v1;
+      y0 += gelu_infer<EXACT>(c[0]) * v0 + gelu_infer<EXACT>(c[1]) * v1;
+      y1 += gelu_infer<EXACT>(c[2]) * v0 + gelu_infer<EXACT>(c[3]) * v1;
     }
     y0 += __shfl_xor_sync(FULL, y0, 1);
     y0 += __shfl_xor_sync(FULL, y0, 2);

@@ -72,7 +72,7 @@ EXPORTS = [
     "fv_batch_set_guess", "fv_set_fusion", "fv_get_fusion", "fv_set_order", "fv_get_order",
     "fv_set_predictor_sum", "fv_get_predictor_sum", "fv_set_flux_staging", "fv_get_flux_staging",
     "fv_levels_local_dt", "fv_levels_classify", "fv_levels_sort", "fv_halo_create", "fv_halo_pack",
-    "fv_halo_unpack", "fv_halo_size", "fv_halo_free",
+    "fv_halo_unpack", "fv_halo_size", "fv_halo_free", "fv_mlp_infer_exact_tanh",
 ]
 
 FV_MLP_PARAMS = 4673
@@ -175,6 +175,7 @@ def lib():
     L.fv_mlp_init.argtypes = [fp, C.c_int, C.c_uint64]
     L.fv_mlp_pack.argtypes = [vp, C.c_int, C.c_int, C.c_double, vp, vp]
     L.fv_mlp_infer.argtypes = [vp, vp, i64, vp, vp]
+    L.fv_mlp_infer_exact_tanh.argtypes = [vp, vp, i64, vp, vp]
     L.fv_mlp_label.argtypes = [vp, i64, C.c_double, C.c_int, vp, vp, vp, vp, vp]
     L.fv_mlp_loss_grad.argtypes = [vp, vp, vp, vp, i64, vp, dp, vp]
     L.fv_mlp_adam.argtypes = [vp, vp, vp, vp, C.c_int, C.c_double, C.c_double, C.c_double,
@@ -413,14 +414,16 @@ def fv_mlp_pack(params, target, gate=-1.0, packed=None, stream=None):
     return packed
 
 
-def fv_mlp_infer(packed, x, y=None, stream=None):
-    """Network outputs of features x (n, 6) float32 CUDA -> y (n,) float32."""
+def fv_mlp_infer(packed, x, y=None, stream=None, exact_tanh=False):
+    """Network outputs of features x (n, 6) float32 CUDA -> y (n,) float32
+    (exact_tanh: fv_mlp_infer_exact_tanh)."""
     import torch
     n = int(x.shape[0])
     if y is None:
         y = torch.empty(n, dtype=torch.float32, device=x.device)
-    _check(lib().fv_mlp_infer(_dptr(packed, "uint8"), _dptr(x, "float32"), n, _dptr(y, "float32"),
-                              _stream(stream)), "fv_mlp_infer")
+    fn = lib().fv_mlp_infer_exact_tanh if exact_tanh else lib().fv_mlp_infer
+    _check(fn(_dptr(packed, "uint8"), _dptr(x, "float32"), n, _dptr(y, "float32"), _stream(stream)),
+           "fv_mlp_infer")
     return y
 
 

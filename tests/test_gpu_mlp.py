@@ -65,12 +65,47 @@ def test_infer_matches_quantised_oracle(fv, oracle_mod, n):
         y = fv.fv_mlp_infer(pk, torch.from_numpy(x).cuda()).cpu().numpy().astype(np.float64)
         ref = oracle_mod.mlp_forward_bf16(th, x)
         err = np.abs(y - ref)
-        # FP32 accumulation order, the hardware tanh (relative error ~2^-11)
-        # and an occasional one-ulp bfloat16 flip of a hidden activation
-        assert err.max() <= 2e-2, err.max()
-        assert err.mean() <= 2e-3, err.mean()
+        # FP32 accumulation order, the hardware tanh (relative error ~2^-11
+        # on each activation; measured on GB300: median 2e-7, max 3.5e-4 of
+        # outputs of order 1) and an occasional one-ulp bfloat16 flip of a
+        # hidden activation
+        assert err.max() <= 2e-3, err.max()
+        assert err.mean() <= 1e-5, err.mean()
     full = oracle_mod.mlp_forward(th.astype(np.float64), x.astype(np.float64))
     assert np.abs(y - full).max() < 0.1
+
+
+@pytest.mark.parametrize("n", [1000, 4099])
+def test_infer_exact_tanh_matches_quantised_oracle_tightly(fv, oracle_mod, n):
+    """With CUDA's tanhf in place of the hardware approximation, the tensor-
+    core pass differs from the oracle's bfloat16-quantised pass only by FP32
+    accumulation order (~1e-6) and the rare one-ulp bfloat16 flip of a hidden
+    activation whose value sits within that rounding of a boundary: the
+    median error is at FP32 level and flips are counted, not tolerated
+    wholesale.  The hardware tanh's share of the error is what the 2e-2
+    bound of the test above allows on top."""
+    import torch
+    rng = np.random.default_rng(300 + n)
+    th = theta_random(fv, 9)
+    x = features(rng, n)
+    thd = torch.from_numpy(th).cuda()
+    for target in (0, 1):
+        pk = fv.fv_mlp_pack(thd, target)
+        xd = torch.from_numpy(x).cuda()
+        y = fv.fv_mlp_infer(pk, xd, exact_tanh=True).cpu().numpy().astype(np.float64)
+        ref = oracle_mod.mlp_forward_bf16(th, x)
+        err = np.abs(y - ref)
+        scale = max(1.0, np.abs(ref).max())
+        # FP32 accumulation order alone: measured median 2e-8, and 1e-7 at
+        # most where no activation flips
+        assert np.median(err) <= 1e-7 * scale, np.median(err)
+        # a flip moves one hidden activation by 2^-8 of itself (measured:
+        # 7e-5 on the output); flips are rare
+        assert err.max() <= 1e-3 * scale, err.max()
+        assert (err > 1e-5 * scale).mean() <= 0.005, (err > 1e-5 * scale).mean()
+        y_hw = fv.fv_mlp_infer(pk, xd).cpu().numpy().astype(np.float64)
+        print(f"target {target}: exact tanh median {np.median(err):.2e} max {err.max():.2e}; "
+              f"hardware tanh median {np.median(np.abs(y_hw - ref)):.2e} max {np.abs(y_hw - ref).max():.2e}")
 
 
 def test_loss_grad_matches_oracle(fv, oracle_mod):
