@@ -388,6 +388,11 @@ int fv_mesh_load(const double *xyz, int64_t n_nodes, const int64_t *tets, int64_
   e = cudaMemset(d.ACC, 0, REC_FA * F * sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(d.BND, 0, REC_FA * F * sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(d.Un, 0, 5 * N * sizeof(double));
+  // levels start at 0: passes that read the state before the first level
+  // assignment (the harvest, the residual hooks) take every cell at U^n
+  if (e == cudaSuccess) e = cudaMemset(d.lev, 0, N);
+  if (e == cudaSuccess) e = cudaMemset(d.lev_tmp, 0, N);
+  if (e == cudaSuccess) e = cudaMemset(d.flev, 0, F);
   if (e == cudaSuccess) e = cudaMemset(d.tdev, 0, sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(d.status, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(d.counters, 0, 3 * sizeof(long long));

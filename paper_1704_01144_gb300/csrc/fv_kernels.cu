@@ -951,6 +951,19 @@ __device__ __forceinline__ void reconstruct_pair(const float Wi[], const float g
   }
 }
 
+// FP32, one side of an interior face with the operations of one lane of
+// reconstruct_pair (explicit round-to-nearest products and fused
+// multiply-adds, so that the result is bitwise the paired one): the value
+// Wc + half * minmod(2 g.r - dW, dW), half = +1/2 (left), -1/2 (right)
+__device__ __forceinline__ float reconstruct_side(float Wc, const float *g, const float r[3], float dW,
+                                                  float half) {
+  float gr = __fmul_rn(g[0], r[0]);
+  gr = __fmaf_rn(g[1], r[1], gr);
+  gr = __fmaf_rn(g[2], r[2], gr);
+  const float a = __fmaf_rn(2.0f, gr, -dW);
+  return __fmaf_rn(half, minmod(a, dW), Wc);
+}
+
 // the reconstructed inputs of face f's Riemann problem from the phase-time
 // primitive and gradient records: WL, WR (a boundary face copies WL into WR),
 // unit normal n and area A; fc = fcell[f], the face's cells.  Returns fc.y:
@@ -1150,18 +1163,10 @@ __device__ __forceinline__ int face_states_fused(const DevMesh &d, const PhaseLe
     to_prim(U, gm1, Wj);
     iface = kL != kR;
 #pragma unroll
-    for (int c = 0; c < 5; ++c) {
-      float dW = Wj[c] - Wi[c];
-      float gir = (g[3 * c] * r[0] + g[3 * c + 1] * r[1]) + g[3 * c + 2] * r[2];
-      WL[c] = Wi[c] + 0.5f * minmod(2.0f * gir - dW, dW);
-    }
+    for (int c = 0; c < 5; ++c) WL[c] = reconstruct_side(Wi[c], g + 3 * c, r, Wj[c] - Wi[c], 0.5f);
     lsq_grad<float>(d, pl, both, R, Wj, g, d.cnb4[R], d.cf4 + R);
 #pragma unroll
-    for (int c = 0; c < 5; ++c) {
-      float dW = Wj[c] - Wi[c];
-      float gjr = (g[3 * c] * r[0] + g[3 * c + 1] * r[1]) + g[3 * c + 2] * r[2];
-      WR[c] = Wj[c] - 0.5f * minmod(2.0f * gjr - dW, dW);
-    }
+    for (int c = 0; c < 5; ++c) WR[c] = reconstruct_side(Wj[c], g + 3 * c, r, Wj[c] - Wi[c], -0.5f);
   } else {
     float Wg[5];
 #pragma unroll
@@ -1618,14 +1623,7 @@ __device__ __forceinline__ void face_states_staged(const float4 (*st)[FLUX_STAGE
       gj[4 * k + 3] = v.w;
     }
     iface = Wi[5] != Wj[5];
-#pragma unroll
-    for (int c = 0; c < 5; ++c) {
-      float dW = Wj[c] - Wi[c];
-      float gir = (gi[3 * c] * r[0] + gi[3 * c + 1] * r[1]) + gi[3 * c + 2] * r[2];
-      float gjr = (gj[3 * c] * r[0] + gj[3 * c + 1] * r[1]) + gj[3 * c + 2] * r[2];
-      WL[c] = Wi[c] + 0.5f * minmod(2.0f * gir - dW, dW);
-      WR[c] = Wj[c] - 0.5f * minmod(2.0f * gjr - dW, dW);
-    }
+    reconstruct_pair(Wi, gi, Wj, gj, r, WL, WR);
   } else {
     iface = false;
     float Wg[5];

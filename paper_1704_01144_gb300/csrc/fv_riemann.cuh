@@ -500,6 +500,15 @@ __device__ __forceinline__ void sample_face14(const GasT<T> &G, const Side14<T> 
   }
 }
 
+// the flux of a face whose Riemann problem failed (vacuum, or Newton did not
+// converge): NaN, so that the failure reaches the state it would corrupt and
+// the state check reports it, the same way whatever the registers held
+template <typename T>
+__device__ __forceinline__ void failed_flux(T F[5]) {
+#pragma unroll
+  for (int c = 0; c < 5; ++c) F[c] = (T)__int_as_float(0x7fc00000);
+}
+
 // Godunov flux per unit area through an interior face with unit normal n;
 // the tangential velocity comes from the upwind side of the contact.
 // Returns 0 or the riemann_star error.
@@ -522,12 +531,18 @@ __device__ __forceinline__ int godunov_flux(const GasT<T> &G, const T WL[5], con
     }
     T p17;
     int rc = riemann_star14<T, GUESS>(G, L, unL, R, unR, ps, us, p17, iters, gabs, gmul);
-    if (rc) return rc;
+    if (rc) {
+      failed_flux(F);
+      return rc;
+    }
     sample_face14(G, L, unL, R, unR, ps, us, p17, r0, un0, p0, side);
   } else {
     int rc = riemann_star<T, GUESS>(G, WL[0], unL, WL[4], WR[0], unR, WR[4], ps, us, iters, gabs,
                                     gmul);
-    if (rc) return rc;
+    if (rc) {
+      failed_flux(F);
+      return rc;
+    }
     sample_face(G, WL[0], unL, WL[4], WR[0], unR, WR[4], ps, us, r0, un0, p0, side);
   }
   const bool left = side == 0;
@@ -562,7 +577,10 @@ __device__ __forceinline__ int boundary_flux(const GasT<T> &G, int bc, const T W
     } else {
       rc = riemann_star(G, WL[0], un, WL[4], WL[0], -un, WL[4], ps, us, iters);
     }
-    if (rc) return rc;
+    if (rc) {
+      failed_flux(F);
+      return rc;
+    }
     F[0] = T(0);
     F[1] = ps * n[0];
     F[2] = ps * n[1];
