@@ -310,3 +310,25 @@ def test_reference_arm_prints_its_contract_line():
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == r["value"] and cb["sample"]
     e = r["e2e"]
     assert e["value"] == r["value"] and e["h2d_bytes_per_step"] == 0 == e["d2h_bytes_per_step"]
+
+
+def test_reference_arm_samples_the_default_workload(monkeypatch, capsys):
+    """The default workload is the 79.87M-tet ground blast; the oracle's
+    reference arm runs a bounded sample of it (the same recipe on a smaller
+    mesh, here shrunk further), restarted from its initial state every few
+    cycles outside the timed region, and says so in its line."""
+    import argparse
+    import bench
+    shape, L = bench.build_workload_shape(bench.DEFAULT_WORKLOAD)
+    assert bench.DEFAULT_WORKLOAD == "ground80m" and shape.n_tets == 79872318 and L == 6
+    assert bench.describe("ground80m", shape, L)["workload"].startswith("ground-plane half-sphere blast")
+    monkeypatch.setattr(bench, "ORACLE_SAMPLE", {"ground80m": (dict(n=12, ratio=8.0), 2)})
+    mesh, prim, Ls = bench.build_workload("ground80m", sample=True)
+    assert mesh.n_tets == 6 * 12 ** 3 and Ls == 6
+    args = argparse.Namespace(workload="ground80m", steps=3, warmup=3)
+    bench.main_reference(args)
+    line = json.loads([ln for ln in capsys.readouterr().out.splitlines() if ln.startswith("{")][-1])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["steps"] == 3
+    assert "79872318 tets" in line["config"]["workload"]
+    assert "10368 tets" in line["config"]["oracle_sample"] and "every 2 cycles" in line["config"]["oracle_sample"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
