@@ -337,6 +337,23 @@ int fv_get_predictor_sum(fv_mesh *m, int *sum_out);
 int fv_set_flux_staging(fv_mesh *m, int enable);
 int fv_get_flux_staging(fv_mesh *m, int *enabled_out);
 
+/*
+ * The per-cell gather of the update kernels (Alg. 2, "Flow sum on cells"):
+ * FV_GATHER_THREAD, one thread per cell reads its four faces' values and
+ * adds them in face order; FV_GATHER_QUAD, four lanes per cell each read one
+ * face's value and the first lane adds them in the same order (a warp-level
+ * gather; bitwise the same results).  Both are deterministic and use no
+ * atomics.  The paper's order, the FP64 predictor sum, batches and the
+ * persistent cycle use the per-thread gather.  Setting it drops a captured
+ * graph.  Errors: FV_ERR_INVALID_ARG
+ * (NULL argument, unknown value, inside a cycle or a batch).
+ */
+#define FV_GATHER_THREAD 0
+#define FV_GATHER_QUAD 1
+#define FV_GATHER_DEFAULT FV_GATHER_THREAD
+int fv_set_gather(fv_mesh *m, int gather);
+int fv_get_gather(fv_mesh *m, int *gather_out);
+
 /* kernel classes of the profiler */
 #define FV_PROF_LEVELS 0 /* level assignment: dt, levels, sorts */
 #define FV_PROF_PRIM 1   /* primitives at the phase time */

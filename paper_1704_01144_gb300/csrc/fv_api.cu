@@ -247,6 +247,7 @@ int fv_mesh_load(const double *xyz, int64_t n_nodes, const int64_t *tets, int64_
   d.fuse_faces = FV_FUSE_FACES_DEFAULT;
   d.pred_sum64 = FV_PREDICTOR_SUM_DEFAULT == FV_SUM_FP64;
   d.flux_staged = FV_FLUX_STAGING_DEFAULT;
+  d.gather_quad = FV_GATHER_DEFAULT == FV_GATHER_QUAD;
   const bool f32 = cfg->precision == FV_FP32_FLUX;
   const int nblk_c = (int)((N + 1023) / 1024), nblk_f = (int)((F + 1023) / 1024);
   // the cell counts (2L buckets per tile), then the face counts (L per tile)
@@ -767,6 +768,25 @@ int fv_set_flux_staging(fv_mesh *m, int enable) {
 int fv_get_flux_staging(fv_mesh *m, int *enabled_out) {
   if (!m || !enabled_out) return fail(FV_ERR_INVALID_ARG, "fv_get_flux_staging: NULL argument");
   *enabled_out = m->d.flux_staged;
+  return FV_OK;
+}
+
+int fv_set_gather(fv_mesh *m, int gather) {
+  if (!m || (gather != FV_GATHER_THREAD && gather != FV_GATHER_QUAD))
+    return fail(FV_ERR_INVALID_ARG, "fv_set_gather: bad argument");
+  if (m->in_batch || (m->in_cycle && m->next_phase > 0))
+    return fail(FV_ERR_INVALID_ARG, "fv_set_gather: mesh is inside a cycle or a batch");
+  m->d.gather_quad = gather == FV_GATHER_QUAD;
+  if (m->cycle_graph) {
+    cudaGraphExecDestroy(m->cycle_graph);
+    m->cycle_graph = nullptr;
+  }
+  return FV_OK;
+}
+
+int fv_get_gather(fv_mesh *m, int *gather_out) {
+  if (!m || !gather_out) return fail(FV_ERR_INVALID_ARG, "fv_get_gather: NULL argument");
+  *gather_out = m->d.gather_quad ? FV_GATHER_QUAD : FV_GATHER_THREAD;
   return FV_OK;
 }
 

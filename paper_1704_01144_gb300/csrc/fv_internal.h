@@ -124,6 +124,8 @@ struct DevMesh {
   // FP32-flux mode, two-rarefaction guess, no fusion: the flux kernel stages
   // its gathered inputs through shared memory (k_flux_staged)
   int flux_staged;
+  // the update's gather: one thread per cell (0) or four lanes per cell (1)
+  int gather_quad;
   // physics
   double gamma, cfl, tol;
   int maxit;

@@ -1450,6 +1450,108 @@ __device__ __forceinline__ void update_item(const DevMesh &d, int stage, int lev
   }
 }
 
+// The update with the gather shared by four lanes per cell (the quad of the
+// cell's four faces, `fv_set_gather`): lane j loads face j's record and
+// applies its sign, the quad's first lane adds the four values in face order
+// ((v0 + v1) + v2) + v3 -- the order of update_item, so the results are
+// bitwise the same -- and updates the cell; lane j resets face j's
+// accumulated integral.  A warp covers 8 cells per step of its loop, which
+// every lane runs the same number of times (the shuffles take the whole
+// warp).  The paper's order and the FP64 predictor sum keep update_item.
+template <bool F32>
+__device__ __forceinline__ void update_range_quad(const DevMesh &d, int stage, int level, int beg, int end) {
+  const unsigned FULL = 0xffffffffu;
+  const size_t N = d.N;
+  const double dtmin = __longlong_as_double((long long)*d.dtmin_bits);
+  const int lane = threadIdx.x & 31, j = lane & 3, lead = lane & ~3;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int base = beg + warp * 8; base < end; base += nwarps * 8) {
+    const int idx = base + (lane >> 2);
+    const bool valid = idx < end;
+    int i = 0, f = 0;
+    unsigned bits = 0;
+    if (valid) {
+      i = d.cl[idx];
+      bits = d.clb[idx];
+      f = reinterpret_cast<const int *>(d.clf + idx)[j];
+    }
+    const bool neg = !((bits >> j) & 1u);
+    if (stage == 1 && F32) {
+      float v[REC_FA32];
+      if (valid) {
+        ldrec<REC_FA32>(d.FA32 + (size_t)f * REC_FA32, v);
+      } else {
+#pragma unroll
+        for (int c = 0; c < REC_FA32; ++c) v[c] = 0.0f;
+      }
+      float S[5];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        const float x = flip(v[c], neg);
+        const float x1 = __shfl_sync(FULL, x, lead + 1), x2 = __shfl_sync(FULL, x, lead + 2),
+                    x3 = __shfl_sync(FULL, x, lead + 3);
+        S[c] = ((x + x1) + x2) + x3;
+      }
+      if (valid && j == 0) {
+        float a[REC_U32];
+        ldrec<REC_U32>(d.Un32 + (size_t)i * REC_U32, a);
+        const float cdt = -(float)scale2(dtmin, (int)a[5]) * d.ivol32[i];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) a[c] = a[c] + cdt * S[c];
+        strec<REC_U32>(d.Us32 + (size_t)i * REC_U32, a);
+      }
+      continue;
+    }
+    const bool reset = stage == 2 && ((bits >> (4 + j)) & 1u);
+    double *src = (reset ? d.ACC : d.FA) + (size_t)f * REC_FA;
+    double v[REC_FA];
+    if (valid) {
+      ldrec<REC_FA>(src, v);
+    } else {
+#pragma unroll
+      for (int c = 0; c < REC_FA; ++c) v[c] = 0.0;
+    }
+    double S[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      const double x = flip(v[c], neg);
+      const double x1 = __shfl_sync(FULL, x, lead + 1), x2 = __shfl_sync(FULL, x, lead + 2),
+                   x3 = __shfl_sync(FULL, x, lead + 3);
+      S[c] = ((x + x1) + x2) + x3;
+    }
+    if (valid && j == 0) {
+      const double iV = d.ivol[i];
+      double u[5];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) u[c] = d.Un[c * N + i];
+      if (stage == 1) {
+        const double cdt = -scale2(dtmin, (int)d.lev[i]) * iV;
+#pragma unroll
+        for (int c = 0; c < 5; ++c) d.Us[c * N + i] = u[c] + cdt * S[c];
+      } else {
+        float r[REC_U32];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          u[c] = u[c] - iV * S[c];
+          r[c] = (float)u[c];
+        }
+#pragma unroll
+        for (int c = 0; c < 5; ++c) d.Un[c * N + i] = u[c];
+        if (F32) {
+          r[5] = (float)level;
+          r[6] = r[7] = 0.0f;
+          strec<REC_U32>(d.Un32 + (size_t)i * REC_U32, r);
+        }
+      }
+    }
+    if (valid && reset) {
+      const double z[REC_FA] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+      strec<REC_FA>(src, z);
+    }
+  }
+}
+
 // ---- phase drivers: one kernel kind over the phase's list range of one
 // mesh (k_phase1), or over the concatenated ranges of a batch of meshes
 // (k_phaseN: a flattened work index, split by a per-block prefix over the
@@ -1522,6 +1624,17 @@ __global__ void KBOUNDS(KIND, T) k_phase1(DevMesh d, const __grid_constant__ Pha
   if (!fused)
     for (int idx = beg + blockIdx.x * blockDim.x + threadIdx.x; idx < end; idx += gridDim.x * blockDim.x)
       run_item<KIND, T, G14>(d, p, G, idx);
+  pdl_trigger();
+}
+
+// the update with the quad gather (fv_set_gather), a kernel of its own so
+// that the per-thread update keeps its registers
+template <typename T>
+__global__ void __launch_bounds__(256, 5) k_update_quad(DevMesh d, const __grid_constant__ PhaseDesc p) {
+  pdl_wait();
+  int beg, end;
+  kind_range(d, p, K_UPD, beg, end);
+  update_range_quad<sizeof(T) == 4>(d, p.stage, p.level, beg, end);
   pdl_trigger();
 }
 
@@ -2343,6 +2456,8 @@ static void phase1_all(const DevMesh &d, const PhaseDesc &pd, const GasT<T> &G, 
     ProfScope sc(ph, FV_PROF_UPDATE, s);
     if (pd.stage == 3)
       launch_pdl(k_phase1<K_CORR, T, G14>, g3, 256, s, d, pd, G);
+    else if (d.gather_quad && !(sizeof(T) == 4 && pd.stage == 1 && d.pred_sum64))
+      launch_pdl(k_update_quad<T>, grid_for(4 * (int64_t)d.N, 256, lc.per_sm[3]), 256, s, d, pd);
     else
       launch_pdl(k_phase1<K_UPD, T, G14>, g3, 256, s, d, pd, G);
   }

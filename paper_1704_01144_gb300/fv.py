@@ -72,7 +72,8 @@ EXPORTS = [
     "fv_batch_set_guess", "fv_set_fusion", "fv_get_fusion", "fv_set_order", "fv_get_order",
     "fv_set_predictor_sum", "fv_get_predictor_sum", "fv_set_flux_staging", "fv_get_flux_staging",
     "fv_levels_local_dt", "fv_levels_classify", "fv_levels_sort", "fv_halo_create", "fv_halo_pack",
-    "fv_halo_unpack", "fv_halo_size", "fv_halo_free", "fv_mlp_infer_exact_tanh",
+    "fv_halo_unpack", "fv_halo_size", "fv_halo_free", "fv_mlp_infer_exact_tanh", "fv_set_gather",
+    "fv_get_gather",
 ]
 
 FV_MLP_PARAMS = 4673
@@ -84,6 +85,7 @@ FV_FUSE_FACES_DEFAULT = 0
 FV_ORDER_FINEST_FIRST, FV_ORDER_PAPER = 0, 1
 FV_SUM_FP32, FV_SUM_FP64 = 0, 1
 FV_HALO_LEVELS, FV_HALO_STATE = 1, 2
+FV_GATHER_THREAD, FV_GATHER_QUAD = 0, 1
 FV_HALO_STATE_DOUBLES = 20
 
 FV_PROF_LEVELS, FV_PROF_PRIM, FV_PROF_GRAD, FV_PROF_FLUX, FV_PROF_UPDATE = range(5)
@@ -164,6 +166,8 @@ def lib():
     L.fv_halo_size.restype = i64
     L.fv_halo_free.argtypes = [vp]
     L.fv_halo_free.restype = None
+    L.fv_set_gather.argtypes = [vp, C.c_int]
+    L.fv_get_gather.argtypes = [vp, C.POINTER(C.c_int)]
     L.fv_set_flux_staging.argtypes = [vp, C.c_int]
     L.fv_get_flux_staging.argtypes = [vp, C.POINTER(C.c_int)]
     L.fv_set_predictor_sum.argtypes = [vp, C.c_int]
@@ -677,6 +681,16 @@ def fv_get_flux_staging(h):
     return bool(a.value)
 
 
+def fv_set_gather(h, gather):
+    _check(lib().fv_set_gather(h, int(gather)), "fv_set_gather")
+
+
+def fv_get_gather(h):
+    a = C.c_int()
+    _check(lib().fv_get_gather(h, C.byref(a)), "fv_get_gather")
+    return a.value
+
+
 def fv_levels_local_dt(h, stream=None) -> float:
     v = C.c_double()
     _check(lib().fv_levels_local_dt(h, C.byref(v), _stream(stream)), "fv_levels_local_dt")
@@ -816,6 +830,12 @@ class Mesh:
 
     def levels_sort(self, stream=None):
         fv_levels_sort(self.h, stream)
+
+    def set_gather(self, gather):
+        fv_set_gather(self.h, gather)
+
+    def get_gather(self):
+        return fv_get_gather(self.h)
 
     def set_flux_staging(self, enable):
         fv_set_flux_staging(self.h, enable)
