@@ -494,7 +494,7 @@ def run_mode(fv, torch, mesh, prim, L, precision, steps, warmup, stream, flush, 
     return g, out
 
 
-def run_e2e(fv, torch, g, steps, warmup, stream):
+def run_e2e(torch, g, steps, warmup, stream):
     """Through the public API with host (pinned) buffers: each step uploads
     the state, advances one cycle and reads the state back."""
     n = g.n
@@ -642,7 +642,7 @@ def gate_sweep(fv, torch, g, prim, guess, stream, flush, gates=(0.1, 0.3, 1.0, 1
     return out
 
 
-def measure_workload(fv, torch, name, modes, args, stream, flush, gpu_index, local, ws,
+def measure_workload(fv, torch, name, modes, args, stream, flush, gpu_index, ws,
                      peaks, peak_src, alu_peaks, traffic, extras=True):
     """Every measurement of one workload: the chosen form (value), plain
     FP64, the learned guess, and (extras) the persistent cycle, the paper's
@@ -712,7 +712,7 @@ def measure_workload(fv, torch, name, modes, args, stream, flush, gpu_index, loc
     e2e = None
     if extras and not args.no_e2e:
         chosen["g"].set_state(prim)      # the e2e steps also start from the initial state
-        e2e = run_e2e(fv, torch, chosen["g"], max(3, min(args.steps, 10)), 1, stream)
+        e2e = run_e2e(torch, chosen["g"], max(3, min(args.steps, 10)), 1, stream)
 
     def roofline(r, fp32_, kernel):
         return roofline_entry(r["prof"], r["prof_face_evals"], r["prof_cell_updates"], fp32_, kernel,
@@ -823,15 +823,14 @@ def main_ours(args):
     traffic = {w: measured_traffic(w) for w in WORKLOADS}
 
     out, chosen = measure_workload(fv, torch, args.workload, modes, args, stream, flush, gpu_index,
-                                   local, ws, peaks, peak_src, alu_peaks, traffic,
-                                   extras=not args.no_extras)
+                                   ws, peaks, peak_src, alu_peaks, traffic, extras=not args.no_extras)
     # the 998,250-tet spherical blast (L = 4) beside the headline: the chosen
     # form and plain FP64, same timing
     sub = None
     if args.workload == DEFAULT_WORKLOAD and not args.no_sub:
         s_out, _ = measure_workload(fv, torch, "blast1m", [m for m in modes if m != "fp32mlp"], args,
-                                    stream, flush, gpu_index, local, ws, peaks, peak_src, alu_peaks,
-                                    traffic, extras=False)
+                                    stream, flush, gpu_index, ws, peaks, peak_src, alu_peaks, traffic,
+                                    extras=False)
         sub = {"value": round(s_out["value"], 1), "unit": "cell-updates/s",
                "ms_per_step": round(s_out["ms_per_step"], 4), "config": s_out["config"],
                "roofline": s_out["roofline"], "roofline_kernels": s_out["roofline_kernels"],
