@@ -322,36 +322,75 @@ __device__ __forceinline__ void make_sides14_pair(const GasT<float> &G, float rL
   R.B = B.y;
 }
 
-// f_K(p) and f_K'(p).  FP64: from p17 = p^(1/7) and rp6 = p^(-6/7), shared
-// by both sides.  FP32: from the root of p/pK itself, with (p/pK)^(1/7) taken
-// as the reciprocal of the inverse root (about one ulp), which keeps f_K
-// smooth enough for Newton's stopping test; forming it as a product with the
-// sixth power of the root would multiply the single-precision error by six.
-__device__ __forceinline__ void pressure_fn14(const Side14<double> &K, double p, double p17,
-                                              double rp6, double &f, double &df) {
-  if (p > K.p) {
-    double q = sqrt(K.A / (p + K.B));
-    f = (p - K.p) * q;
-    df = q * (1.0 - 0.5 * (p - K.p) / (K.B + p));
-  } else {
-    f = K.e * (p17 * K.iq - 1.0);
-    df = K.c * rp6;
-  }
+// f_K(p) and f_K'(p), one branch each: shock14 for p > pK, rare14 otherwise
+// (Toro Eqs. 4.6-4.7, 4.37).  The rarefaction branch in FP64 comes from
+// p17 = p^(1/7) and rp6 = p^(-6/7), shared by both sides; in FP32 from the
+// root of p/pK itself, with (p/pK)^(1/7) taken as the reciprocal of the
+// inverse root (about one ulp), which keeps f_K smooth enough for Newton's
+// stopping test; forming it as a product with the sixth power of the root
+// would multiply the single-precision error by six.
+__device__ __forceinline__ void shock14(const Side14<double> &K, double p, double &f, double &df) {
+  double q = sqrt(K.A / (p + K.B));
+  f = (p - K.p) * q;
+  df = q * (1.0 - 0.5 * (p - K.p) / (K.B + p));
 }
-__device__ __forceinline__ void pressure_fn14(const Side14<float> &K, float p, float, float,
-                                              float &f, float &df) {
-  if (p > K.p) {
-    float q = fsqrt(qdiv(K.A, p + K.B));
-    f = (p - K.p) * q;
-    df = q * (1.0f - qdiv(0.5f * (p - K.p), K.B + p));
-  } else {
-    float pr = qdiv(p, K.p);
-    float ir = rroot7(pr);             // pr^(-1/7), about one ulp
-    float ir2 = ir * ir;
-    float ir6 = ir2 * ir2 * ir2;       // pr^(-6/7), only the slope uses it
-    f = K.e * (qdiv(1.0f, ir) - 1.0f);  // pr^(1/7) - 1 from the reciprocal
-    df = qdiv(ir6, K.r * K.a);
+__device__ __forceinline__ void shock14(const Side14<float> &K, float p, float &f, float &df) {
+  float q = fsqrt(qdiv(K.A, p + K.B));
+  f = (p - K.p) * q;
+  df = q * (1.0f - qdiv(0.5f * (p - K.p), K.B + p));
+}
+__device__ __forceinline__ void rare14(const Side14<double> &K, double, double p17, double rp6,
+                                       double &f, double &df) {
+  f = K.e * (p17 * K.iq - 1.0);
+  df = K.c * rp6;
+}
+__device__ __forceinline__ void rare14(const Side14<float> &K, float p, float, float, float &f,
+                                       float &df) {
+  float pr = qdiv(p, K.p);
+  float ir = rroot7(pr);             // pr^(-1/7), about one ulp
+  float ir2 = ir * ir;
+  float ir6 = ir2 * ir2 * ir2;       // pr^(-6/7), only the slope uses it
+  f = K.e * (qdiv(1.0f, ir) - 1.0f);  // pr^(1/7) - 1 from the reciprocal
+  df = qdiv(ir6, K.r * K.a);
+}
+
+// f_L, f_L', f_R, f_R' at p, the branches sorted across the two sides: a
+// lane runs the shock formula once per side on its shock branch and the
+// rarefaction formula once per side on its rarefaction branch, on that
+// side's constants taken by selection.  A warp whose lanes differ in which
+// side is on which branch (the usual case: the star pressure lies between
+// pL and pR, and a face's orientation decides which side is the higher)
+// runs each formula once instead of each formula once per side.  Every
+// value is the one the branch computes for that side alone.
+template <typename T>
+__device__ __forceinline__ void pressure_fns14(const Side14<T> &L, const Side14<T> &R, T p, T p17,
+                                               T rp6, T &fL, T &dfL, T &fR, T &dfR) {
+  const bool sL = p > L.p, sR = p > R.p;
+  T f, df;
+  if (sL || sR) {
+    const Side14<T> K = sL ? L : R;
+    shock14(K, p, f, df);
+    if (sL) {
+      fL = f;
+      dfL = df;
+    } else {
+      fR = f;
+      dfR = df;
+    }
   }
+  if (sL && sR) shock14(R, p, fR, dfR);
+  if (!(sL && sR)) {
+    const Side14<T> K = sL ? R : L;
+    rare14(K, p, p17, rp6, f, df);
+    if (sL) {
+      fR = f;
+      dfR = df;
+    } else {
+      fL = f;
+      dfL = df;
+    }
+  }
+  if (!(sL || sR)) rare14(R, p, p17, rp6, fR, dfR);
 }
 
 // (ps/pK)^(1/7) for the sampling step
@@ -399,8 +438,7 @@ __device__ __forceinline__ int riemann_star14(const GasT<T> &G, const Side14<T> 
   for (it = 1; it <= G.maxit; ++it) {
     T p17 = T(0), rp6 = T(0);
     if (sizeof(T) == 8 && (p <= L.p || p <= R.p)) roots_of(p, p17, rp6);
-    pressure_fn14(L, p, p17, rp6, fL, dfL);
-    pressure_fn14(R, p, p17, rp6, fR, dfR);
+    pressure_fns14(L, R, p, p17, rp6, fL, dfL, fR, dfR);
     T fsum = fL + fR + du;
     if (at_rounding_floor(fsum, fL, fR, du)) {
       conv = true;
@@ -422,8 +460,7 @@ __device__ __forceinline__ int riemann_star14(const GasT<T> &G, const Side14<T> 
   T p17 = T(0), rp6 = T(0);
   if (sizeof(T) == 8) {
     roots_of(p, p17, rp6);
-    pressure_fn14(L, p, p17, rp6, fL, dfL);
-    pressure_fn14(R, p, p17, rp6, fR, dfR);
+    pressure_fns14(L, R, p, p17, rp6, fL, dfL, fR, dfR);
   } else {
     fL += dfL * dp;
     fR += dfR * dp;
@@ -434,70 +471,51 @@ __device__ __forceinline__ int riemann_star14(const GasT<T> &G, const Side14<T> 
   return 0;
 }
 
-// the state on the face (x/t = 0); p17 = ps^(1/7)
+// the state on the face (x/t = 0); p17 = ps^(1/7).  One code path for both
+// sides: the sampled side K (left when u* >= 0) is taken by selection, and
+// on the right every velocity is mirrored (negated), which turns the right
+// side's wave tests and fan formulas into the left side's; the face
+// velocity is mirrored back at the end.  Negation is exact and rounding is
+// symmetric in sign, so each value is the one the right side's own formulas
+// give, while a warp whose faces sample both sides runs the formulas once.
 template <typename T>
 __device__ __forceinline__ void sample_face14(const GasT<T> &G, const Side14<T> &L, T uL,
                                               const Side14<T> &R, T uR, T ps, T us, T p17, T &r,
                                               T &u, T &p, int &side) {
-  if (T(0) <= us) {
-    side = 0;
-    if (ps > L.p) {
-      T SL = uL - L.a * fsqrt(G.shock_a * qdiv(ps, L.p) + G.shock_b);
-      if (T(0) <= SL) {
-        r = L.r; u = uL; p = L.p;
-      } else {
-        T q = qdiv(ps, L.p);
-        r = L.r * qdiv(q + G.k_gm1_gp1, G.k_gm1_gp1 * q + T(1));
-        u = us; p = ps;
-      }
+  const bool left = T(0) <= us;
+  side = left ? 0 : 1;
+  const Side14<T> K = left ? L : R;
+  const T uK = left ? uL : -uR;  // the side's velocity, mirrored on the right
+  const T uS = left ? us : -us;  // u*, likewise
+  T um;                          // the face velocity, mirrored on the right
+  if (ps > K.p) {
+    T SK = uK - K.a * fsqrt(G.shock_a * qdiv(ps, K.p) + G.shock_b);
+    if (T(0) <= SK) {
+      r = K.r; um = uK; p = K.p;
     } else {
-      T SHL = uL - L.a;
-      if (T(0) <= SHL) {
-        r = L.r; u = uL; p = L.p;
-      } else {
-        T pr17 = ratio17(L, ps, p17);  // (ps/pL)^(1/7)
-        T STL = us - L.a * pr17;
-        if (T(0) >= STL) {
-          r = L.r * ipow5(pr17);
-          u = us; p = ps;
-        } else {
-          T c = qdiv(T(2), G.gp1) + qdiv(G.gm1, G.gp1 * L.a) * uL;
-          r = L.r * ipow5(c);
-          u = qdiv(T(2), G.gp1) * (L.a + T(0.5) * G.gm1 * uL);
-          p = L.p * ipow7(c);
-        }
-      }
+      T q = qdiv(ps, K.p);
+      r = K.r * qdiv(q + G.k_gm1_gp1, G.k_gm1_gp1 * q + T(1));
+      um = uS; p = ps;
     }
   } else {
-    side = 1;
-    if (ps > R.p) {
-      T SR = uR + R.a * fsqrt(G.shock_a * qdiv(ps, R.p) + G.shock_b);
-      if (T(0) >= SR) {
-        r = R.r; u = uR; p = R.p;
-      } else {
-        T q = qdiv(ps, R.p);
-        r = R.r * qdiv(q + G.k_gm1_gp1, G.k_gm1_gp1 * q + T(1));
-        u = us; p = ps;
-      }
+    T SHK = uK - K.a;
+    if (T(0) <= SHK) {
+      r = K.r; um = uK; p = K.p;
     } else {
-      T SHR = uR + R.a;
-      if (T(0) >= SHR) {
-        r = R.r; u = uR; p = R.p;
+      T pr17 = ratio17(K, ps, p17);  // (ps/pK)^(1/7)
+      T STK = uS - K.a * pr17;
+      if (T(0) >= STK) {
+        r = K.r * ipow5(pr17);
+        um = uS; p = ps;
       } else {
-        T pr17 = ratio17(R, ps, p17);
-        T STR = us + R.a * pr17;
-        if (T(0) <= STR) {
-          r = R.r * ipow5(pr17);
-          u = us; p = ps;
-        } else {
-          T c = qdiv(T(2), G.gp1) - qdiv(G.gm1, G.gp1 * R.a) * uR;
-          r = R.r * ipow5(c);
-          u = qdiv(T(2), G.gp1) * (-R.a + T(0.5) * G.gm1 * uR);
-          p = R.p * ipow7(c);
-        }
+        T c = qdiv(T(2), G.gp1) + qdiv(G.gm1, G.gp1 * K.a) * uK;
+        r = K.r * ipow5(c);
+        um = qdiv(T(2), G.gp1) * (K.a + T(0.5) * G.gm1 * uK);
+        p = K.p * ipow7(c);
       }
     }
   }
+  u = left ? um : -um;
 }
 
 // the flux of a face whose Riemann problem failed (vacuum, or Newton did not
