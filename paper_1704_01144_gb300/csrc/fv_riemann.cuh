@@ -393,12 +393,17 @@ __device__ __forceinline__ void pressure_fns14(const Side14<T> &L, const Side14<
   if (!(sL || sR)) rare14(R, p, p17, rp6, fR, dfR);
 }
 
-// (ps/pK)^(1/7) for the sampling step
-__device__ __forceinline__ double ratio17(const Side14<double> &K, double ps, double p17) {
+// (ps/pK)^(1/7) for the sampling step, on the rarefaction branch of side K.
+// FP64: p17 (K.iq = pK^(-1/7)).  FP32: from the side's pressure function at
+// ps, fK = eK ((ps/pK)^(1/7) - 1), which Newton has already formed, instead
+// of another seventh root: 1 + fK/eK carries fK's few-ulp error only in
+// the difference from 1, so it is at least as close as a root taken anew
+// (the one-step extension of fK to ps neglects ~1e-12 relative).
+__device__ __forceinline__ double ratio17(const Side14<double> &K, double p17, double) {
   return p17 * K.iq;
 }
-__device__ __forceinline__ float ratio17(const Side14<float> &K, float ps, float) {
-  return qdiv(1.0f, rroot7(qdiv(ps, K.p)));
+__device__ __forceinline__ float ratio17(const Side14<float> &K, float, float fK) {
+  return 1.0f + qdiv(fK, K.e);
 }
 
 template <typename T>
@@ -412,7 +417,8 @@ __device__ __forceinline__ void roots_of(T p, T &p17, T &rp6) {
 template <typename T, bool GUESS = false>
 __device__ __forceinline__ int riemann_star14(const GasT<T> &G, const Side14<T> &L, T uL,
                                               const Side14<T> &R, T uR, T &ps, T &us, T &ps17,
-                                              int &iters, T gabs = T(0), T gmul = T(1)) {
+                                              T &fLs, T &fRs, int &iters, T gabs = T(0),
+                                              T gmul = T(1)) {
   T du = uR - uL;
   if (G.two_gm1 * (L.a + R.a) <= du) return 1;
   T p;
@@ -467,11 +473,14 @@ __device__ __forceinline__ int riemann_star14(const GasT<T> &G, const Side14<T> 
   }
   ps = p;
   ps17 = p17;
+  fLs = fL;
+  fRs = fR;
   us = T(0.5) * (uL + uR) + T(0.5) * (fR - fL);
   return 0;
 }
 
-// the state on the face (x/t = 0); p17 = ps^(1/7).  One code path for both
+// the state on the face (x/t = 0); p17 = ps^(1/7), fL and fR the pressure
+// functions at ps.  One code path for both
 // sides: the sampled side K (left when u* >= 0) is taken by selection, and
 // on the right every velocity is mirrored (negated), which turns the right
 // side's wave tests and fan formulas into the left side's; the face
@@ -480,11 +489,12 @@ __device__ __forceinline__ int riemann_star14(const GasT<T> &G, const Side14<T> 
 // give, while a warp whose faces sample both sides runs the formulas once.
 template <typename T>
 __device__ __forceinline__ void sample_face14(const GasT<T> &G, const Side14<T> &L, T uL,
-                                              const Side14<T> &R, T uR, T ps, T us, T p17, T &r,
-                                              T &u, T &p, int &side) {
+                                              const Side14<T> &R, T uR, T ps, T us, T p17, T fL,
+                                              T fR, T &r, T &u, T &p, int &side) {
   const bool left = T(0) <= us;
   side = left ? 0 : 1;
   const Side14<T> K = left ? L : R;
+  const T fK = left ? fL : fR;
   const T uK = left ? uL : -uR;  // the side's velocity, mirrored on the right
   const T uS = left ? us : -us;  // u*, likewise
   T um;                          // the face velocity, mirrored on the right
@@ -502,7 +512,7 @@ __device__ __forceinline__ void sample_face14(const GasT<T> &G, const Side14<T> 
     if (T(0) <= SHK) {
       r = K.r; um = uK; p = K.p;
     } else {
-      T pr17 = ratio17(K, ps, p17);  // (ps/pK)^(1/7)
+      T pr17 = ratio17(K, p17, fK);  // (ps/pK)^(1/7)
       T STK = uS - K.a * pr17;
       if (T(0) >= STK) {
         r = K.r * ipow5(pr17);
@@ -547,13 +557,13 @@ __device__ __forceinline__ int godunov_flux(const GasT<T> &G, const T WL[5], con
       L = make_side14(G, WL[0], WL[4]);
       R = make_side14(G, WR[0], WR[4]);
     }
-    T p17;
-    int rc = riemann_star14<T, GUESS>(G, L, unL, R, unR, ps, us, p17, iters, gabs, gmul);
+    T p17, fLs, fRs;
+    int rc = riemann_star14<T, GUESS>(G, L, unL, R, unR, ps, us, p17, fLs, fRs, iters, gabs, gmul);
     if (rc) {
       failed_flux(F);
       return rc;
     }
-    sample_face14(G, L, unL, R, unR, ps, us, p17, r0, un0, p0, side);
+    sample_face14(G, L, unL, R, unR, ps, us, p17, fLs, fRs, r0, un0, p0, side);
   } else {
     int rc = riemann_star<T, GUESS>(G, WL[0], unL, WL[4], WR[0], unR, WR[4], ps, us, iters, gabs,
                                     gmul);
@@ -590,8 +600,8 @@ __device__ __forceinline__ int boundary_flux(const GasT<T> &G, int bc, const T W
     int rc;
     if (G14) {
       Side14<T> S = make_side14(G, WL[0], WL[4]);
-      T p17;
-      rc = riemann_star14(G, S, un, S, -un, ps, us, p17, iters);
+      T p17, fLs, fRs;
+      rc = riemann_star14(G, S, un, S, -un, ps, us, p17, fLs, fRs, iters);
     } else {
       rc = riemann_star(G, WL[0], un, WL[4], WL[0], -un, WL[4], ps, us, iters);
     }
