@@ -1066,11 +1066,15 @@ __device__ __forceinline__ float flip(float v, bool neg) {
 
 // stage 1 (predictor): the flux F1 A is stashed (FP32 in the FP32-flux mode,
 // where it is an FP32 result of the FP32 flux).  stage 2 (corrector of
-// `level`): the step's flux time integral Phi = (dt_k/2) (F1 A + F2 A) is
-// formed in FP64 (in the FP32-flux mode each FP32 flux is widened first, so
-// the sum and the product are FP64 operations) and stored; on
-// a level interface (iface) Phi is added to ACC[f] (the coarse side's
-// integral), on a boundary face (bnd) to BND[f] (the conservation ledger).
+// `level` k): the step's flux time integral Phi = h_k (F1 A + F2 A), h_k =
+// dt_k/2, is kept in units of h_k: Psi = F1 A + F2 A, formed in FP64 (in the
+// FP32-flux mode each FP32 flux is widened first, so the sum is an FP64
+// operation), and stored; the cells of level k take h_k once per cell in
+// their update.  On a level interface (iface) Phi is added to ACC[f], the
+// coarse side's integral, in the coarse level's units h_{k+1} = 2 h_k (the
+// level rule keeps neighbours within one level): ACC += Psi / 2.  On a
+// boundary face (bnd) Phi itself goes to BND[f] (the conservation ledger,
+// which spans cycles and so stays in time units).
 template <typename T>
 __device__ __forceinline__ void flux_store(const DevMesh &d, int stage, int level, int f, const T FAt[5],
                                            bool iface, bool bnd) {
@@ -1085,27 +1089,28 @@ __device__ __forceinline__ void flux_store(const DevMesh &d, int stage, int leve
     }
     return;
   }
-  double h = scale2(__longlong_as_double((long long)*d.dtmin_bits), level - 1);  // dt_k / 2
-  double phi[REC_FA];
+  double psi[REC_FA];
   if (f32) {
     float a[REC_FA32];
     ldrec<REC_FA32>(d.FA32 + (size_t)f * REC_FA32, a);
 #pragma unroll
-    for (int c = 0; c < 5; ++c) phi[c] = h * ((double)a[c] + (double)FAt[c]);
+    for (int c = 0; c < 5; ++c) psi[c] = (double)a[c] + (double)FAt[c];
   } else {
     double a[REC_FA];
     ldrec<REC_FA>(d.FA + (size_t)f * REC_FA, a);
 #pragma unroll
-    for (int c = 0; c < 5; ++c) phi[c] = h * (a[c] + (double)FAt[c]);
+    for (int c = 0; c < 5; ++c) psi[c] = a[c] + (double)FAt[c];
   }
-  phi[5] = 0.0;
-  strec<REC_FA>(d.FA + (size_t)f * REC_FA, phi);
+  psi[5] = 0.0;
+  strec<REC_FA>(d.FA + (size_t)f * REC_FA, psi);
   if (iface || bnd) {
     double *dst = (iface ? d.ACC : d.BND) + (size_t)f * REC_FA;
+    // Psi / 2 in the coarse side's units, or h_k Psi in time units
+    const double w = iface ? 0.5 : scale2(__longlong_as_double((long long)*d.dtmin_bits), level - 1);
     double acc[REC_FA];
     ldrec<REC_FA>(dst, acc);
 #pragma unroll
-    for (int c = 0; c < 5; ++c) acc[c] += phi[c];
+    for (int c = 0; c < 5; ++c) acc[c] = fma(w, psi[c], acc[c]);
     strec<REC_FA>(dst, acc);
   }
 }
@@ -1210,24 +1215,27 @@ __device__ __forceinline__ void flux_item_fused(const DevMesh &d, const GasT<flo
 // atomics), signs applied by flipping bits:
 //  stage 1: U* = U^n + dt_k (-S/V), S = sum sigma F1 A.  In the FP32-flux mode
 //           the predictor is all FP32 (U* only feeds fluxes).
-//  stage 2 (level k): U^{n+1} = U^n - S/V, S = sum sigma Phi in FP64, where
-//           faces to finer neighbours contribute (and reset) their
-//           accumulated integral; the FP32 shadow of U^n is refreshed.
+//  stage 2 (level k): U^{n+1} = U^n - (h_k/V) S, S = sum sigma Psi in FP64
+//           (the flux time integrals in units of h_k = dt_k/2), where faces
+//           to finer neighbours contribute (and reset) their accumulated
+//           integral, kept in the same units; the FP32 shadow of U^n is
+//           refreshed.
 // Positivity is checked by the next level assignment and on demand
 // (fv_status), not here.
 // Order 1 (the paper's order), the corrector of the cell at list position
-// idx, of `level`: the
-// provisional end state U^n - S/V, S = sum sigma phi over the cell's faces,
-// phi = Phi on its own-level faces (and faces to coarser neighbours) and the
-// provisional dt_k F1 A on faces to finer neighbours, whose accumulators
-// start from minus that value (the finer side adds its integrals to them).
+// idx, of `level` k: the
+// provisional end state U^n - (h_k/V) S, S = sum sigma psi over the cell's
+// faces in units of h_k = dt_k/2, psi = Psi on its own-level faces (and
+// faces to coarser neighbours) and the provisional dt_k F1 A = h_k (2 F1 A)
+// on faces to finer neighbours, whose accumulators start from minus that
+// value (the finer side adds its integrals to them, in the same units).
 // The state goes to the FP64 predicted-state array (FP64 mode) or to UsD
 // and the FP32 predicted record (FP32-flux mode), where the finer levels
 // interpolate it.  Every load before the first store.
 template <bool F32>
 __device__ __forceinline__ void correct_cell(const DevMesh &d, int level, int idx) {
   const size_t N = d.N;
-  const double dtk = scale2(__longlong_as_double((long long)*d.dtmin_bits), level);
+  const double hk = scale2(__longlong_as_double((long long)*d.dtmin_bits), level - 1);
   const int i = d.cl[idx];
   const unsigned bits = d.clb[idx];
   const unsigned own = bits & 15u, finer = bits >> 4;
@@ -1243,11 +1251,11 @@ __device__ __forceinline__ void correct_cell(const DevMesh &d, int level, int id
         float a[REC_FA32];
         ldrec<REC_FA32>(d.FA32 + (size_t)f * REC_FA32, a);
 #pragma unroll
-        for (int c = 0; c < 5; ++c) v[c] = dtk * (double)a[c];
+        for (int c = 0; c < 5; ++c) v[c] = 2.0 * (double)a[c];
       } else {
         ldrec<REC_FA>(d.FA + (size_t)f * REC_FA, v);
 #pragma unroll
-        for (int c = 0; c < 5; ++c) v[c] = dtk * v[c];
+        for (int c = 0; c < 5; ++c) v[c] = 2.0 * v[c];
       }
     } else {
       ldrec<REC_FA>(d.FA + (size_t)f * REC_FA, v);
@@ -1255,12 +1263,12 @@ __device__ __forceinline__ void correct_cell(const DevMesh &d, int level, int id
 #pragma unroll
     for (int c = 0; c < 5; ++c) S[c] = j == 0 ? flip(v[c], neg) : S[c] + flip(v[c], neg);
   }
-  const double iV = d.ivol[i];
+  const double hV = hk * d.ivol[i];
   double u[5];
 #pragma unroll
   for (int c = 0; c < 5; ++c) u[c] = d.Un[c * N + i];
 #pragma unroll
-  for (int c = 0; c < 5; ++c) u[c] = u[c] - iV * S[c];
+  for (int c = 0; c < 5; ++c) u[c] = u[c] - hV * S[c];
   double *Up = F32 ? d.UsD : d.Us;
 #pragma unroll
   for (int c = 0; c < 5; ++c) Up[c * N + i] = u[c];
@@ -1284,25 +1292,23 @@ __device__ __forceinline__ void correct_cell(const DevMesh &d, int level, int id
         float a[REC_FA32];
         ldrec<REC_FA32>(d.FA32 + (size_t)f * REC_FA32, a);
 #pragma unroll
-        for (int c = 0; c < 5; ++c) p[c] = dtk * (double)a[c];
+        for (int c = 0; c < 5; ++c) p[c] = (double)a[c];
       } else {
         ldrec<REC_FA>(d.FA + (size_t)f * REC_FA, p);
-#pragma unroll
-        for (int c = 0; c < 5; ++c) p[c] = dtk * p[c];
       }
       ldrec<REC_FA>(d.ACC + (size_t)f * REC_FA, acc);
 #pragma unroll
-      for (int c = 0; c < 5; ++c) acc[c] -= p[c];
+      for (int c = 0; c < 5; ++c) acc[c] = fma(-2.0, p[c], acc[c]);
       strec<REC_FA>(d.ACC + (size_t)f * REC_FA, acc);
     }
   }
 }
 
 // Order 1, the commit of the cell at list position idx at the end of its step (Alg. 2's intensive
-// correction): U^{n+1} = Up - (1/V) sum sigma ACC over the faces to finer
-// neighbours (ACC = their integral minus the provisional one), which are
-// reset; a cell without finer neighbours takes its provisional state as it
-// is.
+// correction): U^{n+1} = Up - (h_k/V) sum sigma ACC over the faces to finer
+// neighbours (ACC = their integral minus the provisional one, in units of
+// the cell's h_k = dt_k/2), which are reset; a cell without finer
+// neighbours takes its provisional state as it is.
 template <bool F32>
 __device__ __forceinline__ void commit_cell(const DevMesh &d, int idx) {
   const size_t N = d.N;
@@ -1326,9 +1332,9 @@ __device__ __forceinline__ void commit_cell(const DevMesh &d, int idx) {
 #pragma unroll
       for (int c = 0; c < 5; ++c) S[c] += flip(v[c], neg);
     }
-    const double iV = d.ivol[i];
+    const double hV = scale2(__longlong_as_double((long long)*d.dtmin_bits), (int)d.lev[i] - 1) * d.ivol[i];
 #pragma unroll
-    for (int c = 0; c < 5; ++c) u[c] = u[c] - iV * S[c];
+    for (int c = 0; c < 5; ++c) u[c] = u[c] - hV * S[c];
     const double z[REC_FA] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
 #pragma unroll
     for (int j = 0; j < 4; ++j)
@@ -1430,10 +1436,11 @@ __device__ __forceinline__ void update_item(const DevMesh &d, int stage, int lev
 #pragma unroll
     for (int c = 0; c < 5; ++c) d.Us[c * N + i] = u[c] + cdt * S[c];
   } else {
+    const double hV = scale2(dtmin, level - 1) * iV;
     float r[REC_U32];
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
-      u[c] = u[c] - iV * S[c];
+      u[c] = u[c] - hV * S[c];
       r[c] = (float)u[c];
     }
 #pragma unroll
@@ -1530,10 +1537,11 @@ __device__ __forceinline__ void update_range_quad(const DevMesh &d, int stage, i
 #pragma unroll
         for (int c = 0; c < 5; ++c) d.Us[c * N + i] = u[c] + cdt * S[c];
       } else {
+        const double hV = scale2(dtmin, level - 1) * iV;
         float r[REC_U32];
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
-          u[c] = u[c] - iV * S[c];
+          u[c] = u[c] - hV * S[c];
           r[c] = (float)u[c];
         }
 #pragma unroll
