@@ -314,6 +314,7 @@ int fv_mesh_load(const double *xyz, int64_t n_nodes, const int64_t *tets, int64_
   AL(d.dteps, N);
   AL(d.dthi_bits, 1);
   AL(d.dtmin_bits, 1);
+  AL(d.sweep_changed, FV_MAXL);
   AL(d.tdev, 1);
   AL(d.status, 1);
   AL(d.counters, 3);

@@ -103,6 +103,7 @@ struct DevMesh {
   float *dteps;           // relative bound of the estimate (0: dt holds the exact value)
   unsigned long long *dthi_bits;  // smallest upper bound of the estimates (bit pattern)
   unsigned long long *dtmin_bits;  // bit pattern of dt_min (positive double)
+  int *sweep_changed;     // per smoothing sweep of the level rule: 1 if it lowered a level
   double *tdev;           // physical time
   int *status;            // sticky status bits
   long long *counters;    // [0] cycles, [1] weighted cell updates, [2] face evaluations

@@ -380,6 +380,7 @@ __device__ __forceinline__ int8_t level0_certified_of(const DevMesh &d, const Le
 __global__ void __launch_bounds__(256) k_levels0_certified(DevMesh d) {
   __shared__ LevelRule r;
   pdl_wait();
+  if (blockIdx.x == 0 && threadIdx.x < FV_MAXL) d.sweep_changed[threadIdx.x] = 0;
   level_rule_fill(r, d);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x)
     d.lev_tmp[i] = level0_certified_of(d, r, i);
@@ -399,11 +400,21 @@ __device__ __forceinline__ int8_t smooth_of(const DevMesh &d, const int8_t *src,
   return (int8_t)k;
 }
 
+// Sweep number sw.  A sweep that lowers no level has reached the fixed point
+// and written it to dst, so src and dst both hold it: every later sweep
+// returns at once (sweep_changed is cleared by k_levels0_certified).
 __global__ void __launch_bounds__(256) k_smooth(DevMesh d, const int8_t *__restrict__ src,
-                                                int8_t *__restrict__ dst) {
+                                                int8_t *__restrict__ dst, int sw) {
   pdl_wait();
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x)
-    dst[i] = smooth_of(d, src, i);
+  if (sw == 0 || d.sweep_changed[sw - 1]) {
+    bool lowered = false;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x) {
+      const int8_t k = smooth_of(d, src, i);
+      lowered |= k != src[i];
+      dst[i] = k;
+    }
+    if (__syncthreads_or(lowered) && threadIdx.x == 0) d.sweep_changed[sw] = 1;
+  }
   pdl_trigger();
 }
 
@@ -426,7 +437,12 @@ __device__ __forceinline__ int cell_key_store(const DevMesh &d, int i) {
   const int key = 2 * k + (finer ? 0 : 1);
   d.ckey[i] = (uint8_t)key;
   d.cmask[i] = (uint8_t)finer;
-  if (d.Un32) d.Un32[(size_t)i * REC_U32 + 5] = (float)k;
+  // written only where it changed (a few cells per thousand a cycle), so
+  // the other records are read here but not written back
+  if (d.Un32) {
+    float *lv = d.Un32 + (size_t)i * REC_U32 + 5;
+    if (*lv != (float)k) *lv = (float)k;
+  }
   return key;
 }
 
@@ -2383,7 +2399,7 @@ int launch_levels_classify(const DevMesh &d, int L, cudaStream_t s) {
       dst = d.lev_tmp;
     }
     for (int sw = 0; sw < L - 1; ++sw) {
-      launch_pdl(k_smooth, g, 256, s, d, src, dst);
+      launch_pdl(k_smooth, g, 256, s, d, src, dst, sw);
       const int8_t *t = dst;
       dst = (int8_t *)src;
       src = t;
