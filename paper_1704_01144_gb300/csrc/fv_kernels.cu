@@ -303,10 +303,10 @@ __device__ __forceinline__ void dt32_cell(const DevMesh &d, int i, float &hi32, 
 // pass 2 of one cell: exact if its lower bound reaches the smallest upper
 // bound hi (hi_rd: hi rounded down to FP32), so that it can hold the
 // minimum; lowers m by its exact value then
-__device__ __forceinline__ void dt_min_exact_cell(const DevMesh &d, int i, double hi, float hi_rd, double &m) {
-  const float e = d.dteps[i];
+__device__ __forceinline__ void dt_min_exact_cell(const DevMesh &d, int i, float e, float v, double hi,
+                                                  float hi_rd, double &m) {
   if (e > 0.0f) {
-    if (__fmul_rd(d.dt32[i], __fsub_rd(1.0f, e)) <= hi_rd) {
+    if (__fmul_rd(v, __fsub_rd(1.0f, e)) <= hi_rd) {
       m = fmin(m, local_dt_of(d, i));
       d.dteps[i] = 0.0f;
     }
@@ -327,15 +327,37 @@ __global__ void __launch_bounds__(256) k_dt32(DevMesh d) {
   pdl_trigger();
 }
 
+// a cell's estimate and its bound for the passes below, DT_UNROLL cells per
+// thread at a time: both loads of every cell issued before any is used, so
+// a thread keeps 2 x DT_UNROLL loads in flight instead of waiting on the
+// bound, then on the estimate, cell after cell
+#define DT_UNROLL 4
+__device__ __forceinline__ void load_estimates(const DevMesh &d, int i0, int stride, float e[DT_UNROLL],
+                                               float v[DT_UNROLL]) {
+#pragma unroll
+  for (int u = 0; u < DT_UNROLL; ++u) {
+    const int i = i0 + u * stride;
+    e[u] = i < d.N ? d.dteps[i] : 0.0f;
+    v[u] = i < d.N ? d.dt32[i] : 0.0f;
+  }
+}
+
 // pass 2: every cell that can hold the minimum (lower bound <= the smallest
-// upper bound) is made exact; dt_min = the exact minimum over them
+// upper bound) is made exact; dt_min = the exact minimum over them (a
+// minimum: the same in any order)
 __global__ void __launch_bounds__(256) k_dt_min_exact(DevMesh d) {
   pdl_wait();
   const double hi = __longlong_as_double((long long)*d.dthi_bits);
   const float hi_rd = __double2float_rd(hi);
   double m = __longlong_as_double(0x7ff0000000000000LL);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x)
-    dt_min_exact_cell(d, i, hi, hi_rd, m);
+  const int stride = gridDim.x * blockDim.x;
+  for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < d.N; i0 += DT_UNROLL * stride) {
+    float e[DT_UNROLL], v[DT_UNROLL];
+    load_estimates(d, i0, stride, e, v);
+#pragma unroll
+    for (int u = 0; u < DT_UNROLL; ++u)
+      if (i0 + u * stride < d.N) dt_min_exact_cell(d, i0 + u * stride, e[u], v[u], hi, hi_rd, m);
+  }
   block_min_to(m, d.dtmin_bits);
   pdl_trigger();
 }
@@ -357,10 +379,9 @@ __device__ __forceinline__ void level_rule_fill(LevelRule &r, const DevMesh &d) 
 
 // k_i = max{k <= L-1 : 2^k dt_min <= dt_i}, taken on the exact value, or on
 // the estimate's interval when no threshold falls inside it
-__device__ __forceinline__ int8_t level0_certified_of(const DevMesh &d, const LevelRule &r, int i) {
-  const float e = d.dteps[i];
+__device__ __forceinline__ int8_t level0_certified_of(const DevMesh &d, const LevelRule &r, int i, float e,
+                                                     float v) {
   if (e > 0.0f) {
-    const float v = d.dt32[i];
     const float lo = __fmul_rd(v, __fsub_rd(1.0f, e)), hi = __fmul_ru(v, __fadd_ru(1.0f, e));
     int klo = 0, khi = 0;
     for (int k = 1; k < d.L; ++k) {
@@ -382,8 +403,14 @@ __global__ void __launch_bounds__(256) k_levels0_certified(DevMesh d) {
   pdl_wait();
   if (blockIdx.x == 0 && threadIdx.x < FV_MAXL) d.sweep_changed[threadIdx.x] = 0;
   level_rule_fill(r, d);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x)
-    d.lev_tmp[i] = level0_certified_of(d, r, i);
+  const int stride = gridDim.x * blockDim.x;
+  for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < d.N; i0 += DT_UNROLL * stride) {
+    float e[DT_UNROLL], v[DT_UNROLL];
+    load_estimates(d, i0, stride, e, v);
+#pragma unroll
+    for (int u = 0; u < DT_UNROLL; ++u)
+      if (i0 + u * stride < d.N) d.lev_tmp[i0 + u * stride] = level0_certified_of(d, r, i0 + u * stride, e[u], v[u]);
+  }
   pdl_trigger();
 }
 
@@ -664,7 +691,8 @@ __global__ void __launch_bounds__(256) k_dt_multi(MultiTiles a, int op) {
   } else {
     const double hi = __longlong_as_double((long long)*d.dthi_bits);
     const float hi_rd = __double2float_rd(hi);
-    for (int i = tile * SORT_TILE + threadIdx.x; i < end; i += blockDim.x) dt_min_exact_cell(d, i, hi, hi_rd, m);
+    for (int i = tile * SORT_TILE + threadIdx.x; i < end; i += blockDim.x)
+      dt_min_exact_cell(d, i, d.dteps[i], d.dt32[i], hi, hi_rd, m);
     block_min_to(m, d.dtmin_bits);
   }
 }
@@ -678,7 +706,7 @@ __global__ void __launch_bounds__(256) k_cells_multi(MultiTiles a, int op) {
   __shared__ LevelRule r;
   if (op == 0) level_rule_fill(r, d);
   for (int i = tile * SORT_TILE + threadIdx.x; i < min(d.N, (tile + 1) * SORT_TILE); i += blockDim.x) {
-    if (op == 0) d.lev_tmp[i] = level0_certified_of(d, r, i);
+    if (op == 0) d.lev_tmp[i] = level0_certified_of(d, r, i, d.dteps[i], d.dt32[i]);
     else if (op == 1) d.lev[i] = d.lev_tmp[i];
     else if (op == 2) d.lev[i] = smooth_of(d, d.lev_tmp, i);
     else if (op == 3) d.lev_tmp[i] = smooth_of(d, d.lev, i);
