@@ -143,10 +143,12 @@ __device__ __forceinline__ double minmod(double a, double b) {
   if (a < 0.0 && b < 0.0) return a > b ? a : b;
   return 0.0;
 }
+// FP32: as max(min(a, b), 0) + min(max(a, b), 0), four min/max and an add
+// without comparisons or selects; the same value as the branches above for
+// every pair of numbers (one term is the result and the other zero, so the
+// add is exact; a pair of opposite signs or with a zero gives +0)
 __device__ __forceinline__ float minmod(float a, float b) {
-  if (a > 0.f && b > 0.f) return a < b ? a : b;
-  if (a < 0.f && b < 0.f) return a > b ? a : b;
-  return 0.f;
+  return fmaxf(fminf(a, b), 0.f) + fminf(fmaxf(a, b), 0.f);
 }
 
 // ------------------------------------------------ level assignment (a1-a2)
