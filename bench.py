@@ -162,8 +162,11 @@ def measured_traffic(workload: str = "blast1m"):
         return None
     vals = {}
     with open(path) as fh:
+        block = False  # the indented figures after the "Machine-readable" line
         for ln in fh:
-            if ln.startswith("    ") and ":" in ln:
+            if ln.startswith("Machine-readable"):
+                block = True
+            elif block and ln.startswith("    ") and ":" in ln:
                 k, v = ln.strip().split(":", 1)
                 vals[k.strip()] = v.strip()
     if vals.get("kernel_source_sha256_16") != kernel_source_hash():
