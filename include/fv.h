@@ -402,7 +402,8 @@ void fv_batch_free(fv_batch *b);
  * and data harvesting: for i < count, with primitives WL_dev/WR_dev
  * [5*count] = (rho, u, v, w, p) and unit normals n_dev[3*count]
  * (structure of arrays), writes the flux per unit area F_dev[5*count] and
- * the Newton iterations iters_dev[count] (-1 where the solver failed).
+ * the Newton iterations iters_dev[count] (-1 where the solver failed; 0
+ * where no Riemann problem is solved: a transmissive boundary).
  * bc = FV_BC_INTERIOR: exact Riemann problem between WL and WR;
  * FV_BC_WALL / FV_BC_TRANSMISSIVE: boundary flux of WL (WR unused).
  * Arithmetic follows cfg->precision; gamma, newton_tol and newton_max_iter

@@ -270,7 +270,7 @@ def test_flux_with_learned_guess_matches_oracle(fv, oracle_mod, precision):
         pk = fv.fv_mlp_pack(torch.from_numpy(theta_random(fv, 30 + target)).cuda(), target)
         F, it = fv.fv_godunov_flux_batch_mlp(WL, WR, nrm, cfg, pk)
         F, it = F.cpu().numpy(), it.cpu().numpy()
-        assert np.all(it > 0)
+        assert np.all(it >= 0)  # -1: the solver failed
         wl, wr, nn = WL.cpu().numpy(), WR.cpu().numpy(), nrm.cpu().numpy()
         tol = 1e-12 if precision == 0 else 5e-5
         for i in range(0, n, 11):

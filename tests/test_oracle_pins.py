@@ -98,6 +98,30 @@ def test_two_rarefaction_guess_is_exact(oracle_mod):
     assert seen > 20
 
 
+def test_two_rarefaction_guess_near_weak_shocks(oracle_mod):
+    """Where the exact star pressure lies above the lower side pressure by at
+    most 2^-10 (one or both waves weak shocks), the two-rarefaction estimate
+    misses it by about the cube of that excess (a weak shock's Hugoniot and
+    the isentrope through the same state agree to second order), so by
+    less than 1.2e-9 relative."""
+    rng = np.random.default_rng(12)
+    seen = 0
+    for _ in range(1000):
+        r = rng.uniform(0.2, 2, 2)
+        p0 = rng.uniform(0.2, 2)
+        pl, pr = p0, p0 * (1 + rng.uniform(-1, 1) * rng.uniform(0, 2e-3))
+        du = -rng.uniform(0, 2e-3) * np.sqrt(1.4 * min(pl, pr) / r.max())
+        ps, _, _ = oracle_mod.riemann((r[0], 0.0, pl), (r[1], du, pr), tol=1e-14, maxit=100)
+        excess = ps / min(pl, pr) - 1
+        if 0 < excess <= 2.0 ** -10:
+            seen += 1
+            guess = oracle_mod.tr_guess((r[0], 0.0, pl, r[1], du, pr))
+            err = abs(guess - ps) / ps
+            assert err <= 1.2 * excess ** 3 + 1e-15, (r, pl, pr, du)
+            assert err <= 1.2e-9
+    assert seen > 300
+
+
 def test_sampled_solution_is_mirror_symmetric_and_continuous(oracle_mod):
     """Mirroring x -> -x swaps the sides and negates velocities: the state at
     xi of (WL | WR) equals the mirrored state at -xi of (mirror WR | mirror
