@@ -146,7 +146,7 @@ __device__ __forceinline__ double minmod(double a, double b) {
 // FP32: as max(min(a, b), 0) + min(max(a, b), 0), four min/max and an add
 // without comparisons or selects; the same value as the branches above for
 // every pair of numbers (one term is the result and the other zero, so the
-// add is exact; a pair of opposite signs or with a zero gives +0)
+// add is exact; a pair of opposite signs or with a zero gives a zero)
 __device__ __forceinline__ float minmod(float a, float b) {
   return fmaxf(fminf(a, b), 0.f) + fminf(fmaxf(a, b), 0.f);
 }

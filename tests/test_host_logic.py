@@ -289,6 +289,31 @@ def test_committed_traffic_counters_parse(monkeypatch):
     for key in ("flux_fp32", "update_fp32", "flux_fp64", "update_fp64"):
         v = float(t[f"{key}_dram_bytes_per_unit"])
         assert 50.0 < v < 1000.0
+    # only the machine-readable block is read, not the commands above it
+    assert all(k == "kernel_source_sha256_16" or k.endswith("_per_unit") for k in t), t
+
+
+def test_branch_free_minmod_equals_the_limiter():
+    """The FP32 flux's limiter, max(min(a, b), 0) + min(max(a, b), 0), is the
+    minmod of the branches (the smaller magnitude when a and b share a sign,
+    else 0) for every pair of finite floats, signed zeros and subnormals
+    included; checked in float32."""
+    rng = np.random.default_rng(3)
+    special = np.array([0.0, -0.0, 1e-45, -1e-45, 1e-38, -1e-38, 1.0, -1.0, 3.4e38, -3.4e38,
+                        np.float32(2.0) ** -126, 7.0, -7.0], dtype=np.float32)
+    mags = np.exp(rng.uniform(-80, 80, 20000)).astype(np.float32)
+    vals = np.concatenate([special, mags * rng.choice([-1.0, 1.0], mags.size).astype(np.float32)])
+    a = np.repeat(vals, 7)
+    b = np.concatenate([np.roll(vals, k) for k in range(7)])
+    a = np.concatenate([a, np.repeat(special, special.size)])
+    b = np.concatenate([b, np.tile(special, special.size)])
+    zero = np.float32(0.0)
+    got = np.fmax(np.fmin(a, b), zero) + np.fmin(np.fmax(a, b), zero)
+    same = (a > 0) & (b > 0)
+    neg = (a < 0) & (b < 0)
+    want = np.where(same, np.minimum(a, b), np.where(neg, np.maximum(a, b), zero))
+    assert got.dtype == np.float32
+    assert np.array_equal(got, want)
 
 
 def test_reference_arm_prints_its_contract_line():
