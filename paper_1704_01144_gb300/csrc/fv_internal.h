@@ -20,9 +20,10 @@
 //          state, which only ever feeds fluxes)
 //   phase  W[N][8] primitives at the phase time, G[N][16] gradients (FP64 or
 //          FP32 by mode); FA[F][6] predictor flux x area (FP64 mode; FA32
-//          [F][8] in FP32 mode), then the step's flux time integral;
-//          ACC[F][6] fine-side integral on level interfaces; BND[F][6]
-//          boundary ledger
+//          [F][8] in FP32 mode), then the step's flux time integral in
+//          units of the level's half step dt_k/2; ACC[F][6] fine-side
+//          integral on level interfaces, in units of the coarse level's
+//          half step; BND[F][6] boundary ledger (time units)
 //   lists  cl[N] cells sorted by (level, has-finer-neighbour), coff[2L+1],
 //          with clf/cln/clb the sorted faces, neighbours and bits of each
 //          entry; fl[F] faces sorted by face level, foff[L+1], with flc the
